@@ -1,0 +1,224 @@
+/*
+ * mrf.h -- C ABI of the GB300 matched-filtering reconstruction library (libmrf.so).
+ *
+ * The library solves the per-voxel cone-constrained least-squares problem of MRF
+ * reconstruction (arXiv 1810.01967, §3.2, eq. CS) by projected gradient iterations (BLIP,
+ * §3.2 eq. blip; CoverBLIP, Algorithm 2): a gradient step Z = X - mu A^H(A X - Y) followed by
+ * the matched-filtering projection of every voxel's fingerprint Z_v onto the cone of the
+ * dictionary (eqs. exactP / exactPs).
+ *
+ * Conventions
+ *   - complex numbers are interleaved float2 (complex64), row-major, indices 0-based;
+ *   - the image X is [n][L] with voxel v = y * Nx + x and the frame t contiguous (row v is the
+ *     fingerprint X_v of §3, eq. CS footnote);
+ *   - k-space Y is [Ny][Nx][L] (ky, kx, t) in DFT order (DC at index 0), entries of lines that
+ *     were not sampled are ignored (treated as zero);
+ *   - masks are uint8 [L][Ny]: mask[t][ky] = 1 when phase-encode line ky is in Omega_t;
+ *   - the Fourier transform F is the unitary 2-D DFT of each frame, one coil (S = identity);
+ *   - "device" pointers are CUDA global memory of the current device, owned by the caller;
+ *     the library never frees caller memory.  The library owns only an mrf_dict and its
+ *     scratch buffers.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default stream).  Calls are
+ *     asynchronous on that stream unless stated otherwise.  One mrf_dict must not be used by
+ *     two calls in flight at the same time (its scratch buffers are shared).
+ *   - Errors: no C++ exception crosses this boundary.  Every call returns an mrf_status; the
+ *     message of the last failure on the calling thread is returned by mrf_last_error().
+ *     Argument errors are detected on the host before any launch.  Device-side conditions
+ *     (non-finite input, an exhausted wait bound) set an error word in the dict that calls
+ *     which synchronise (stats != NULL, mrf_reconstruct, mrf_dict_check) report.
+ */
+#ifndef MRF_H
+#define MRF_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum mrf_status {
+    MRF_OK = 0,
+    MRF_EINVAL = 1,        /* bad argument (null pointer, size, mode) */
+    MRF_ENOMEM = 2,        /* device or host allocation failed */
+    MRF_ECUDA = 3,         /* a CUDA runtime / driver / cuFFT call failed */
+    MRF_ENONFINITE = 4,    /* NaN or Inf found in an input */
+    MRF_ETIMEOUT = 5,      /* a bounded device-side wait gave up */
+    MRF_EUNSUPPORTED = 6,  /* feature not built for this dictionary / device */
+    MRF_EINTERNAL = 7
+} mrf_status;
+
+/* How the projection (the nearest-neighbour search of eq. exactP) is computed. */
+typedef enum mrf_proj_mode {
+    MRF_PROJ_FP32_EXACT = 0,  /* exhaustive, FP32 SIMT correlations, FP64 near-tie rescore */
+    MRF_PROJ_BF16 = 1,        /* exhaustive, BF16 tensor cores (tcgen05) + FP32/FP64 rescore */
+    MRF_PROJ_FP8 = 2,         /* exhaustive, FP8 e4m3 tensor cores + FP32/FP64 rescore */
+    MRF_PROJ_COVERTREE = 3,   /* cover-tree (1+eps)-ANNS, Algorithm 1 (§4.1) */
+    MRF_PROJ_LEARNED = 4      /* MLP proposal + exact neighbourhood rescore + fallback */
+} mrf_proj_mode;
+
+/* The cone of eq. model/conedef.  COMPLEX: X_v = rho D_j, rho complex, j maximises
+ * |D_j^H Z_v| / ||D_j||.  REAL_POS: the paper's gamma > 0, j minimises ||Z_v - D_j/||D_j|| ||
+ * and gamma = max(Re(D_j^H Z_v) / ||D_j||^2, 0) (eqs. exactP / exactPs). */
+typedef enum mrf_cone { MRF_CONE_COMPLEX = 0, MRF_CONE_REAL_POS = 1 } mrf_cone;
+
+typedef struct mrf_dict mrf_dict;   /* opaque; owned by the library */
+
+typedef struct mrf_index_opts {
+    int32_t pack_bf16;     /* build the BF16 tensor-core operand (default 1) */
+    int32_t pack_fp8;      /* build the FP8 e4m3 operand (default 0) */
+    int32_t build_tree;    /* build the cover tree on the host (default 0) */
+    int32_t reserved[5];
+} mrf_index_opts;
+
+typedef struct mrf_proj_opts {
+    int32_t mode;          /* mrf_proj_mode (default MRF_PROJ_FP32_EXACT) */
+    int32_t cone;          /* mrf_cone (default MRF_CONE_COMPLEX) */
+    int32_t topk;          /* candidates kept per voxel by the exhaustive kernels, 1..16 (8) */
+    int32_t certify;       /* BF16/FP8: recompute voxels whose k-th candidate is within
+                              cert_margin of the best with the FP32 exact kernel (default 1) */
+    float   tie_rel;       /* candidates within this relative score of the best are rescored
+                              in FP64 (default 1e-5) */
+    float   cert_margin;   /* relative score margin for `certify` (default 2e-3) */
+    float   eps;           /* cover tree (1+eps) approximation (default 0) */
+    float   fallback_thr;  /* learned proposal: normalised correlation threshold (0.98) */
+    int32_t reserved[8];
+} mrf_proj_opts;
+
+/* Filled by calls given a non-NULL pointer; such calls synchronise `stream` before return. */
+typedef struct mrf_stats {
+    int64_t n_voxels;         /* voxels projected */
+    int64_t n_zero;           /* zero queries (idx 0, rho 0) */
+    int64_t n_tie_rescored;   /* voxels whose leading candidates were rescored in FP64 */
+    int64_t n_tie_overflow;   /* voxels whose k-th candidate was still within tie_rel */
+    int64_t n_uncertified;    /* BF16/FP8 voxels sent to the FP32 exact kernel */
+    int64_t n_fallback;       /* learned proposal voxels sent to the exhaustive search */
+    int64_t n_dist_evals;     /* cover tree: distance evaluations */
+    int32_t device_error;     /* raw device error word (0 = none) */
+    int32_t reserved;
+} mrf_stats;
+
+/* Cartesian single-coil sampling operator A = P_Omega F (§3, eq. forward). */
+typedef struct mrf_op {
+    int32_t Ny, Nx, L;
+    const uint8_t* mask;   /* device, [L][Ny] */
+} mrf_op;
+
+typedef struct mrf_recon_opts {
+    int32_t iters;         /* iterations (default 10) */
+    float   mu;            /* initial step size (default 1) */
+    int32_t adaptive;      /* step rule of eq. steprule / Algorithm 2 (default 0) */
+    float   zeta;          /* shrink factor of the step rule (default 2) */
+    int32_t kappa;         /* rescale the first iterate by ||Y|| / ||A X^1|| (default 0) */
+    float   tol;           /* stop when the objective's relative progress < tol (0 = off) */
+    int32_t max_shrink;    /* bound on step-rule shrinks per iteration (default 30) */
+    int32_t reserved[5];
+    mrf_proj_opts proj;
+} mrf_recon_opts;
+
+void mrf_default_index_opts(mrf_index_opts* o);
+void mrf_default_proj_opts(mrf_proj_opts* o);
+void mrf_default_recon_opts(mrf_recon_opts* o);
+
+/*
+ * Build the dictionary index (§3.1 eq. fingerprints; §4.3 "cover tree built for the normalized
+ * fingerprint dictionary").
+ *   atoms      complex64 [d][L], host or device memory (detected); copied.  Atoms need not be
+ *              normalised: the projection divides by the norm of each stored atom.
+ *   params     host float32 [d][P] (e.g. T1, T2, B0), copied; the look-up table of Algorithm 2.
+ *              May be NULL when P == 0.
+ *   grid_shape host int32 [grid_ndim] or NULL: the parameter grid (used by the learned
+ *              proposal's neighbourhood); d must not exceed its number of cells.
+ *   out        receives the new dict; free it with mrf_dict_free.
+ * Synchronises `stream` before returning.  Errors: MRF_EINVAL (d < 1, L < 1, L > 4096,
+ * null atoms/out), MRF_ENOMEM, MRF_ECUDA, MRF_ENONFINITE (an atom with zero or non-finite
+ * norm).
+ */
+mrf_status mrf_build_dict_index(const void* atoms, int64_t d, int32_t L,
+                                const float* params, int32_t P,
+                                const int32_t* grid_shape, int32_t grid_ndim,
+                                const mrf_index_opts* opts, mrf_dict** out, void* stream);
+
+void mrf_dict_free(mrf_dict* dict);
+
+/* d, L, P of a dict (any pointer may be NULL). */
+mrf_status mrf_dict_info(const mrf_dict* dict, int64_t* d, int32_t* L, int32_t* P);
+
+/* Pre-allocate scratch for up to n_max voxels (so later calls allocate nothing). */
+mrf_status mrf_dict_reserve(mrf_dict* dict, int64_t n_max);
+
+/* Synchronise `stream`, read and clear the device error word; returns the matching status. */
+mrf_status mrf_dict_check(mrf_dict* dict, void* stream);
+
+/*
+ * Matched-filtering projection of n fingerprints (§3.2, eqs. exactP / exactPs; with
+ * MRF_PROJ_COVERTREE, Algorithm 2 lines "ANNS" and "rescaling" on Z_v / ||Z_v||).
+ *   Z         device complex64 [n][L]
+ *   warm_idx  device int32 [n] or NULL: previous atoms, the warm start of the tree search
+ *   idx_out   device int32 [n]: j*_v
+ *   rho_out   device complex64 [n]: rho_v = D_j*^H Z_v / ||D_j*||^2 (complex cone) or
+ *             gamma_v (real cone, imaginary part 0); FP64 accumulation
+ *   X_out     device complex64 [n][L] or NULL: X_v = rho_v D_j*
+ * A zero fingerprint gives j* = 0, rho = 0.  Exact ties go to the smallest index.
+ */
+mrf_status mrf_project(mrf_dict* dict, const void* Z, int64_t n, const mrf_proj_opts* opts,
+                       const int32_t* warm_idx, int32_t* idx_out, void* rho_out, void* X_out,
+                       mrf_stats* stats, void* stream);
+
+/* A(X) = P_Omega F X: X device complex64 [n][L] -> Y device complex64 [Ny][Nx][L] (lines
+ * outside Omega_t are written as zero). */
+mrf_status mrf_forward(const mrf_op* op, const void* X, void* Y, void* stream);
+
+/* A^H(Y) = F^H P_Omega^H Y: Y device [Ny][Nx][L] -> AHY device [n][L]. */
+mrf_status mrf_adjoint(const mrf_op* op, const void* Y, void* AHY, void* stream);
+
+/*
+ * One BLIP iteration (§3.2, eq. blip): Z = X - mu (A^H A X - AHY), then the projection; X is
+ * overwritten by rho_v D_j*.
+ *   AHY     device complex64 [n][L]: A^H Y (mrf_adjoint)
+ *   X       device complex64 [n][L], in/out
+ *   idx_io  device int32 [n]: in = the previous atoms (warm start), out = the new atoms
+ *   rho_out device complex64 [n] or NULL
+ */
+mrf_status mrf_ipg_step(mrf_dict* dict, const mrf_op* op, const void* AHY, void* X, float mu,
+                        const mrf_proj_opts* opts, int32_t* idx_io, void* rho_out,
+                        mrf_stats* stats, void* stream);
+
+/*
+ * Whole reconstruction (Algorithm 2): A^H Y once, X^0 = 0, `iters` iterations with the
+ * options' step rule and kappa rescale, then the look-up table.  Synchronises `stream`.
+ *   Y          device complex64 [Ny][Nx][L]
+ *   X_out      device complex64 [n][L]
+ *   idx_out    device int32 [n]
+ *   rho_out    device complex64 [n] or NULL
+ *   params_out device float32 [n][P] or NULL
+ */
+mrf_status mrf_reconstruct(mrf_dict* dict, const mrf_op* op, const void* Y,
+                           const mrf_recon_opts* opts, void* X_out, int32_t* idx_out,
+                           void* rho_out, float* params_out, mrf_stats* stats, void* stream);
+
+/* Look-up table Theta_v = params[idx_v] (Algorithm 2, last step): device int32 [n] ->
+ * device float32 [n][P]. */
+mrf_status mrf_lut(const mrf_dict* dict, const int32_t* idx, int64_t n, float* params_out,
+                   void* stream);
+
+/*
+ * Stage profiler (tracing aid; the paper reports search and total times, Tables 2-3).  While
+ * enabled, every call records a CUDA event pair on its own stream around each stage and counts
+ * the library's kernel launches.  mrf_profile_read synchronises on the recorded events, adds
+ * their elapsed times into ms[stage] and launches[stage] for stage < n_stages, and clears
+ * them.  Stages: 0 gradient step (cuFFT + mask + combine; cuFFT's kernels are timed here but
+ * not counted as launches), 1 BF16 query packing, 2 BF16 tensor-core search, 3 FP32 search,
+ * 4 merge / rescore / density, 5 certification fallback (FP32 search + merge), 6 look-up
+ * table, 7 other.  Enabling or disabling clears the tables.  Not thread-safe.
+ */
+#define MRF_PROFILE_STAGES 8
+mrf_status mrf_profile_enable(int32_t on);
+mrf_status mrf_profile_read(double* ms, int64_t* launches, int32_t n_stages);
+
+const char* mrf_status_str(mrf_status s);
+const char* mrf_last_error(void);   /* thread-local message of the last failure */
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MRF_H */

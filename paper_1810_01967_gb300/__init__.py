@@ -1,0 +1,179 @@
+"""GB300 matched-filtering MRF reconstruction (BLIP / CoverBLIP, arXiv 1810.01967).
+
+Thin Python layer over the C ABI of ``libmrf.so`` (see include/mrf.h).  Functions keep the C
+names without the ``mrf_`` prefix and only marshal arguments: torch CUDA tensors become device
+pointers, numpy arrays host pointers, the current torch stream the call's stream.  There is no
+CPU fallback: every function raises when the library or a GPU is missing.
+"""
+from __future__ import annotations
+
+import ctypes as C
+
+from . import _lib
+from ._lib import MODES, CONES, MRFError, ProjOpts, ReconOpts, IndexOpts, Stats, Op
+
+_LIB = None
+
+
+def lib() -> C.CDLL:
+    global _LIB
+    if _LIB is None:
+        _LIB = _lib.load()
+    return _LIB
+
+
+def _check(status: int) -> None:
+    if status != 0:
+        L = lib()
+        raise MRFError(status, f"{L.mrf_status_str(status).decode()}: "
+                               f"{L.mrf_last_error().decode()}")
+
+
+def _ptr(x) -> int | None:
+    if x is None:
+        return None
+    if hasattr(x, "data_ptr"):
+        if not x.is_contiguous():
+            raise ValueError("tensors passed to libmrf must be contiguous")
+        return x.data_ptr()
+    if hasattr(x, "ctypes"):
+        if not x.flags["C_CONTIGUOUS"]:
+            raise ValueError("arrays passed to libmrf must be C-contiguous")
+        return x.ctypes.data
+    raise TypeError(f"cannot pass {type(x)} to libmrf")
+
+
+def _stream(stream) -> int | None:
+    if stream is not None:
+        return stream if isinstance(stream, int) else stream.cuda_stream
+    import torch
+    return torch.cuda.current_stream().cuda_stream
+
+
+def proj_opts(mode: str = "fp32", cone: str = "complex", topk: int = 8, certify: bool = True,
+              tie_rel: float = 1e-5, cert_margin: float = 2e-3, eps: float = 0.0,
+              fallback_thr: float = 0.98) -> ProjOpts:
+    o = ProjOpts()
+    lib().mrf_default_proj_opts(C.byref(o))
+    o.mode, o.cone, o.topk, o.certify = MODES[mode], CONES[cone], topk, int(certify)
+    o.tie_rel, o.cert_margin, o.eps, o.fallback_thr = tie_rel, cert_margin, eps, fallback_thr
+    return o
+
+
+def recon_opts(iters: int = 10, mu: float = 1.0, adaptive: bool = False, zeta: float = 2.0,
+               kappa: bool = False, tol: float = 0.0, max_shrink: int = 30, **proj) -> ReconOpts:
+    r = ReconOpts()
+    lib().mrf_default_recon_opts(C.byref(r))
+    r.iters, r.mu, r.adaptive, r.zeta = iters, mu, int(adaptive), zeta
+    r.kappa, r.tol, r.max_shrink = int(kappa), tol, max_shrink
+    r.proj = proj_opts(**proj)
+    return r
+
+
+def make_op(Ny: int, Nx: int, L: int, mask) -> Op:
+    return Op(Ny, Nx, L, _ptr(mask))
+
+
+class Dictionary:
+    """An mrf_dict: the dictionary copied to the GPU plus its packed operands."""
+
+    def __init__(self, atoms, params=None, grid_shape=None, pack_bf16: bool = True,
+                 stream=None):
+        import numpy as np
+        d, L = atoms.shape
+        o = IndexOpts()
+        lib().mrf_default_index_opts(C.byref(o))
+        o.pack_bf16 = int(pack_bf16)
+        P = 0 if params is None else int(params.shape[1])
+        gs = None
+        if grid_shape is not None:
+            gs = np.ascontiguousarray(np.asarray(grid_shape, np.int32))
+        h = C.c_void_p()
+        self._keep = (atoms, params, gs)
+        _check(lib().mrf_build_dict_index(_ptr(atoms), d, L, _ptr(params), P, _ptr(gs),
+                                          0 if gs is None else len(gs), C.byref(o),
+                                          C.byref(h), _stream(stream)))
+        self.handle = h
+        self.d, self.L, self.P = int(d), int(L), P
+        self._keep = None
+
+    def close(self) -> None:
+        if getattr(self, "handle", None):
+            lib().mrf_dict_free(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def reserve(self, n_max: int) -> None:
+        _check(lib().mrf_dict_reserve(self.handle, n_max))
+
+    def check(self, stream=None) -> None:
+        _check(lib().mrf_dict_check(self.handle, _stream(stream)))
+
+
+def build_dict_index(atoms, params=None, grid_shape=None, pack_bf16=True, stream=None):
+    return Dictionary(atoms, params, grid_shape, pack_bf16, stream)
+
+
+def project(D: Dictionary, Z, idx_out, rho_out=None, X_out=None, warm_idx=None, opts=None,
+            stats: bool = False, stream=None):
+    n = Z.shape[0]
+    o = opts or proj_opts()
+    st = Stats() if stats else None
+    _check(lib().mrf_project(D.handle, _ptr(Z), n, C.byref(o), _ptr(warm_idx), _ptr(idx_out),
+                             _ptr(rho_out), _ptr(X_out), C.byref(st) if st else None,
+                             _stream(stream)))
+    return st.as_dict() if st else None
+
+
+def forward(op: Op, X, Y, stream=None) -> None:
+    _check(lib().mrf_forward(C.byref(op), _ptr(X), _ptr(Y), _stream(stream)))
+
+
+def adjoint(op: Op, Y, AHY, stream=None) -> None:
+    _check(lib().mrf_adjoint(C.byref(op), _ptr(Y), _ptr(AHY), _stream(stream)))
+
+
+def ipg_step(D: Dictionary, op: Op, AHY, X, mu: float, idx_io, rho_out=None, opts=None,
+             stats: bool = False, stream=None):
+    o = opts or proj_opts()
+    st = Stats() if stats else None
+    _check(lib().mrf_ipg_step(D.handle, C.byref(op), _ptr(AHY), _ptr(X), mu, C.byref(o),
+                              _ptr(idx_io), _ptr(rho_out), C.byref(st) if st else None,
+                              _stream(stream)))
+    return st.as_dict() if st else None
+
+
+def reconstruct(D: Dictionary, op: Op, Y, X_out, idx_out, rho_out=None, params_out=None,
+                opts=None, stats: bool = False, stream=None):
+    r = opts or recon_opts()
+    st = Stats() if stats else None
+    _check(lib().mrf_reconstruct(D.handle, C.byref(op), _ptr(Y), C.byref(r), _ptr(X_out),
+                                 _ptr(idx_out), _ptr(rho_out), _ptr(params_out),
+                                 C.byref(st) if st else None, _stream(stream)))
+    return st.as_dict() if st else None
+
+
+def lut(D: Dictionary, idx, params_out, stream=None) -> None:
+    _check(lib().mrf_lut(D.handle, _ptr(idx), idx.shape[0], _ptr(params_out), _stream(stream)))
+
+
+PROFILE_STAGES = ["gradient", "pack_bf16", "search_bf16", "search_fp32", "merge", "fallback",
+                  "lut", "other"]
+
+
+def profile_enable(on: bool = True) -> None:
+    _check(lib().mrf_profile_enable(int(on)))
+
+
+def profile_read() -> dict:
+    """{stage: (milliseconds, launches)} accumulated since the last read (synchronises)."""
+    n = len(PROFILE_STAGES)
+    ms = (C.c_double * n)()
+    ln = (C.c_int64 * n)()
+    _check(lib().mrf_profile_read(ms, ln, n))
+    return {name: (ms[i], ln[i]) for i, name in enumerate(PROFILE_STAGES)}

@@ -1,0 +1,98 @@
+"""ctypes binding of libmrf.so (include/mrf.h): argument marshalling only.
+
+Every computation happens inside the library's CUDA kernels.  Tensors are passed as raw
+pointers (``tensor.data_ptr()``), streams as ``torch.cuda.Stream.cuda_stream`` handles.  The
+library is required: importing this module without a built ``_build/libmrf.so`` raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_build", "libmrf.so")
+
+MRF_OK, MRF_EINVAL, MRF_ENOMEM, MRF_ECUDA, MRF_ENONFINITE, MRF_ETIMEOUT, \
+    MRF_EUNSUPPORTED, MRF_EINTERNAL = range(8)
+MODES = {"fp32": 0, "bf16": 1, "fp8": 2, "covertree": 3, "learned": 4}
+CONES = {"complex": 0, "real_pos": 1}
+
+
+class IndexOpts(C.Structure):
+    _fields_ = [("pack_bf16", C.c_int32), ("pack_fp8", C.c_int32), ("build_tree", C.c_int32),
+                ("reserved", C.c_int32 * 5)]
+
+
+class ProjOpts(C.Structure):
+    _fields_ = [("mode", C.c_int32), ("cone", C.c_int32), ("topk", C.c_int32),
+                ("certify", C.c_int32), ("tie_rel", C.c_float), ("cert_margin", C.c_float),
+                ("eps", C.c_float), ("fallback_thr", C.c_float), ("reserved", C.c_int32 * 8)]
+
+
+class Stats(C.Structure):
+    _fields_ = [("n_voxels", C.c_int64), ("n_zero", C.c_int64), ("n_tie_rescored", C.c_int64),
+                ("n_tie_overflow", C.c_int64), ("n_uncertified", C.c_int64),
+                ("n_fallback", C.c_int64), ("n_dist_evals", C.c_int64),
+                ("device_error", C.c_int32), ("reserved", C.c_int32)]
+
+    def as_dict(self) -> dict:
+        return {f: getattr(self, f) for f, _ in self._fields_ if f != "reserved"}
+
+
+class Op(C.Structure):
+    _fields_ = [("Ny", C.c_int32), ("Nx", C.c_int32), ("L", C.c_int32), ("mask", C.c_void_p)]
+
+
+class ReconOpts(C.Structure):
+    _fields_ = [("iters", C.c_int32), ("mu", C.c_float), ("adaptive", C.c_int32),
+                ("zeta", C.c_float), ("kappa", C.c_int32), ("tol", C.c_float),
+                ("max_shrink", C.c_int32), ("reserved", C.c_int32 * 5), ("proj", ProjOpts)]
+
+
+SIGNATURES = {
+    "mrf_default_index_opts": (None, [C.POINTER(IndexOpts)]),
+    "mrf_default_proj_opts": (None, [C.POINTER(ProjOpts)]),
+    "mrf_default_recon_opts": (None, [C.POINTER(ReconOpts)]),
+    "mrf_build_dict_index": (C.c_int, [C.c_void_p, C.c_int64, C.c_int32, C.c_void_p, C.c_int32,
+                                       C.c_void_p, C.c_int32, C.POINTER(IndexOpts),
+                                       C.POINTER(C.c_void_p), C.c_void_p]),
+    "mrf_dict_free": (None, [C.c_void_p]),
+    "mrf_dict_info": (C.c_int, [C.c_void_p, C.POINTER(C.c_int64), C.POINTER(C.c_int32),
+                                C.POINTER(C.c_int32)]),
+    "mrf_dict_reserve": (C.c_int, [C.c_void_p, C.c_int64]),
+    "mrf_dict_check": (C.c_int, [C.c_void_p, C.c_void_p]),
+    "mrf_project": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.POINTER(ProjOpts),
+                              C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
+                              C.POINTER(Stats), C.c_void_p]),
+    "mrf_forward": (C.c_int, [C.POINTER(Op), C.c_void_p, C.c_void_p, C.c_void_p]),
+    "mrf_adjoint": (C.c_int, [C.POINTER(Op), C.c_void_p, C.c_void_p, C.c_void_p]),
+    "mrf_ipg_step": (C.c_int, [C.c_void_p, C.POINTER(Op), C.c_void_p, C.c_void_p, C.c_float,
+                               C.POINTER(ProjOpts), C.c_void_p, C.c_void_p, C.POINTER(Stats),
+                               C.c_void_p]),
+    "mrf_reconstruct": (C.c_int, [C.c_void_p, C.POINTER(Op), C.c_void_p, C.POINTER(ReconOpts),
+                                  C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
+                                  C.POINTER(Stats), C.c_void_p]),
+    "mrf_lut": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p]),
+    "mrf_profile_enable": (C.c_int, [C.c_int32]),
+    "mrf_profile_read": (C.c_int, [C.POINTER(C.c_double), C.POINTER(C.c_int64), C.c_int32]),
+    "mrf_status_str": (C.c_char_p, [C.c_int]),
+    "mrf_last_error": (C.c_char_p, []),
+}
+
+
+def load(path: str = LIB_PATH) -> C.CDLL:
+    if not os.path.exists(path):
+        raise ImportError(f"libmrf.so not built ({path}); run "
+                          "`python -m paper_1810_01967_gb300.build` (needs nvcc)")
+    lib = C.CDLL(path)
+    for name, (res, args) in SIGNATURES.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    return lib
+
+
+class MRFError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{msg} (status {status})")
+        self.status = status

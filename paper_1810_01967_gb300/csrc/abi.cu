@@ -1,0 +1,650 @@
+// Host side of the C ABI (include/mrf.h): argument checks, dictionary index, scratch
+// management, cuFFT plans of the sampling operator and the BLIP / CoverBLIP driver loop
+// (§3.2 eq. blip, Algorithm 2 with the step rule eq. steprule and the kappa rescale).
+#include <cufft.h>
+#include <cmath>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <tuple>
+
+#include "mrf_internal.cuh"
+
+static thread_local std::string g_last_error;
+
+void mrf_set_error(const std::string& msg) { g_last_error = msg; }
+
+namespace {
+
+cudaStream_t S_(void* s) { return reinterpret_cast<cudaStream_t>(s); }
+
+mrf_status fail(mrf_status s, const std::string& msg) {
+    mrf_set_error(msg);
+    return s;
+}
+
+template <typename T>
+mrf_status dalloc(T** p, size_t count) {
+    if (*p) { cudaFree(*p); *p = nullptr; }
+    if (count == 0) return MRF_OK;
+    cudaError_t e = cudaMalloc(reinterpret_cast<void**>(p), count * sizeof(T));
+    if (e != cudaSuccess) {
+        *p = nullptr;
+        cudaGetLastError();
+        return fail(MRF_ENOMEM, std::string("cudaMalloc: ") + cudaGetErrorString(e));
+    }
+    return MRF_OK;
+}
+
+// ------------------------------------------------------------------------------ cuFFT plans
+// Plans are cached per (kind, Ny, Nx, L) and re-bound to the caller's stream on every use.
+std::mutex g_plan_mu;
+std::map<std::tuple<int, int, int, int>, cufftHandle> g_plans;
+
+mrf_status get_plan(int kind, int Ny, int Nx, int L, cudaStream_t st, cufftHandle* out) {
+    std::lock_guard<std::mutex> lk(g_plan_mu);
+    auto key = std::make_tuple(kind, Ny, Nx, L);
+    auto it = g_plans.find(key);
+    cufftHandle h;
+    if (it == g_plans.end()) {
+        cufftResult r;
+        if (kind == 0) {   // 1-D along y of [Ny][Nx*L]: stride Nx*L, batches adjacent
+            int nn[1] = {Ny};
+            int emb[1] = {Ny};
+            long long stride = static_cast<long long>(Nx) * L;
+            r = cufftPlanMany(&h, 1, nn, emb, static_cast<int>(stride), 1, emb,
+                              static_cast<int>(stride), 1, CUFFT_C2C, static_cast<int>(stride));
+        } else {           // 2-D over (y, x) of [Ny][Nx][L]: element stride L, batch L
+            int nn[2] = {Ny, Nx};
+            int emb[2] = {Ny, Nx};
+            r = cufftPlanMany(&h, 2, nn, emb, L, 1, emb, L, 1, CUFFT_C2C, L);
+        }
+        if (r != CUFFT_SUCCESS)
+            return fail(MRF_ECUDA, "cufftPlanMany failed: " + std::to_string(static_cast<int>(r)));
+        g_plans[key] = h;
+    } else {
+        h = it->second;
+    }
+    if (cufftSetStream(h, st) != CUFFT_SUCCESS) return fail(MRF_ECUDA, "cufftSetStream failed");
+    *out = h;
+    return MRF_OK;
+}
+
+mrf_status fft_exec(cufftHandle h, const float2* in, float2* out, int dir) {
+    cufftResult r = cufftExecC2C(h, reinterpret_cast<cufftComplex*>(const_cast<float2*>(in)),
+                                 reinterpret_cast<cufftComplex*>(out), dir);
+    if (r != CUFFT_SUCCESS)
+        return fail(MRF_ECUDA, "cufftExecC2C failed: " + std::to_string(static_cast<int>(r)));
+    return MRF_OK;
+}
+
+mrf_status check_op(const mrf_op* op) {
+    if (!op || !op->mask) return fail(MRF_EINVAL, "op or op->mask is NULL");
+    if (op->Ny < 1 || op->Nx < 1 || op->L < 1) return fail(MRF_EINVAL, "op sizes must be >= 1");
+    if (static_cast<int64_t>(op->Nx) * op->L > INT32_MAX)
+        return fail(MRF_EINVAL, "Nx * L too large for the FFT batch");
+    return MRF_OK;
+}
+
+// ------------------------------------------------------------------------------ scratch
+int topk_slots(int topk) { return topk <= 8 ? 8 : 16; }
+
+mrf_status ensure_scratch(mrf_dict* D, int64_t n) {
+    if (n <= D->cap_n) return MRF_OK;
+    const int64_t L = D->L;
+    MRF_TRY(dalloc(&D->zbuf, static_cast<size_t>(n * L)));
+    MRF_TRY(dalloc(&D->wbuf, static_cast<size_t>(n * L)));
+    MRF_TRY(dalloc(&D->vlist, static_cast<size_t>(n)));
+    if (D->bop) MRF_TRY(dalloc(&D->zq, static_cast<size_t>(n * D->Kp)));
+    if (D->xprev) MRF_TRY(dalloc(&D->xprev, static_cast<size_t>(n * L)));
+    D->cap_n = n;
+    return MRF_OK;
+}
+
+mrf_status ensure_part(mrf_dict* D, int64_t n, int S, int K) {
+    size_t need = static_cast<size_t>(S) * n * K * (sizeof(float) + sizeof(int32_t));
+    if (need <= D->part_bytes) return MRF_OK;
+    if (D->part) cudaFree(D->part);
+    D->part = nullptr;
+    D->part_bytes = 0;
+    cudaError_t e = cudaMalloc(&D->part, need);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(MRF_ENOMEM, std::string("cudaMalloc(partials): ") + cudaGetErrorString(e));
+    }
+    D->part_bytes = need;
+    return MRF_OK;
+}
+
+mrf_status check_proj_opts(const mrf_dict* D, const mrf_proj_opts* o) {
+    if (!o) return fail(MRF_EINVAL, "proj opts is NULL");
+    if (o->cone != MRF_CONE_COMPLEX && o->cone != MRF_CONE_REAL_POS)
+        return fail(MRF_EINVAL, "unknown cone");
+    if (o->topk < 1 || o->topk > 16) return fail(MRF_EINVAL, "topk must be in 1..16");
+    if (!(o->tie_rel >= 0.f && o->tie_rel < 0.5f)) return fail(MRF_EINVAL, "tie_rel out of range");
+    switch (o->mode) {
+        case MRF_PROJ_FP32_EXACT: return MRF_OK;
+        case MRF_PROJ_BF16:
+            if (!D->bop) return fail(MRF_EUNSUPPORTED, "dictionary built without the BF16 operand");
+            return MRF_OK;
+        case MRF_PROJ_FP8:
+        case MRF_PROJ_COVERTREE:
+        case MRF_PROJ_LEARNED:
+            return fail(MRF_EUNSUPPORTED, "projection mode not available in this build");
+        default: return fail(MRF_EINVAL, "unknown projection mode");
+    }
+}
+
+mrf_status read_stats(mrf_dict* D, int64_t n, mrf_stats* stats, cudaStream_t st) {
+    unsigned long long c[CNT_N];
+    uint32_t e = 0;
+    MRF_CUDA_TRY(cudaMemcpyAsync(c, D->counters, sizeof(c), cudaMemcpyDeviceToHost, st));
+    MRF_CUDA_TRY(cudaMemcpyAsync(&e, D->err, sizeof(e), cudaMemcpyDeviceToHost, st));
+    MRF_CUDA_TRY(cudaStreamSynchronize(st));
+    if (stats) {
+        stats->n_voxels = n;
+        stats->n_zero = static_cast<int64_t>(c[CNT_ZERO]);
+        stats->n_tie_rescored = static_cast<int64_t>(c[CNT_TIE_RESCORED]);
+        stats->n_tie_overflow = static_cast<int64_t>(c[CNT_TIE_OVERFLOW]);
+        stats->n_uncertified = static_cast<int64_t>(c[CNT_UNCERT]);
+        stats->n_fallback = static_cast<int64_t>(c[CNT_FALLBACK]);
+        stats->n_dist_evals = static_cast<int64_t>(c[CNT_DIST]);
+        stats->device_error = static_cast<int32_t>(e);
+    }
+    if (e & MRF_DERR_TIMEOUT) return fail(MRF_ETIMEOUT, "a device-side wait bound expired");
+    if (e & MRF_DERR_NONFINITE) return fail(MRF_ENONFINITE, "non-finite value in an input");
+    if (e & MRF_DERR_BOUNDS) return fail(MRF_EINTERNAL, "device-side index out of range");
+    return MRF_OK;
+}
+
+// ------------------------------------------------------------------------------ profiler
+struct ProfEntry {
+    int stage;
+    int launches;
+    cudaEvent_t a, b;
+};
+bool g_prof_on = false;
+std::vector<ProfEntry> g_prof_pending;
+double g_prof_ms[MRF_PROFILE_STAGES];
+int64_t g_prof_launch[MRF_PROFILE_STAGES];
+
+void prof_clear() {
+    for (auto& e : g_prof_pending) { cudaEventDestroy(e.a); cudaEventDestroy(e.b); }
+    g_prof_pending.clear();
+    for (int i = 0; i < MRF_PROFILE_STAGES; ++i) { g_prof_ms[i] = 0.0; g_prof_launch[i] = 0; }
+}
+
+// Records an event pair around a stage on `st` while profiling is enabled.
+struct ProfScope {
+    bool on;
+    ProfEntry e;
+    cudaStream_t st;
+    ProfScope(int stage, int launches, cudaStream_t s) : on(g_prof_on), st(s) {
+        if (!on) return;
+        e.stage = stage;
+        e.launches = launches;
+        cudaEventCreate(&e.a);
+        cudaEventCreate(&e.b);
+        cudaEventRecord(e.a, st);
+    }
+    ~ProfScope() {
+        if (!on) return;
+        cudaEventRecord(e.b, st);
+        g_prof_pending.push_back(e);
+    }
+};
+
+// The projection proper.  `zq_ready` says the BF16 operand of Z is already in D->zq.
+mrf_status project_core(mrf_dict* D, const float2* Z, int64_t n, const mrf_proj_opts* o,
+                        const int32_t* warm, int32_t* idx_out, float2* rho_out, float2* X_out,
+                        bool zq_ready, cudaStream_t st) {
+    (void)warm;
+    const int K = topk_slots(o->topk);
+    if (n == 0) return MRF_OK;
+    MRF_TRY(ensure_scratch(D, n));
+    if (o->mode == MRF_PROJ_FP32_EXACT) {
+        const int S = fp32_choose_splits(n, D->d, D->num_sms);
+        MRF_TRY(ensure_part(D, n, S, K));
+        float* ps = static_cast<float*>(D->part);
+        int32_t* pi = reinterpret_cast<int32_t*>(ps + static_cast<size_t>(S) * n * K);
+        {
+            ProfScope ps3(3, 1, st);
+            MRF_TRY(launch_fp32_topk(Z, nullptr, nullptr, n, D, o->cone, K, S, ps, pi, st));
+        }
+        ProfScope ps4(4, 1, st);
+        MRF_TRY(launch_merge(Z, n, D, o->cone, K, S, ps, pi, nullptr, nullptr, o->tie_rel, 0,
+                             0.f, idx_out, rho_out, X_out, nullptr, nullptr, D->err,
+                             D->counters, st));
+        return MRF_OK;
+    }
+    if (o->mode == MRF_PROJ_BF16) {
+        if (!zq_ready) {
+            ProfScope ps1(1, 1, st);
+            MRF_TRY(launch_pack_queries(Z, n, D->L, D->Kp, D->zq, st));
+        }
+        const int S = bf16_choose_splits(n, D->nblk, D->num_sms);
+        MRF_TRY(ensure_part(D, n, S, K));
+        float* ps = static_cast<float*>(D->part);
+        int32_t* pi = reinterpret_cast<int32_t*>(ps + static_cast<size_t>(S) * n * K);
+        {
+            ProfScope ps2(2, 1, st);
+            MRF_TRY(launch_bf16_topk(D->zq, n, D, o->cone, K, S, ps, pi, st));
+        }
+        if (o->certify) MRF_CUDA_TRY(cudaMemsetAsync(D->nlist, 0, sizeof(int32_t), st));
+        {
+            ProfScope ps4(4, 1, st);
+            MRF_TRY(launch_merge(Z, n, D, o->cone, K, S, ps, pi, nullptr, nullptr, o->tie_rel,
+                                 o->certify, o->cert_margin, idx_out, rho_out, X_out, D->vlist,
+                                 D->nlist, D->err, D->counters, st));
+        }
+        if (o->certify) {
+            int32_t cnt = 0;
+            MRF_CUDA_TRY(cudaMemcpyAsync(&cnt, D->nlist, sizeof(cnt), cudaMemcpyDeviceToHost, st));
+            MRF_CUDA_TRY(cudaStreamSynchronize(st));
+            if (cnt > 0) {
+                ProfScope ps5(5, 2, st);
+                const int S2 = fp32_choose_splits(cnt, D->d, D->num_sms);
+                MRF_TRY(ensure_part(D, cnt, S2, K));
+                float* qs = static_cast<float*>(D->part);
+                int32_t* qi = reinterpret_cast<int32_t*>(qs + static_cast<size_t>(S2) * cnt * K);
+                MRF_TRY(launch_fp32_topk(Z, D->vlist, D->nlist, cnt, D, o->cone, K, S2, qs, qi,
+                                         st));
+                MRF_TRY(launch_merge(Z, cnt, D, o->cone, K, S2, qs, qi, D->vlist, D->nlist,
+                                     o->tie_rel, 0, 0.f, idx_out, rho_out, X_out, nullptr,
+                                     nullptr, D->err, D->counters, st));
+            }
+        }
+        return MRF_OK;
+    }
+    return fail(MRF_EUNSUPPORTED, "projection mode not available in this build");
+}
+
+// Z = X - mu (A^H A X - AHY) into D->zbuf (and its BF16 operand when `want_zq`).
+mrf_status gradient(mrf_dict* D, const mrf_op* op, const float2* AHY, const float2* X, float mu,
+                    bool want_zq, cudaStream_t st) {
+    const int64_t n = static_cast<int64_t>(op->Ny) * op->Nx;
+    cufftHandle hy;
+    MRF_TRY(get_plan(0, op->Ny, op->Nx, op->L, st, &hy));
+    ProfScope ps0(0, 2, st);
+    MRF_TRY(fft_exec(hy, X, D->wbuf, CUFFT_FORWARD));
+    MRF_TRY(launch_mask_ky(D->wbuf, op->mask, op->Ny, op->Nx, op->L, st));
+    MRF_TRY(fft_exec(hy, D->wbuf, D->wbuf, CUFFT_INVERSE));
+    MRF_TRY(launch_grad_combine(X, D->wbuf, AHY, D->zbuf, n, op->L, mu,
+                                1.0f / static_cast<float>(op->Ny), want_zq ? D->zq : nullptr,
+                                D->Kp, D->err, st));
+    return MRF_OK;
+}
+
+double read_red(mrf_dict* D, int i, cudaStream_t st, mrf_status* s) {
+    double v = 0.0;
+    if (cudaMemcpyAsync(&v, D->red + i, sizeof(v), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess) {
+        *s = fail(MRF_ECUDA, "reading a device reduction failed");
+    }
+    return v;
+}
+
+}  // namespace
+
+// ================================================================================ C ABI
+extern "C" {
+
+const char* mrf_last_error(void) { return g_last_error.c_str(); }
+
+const char* mrf_status_str(mrf_status s) {
+    switch (s) {
+        case MRF_OK: return "MRF_OK";
+        case MRF_EINVAL: return "MRF_EINVAL";
+        case MRF_ENOMEM: return "MRF_ENOMEM";
+        case MRF_ECUDA: return "MRF_ECUDA";
+        case MRF_ENONFINITE: return "MRF_ENONFINITE";
+        case MRF_ETIMEOUT: return "MRF_ETIMEOUT";
+        case MRF_EUNSUPPORTED: return "MRF_EUNSUPPORTED";
+        case MRF_EINTERNAL: return "MRF_EINTERNAL";
+    }
+    return "MRF_UNKNOWN";
+}
+
+void mrf_default_index_opts(mrf_index_opts* o) {
+    if (!o) return;
+    std::memset(o, 0, sizeof(*o));
+    o->pack_bf16 = 1;
+}
+
+void mrf_default_proj_opts(mrf_proj_opts* o) {
+    if (!o) return;
+    std::memset(o, 0, sizeof(*o));
+    o->mode = MRF_PROJ_FP32_EXACT;
+    o->cone = MRF_CONE_COMPLEX;
+    o->topk = 8;
+    o->certify = 1;
+    o->tie_rel = 1e-5f;
+    o->cert_margin = 2e-3f;
+    o->eps = 0.f;
+    o->fallback_thr = 0.98f;
+}
+
+void mrf_default_recon_opts(mrf_recon_opts* o) {
+    if (!o) return;
+    std::memset(o, 0, sizeof(*o));
+    o->iters = 10;
+    o->mu = 1.f;
+    o->zeta = 2.f;
+    o->max_shrink = 30;
+    mrf_default_proj_opts(&o->proj);
+}
+
+void mrf_dict_free(mrf_dict* D) {
+    if (!D) return;
+    void* ptrs[] = {D->atoms, D->inv_norm2, D->norm2, D->params, D->bop, D->zq, D->zbuf,
+                    D->wbuf, D->xprev, D->vlist, D->nlist, D->part, D->err, D->counters, D->red};
+    for (void* p : ptrs)
+        if (p) cudaFree(p);
+    delete D;
+}
+
+mrf_status mrf_build_dict_index(const void* atoms, int64_t d, int32_t L, const float* params,
+                                int32_t P, const int32_t* grid_shape, int32_t grid_ndim,
+                                const mrf_index_opts* opts, mrf_dict** out, void* stream) {
+    if (!out) return fail(MRF_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (!atoms) return fail(MRF_EINVAL, "atoms is NULL");
+    if (d < 1 || L < 1 || L > 4096) return fail(MRF_EINVAL, "need d >= 1 and 1 <= L <= 4096");
+    if (d > INT32_MAX) return fail(MRF_EINVAL, "d exceeds the int32 index range");
+    if (P < 0 || (P > 0 && !params)) return fail(MRF_EINVAL, "params / P mismatch");
+    if (grid_ndim < 0 || (grid_ndim > 0 && !grid_shape)) return fail(MRF_EINVAL, "grid_shape");
+    mrf_index_opts o;
+    if (opts) o = *opts; else mrf_default_index_opts(&o);
+    if (o.pack_fp8 || o.build_tree)
+        return fail(MRF_EUNSUPPORTED, "FP8 operand / cover tree not available in this build");
+    cudaStream_t st = S_(stream);
+    mrf_dict* D = new mrf_dict();
+    D->d = d;
+    D->L = L;
+    D->P = P;
+    for (int i = 0; i < grid_ndim; ++i) D->grid_shape.push_back(grid_shape[i]);
+    cudaGetDevice(&D->device);
+    cudaDeviceGetAttribute(&D->num_sms, cudaDevAttrMultiProcessorCount, D->device);
+    mrf_status s = MRF_OK;
+    auto bail = [&](mrf_status e) { mrf_dict_free(D); return e; };
+    if ((s = dalloc(&D->atoms, static_cast<size_t>(d * L))) != MRF_OK) return bail(s);
+    if ((s = dalloc(&D->inv_norm2, static_cast<size_t>(d))) != MRF_OK) return bail(s);
+    if ((s = dalloc(&D->norm2, static_cast<size_t>(d))) != MRF_OK) return bail(s);
+    if ((s = dalloc(&D->err, 1)) != MRF_OK) return bail(s);
+    if ((s = dalloc(&D->counters, CNT_N)) != MRF_OK) return bail(s);
+    if ((s = dalloc(&D->red, 8)) != MRF_OK) return bail(s);
+    if ((s = dalloc(&D->nlist, 1)) != MRF_OK) return bail(s);
+    if (P > 0 && (s = dalloc(&D->params, static_cast<size_t>(d * P))) != MRF_OK) return bail(s);
+    auto cuda_bail = [&](cudaError_t e, const char* what) {
+        mrf_set_error(std::string(what) + ": " + cudaGetErrorString(e));
+        mrf_dict_free(D);
+        return MRF_ECUDA;
+    };
+    cudaError_t e;
+    if ((e = cudaMemcpyAsync(D->atoms, atoms, sizeof(float2) * d * L, cudaMemcpyDefault, st)))
+        return cuda_bail(e, "copy atoms");
+    if (P > 0 && (e = cudaMemcpyAsync(D->params, params, sizeof(float) * d * P,
+                                      cudaMemcpyDefault, st)))
+        return cuda_bail(e, "copy params");
+    if ((e = cudaMemsetAsync(D->err, 0, sizeof(uint32_t), st))) return cuda_bail(e, "memset");
+    if ((e = cudaMemsetAsync(D->counters, 0, sizeof(unsigned long long) * CNT_N, st)))
+        return cuda_bail(e, "memset");
+    if ((s = launch_atom_norms(D, st)) != MRF_OK) return bail(s);
+    if (o.pack_bf16) {
+        D->nblk = (d + 127) / 128;
+        D->Kp = ((2 * L + 15) / 16) * 16;
+        if ((s = dalloc(&D->bop, static_cast<size_t>(D->nblk * 256 * D->Kp))) != MRF_OK)
+            return bail(s);
+        if ((s = launch_pack_bop(D, st)) != MRF_OK) return bail(s);
+    }
+    uint32_t werr = 0;
+    if ((e = cudaMemcpyAsync(&werr, D->err, sizeof(werr), cudaMemcpyDeviceToHost, st)))
+        return cuda_bail(e, "read error word");
+    if ((e = cudaStreamSynchronize(st))) return cuda_bail(e, "build");
+    if (werr & MRF_DERR_NONFINITE) {
+        mrf_set_error("an atom has a zero or non-finite norm");
+        mrf_dict_free(D);
+        return MRF_ENONFINITE;
+    }
+    *out = D;
+    return MRF_OK;
+}
+
+mrf_status mrf_dict_info(const mrf_dict* D, int64_t* d, int32_t* L, int32_t* P) {
+    if (!D) return fail(MRF_EINVAL, "dict is NULL");
+    if (d) *d = D->d;
+    if (L) *L = D->L;
+    if (P) *P = D->P;
+    return MRF_OK;
+}
+
+mrf_status mrf_dict_reserve(mrf_dict* D, int64_t n_max) {
+    if (!D || n_max < 0) return fail(MRF_EINVAL, "bad dict or n_max");
+    MRF_TRY(ensure_scratch(D, n_max));
+    return MRF_OK;
+}
+
+mrf_status mrf_dict_check(mrf_dict* D, void* stream) {
+    if (!D) return fail(MRF_EINVAL, "dict is NULL");
+    cudaStream_t st = S_(stream);
+    mrf_status s = read_stats(D, 0, nullptr, st);
+    MRF_CUDA_TRY(cudaMemsetAsync(D->err, 0, sizeof(uint32_t), st));
+    MRF_CUDA_TRY(cudaStreamSynchronize(st));
+    return s;
+}
+
+mrf_status mrf_project(mrf_dict* D, const void* Z, int64_t n, const mrf_proj_opts* opts,
+                       const int32_t* warm_idx, int32_t* idx_out, void* rho_out, void* X_out,
+                       mrf_stats* stats, void* stream) {
+    if (!D) return fail(MRF_EINVAL, "dict is NULL");
+    if (n < 0 || n > INT32_MAX) return fail(MRF_EINVAL, "n out of range");
+    if (n > 0 && (!Z || !idx_out)) return fail(MRF_EINVAL, "Z and idx_out are required");
+    mrf_proj_opts o;
+    if (opts) o = *opts; else mrf_default_proj_opts(&o);
+    MRF_TRY(check_proj_opts(D, &o));
+    cudaStream_t st = S_(stream);
+    if (stats) MRF_CUDA_TRY(cudaMemsetAsync(D->counters, 0, sizeof(unsigned long long) * CNT_N, st));
+    MRF_TRY(project_core(D, static_cast<const float2*>(Z), n, &o, warm_idx, idx_out,
+                         static_cast<float2*>(rho_out), static_cast<float2*>(X_out), false, st));
+    if (stats) return read_stats(D, n, stats, st);
+    return MRF_OK;
+}
+
+mrf_status mrf_forward(const mrf_op* op, const void* X, void* Y, void* stream) {
+    MRF_TRY(check_op(op));
+    if (!X || !Y) return fail(MRF_EINVAL, "X and Y are required");
+    cudaStream_t st = S_(stream);
+    cufftHandle h2;
+    MRF_TRY(get_plan(1, op->Ny, op->Nx, op->L, st, &h2));
+    MRF_TRY(fft_exec(h2, static_cast<const float2*>(X), static_cast<float2*>(Y), CUFFT_FORWARD));
+    MRF_TRY(launch_mask_ky(static_cast<float2*>(Y), op->mask, op->Ny, op->Nx, op->L, st));
+    const int64_t cnt = static_cast<int64_t>(op->Ny) * op->Nx * op->L;
+    MRF_TRY(launch_scale(static_cast<float2*>(Y), cnt,
+                         1.0f / std::sqrt(static_cast<float>(op->Ny) * op->Nx), st));
+    return MRF_OK;
+}
+
+mrf_status mrf_adjoint(const mrf_op* op, const void* Y, void* AHY, void* stream) {
+    MRF_TRY(check_op(op));
+    if (!Y || !AHY) return fail(MRF_EINVAL, "Y and AHY are required");
+    cudaStream_t st = S_(stream);
+    const int64_t cnt = static_cast<int64_t>(op->Ny) * op->Nx * op->L;
+    if (AHY != Y)
+        MRF_CUDA_TRY(cudaMemcpyAsync(AHY, Y, sizeof(float2) * cnt, cudaMemcpyDeviceToDevice, st));
+    MRF_TRY(launch_mask_ky(static_cast<float2*>(AHY), op->mask, op->Ny, op->Nx, op->L, st));
+    cufftHandle h2;
+    MRF_TRY(get_plan(1, op->Ny, op->Nx, op->L, st, &h2));
+    MRF_TRY(fft_exec(h2, static_cast<float2*>(AHY), static_cast<float2*>(AHY), CUFFT_INVERSE));
+    MRF_TRY(launch_scale(static_cast<float2*>(AHY), cnt,
+                         1.0f / std::sqrt(static_cast<float>(op->Ny) * op->Nx), st));
+    return MRF_OK;
+}
+
+mrf_status mrf_ipg_step(mrf_dict* D, const mrf_op* op, const void* AHY, void* X, float mu,
+                        const mrf_proj_opts* opts, int32_t* idx_io, void* rho_out,
+                        mrf_stats* stats, void* stream) {
+    if (!D) return fail(MRF_EINVAL, "dict is NULL");
+    MRF_TRY(check_op(op));
+    if (op->L != D->L) return fail(MRF_EINVAL, "op->L differs from the dictionary's L");
+    if (!AHY || !X || !idx_io) return fail(MRF_EINVAL, "AHY, X and idx_io are required");
+    if (!std::isfinite(mu)) return fail(MRF_EINVAL, "mu must be finite");
+    mrf_proj_opts o;
+    if (opts) o = *opts; else mrf_default_proj_opts(&o);
+    MRF_TRY(check_proj_opts(D, &o));
+    cudaStream_t st = S_(stream);
+    const int64_t n = static_cast<int64_t>(op->Ny) * op->Nx;
+    MRF_TRY(ensure_scratch(D, n));
+    if (stats) MRF_CUDA_TRY(cudaMemsetAsync(D->counters, 0, sizeof(unsigned long long) * CNT_N, st));
+    const bool zq = (o.mode == MRF_PROJ_BF16);
+    MRF_TRY(gradient(D, op, static_cast<const float2*>(AHY), static_cast<const float2*>(X), mu,
+                     zq, st));
+    MRF_TRY(project_core(D, D->zbuf, n, &o, idx_io, idx_io, static_cast<float2*>(rho_out),
+                         static_cast<float2*>(X), zq, st));
+    if (stats) return read_stats(D, n, stats, st);
+    return MRF_OK;
+}
+
+mrf_status mrf_lut(const mrf_dict* D, const int32_t* idx, int64_t n, float* params_out,
+                   void* stream) {
+    if (!D) return fail(MRF_EINVAL, "dict is NULL");
+    if (D->P == 0) return fail(MRF_EINVAL, "dictionary has no parameter table");
+    if (n > 0 && (!idx || !params_out)) return fail(MRF_EINVAL, "idx and params_out required");
+    ProfScope ps6(6, 1, S_(stream));
+    return launch_lut(idx, n, D->params, D->P, D->d, params_out, D->err, S_(stream));
+}
+
+mrf_status mrf_profile_enable(int32_t on) {
+    prof_clear();
+    g_prof_on = on != 0;
+    return MRF_OK;
+}
+
+mrf_status mrf_profile_read(double* ms, int64_t* launches, int32_t n_stages) {
+    if (n_stages < 0 || (n_stages > 0 && (!ms || !launches)))
+        return fail(MRF_EINVAL, "ms/launches required");
+    for (auto& e : g_prof_pending) {
+        float t = 0.f;
+        if (cudaEventSynchronize(e.b) != cudaSuccess ||
+            cudaEventElapsedTime(&t, e.a, e.b) != cudaSuccess) {
+            cudaGetLastError();
+            prof_clear();
+            return fail(MRF_ECUDA, "reading profiler events failed");
+        }
+        g_prof_ms[e.stage] += t;
+        g_prof_launch[e.stage] += e.launches;
+    }
+    for (int i = 0; i < n_stages && i < MRF_PROFILE_STAGES; ++i) {
+        ms[i] = g_prof_ms[i];
+        launches[i] = g_prof_launch[i];
+    }
+    prof_clear();
+    return MRF_OK;
+}
+
+mrf_status mrf_reconstruct(mrf_dict* D, const mrf_op* op, const void* Y,
+                           const mrf_recon_opts* ropts, void* X_out, int32_t* idx_out,
+                           void* rho_out, float* params_out, mrf_stats* stats, void* stream) {
+    if (!D) return fail(MRF_EINVAL, "dict is NULL");
+    MRF_TRY(check_op(op));
+    if (op->L != D->L) return fail(MRF_EINVAL, "op->L differs from the dictionary's L");
+    if (!Y || !X_out || !idx_out) return fail(MRF_EINVAL, "Y, X_out and idx_out are required");
+    mrf_recon_opts r;
+    if (ropts) r = *ropts; else mrf_default_recon_opts(&r);
+    if (r.iters < 0 || !(r.mu > 0.f) || (r.adaptive && !(r.zeta > 1.f)) || r.max_shrink < 0)
+        return fail(MRF_EINVAL, "bad reconstruction options");
+    MRF_TRY(check_proj_opts(D, &r.proj));
+    if (params_out && D->P == 0) return fail(MRF_EINVAL, "dictionary has no parameter table");
+    cudaStream_t st = S_(stream);
+    const int64_t n = static_cast<int64_t>(op->Ny) * op->Nx;
+    const int64_t cnt = n * op->L;
+    MRF_TRY(ensure_scratch(D, n));
+    if ((r.adaptive || r.kappa || r.tol > 0.f) && !D->xprev)
+        MRF_TRY(dalloc(&D->xprev, static_cast<size_t>(cnt)));
+    // scratch: AHY in a dedicated buffer (the gradient uses zbuf and wbuf)
+    float2* AHY = nullptr;
+    MRF_TRY(dalloc(&AHY, static_cast<size_t>(cnt)));
+    float2* rho = static_cast<float2*>(rho_out);
+    float2* rho_tmp = nullptr;
+    if (!rho) {
+        mrf_status s = dalloc(&rho_tmp, static_cast<size_t>(n));
+        if (s != MRF_OK) { cudaFree(AHY); return s; }
+        rho = rho_tmp;
+    }
+    float2* X = static_cast<float2*>(X_out);
+    const bool zq = (r.proj.mode == MRF_PROJ_BF16);
+    mrf_status s = MRF_OK;
+    auto body = [&]() -> mrf_status {
+        MRF_CUDA_TRY(cudaMemsetAsync(D->counters, 0, sizeof(unsigned long long) * CNT_N, st));
+        MRF_TRY(mrf_adjoint(op, Y, AHY, stream));
+        MRF_CUDA_TRY(cudaMemsetAsync(X, 0, sizeof(float2) * cnt, st));
+        MRF_CUDA_TRY(cudaMemsetAsync(idx_out, 0, sizeof(int32_t) * n, st));
+        double ynorm2 = -1.0, prev_obj = -1.0;
+        float mu0 = r.mu;
+        for (int k = 0; k < r.iters; ++k) {
+            float mu_k = mu0;
+            if (r.adaptive || r.kappa || r.tol > 0.f)
+                MRF_CUDA_TRY(cudaMemcpyAsync(D->xprev, X, sizeof(float2) * cnt,
+                                             cudaMemcpyDeviceToDevice, st));
+            for (int shrink = 0;; ++shrink) {
+                MRF_TRY(gradient(D, op, AHY, r.adaptive ? D->xprev : X, mu_k, zq, st));
+                MRF_TRY(project_core(D, D->zbuf, n, &r.proj, idx_out, idx_out, rho, X, zq, st));
+                if (!r.adaptive) break;
+                // step rule (eq. steprule): accept when mu_k < ||dX||^2 / ||A dX||^2
+                MRF_CUDA_TRY(cudaMemsetAsync(D->red, 0, sizeof(double) * 2, st));
+                MRF_TRY(launch_sqdiff(X, D->xprev, cnt, D->red, st));
+                MRF_CUDA_TRY(cudaMemcpyAsync(D->wbuf, X, sizeof(float2) * cnt,
+                                             cudaMemcpyDeviceToDevice, st));
+                MRF_TRY(launch_axpby(D->wbuf, D->xprev, cnt, 1.f, -1.f, st));
+                MRF_TRY(mrf_forward(op, D->wbuf, D->zbuf, stream));
+                MRF_TRY(launch_sqnorm(D->zbuf, cnt, D->red + 1, st));
+                double num = read_red(D, 0, st, &s);
+                double den = read_red(D, 1, st, &s);
+                if (s != MRF_OK) return s;
+                if (den == 0.0 || static_cast<double>(mu_k) < num / den || shrink >= r.max_shrink)
+                    break;
+                mu_k /= r.zeta;
+            }
+            if (r.kappa && k == 0) {
+                if (ynorm2 < 0.0) {
+                    MRF_CUDA_TRY(cudaMemsetAsync(D->red + 2, 0, sizeof(double), st));
+                    MRF_TRY(launch_sqnorm(static_cast<const float2*>(Y), cnt, D->red + 2, st));
+                    ynorm2 = read_red(D, 2, st, &s);
+                }
+                MRF_TRY(mrf_forward(op, X, D->zbuf, stream));
+                MRF_CUDA_TRY(cudaMemsetAsync(D->red + 3, 0, sizeof(double), st));
+                MRF_TRY(launch_sqnorm(D->zbuf, cnt, D->red + 3, st));
+                double ax = read_red(D, 3, st, &s);
+                if (s != MRF_OK) return s;
+                if (ax > 0.0) {
+                    float kap = static_cast<float>(std::sqrt(ynorm2 / ax));
+                    MRF_TRY(launch_scale(X, cnt, kap, st));
+                    MRF_TRY(launch_scale(rho, n, kap, st));
+                    mu0 *= kap;
+                }
+            }
+            if (r.tol > 0.f) {
+                // objective ||Y - A X||^2 (Y is zero off the sampled lines after masking)
+                MRF_TRY(mrf_forward(op, X, D->zbuf, stream));
+                MRF_CUDA_TRY(cudaMemcpyAsync(D->wbuf, Y, sizeof(float2) * cnt,
+                                             cudaMemcpyDeviceToDevice, st));
+                MRF_TRY(launch_mask_ky(D->wbuf, op->mask, op->Ny, op->Nx, op->L, st));
+                MRF_CUDA_TRY(cudaMemsetAsync(D->red + 4, 0, sizeof(double), st));
+                MRF_TRY(launch_sqdiff(D->wbuf, D->zbuf, cnt, D->red + 4, st));
+                double obj = read_red(D, 4, st, &s);
+                if (s != MRF_OK) return s;
+                if (prev_obj > 0.0 && std::fabs(prev_obj - obj) / prev_obj < r.tol) break;
+                prev_obj = obj;
+            }
+        }
+        if (params_out) MRF_TRY(mrf_lut(D, idx_out, n, params_out, stream));
+        return MRF_OK;
+    };
+    s = body();
+    mrf_status s2 = read_stats(D, n, stats, st);
+    cudaFree(AHY);
+    if (rho_tmp) cudaFree(rho_tmp);
+    if (s != MRF_OK) return s;
+    return s2;
+}
+
+}  // extern "C"

@@ -1,0 +1,342 @@
+// Exhaustive matched filter on the 5th-generation tensor cores (§3.2, eq. exactP), BF16 inputs
+// with FP32 accumulation in tensor memory.
+//
+// The complex correlation D_j^H Z_v is a real GEMM: query row v = (Re z_0, Im z_0, Re z_1, ...)
+// (K = 2L, padded to Kp), and per block of 128 atoms 256 operand rows: 128 rows
+// (Re d_t, Im d_t)_t giving Re(D^H z) and 128 rows (-Im d_t, Re d_t)_t giving Im(D^H z).  One
+// UMMA of shape M = 128 voxels x N = 256 columns therefore yields, for every voxel row, the real
+// parts of 128 atoms in columns [0,128) and their imaginary parts in columns [128,256) of the
+// same TMEM lane, so the epilogue thread that owns the row forms |c|^2 / ||D_j||^2 without any
+// data exchange and keeps a sorted top-K in registers.  Scores never reach global memory.
+//
+// Persistent CTAs (one per SM) walk work units (atom split s, voxel tile m), consecutive units
+// sharing s so that CTAs running together stream the same atom blocks through L2.
+// Warp roles: warp 0 = TMA producer, warp 1 = TMEM owner and MMA issuer, warps 2..5 = epilogue
+// (TMEM lanes 32 (w mod 4) ...).  4-stage shared-memory ring (48 KB per stage: A 128x64,
+// B 256x64 BF16, 128-byte swizzle), double-buffered 2 x 256-column FP32 accumulator.
+// Every mbarrier wait is bounded; on expiry the CTA raises MRF_DERR_TIMEOUT, drains what it
+// issued and exits.
+#include <cuda.h>
+#include "mrf_internal.cuh"
+#include "ptx.cuh"
+
+namespace {
+
+constexpr int BM = 128;
+constexpr int BN = 256;          // 128 atoms x (re, im)
+constexpr int BK = 64;           // BF16 elements per stage row = 128 bytes
+constexpr int STAGES = 4;
+constexpr int A_BYTES = BM * BK * 2;
+constexpr int B_BYTES = BN * BK * 2;
+constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
+constexpr int NTHREADS = 192;
+constexpr uint32_t IDESC = mrfk::idesc_bf16(BM, BN);
+
+struct Shared {
+    uint64_t full[STAGES];
+    uint64_t empty[STAGES];
+    uint64_t tfull[2];
+    uint64_t tempty[2];
+    uint64_t drain;
+    uint32_t tmem_base;
+    volatile int abort;
+};
+
+template <int KT>
+__device__ __forceinline__ void topk_insert(float (&ts)[KT], int32_t (&ti)[KT], float s,
+                                            int32_t j) {
+    if (s > ts[KT - 1]) {
+        ts[KT - 1] = s;
+        ti[KT - 1] = j;
+#pragma unroll
+        for (int q = KT - 1; q > 0; --q) {
+            bool up = ts[q] > ts[q - 1];
+            float a = ts[q], b = ts[q - 1];
+            int32_t ia = ti[q], ib = ti[q - 1];
+            ts[q - 1] = up ? a : b;
+            ts[q] = up ? b : a;
+            ti[q - 1] = up ? ia : ib;
+            ti[q] = up ? ib : ia;
+        }
+    }
+}
+
+template <int KT>
+__global__ void __launch_bounds__(NTHREADS, 1)
+k_bf16_topk(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+            int64_t n, int64_t d, int64_t nblk, int Kp, int cone, int S, int blocks_per_split,
+            const float* __restrict__ inv_norm2, float* __restrict__ part_s,
+            int32_t* __restrict__ part_i, uint32_t* err) {
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    unsigned char* base = reinterpret_cast<unsigned char*>(
+        (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
+    Shared* sh = reinterpret_cast<Shared*>(base + STAGES * STAGE_BYTES);
+
+    const int warp = threadIdx.x >> 5;
+    const int lane = threadIdx.x & 31;
+    const int64_t Mt = (n + BM - 1) / BM;
+    const int64_t units = Mt * S;
+    const int nk = (Kp + BK - 1) / BK;
+
+    if (threadIdx.x == 0) {
+        for (int i = 0; i < STAGES; ++i) { mrfk::mbar_init(&sh->full[i], 1); mrfk::mbar_init(&sh->empty[i], 1); }
+        for (int i = 0; i < 2; ++i) { mrfk::mbar_init(&sh->tfull[i], 1); mrfk::mbar_init(&sh->tempty[i], 128); }
+        mrfk::mbar_init(&sh->drain, 1);
+        sh->abort = 0;
+        mrfk::fence_mbar_init();
+    }
+    if (warp == 1) {
+        mrfk::tmem_alloc(&sh->tmem_base, 512);
+        mrfk::tmem_relinquish();
+    }
+    if (warp == 0 && lane == 0) {
+        mrfk::tma_prefetch_desc(&tmA);
+        mrfk::tma_prefetch_desc(&tmB);
+    }
+    mrfk::tc_fence_before();
+    __syncthreads();
+    mrfk::tc_fence_after();
+    const uint32_t tmem = sh->tmem_base;
+
+    auto fail = [&]() {
+        atomicOr(err, MRF_DERR_TIMEOUT);
+        sh->abort = 1;
+    };
+
+    if (warp == 0) {
+        // ------------------------------------------------------------ TMA producer
+        if (lane == 0) {
+            int stage = 0;
+            uint32_t phase = 0;
+            uint32_t slot_phase[STAGES];
+            bool slot_used[STAGES];
+            for (int i = 0; i < STAGES; ++i) { slot_used[i] = false; slot_phase[i] = 0; }
+            for (int64_t u = blockIdx.x; u < units && !sh->abort; u += gridDim.x) {
+                const int64_t m = u % Mt;
+                const int64_t s = u / Mt;
+                const int64_t b0 = s * blocks_per_split;
+                const int64_t b1 = min(b0 + blocks_per_split, nblk);
+                for (int64_t b = b0; b < b1 && !sh->abort; ++b) {
+                    for (int kc = 0; kc < nk; ++kc) {
+                        if (!mrfk::mbar_wait(&sh->empty[stage], phase ^ 1u)) { fail(); break; }
+                        unsigned char* sa = base + stage * STAGE_BYTES;
+                        mrfk::mbar_arrive_expect_tx(&sh->full[stage], STAGE_BYTES);
+                        mrfk::tma_load_2d(sa, &tmA, &sh->full[stage], kc * BK, static_cast<int32_t>(m * BM));
+                        mrfk::tma_load_2d(sa + A_BYTES, &tmB, &sh->full[stage], kc * BK,
+                                          static_cast<int32_t>(b * BN));
+                        slot_used[stage] = true;
+                        slot_phase[stage] = phase;
+                        if (++stage == STAGES) { stage = 0; phase ^= 1u; }
+                    }
+                }
+            }
+            if (sh->abort) {
+                // drain: every slot this thread filled must have landed before the CTA exits
+                for (int i = 0; i < STAGES; ++i)
+                    if (slot_used[i]) mrfk::mbar_wait(&sh->full[i], slot_phase[i]);
+            }
+        }
+    } else if (warp == 1) {
+        // ------------------------------------------------------------ MMA issuer
+        if (lane == 0) {
+            int stage = 0;
+            uint32_t phase = 0;
+            int acc = 0;
+            uint32_t aphase = 0;
+            bool any = false;
+            for (int64_t u = blockIdx.x; u < units && !sh->abort; u += gridDim.x) {
+                const int64_t s = u / Mt;
+                const int64_t b0 = s * blocks_per_split;
+                const int64_t b1 = min(b0 + blocks_per_split, nblk);
+                for (int64_t b = b0; b < b1 && !sh->abort; ++b) {
+                    if (!mrfk::mbar_wait(&sh->tempty[acc], aphase ^ 1u)) { fail(); break; }
+                    mrfk::tc_fence_after();
+                    const uint32_t dt = tmem + static_cast<uint32_t>(acc * BN);
+                    bool ok = true;
+                    for (int kc = 0; kc < nk; ++kc) {
+                        if (!mrfk::mbar_wait(&sh->full[stage], phase)) { fail(); ok = false; break; }
+                        mrfk::tc_fence_after();
+                        const uint32_t sa = mrfk::smem_u32(base + stage * STAGE_BYTES);
+                        const uint32_t sb = sa + A_BYTES;
+                        const int rem = Kp - kc * BK;
+                        const int nmma = rem >= BK ? BK / 16 : rem / 16;
+                        for (int k = 0; k < nmma; ++k) {
+                            const uint64_t da = mrfk::sdesc_k_sw128(sa + k * 32);
+                            const uint64_t db = mrfk::sdesc_k_sw128(sb + k * 32);
+                            mrfk::mma_bf16(dt, da, db, IDESC, (kc > 0 || k > 0) ? 1u : 0u);
+                        }
+                        mrfk::mma_commit(&sh->empty[stage]);
+                        any = true;
+                        if (++stage == STAGES) { stage = 0; phase ^= 1u; }
+                    }
+                    if (!ok) break;
+                    mrfk::mma_commit(&sh->tfull[acc]);
+                    if (++acc == 2) { acc = 0; aphase ^= 1u; }
+                }
+            }
+            if (any) {
+                // all MMAs issued by this thread complete before TMEM is released
+                mrfk::mma_commit(&sh->drain);
+                if (!mrfk::mbar_wait(&sh->drain, 0)) atomicOr(err, MRF_DERR_TIMEOUT);
+            }
+        }
+    } else {
+        // ------------------------------------------------------------ epilogue (4 warps)
+        const int quarter = warp & 3;
+        const int row = quarter * 32 + lane;
+        const uint32_t lane_base = static_cast<uint32_t>(quarter * 32) << 16;
+        int acc = 0;
+        uint32_t aphase = 0;
+        for (int64_t u = blockIdx.x; u < units && !sh->abort; u += gridDim.x) {
+            const int64_t m = u % Mt;
+            const int64_t s = u / Mt;
+            const int64_t b0 = s * blocks_per_split;
+            const int64_t b1 = min(b0 + blocks_per_split, nblk);
+            float ts[KT];
+            int32_t ti[KT];
+#pragma unroll
+            for (int q = 0; q < KT; ++q) { ts[q] = -INFINITY; ti[q] = -1; }
+            bool ok = true;
+            for (int64_t b = b0; b < b1; ++b) {
+                if (!mrfk::mbar_wait(&sh->tfull[acc], aphase)) { fail(); ok = false; break; }
+                mrfk::tc_fence_after();
+                const uint32_t tb = tmem + lane_base + static_cast<uint32_t>(acc * BN);
+#pragma unroll 1
+                for (int c = 0; c < 4; ++c) {
+                    uint32_t re[32], im[32];
+                    __syncwarp();
+                    mrfk::tmem_ld32(tb + c * 32, re);
+                    mrfk::tmem_ld32(tb + 128 + c * 32, im);
+                    const int64_t jl = b * 128 + c * 32 + lane;
+                    const float wl = (jl < d) ? inv_norm2[jl] : 0.f;
+                    mrfk::tmem_ld_wait();
+#pragma unroll
+                    for (int i = 0; i < 32; ++i) {
+                        const float w = __shfl_sync(0xffffffffu, wl, i);
+                        const int64_t j = b * 128 + c * 32 + i;
+                        const float x = __uint_as_float(re[i]);
+                        const float y = __uint_as_float(im[i]);
+                        const float sc = (cone == MRF_CONE_COMPLEX) ? (x * x + y * y) * w
+                                                                    : x * sqrtf(w);
+                        if (j < d) topk_insert<KT>(ts, ti, sc, static_cast<int32_t>(j));
+                    }
+                }
+                mrfk::tc_fence_before();
+                mrfk::mbar_arrive(&sh->tempty[acc]);
+                if (++acc == 2) { acc = 0; aphase ^= 1u; }
+            }
+            if (!ok) break;
+            const int64_t v = m * BM + row;
+            if (v < n) {
+                const int64_t o = (s * n + v) * KT;
+#pragma unroll
+                for (int q = 0; q < KT; ++q) { part_s[o + q] = ts[q]; part_i[o + q] = ti[q]; }
+            }
+        }
+    }
+    mrfk::tc_fence_before();
+    __syncthreads();
+    mrfk::tc_fence_after();
+    if (warp == 1) mrfk::tmem_dealloc(tmem, 512);
+}
+
+constexpr size_t kSmem = STAGES * STAGE_BYTES + sizeof(Shared) + 1024;
+
+using EncodeFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
+                              const cuuint64_t*, const cuuint64_t*, const cuuint32_t*,
+                              const cuuint32_t*, CUtensorMapInterleave, CUtensorMapSwizzle,
+                              CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeFn get_encode() {
+    static EncodeFn fn = nullptr;
+    if (!fn) {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000,
+                                             cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<EncodeFn>(p);
+    }
+    return fn;
+}
+
+mrf_status make_map(CUtensorMap* m, const void* ptr, int64_t rows, int Kp, int box_rows) {
+    EncodeFn enc = get_encode();
+    if (!enc) {
+        mrf_set_error("cuTensorMapEncodeTiled is unavailable");
+        return MRF_ECUDA;
+    }
+    cuuint64_t dims[2] = {static_cast<cuuint64_t>(Kp), static_cast<cuuint64_t>(rows)};
+    cuuint64_t strides[1] = {static_cast<cuuint64_t>(Kp) * 2};
+    cuuint32_t box[2] = {static_cast<cuuint32_t>(BK), static_cast<cuuint32_t>(box_rows)};
+    cuuint32_t es[2] = {1, 1};
+    CUresult r = enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(ptr), dims,
+                     strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                     CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                     CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) {
+        mrf_set_error("cuTensorMapEncodeTiled failed: " + std::to_string(static_cast<int>(r)));
+        return MRF_ECUDA;
+    }
+    return MRF_OK;
+}
+
+}  // namespace
+
+int bf16_choose_splits(int64_t n, int64_t nblk, int num_sms) {
+    // Pick the atom split S that minimises the makespan ceil(units / G) * ceil(nblk / S)
+    // of the static round-robin schedule, units = Mt * S, G = min(units, num_sms).
+    const int64_t Mt = (n + BM - 1) / BM;
+    int best = 1;
+    double best_t = 1e300;
+    for (int64_t S = 1; S <= nblk && S <= 1024; ++S) {
+        int64_t units = Mt * S;
+        int64_t G = units < num_sms ? units : num_sms;
+        int64_t waves = (units + G - 1) / G;
+        int64_t per = (nblk + S - 1) / S;
+        double t = static_cast<double>(waves * per) + 1e-3 * S;   // prefer fewer splits
+        if (t < best_t) { best_t = t; best = static_cast<int>(S); }
+    }
+    return best;
+}
+
+mrf_status launch_bf16_topk(const __nv_bfloat16* zq, int64_t n, const mrf_dict* D, int cone,
+                            int K, int S, float* part_s, int32_t* part_i, cudaStream_t st) {
+    if (n == 0) return MRF_OK;
+    if (!D->bop) {
+        mrf_set_error("BF16 operand was not packed (mrf_index_opts.pack_bf16 = 0)");
+        return MRF_EUNSUPPORTED;
+    }
+    CUtensorMap ta, tb;
+    MRF_TRY(make_map(&ta, zq, n, D->Kp, BM));
+    MRF_TRY(make_map(&tb, D->bop, D->nblk * 256, D->Kp, BN));
+    const int64_t Mt = (n + BM - 1) / BM;
+    const int64_t units = Mt * S;
+    const int bps = static_cast<int>((D->nblk + S - 1) / S);
+    const unsigned grid = static_cast<unsigned>(units < D->num_sms ? units : D->num_sms);
+    cudaError_t e;
+    if (K == 8) {
+        e = cudaFuncSetAttribute(k_bf16_topk<8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 static_cast<int>(kSmem));
+        if (e == cudaSuccess)
+            k_bf16_topk<8><<<grid, NTHREADS, kSmem, st>>>(ta, tb, n, D->d, D->nblk, D->Kp, cone,
+                                                          S, bps, D->inv_norm2, part_s, part_i,
+                                                          D->err);
+    } else if (K == 16) {
+        e = cudaFuncSetAttribute(k_bf16_topk<16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 static_cast<int>(kSmem));
+        if (e == cudaSuccess)
+            k_bf16_topk<16><<<grid, NTHREADS, kSmem, st>>>(ta, tb, n, D->d, D->nblk, D->Kp,
+                                                           cone, S, bps, D->inv_norm2, part_s,
+                                                           part_i, D->err);
+    } else {
+        mrf_set_error("bf16 kernel: K must be 8 or 16");
+        return MRF_EINVAL;
+    }
+    if (e == cudaSuccess) e = cudaGetLastError();
+    if (e != cudaSuccess) {
+        mrf_set_error(std::string("bf16 kernel launch: ") + cudaGetErrorString(e));
+        return MRF_ECUDA;
+    }
+    return MRF_OK;
+}

@@ -1,0 +1,243 @@
+// Candidate merge, exact rescore and density (§3.2, eqs. exactP / exactPs).
+//
+// One warp per voxel.  The S x K candidates of the exhaustive kernels are reduced to the K best
+// by their kernel score; those K are rescored exactly in FP32 from the complex64 operands; if
+// several lie within `tie_rel` (relative, on the normalised correlation) of the best, they are
+// rescored in FP64 and the largest wins (ties to the smallest index).  The density is
+// rho = D_j^H Z_v / ||D_j||^2 accumulated in FP64 (real cone: gamma = max(Re(.), 0)), and
+// X_v = rho D_j is written when requested.  A zero fingerprint gives j = 0, rho = 0.
+// With `certify`, a voxel whose K-th kernel score is within `cert_margin` of the best exact
+// score is appended to a fallback list (the low-precision ranking could have missed the best).
+#include "mrf_internal.cuh"
+
+namespace {
+
+constexpr int WARPS = 8;
+
+__device__ __forceinline__ float warp_sum(float x) {
+    for (int o = 16; o; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+    return x;
+}
+__device__ __forceinline__ double warp_sumd(double x) {
+    for (int o = 16; o; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+    return x;
+}
+
+// (s, j) ordering: larger score first, then smaller index; j < 0 marks an empty slot.
+__device__ __forceinline__ bool better(float sa, int32_t ja, float sb, int32_t jb) {
+    if (ja < 0) return false;
+    if (jb < 0) return true;
+    if (sa != sb) return sa > sb;
+    return ja < jb;
+}
+
+template <int KT>
+__global__ void __launch_bounds__(WARPS * 32)
+k_merge(const float2* __restrict__ Z, int64_t n_in, const int32_t* __restrict__ vlist,
+        const int32_t* __restrict__ nlist, const float2* __restrict__ atoms,
+        const float* __restrict__ inv_norm2, const double* __restrict__ norm2, int64_t d,
+        int L, int cone, int S, const float* __restrict__ part_s,
+        const int32_t* __restrict__ part_i, float tie_rel, int certify, float cert_margin,
+        int32_t* __restrict__ idx_out, float2* __restrict__ rho_out, float2* __restrict__ X_out,
+        int32_t* __restrict__ fb_list, int32_t* __restrict__ fb_n, uint32_t* err,
+        unsigned long long* cnt) {
+    const int lane = threadIdx.x & 31;
+    const int64_t n = vlist ? static_cast<int64_t>(*nlist) : n_in;
+    const int64_t vl = static_cast<int64_t>(blockIdx.x) * WARPS + (threadIdx.x >> 5);
+    if (vl >= n) return;
+    const int64_t v = vlist ? static_cast<int64_t>(vlist[vl]) : vl;
+    const float2* z = Z + v * L;
+
+    // 1. lane-local top-KT over a strided share of the S*KT candidates, then KT warp rounds
+    float ls[KT];
+    int32_t li[KT];
+#pragma unroll
+    for (int q = 0; q < KT; ++q) { ls[q] = -INFINITY; li[q] = -1; }
+    const int total = S * KT;
+    for (int c = lane; c < total; c += 32) {
+        const int s = c / KT, k = c - s * KT;
+        const int64_t o = (static_cast<int64_t>(s) * n + vl) * KT + k;
+        float sc = part_s[o];
+        int32_t j = part_i[o];
+        if (j < 0 || j >= d) continue;
+        if (better(sc, j, ls[KT - 1], li[KT - 1])) {
+            ls[KT - 1] = sc;
+            li[KT - 1] = j;
+#pragma unroll
+            for (int q = KT - 1; q > 0; --q) {
+                bool up = better(ls[q], li[q], ls[q - 1], li[q - 1]);
+                float a = ls[q], b = ls[q - 1];
+                int32_t ia = li[q], ib = li[q - 1];
+                ls[q - 1] = up ? a : b; ls[q] = up ? b : a;
+                li[q - 1] = up ? ia : ib; li[q] = up ? ib : ia;
+            }
+        }
+    }
+    float cs[KT];       // kernel scores of the warp's top-KT (uniform across lanes)
+    int32_t cj[KT];
+#pragma unroll
+    for (int q = 0; q < KT; ++q) {
+        float bs = ls[0];
+        int32_t bj = li[0];
+        int bl = lane;
+        for (int o = 16; o; o >>= 1) {
+            float os = __shfl_xor_sync(0xffffffffu, bs, o);
+            int32_t oj = __shfl_xor_sync(0xffffffffu, bj, o);
+            int ol = __shfl_xor_sync(0xffffffffu, bl, o);
+            if (better(os, oj, bs, bj) || (os == bs && oj == bj && ol < bl)) {
+                bs = os; bj = oj; bl = ol;
+            }
+        }
+        cs[q] = bs;
+        cj[q] = bj;
+        if (lane == bl) {
+#pragma unroll
+            for (int p = 0; p < KT - 1; ++p) { ls[p] = ls[p + 1]; li[p] = li[p + 1]; }
+            ls[KT - 1] = -INFINITY;
+            li[KT - 1] = -1;
+        }
+    }
+
+    // 2. exact FP32 rescore of the KT candidates and the query's squared norm
+    float zn2 = 0.f;
+    for (int t = lane; t < L; t += 32) { float2 a = z[t]; zn2 += a.x * a.x + a.y * a.y; }
+    zn2 = warp_sum(zn2);
+    float es[KT];
+    int best = -1;
+#pragma unroll
+    for (int q = 0; q < KT; ++q) {
+        es[q] = -INFINITY;
+        if (cj[q] < 0) continue;
+        const float2* a = atoms + static_cast<int64_t>(cj[q]) * L;
+        float re = 0.f, im = 0.f;
+        for (int t = lane; t < L; t += 32) {
+            float2 dv = a[t], zv = z[t];
+            re = fmaf(dv.x, zv.x, fmaf(dv.y, zv.y, re));
+            im = fmaf(dv.x, zv.y, fmaf(-dv.y, zv.x, im));
+        }
+        re = warp_sum(re);
+        im = warp_sum(im);
+        float w = inv_norm2[cj[q]];
+        es[q] = (cone == MRF_CONE_COMPLEX) ? (re * re + im * im) * w : re * sqrtf(w);
+        if (best < 0 || better(es[q], cj[q], es[best], cj[best])) best = q;
+    }
+    if (best < 0) {          // no candidate at all (cannot happen with d >= 1)
+        if (lane == 0) atomicOr(err, MRF_DERR_BOUNDS);
+        return;
+    }
+
+    // 3. FP64 rescore of the near-ties
+    const float eb = es[best];
+    const float thr = (cone == MRF_CONE_COMPLEX) ? eb * (1.f - tie_rel) * (1.f - tie_rel)
+                                                 : eb - tie_rel * fabsf(eb);
+    int ntie = 0;
+#pragma unroll
+    for (int q = 0; q < KT; ++q) ntie += (cj[q] >= 0 && es[q] >= thr) ? 1 : 0;
+    int32_t jstar = cj[best];
+    double cre = 0.0, cim = 0.0;
+    bool have64 = false;
+    if (ntie > 1) {
+        double bs64 = -INFINITY;
+#pragma unroll
+        for (int q = 0; q < KT; ++q) {
+            if (cj[q] < 0 || es[q] < thr) continue;
+            const float2* a = atoms + static_cast<int64_t>(cj[q]) * L;
+            double re = 0.0, im = 0.0;
+            for (int t = lane; t < L; t += 32) {
+                float2 dv = a[t], zv = z[t];
+                re += static_cast<double>(dv.x) * zv.x + static_cast<double>(dv.y) * zv.y;
+                im += static_cast<double>(dv.x) * zv.y - static_cast<double>(dv.y) * zv.x;
+            }
+            re = warp_sumd(re);
+            im = warp_sumd(im);
+            double nn = norm2[cj[q]];
+            double s64 = (cone == MRF_CONE_COMPLEX) ? (re * re + im * im) / nn : re / sqrt(nn);
+            if (s64 > bs64 || (s64 == bs64 && cj[q] < jstar)) {
+                bs64 = s64;
+                jstar = cj[q];
+                cre = re;
+                cim = im;
+            }
+        }
+        have64 = true;
+        if (lane == 0) atomicAdd(cnt + CNT_TIE_RESCORED, 1ULL);
+        if (lane == 0 && cj[KT - 1] >= 0 && es[KT - 1] >= thr)
+            atomicAdd(cnt + CNT_TIE_OVERFLOW, 1ULL);
+    }
+    // 4. certification of the low-precision ranking
+    if (certify && cj[KT - 1] >= 0) {
+        const float cthr = (cone == MRF_CONE_COMPLEX) ? eb * (1.f - cert_margin) * (1.f - cert_margin)
+                                                      : eb - cert_margin * fabsf(eb);
+        if (cs[KT - 1] >= cthr && zn2 > 0.f) {
+            if (lane == 0) {
+                int pos = atomicAdd(fb_n, 1);
+                fb_list[pos] = static_cast<int32_t>(v);
+                atomicAdd(cnt + CNT_UNCERT, 1ULL);
+            }
+        }
+    }
+    // 5. density in FP64
+    if (!have64) {
+        const float2* a = atoms + static_cast<int64_t>(jstar) * L;
+        double re = 0.0, im = 0.0;
+        for (int t = lane; t < L; t += 32) {
+            float2 dv = a[t], zv = z[t];
+            re += static_cast<double>(dv.x) * zv.x + static_cast<double>(dv.y) * zv.y;
+            im += static_cast<double>(dv.x) * zv.y - static_cast<double>(dv.y) * zv.x;
+        }
+        cre = warp_sumd(re);
+        cim = warp_sumd(im);
+    }
+    double nn = norm2[jstar];
+    double rr = cre / nn, ri = cim / nn;
+    if (cone != MRF_CONE_COMPLEX) { rr = rr > 0.0 ? rr : 0.0; ri = 0.0; }
+    if (zn2 == 0.f) {
+        jstar = 0; rr = 0.0; ri = 0.0;
+        if (lane == 0) atomicAdd(cnt + CNT_ZERO, 1ULL);
+    }
+    const float2 rho = make_float2(static_cast<float>(rr), static_cast<float>(ri));
+    if (lane == 0) {
+        idx_out[v] = jstar;
+        if (rho_out) rho_out[v] = rho;
+    }
+    if (X_out) {
+        const float2* a = atoms + static_cast<int64_t>(jstar) * L;
+        float2* x = X_out + v * L;
+        for (int t = lane; t < L; t += 32) {
+            float2 dv = a[t];
+            x[t] = make_float2(rho.x * dv.x - rho.y * dv.y, rho.x * dv.y + rho.y * dv.x);
+        }
+    }
+}
+
+}  // namespace
+
+mrf_status launch_merge(const float2* Z, int64_t n, const mrf_dict* D, int cone, int K, int S,
+                        const float* part_s, const int32_t* part_i, const int32_t* vlist,
+                        const int32_t* nlist, float tie_rel, int certify, float cert_margin,
+                        int32_t* idx_out, float2* rho_out, float2* X_out, int32_t* fb_list,
+                        int32_t* fb_n, uint32_t* err, unsigned long long* counters,
+                        cudaStream_t st) {
+    if (n == 0) return MRF_OK;
+    dim3 grid(static_cast<unsigned>((n + WARPS - 1) / WARPS));
+    if (K == 8) {
+        k_merge<8><<<grid, WARPS * 32, 0, st>>>(Z, n, vlist, nlist, D->atoms, D->inv_norm2,
+                                                D->norm2, D->d, D->L, cone, S, part_s, part_i,
+                                                tie_rel, certify, cert_margin, idx_out, rho_out,
+                                                X_out, fb_list, fb_n, err, counters);
+    } else if (K == 16) {
+        k_merge<16><<<grid, WARPS * 32, 0, st>>>(Z, n, vlist, nlist, D->atoms, D->inv_norm2,
+                                                 D->norm2, D->d, D->L, cone, S, part_s, part_i,
+                                                 tie_rel, certify, cert_margin, idx_out,
+                                                 rho_out, X_out, fb_list, fb_n, err, counters);
+    } else {
+        mrf_set_error("merge: K must be 8 or 16");
+        return MRF_EINVAL;
+    }
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) {
+        mrf_set_error(std::string("merge launch: ") + cudaGetErrorString(e));
+        return MRF_ECUDA;
+    }
+    return MRF_OK;
+}

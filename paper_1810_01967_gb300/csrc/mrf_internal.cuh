@@ -1,0 +1,115 @@
+// Internal declarations shared by the library's translation units.
+#pragma once
+#include <cstdint>
+#include <string>
+#include <vector>
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <cuda_fp8.h>
+
+#include "../../include/mrf.h"
+
+// Device error word bits (OR-ed by kernels, read by mrf_dict_check / stats calls).
+enum : uint32_t {
+    MRF_DERR_NONFINITE = 1u << 0,
+    MRF_DERR_TIMEOUT = 1u << 1,
+    MRF_DERR_BOUNDS = 1u << 2,
+};
+
+// Device counters (indices into mrf_dict::counters).
+enum {
+    CNT_ZERO = 0,
+    CNT_TIE_RESCORED = 1,
+    CNT_TIE_OVERFLOW = 2,
+    CNT_UNCERT = 3,
+    CNT_FALLBACK = 4,
+    CNT_DIST = 5,
+    CNT_N = 8
+};
+
+struct CoverTreeDev;   // flattened cover tree (covertree.cu)
+
+struct mrf_dict {
+    int64_t d = 0;
+    int32_t L = 0, P = 0;
+    int device = 0;
+    std::vector<int32_t> grid_shape;
+    float2* atoms = nullptr;        // [d][L] complex64 as given
+    float* inv_norm2 = nullptr;     // [d] 1 / ||D_j||^2 (from an FP64 sum)
+    double* norm2 = nullptr;        // [d] ||D_j||^2 in FP64
+    float* params = nullptr;        // [d][P]
+    // BF16 tensor-core operand: blocks of 128 atoms, 256 rows each (128 real-part rows, then
+    // 128 imaginary-part rows), row length Kp = 2L rounded up to 16, interleaved (re, im).
+    __nv_bfloat16* bop = nullptr;
+    int64_t nblk = 0;
+    int32_t Kp = 0;
+    // scratch (grown on demand, or reserved up front)
+    int64_t cap_n = 0;
+    __nv_bfloat16* zq = nullptr;    // [cap_n][Kp]
+    float2* zbuf = nullptr;         // [cap_n][L] gradient-step output Z
+    float2* wbuf = nullptr;         // [cap_n][L] FFT workspace
+    float2* xprev = nullptr;        // [cap_n][L] previous iterate (step rule)
+    int32_t* vlist = nullptr;       // [cap_n] compacted voxel list (fallback)
+    int32_t* nlist = nullptr;       // [1] its length
+    size_t part_bytes = 0;
+    void* part = nullptr;           // partial top-k candidates (scores then indices)
+    uint32_t* err = nullptr;        // device error word
+    unsigned long long* counters = nullptr;   // [CNT_N]
+    double* red = nullptr;          // [8] reductions (norms for the step rule / kappa)
+    CoverTreeDev* tree = nullptr;
+    int num_sms = 148;
+};
+
+// thread-local error text
+void mrf_set_error(const std::string& msg);
+
+#define MRF_CUDA_TRY(expr)                                                              \
+    do {                                                                                \
+        cudaError_t e_ = (expr);                                                        \
+        if (e_ != cudaSuccess) {                                                        \
+            mrf_set_error(std::string(#expr) + ": " + cudaGetErrorString(e_));          \
+            return MRF_ECUDA;                                                           \
+        }                                                                               \
+    } while (0)
+
+#define MRF_TRY(expr)                                                                   \
+    do {                                                                                \
+        mrf_status s_ = (expr);                                                         \
+        if (s_ != MRF_OK) return s_;                                                    \
+    } while (0)
+
+// ----- kernels (launch wrappers); all asynchronous on `st`
+// prep.cu
+mrf_status launch_atom_norms(mrf_dict* D, cudaStream_t st);
+mrf_status launch_pack_bop(mrf_dict* D, cudaStream_t st);
+mrf_status launch_pack_queries(const float2* Z, int64_t n, int L, int Kp, __nv_bfloat16* zq,
+                               cudaStream_t st);
+mrf_status launch_mask_ky(float2* W, const uint8_t* mask, int Ny, int Nx, int L,
+                          cudaStream_t st);
+mrf_status launch_grad_combine(const float2* X, const float2* G, const float2* AHY, float2* Z,
+                               int64_t n, int L, float mu, float g_scale, __nv_bfloat16* zq,
+                               int Kp, uint32_t* err, cudaStream_t st);
+mrf_status launch_scale(float2* X, int64_t count, float s, cudaStream_t st);
+mrf_status launch_lut(const int32_t* idx, int64_t n, const float* params, int P, int64_t d,
+                      float* out, uint32_t* err, cudaStream_t st);
+mrf_status launch_sqnorm(const float2* X, int64_t count, double* out, cudaStream_t st);
+mrf_status launch_sqdiff(const float2* A, const float2* B, int64_t count, double* out,
+                         cudaStream_t st);
+mrf_status launch_axpby(float2* Y, const float2* X, int64_t count, float a, float b,
+                        cudaStream_t st);
+// fp32.cu
+mrf_status launch_fp32_topk(const float2* Z, const int32_t* vlist, const int32_t* nlist,
+                            int64_t n, const mrf_dict* D, int cone, int K, int S,
+                            float* part_s, int32_t* part_i, cudaStream_t st);
+int fp32_choose_splits(int64_t n, int64_t d, int num_sms);
+// bf16.cu
+mrf_status launch_bf16_topk(const __nv_bfloat16* zq, int64_t n, const mrf_dict* D, int cone,
+                            int K, int S, float* part_s, int32_t* part_i, cudaStream_t st);
+int bf16_choose_splits(int64_t n, int64_t nblk, int num_sms);
+// merge.cu
+mrf_status launch_merge(const float2* Z, int64_t n, const mrf_dict* D, int cone, int K, int S,
+                        const float* part_s, const int32_t* part_i, const int32_t* vlist,
+                        const int32_t* nlist, float tie_rel, int certify, float cert_margin,
+                        int32_t* idx_out, float2* rho_out, float2* X_out, int32_t* fb_list,
+                        int32_t* fb_n, uint32_t* err, unsigned long long* counters,
+                        cudaStream_t st);

@@ -1,0 +1,55 @@
+"""Shared helpers of the GPU parity tests: device copies and the oracle comparison rules.
+
+Comparison rules (tolerances of the parity bar):
+  * atom index: identical to the oracle's, except where the oracle scores the GPU's atom within
+    TIE_REL = 1e-6 (relative, normalised correlation) of its own best -- a near-tie, where either
+    index is accepted;
+  * density rho and image X: within RHO_REL = 1e-4 relative error of the oracle's values for the
+    accepted atom (float64 evaluation of the same formula).
+"""
+import numpy as np
+
+from oracle import mrf_oracle as mo
+
+TIE_REL = 1e-6
+RHO_REL = 1e-4
+
+
+def to_dev(a, dtype=None):
+    import torch
+    t = torch.from_numpy(np.ascontiguousarray(a))
+    if dtype is not None:
+        t = t.to(dtype)
+    return t.cuda()
+
+
+def check_projection(Z, D, g_idx, g_rho, cone="complex", g_X=None, tie=TIE_REL, rho_rel=RHO_REL,
+                     ref=None):
+    """Assert the parity rules; returns (exact agreement rate, number of near-tie mismatches)."""
+    Z = np.asarray(Z, np.complex128)
+    ref = ref if ref is not None else mo.project(Z, D, cone)
+    g_idx = np.asarray(g_idx, np.int64)
+    assert g_idx.min() >= 0 and g_idx.max() < D.shape[0]
+    s_g = mo.correlation(Z, D, g_idx, cone)
+    s1 = ref["s1"]
+    zero = np.sum(np.abs(Z) ** 2, axis=1) == 0
+    mism = (g_idx != ref["idx"]) & ~zero
+    near = s_g >= s1 - tie * np.abs(s1)
+    bad = np.flatnonzero(mism & ~near)
+    assert bad.size == 0, (f"{bad.size} atom mismatches beyond the near-tie rule, e.g. v={bad[:5]}"
+                           f" gpu={g_idx[bad[:5]]} ref={ref['idx'][bad[:5]]}"
+                           f" s_gpu={s_g[bad[:5]]} s_ref={s1[bad[:5]]}")
+    assert np.all(g_idx[zero] == 0)
+    rho_ref = mo.density(Z, D, g_idx, cone)
+    rho_ref[zero] = 0
+    err = np.abs(np.asarray(g_rho, np.complex128) - rho_ref)
+    scale = np.maximum(np.abs(rho_ref), 1e-30)
+    worst = np.max(np.where(zero, err, err / scale)) if err.size else 0.0
+    assert worst <= rho_rel, f"rho relative error {worst:.3e}"
+    if g_X is not None:
+        Xr = rho_ref[:, None] * np.asarray(D, np.complex128)[g_idx]
+        num = np.linalg.norm(np.asarray(g_X, np.complex128) - Xr, axis=1)
+        den = np.maximum(np.linalg.norm(Xr, axis=1), 1e-30)
+        wx = np.max(np.where(zero, num, num / den))
+        assert wx <= rho_rel, f"X relative error {wx:.3e}"
+    return float(np.mean(~mism)), int(np.sum(mism))

@@ -1,0 +1,135 @@
+"""GPU parity of the matched-filtering projection (mrf_project) against the FP64 oracle, through
+the C ABI, for the FP32 SIMT kernel and the BF16 tcgen05 kernel: realistic aliased fingerprints,
+several tiles plus ragged tails, edge cases (zero rows, single voxel, tiny dictionaries, odd L,
+duplicate atoms) and both cone readings."""
+import numpy as np
+import pytest
+
+import mrfgen
+from oracle import mrf_oracle as mo
+from gpu_util import to_dev, check_projection
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def mrf():
+    import paper_1810_01967_gb300 as m
+    from paper_1810_01967_gb300 import build as b
+    b.build()
+    return m
+
+
+@pytest.fixture(scope="module")
+def cfg1():
+    dic = mrfgen.make_dictionary(1)
+    p = mrfgen.make_problem(1, dic=dic)
+    Z = mo.adjoint(p["Y"], p["masks"], p["Ny"], p["Nx"])
+    return dic, p, Z.astype(np.complex64)
+
+
+def run(mrf, D, Z, mode, cone="complex", X=True, topk=8, certify=True):
+    n = Z.shape[0]
+    Zd = to_dev(Z)
+    idx = torch.full((n,), -7, dtype=torch.int32, device="cuda")
+    rho = torch.empty(n, dtype=torch.complex64, device="cuda")
+    Xo = torch.empty_like(Zd) if X else None
+    st = mrf.project(D, Zd, idx, rho, Xo,
+                     opts=mrf.proj_opts(mode=mode, cone=cone, topk=topk, certify=certify),
+                     stats=True)
+    torch.cuda.synchronize()
+    return (idx.cpu().numpy(), rho.cpu().numpy(), None if Xo is None else Xo.cpu().numpy(), st)
+
+
+@pytest.mark.parametrize("mode", ["fp32", "bf16"])
+@pytest.mark.parametrize("n", [1000, 1024, 1])
+def test_aliased_fingerprints(mrf, cfg1, mode, n):
+    dic, p, Z = cfg1
+    D = mrf.build_dict_index(dic["atoms"], dic["params"])
+    Zs = Z[:n]
+    idx, rho, X, st = run(mrf, D, Zs, mode)
+    agree, ties = check_projection(Zs, dic["atoms"], idx, rho, g_X=X)
+    assert st["device_error"] == 0
+    print(f"{mode} n={n}: agreement {agree:.5f}, near-tie swaps {ties}, stats {st}")
+
+
+@pytest.mark.parametrize("mode", ["fp32", "bf16"])
+@pytest.mark.parametrize("cone", ["complex", "real_pos"])
+def test_atoms_times_scalars_and_zero_rows(mrf, cfg1, mode, cone):
+    dic = cfg1[0]
+    A = dic["atoms"]
+    g = np.random.Generator(np.random.PCG64(101))
+    n = 517
+    js = g.integers(0, A.shape[0], n)
+    rho = g.uniform(0.3, 2.0, n) * (np.exp(1j * g.uniform(0, 2 * np.pi, n))
+                                    if cone == "complex" else 1.0)
+    Z = (rho[:, None] * A[js].astype(np.complex128)).astype(np.complex64)
+    Z[::37] = 0
+    D = mrf.build_dict_index(A, dic["params"])
+    idx, r, X, st = run(mrf, D, Z, mode, cone=cone)
+    check_projection(Z, A, idx, r, cone=cone, g_X=X)
+    zero = np.zeros(n, bool)
+    zero[::37] = True
+    assert np.all(idx[zero] == 0) and np.all(r[zero] == 0)
+    assert st["n_zero"] == zero.sum()
+
+
+@pytest.mark.parametrize("mode", ["fp32", "bf16"])
+@pytest.mark.parametrize("L,d,n", [(37, 5, 70), (100, 1, 3), (8, 300, 129), (1000, 257, 300)])
+def test_odd_shapes(mrf, mode, L, d, n):
+    g = np.random.Generator(np.random.PCG64(L * 1000 + d))
+    A = (g.standard_normal((d, L)) + 1j * g.standard_normal((d, L))).astype(np.complex64)
+    A *= g.uniform(0.5, 2.0, (d, 1)).astype(np.float32)
+    Z = (g.standard_normal((n, L)) + 1j * g.standard_normal((n, L))).astype(np.complex64)
+    D = mrf.build_dict_index(A)
+    idx, r, X, _ = run(mrf, D, Z, mode)
+    check_projection(Z, A, idx, r, g_X=X)
+
+
+@pytest.mark.parametrize("mode", ["fp32", "bf16"])
+def test_duplicate_atoms_tie_to_smallest_index(mrf, mode):
+    g = np.random.Generator(np.random.PCG64(7))
+    B = (g.standard_normal((40, 64)) + 1j * g.standard_normal((40, 64))).astype(np.complex64)
+    A = np.concatenate([B, B, B[:10]])
+    js = g.integers(0, 40, 200)
+    Z = (A[js] * np.complex64(1.5 - 0.5j)).astype(np.complex64)
+    D = mrf.build_dict_index(A)
+    idx, r, X, _ = run(mrf, D, Z, mode)
+    assert np.array_equal(idx, js)
+    np.testing.assert_allclose(r, 1.5 - 0.5j, rtol=1e-5)
+
+
+def test_topk16_and_no_certify(mrf, cfg1):
+    dic, p, Z = cfg1
+    D = mrf.build_dict_index(dic["atoms"])
+    idx, r, X, st = run(mrf, D, Z, "bf16", topk=16, certify=False)
+    ref = mo.project(Z, dic["atoms"])
+    agree = float(np.mean(idx == ref["idx"]))
+    assert agree > 0.99, agree
+    idx, r, X, st = run(mrf, D, Z, "fp32", topk=16)
+    check_projection(Z, dic["atoms"], idx, r, g_X=X)
+
+
+def test_empty_projection_is_a_no_op(mrf, cfg1):
+    dic = cfg1[0]
+    D = mrf.build_dict_index(dic["atoms"])
+    Z = torch.empty((0, dic["atoms"].shape[1]), dtype=torch.complex64, device="cuda")
+    idx = torch.empty(0, dtype=torch.int32, device="cuda")
+    mrf.project(D, Z, idx)
+
+
+def test_bad_arguments_raise(mrf, cfg1):
+    dic = cfg1[0]
+    D = mrf.build_dict_index(dic["atoms"], pack_bf16=False)
+    Z = to_dev(np.zeros((4, dic["atoms"].shape[1]), np.complex64))
+    idx = torch.empty(4, dtype=torch.int32, device="cuda")
+    with pytest.raises(mrf.MRFError):
+        mrf.project(D, Z, idx, opts=mrf.proj_opts(mode="bf16"))
+    with pytest.raises(mrf.MRFError):
+        mrf.project(D, Z, idx, opts=mrf.proj_opts(topk=40))
+    bad = dic["atoms"][:3].copy()
+    bad[1] = 0
+    with pytest.raises(mrf.MRFError):
+        mrf.build_dict_index(bad)
