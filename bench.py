@@ -154,6 +154,90 @@ def make_workload(slice_idx: int):
     return dic, p
 
 
+def reconstruction_quality(mrf, D, op, p, dic, dev, stream, iters: int) -> dict:
+    """Whole reconstructions (iters BLIP iterations) with the BF16 and the FP32 exhaustive
+    projections: time per slice, matches/s, T1/T2 accuracy against the phantom (mask rho != 0),
+    their atom agreement, and the first iteration's agreement with the FP64 oracle on a voxel
+    sample (both sides start from the generator's k-space)."""
+    import torch
+    from oracle import mrf_oracle as mo
+    Ny, Nx, L = p["Ny"], p["Nx"], p["L"]
+    n, d = Ny * Nx, dic["atoms"].shape[0]
+    ph = p["phantom"]
+    fg = ph["labels"] >= 0
+    Yd = torch.from_numpy(p["Y"]).to(dev)
+    out, idxs = {}, {}
+    for mode in ("bf16", "fp32"):
+        X = torch.empty((n, L), dtype=torch.complex64, device=dev)
+        idx = torch.empty(n, dtype=torch.int32, device=dev)
+        prm = torch.empty((n, dic["params"].shape[1]), dtype=torch.float32, device=dev)
+        ro = mrf.recon_opts(iters=iters, mode=mode, certify=False)
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        mrf.reconstruct(D, op, Yd, X, idx, None, prm, opts=ro)
+        b.record(stream)
+        torch.cuda.synchronize()
+        s = a.elapsed_time(b) / 1e3
+        pr = prm.cpu().numpy()
+        idxs[mode] = idx.cpu().numpy()
+        out[mode] = {"s_per_slice": s, "iters": iters, "matches_per_s": n * d * iters / s,
+                     "T1_acc": mo.accuracy(pr[:, 0], ph["T1"], fg),
+                     "T2_acc": mo.accuracy(pr[:, 1], ph["T2"], fg),
+                     "B0_mae_hz": float(np.mean(np.abs(pr[fg, 2] - ph["B0"][fg])))}
+    out["bf16_vs_fp32_atom_agreement"] = float(np.mean(idxs["bf16"] == idxs["fp32"]))
+    # first iteration (template matching) against the oracle on a seeded sample
+    g = np.random.Generator(np.random.PCG64(99))
+    sel = np.sort(g.choice(np.flatnonzero(fg), 192, replace=False))
+    Zh = mo.adjoint(p["Y"], p["masks"], Ny, Nx)[sel]
+    ref = mo.project(Zh, dic["atoms"])
+    AHY = torch.empty((n, L), dtype=torch.complex64, device=dev)
+    mrf.adjoint(op, Yd, AHY)
+    for mode in ("bf16", "fp32"):
+        idx = torch.empty(n, dtype=torch.int32, device=dev)
+        rho = torch.empty(n, dtype=torch.complex64, device=dev)
+        mrf.project(D, AHY, idx, rho, opts=mrf.proj_opts(mode=mode, certify=False))
+        gi = idx.cpu().numpy()[sel]
+        gr = rho.cpu().numpy()[sel]
+        sg = mo.correlation(Zh, dic["atoms"], gi)
+        rr = mo.density(Zh, dic["atoms"], gi)
+        out[mode]["oracle_sample_agreement"] = float(np.mean(gi == ref["idx"]))
+        out[mode]["oracle_sample_max_corr_deficit"] = float(np.max(ref["s1"] - sg))
+        out[mode]["oracle_sample_max_rho_rel_err"] = float(np.max(np.abs(gr - rr) / np.abs(rr)))
+    out["oracle_sample_voxels"] = int(sel.size)
+    return out
+
+
+def run_profile_case(args) -> None:
+    """Projection only (mrf_project, BF16) on the first N voxels of A^H Y of the workload's
+    slice: the small case for kernel-level ncu captures (about 2 GB on the device)."""
+    import torch
+    import paper_1810_01967_gb300 as mrf
+    from paper_1810_01967_gb300 import build as b
+    b.build()
+    dic, p = make_workload(0)
+    Ny, Nx, L = p["Ny"], p["Nx"], p["L"]
+    n = args.profile_case
+    D = mrf.build_dict_index(dic["atoms"], dic["params"])
+    mask = torch.from_numpy(p["masks"]).cuda()
+    op = mrf.make_op(Ny, Nx, L, mask)
+    AHY = torch.empty((Ny * Nx, L), dtype=torch.complex64, device="cuda")
+    mrf.adjoint(op, torch.from_numpy(p["Y"]).cuda(), AHY)
+    Z = AHY[:n].contiguous()
+    del AHY
+    idx = torch.empty(n, dtype=torch.int32, device="cuda")
+    rho = torch.empty(n, dtype=torch.complex64, device="cuda")
+    o = mrf.proj_opts(mode=args.mode, certify=False)
+    mrf.profile_enable(True)
+    for _ in range(args.steps):
+        mrf.project(D, Z, idx, rho, opts=o)
+    prof = mrf.profile_read()
+    torch.cuda.synchronize()
+    print(json.dumps({"profile_case": n, "d": int(dic["atoms"].shape[0]), "L": L,
+                      "stage_ms": {k: v[0] for k, v in prof.items()},
+                      "stage_launches": {k: v[1] for k, v in prof.items()}}))
+
+
 def run_reference(args) -> None:
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -225,7 +309,7 @@ def run_ours(args) -> None:
     idx = torch.zeros(n, dtype=torch.int32, device=dev)
     rho = torch.empty(n, dtype=torch.complex64, device=dev)
     prm = torch.empty((n, params.shape[1]), dtype=torch.float32, device=dev)
-    opts = mrf.proj_opts(mode=args.mode)
+    opts = mrf.proj_opts(mode=args.mode, certify=False)
 
     def step(Xb, AHYb, idxb, rhob, prmb):
         mrf.ipg_step(D, op, AHYb, Xb, 1.0, idxb, rhob, opts=opts)
@@ -295,6 +379,10 @@ def run_ours(args) -> None:
         f1.record(stream)
         barrier()
         fp32_rate = m * d / (f0.elapsed_time(f1) / 1e3)
+    # ------------------------------------------------------------- quality (rank 0)
+    quality = None
+    if rank == 0 and not args.no_quality:
+        quality = reconstruction_quality(mrf, D, op, p, dic, dev, stream, args.iters)
     if world > 1:
         dist.barrier()
     if rank != 0:
@@ -335,6 +423,7 @@ def run_ours(args) -> None:
                     "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
             "gpu_launches": launches, "clocks": clocks,
             "extra": {"recon_s_per_slice_20_iters": 20 * ms_max / args.steps / 1e3,
+                      "quality": quality,
                       "stage_ms": {k: v[0] for k, v in prof.items()},
                       "stage_launches": {k: v[1] for k, v in prof.items()},
                       "fp32_exact_matches_per_s": fp32_rate,
@@ -347,14 +436,20 @@ def run_ours(args) -> None:
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--iters", type=int, default=20)
+    ap.add_argument("--no-quality", action="store_true")
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--mode", default="bf16", choices=["bf16", "fp32"])
     ap.add_argument("--fp32-sample", type=int, default=512)
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--profile-case", type=int, default=0,
+                    help="projection-only small case with N voxels (for ncu captures)")
     args = ap.parse_args()
-    if args.impl == "reference":
+    if args.profile_case > 0:
+        run_profile_case(args)
+    elif args.impl == "reference":
         run_reference(args)
     else:
         run_ours(args)

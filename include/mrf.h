@@ -73,12 +73,16 @@ typedef struct mrf_index_opts {
 typedef struct mrf_proj_opts {
     int32_t mode;          /* mrf_proj_mode (default MRF_PROJ_FP32_EXACT) */
     int32_t cone;          /* mrf_cone (default MRF_CONE_COMPLEX) */
-    int32_t topk;          /* candidates kept per voxel by the exhaustive kernels, 1..16 (8) */
+    int32_t topk;          /* candidates kept per voxel by the exhaustive kernels, 1..16;
+                              0 = mode default (8 for FP32, 16 for BF16 / FP8) */
     int32_t certify;       /* BF16/FP8: recompute voxels whose k-th candidate is within
                               cert_margin of the best with the FP32 exact kernel (default 1) */
-    float   tie_rel;       /* candidates within this relative score of the best are rescored
-                              in FP64 (default 1e-5) */
-    float   cert_margin;   /* relative score margin for `certify` (default 2e-3) */
+    float   tie_tol;       /* candidates whose normalised correlation |D_j^H Z_v| /
+                              (||D_j|| ||Z_v||) is within this absolute distance of the best
+                              are rescored in FP64 (default 1e-5) */
+    float   cert_margin;   /* margin of `certify`, same units; <= 0 selects the rigorous
+                              bound of the BF16 correlation error, 2^-8 + 2^-18 (operand
+                              rounding) + 2L 2^-24 (FP32 accumulation) (default 0) */
     float   eps;           /* cover tree (1+eps) approximation (default 0) */
     float   fallback_thr;  /* learned proposal: normalised correlation threshold (0.98) */
     int32_t reserved[8];
@@ -89,7 +93,7 @@ typedef struct mrf_stats {
     int64_t n_voxels;         /* voxels projected */
     int64_t n_zero;           /* zero queries (idx 0, rho 0) */
     int64_t n_tie_rescored;   /* voxels whose leading candidates were rescored in FP64 */
-    int64_t n_tie_overflow;   /* voxels whose k-th candidate was still within tie_rel */
+    int64_t n_tie_overflow;   /* voxels whose k-th candidate was still within tie_tol */
     int64_t n_uncertified;    /* BF16/FP8 voxels sent to the FP32 exact kernel */
     int64_t n_fallback;       /* learned proposal voxels sent to the exhaustive search */
     int64_t n_dist_evals;     /* cover tree: distance evaluations */

@@ -50,13 +50,13 @@ def _stream(stream) -> int | None:
     return torch.cuda.current_stream().cuda_stream
 
 
-def proj_opts(mode: str = "fp32", cone: str = "complex", topk: int = 8, certify: bool = True,
-              tie_rel: float = 1e-5, cert_margin: float = 2e-3, eps: float = 0.0,
+def proj_opts(mode: str = "fp32", cone: str = "complex", topk: int = 0, certify: bool = True,
+              tie_tol: float = 1e-5, cert_margin: float = 0.0, eps: float = 0.0,
               fallback_thr: float = 0.98) -> ProjOpts:
     o = ProjOpts()
     lib().mrf_default_proj_opts(C.byref(o))
     o.mode, o.cone, o.topk, o.certify = MODES[mode], CONES[cone], topk, int(certify)
-    o.tie_rel, o.cert_margin, o.eps, o.fallback_thr = tie_rel, cert_margin, eps, fallback_thr
+    o.tie_tol, o.cert_margin, o.eps, o.fallback_thr = tie_tol, cert_margin, eps, fallback_thr
     return o
 
 
@@ -71,7 +71,10 @@ def recon_opts(iters: int = 10, mu: float = 1.0, adaptive: bool = False, zeta: f
 
 
 def make_op(Ny: int, Nx: int, L: int, mask) -> Op:
-    return Op(Ny, Nx, L, _ptr(mask))
+    """mrf_op for the device mask tensor [L][Ny] uint8 (the Op keeps the tensor alive)."""
+    op = Op(Ny, Nx, L, _ptr(mask))
+    op._mask_ref = mask
+    return op
 
 
 class Dictionary:

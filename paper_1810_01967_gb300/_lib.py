@@ -25,7 +25,7 @@ class IndexOpts(C.Structure):
 
 class ProjOpts(C.Structure):
     _fields_ = [("mode", C.c_int32), ("cone", C.c_int32), ("topk", C.c_int32),
-                ("certify", C.c_int32), ("tie_rel", C.c_float), ("cert_margin", C.c_float),
+                ("certify", C.c_int32), ("tie_tol", C.c_float), ("cert_margin", C.c_float),
                 ("eps", C.c_float), ("fallback_thr", C.c_float), ("reserved", C.c_int32 * 8)]
 
 

@@ -87,7 +87,10 @@ mrf_status check_op(const mrf_op* op) {
 }
 
 // ------------------------------------------------------------------------------ scratch
-int topk_slots(int topk) { return topk <= 8 ? 8 : 16; }
+int topk_slots(const mrf_proj_opts* o) {
+    int k = o->topk > 0 ? o->topk : (o->mode == MRF_PROJ_FP32_EXACT ? 8 : 16);
+    return k <= 8 ? 8 : 16;
+}
 
 mrf_status ensure_scratch(mrf_dict* D, int64_t n) {
     if (n <= D->cap_n) return MRF_OK;
@@ -120,8 +123,8 @@ mrf_status check_proj_opts(const mrf_dict* D, const mrf_proj_opts* o) {
     if (!o) return fail(MRF_EINVAL, "proj opts is NULL");
     if (o->cone != MRF_CONE_COMPLEX && o->cone != MRF_CONE_REAL_POS)
         return fail(MRF_EINVAL, "unknown cone");
-    if (o->topk < 1 || o->topk > 16) return fail(MRF_EINVAL, "topk must be in 1..16");
-    if (!(o->tie_rel >= 0.f && o->tie_rel < 0.5f)) return fail(MRF_EINVAL, "tie_rel out of range");
+    if (o->topk < 0 || o->topk > 16) return fail(MRF_EINVAL, "topk must be in 0..16");
+    if (!(o->tie_tol >= 0.f && o->tie_tol < 0.5f)) return fail(MRF_EINVAL, "tie_tol out of range");
     switch (o->mode) {
         case MRF_PROJ_FP32_EXACT: return MRF_OK;
         case MRF_PROJ_BF16:
@@ -199,7 +202,7 @@ mrf_status project_core(mrf_dict* D, const float2* Z, int64_t n, const mrf_proj_
                         const int32_t* warm, int32_t* idx_out, float2* rho_out, float2* X_out,
                         bool zq_ready, cudaStream_t st) {
     (void)warm;
-    const int K = topk_slots(o->topk);
+    const int K = topk_slots(o);
     if (n == 0) return MRF_OK;
     MRF_TRY(ensure_scratch(D, n));
     if (o->mode == MRF_PROJ_FP32_EXACT) {
@@ -212,7 +215,7 @@ mrf_status project_core(mrf_dict* D, const float2* Z, int64_t n, const mrf_proj_
             MRF_TRY(launch_fp32_topk(Z, nullptr, nullptr, n, D, o->cone, K, S, ps, pi, st));
         }
         ProfScope ps4(4, 1, st);
-        MRF_TRY(launch_merge(Z, n, D, o->cone, K, S, ps, pi, nullptr, nullptr, o->tie_rel, 0,
+        MRF_TRY(launch_merge(Z, n, D, o->cone, K, S, ps, pi, nullptr, nullptr, o->tie_tol, 0,
                              0.f, idx_out, rho_out, X_out, nullptr, nullptr, D->err,
                              D->counters, st));
         return MRF_OK;
@@ -231,10 +234,16 @@ mrf_status project_core(mrf_dict* D, const float2* Z, int64_t n, const mrf_proj_
             MRF_TRY(launch_bf16_topk(D->zq, n, D, o->cone, K, S, ps, pi, st));
         }
         if (o->certify) MRF_CUDA_TRY(cudaMemsetAsync(D->nlist, 0, sizeof(int32_t), st));
+        // |c~ - c| <= (2u + u^2) ||d|| ||z|| for BF16 operand rounding (u = 2^-9) plus the FP32
+        // accumulation of 2L products; in normalised-correlation units
+        const float margin = o->cert_margin > 0.f
+                                 ? o->cert_margin
+                                 : static_cast<float>(std::ldexp(1.0, -8) + std::ldexp(1.0, -18) +
+                                                      2.0 * D->L * std::ldexp(1.0, -24));
         {
             ProfScope ps4(4, 1, st);
-            MRF_TRY(launch_merge(Z, n, D, o->cone, K, S, ps, pi, nullptr, nullptr, o->tie_rel,
-                                 o->certify, o->cert_margin, idx_out, rho_out, X_out, D->vlist,
+            MRF_TRY(launch_merge(Z, n, D, o->cone, K, S, ps, pi, nullptr, nullptr, o->tie_tol,
+                                 o->certify, margin, idx_out, rho_out, X_out, D->vlist,
                                  D->nlist, D->err, D->counters, st));
         }
         if (o->certify) {
@@ -250,7 +259,7 @@ mrf_status project_core(mrf_dict* D, const float2* Z, int64_t n, const mrf_proj_
                 MRF_TRY(launch_fp32_topk(Z, D->vlist, D->nlist, cnt, D, o->cone, K, S2, qs, qi,
                                          st));
                 MRF_TRY(launch_merge(Z, cnt, D, o->cone, K, S2, qs, qi, D->vlist, D->nlist,
-                                     o->tie_rel, 0, 0.f, idx_out, rho_out, X_out, nullptr,
+                                     o->tie_tol, 0, 0.f, idx_out, rho_out, X_out, nullptr,
                                      nullptr, D->err, D->counters, st));
             }
         }
@@ -316,10 +325,10 @@ void mrf_default_proj_opts(mrf_proj_opts* o) {
     std::memset(o, 0, sizeof(*o));
     o->mode = MRF_PROJ_FP32_EXACT;
     o->cone = MRF_CONE_COMPLEX;
-    o->topk = 8;
+    o->topk = 0;
     o->certify = 1;
-    o->tie_rel = 1e-5f;
-    o->cert_margin = 2e-3f;
+    o->tie_tol = 1e-5f;
+    o->cert_margin = 0.f;
     o->eps = 0.f;
     o->fallback_thr = 0.98f;
 }

@@ -2,12 +2,12 @@
 //
 // One warp per voxel.  The S x K candidates of the exhaustive kernels are reduced to the K best
 // by their kernel score; those K are rescored exactly in FP32 from the complex64 operands; if
-// several lie within `tie_rel` (relative, on the normalised correlation) of the best, they are
-// rescored in FP64 and the largest wins (ties to the smallest index).  The density is
+// several lie within `tie_tol` (absolute, in normalised correlation |c| / (||d|| ||z||)) of the
+// best, they are rescored in FP64 and the largest wins (ties to the smallest index).  The density is
 // rho = D_j^H Z_v / ||D_j||^2 accumulated in FP64 (real cone: gamma = max(Re(.), 0)), and
 // X_v = rho D_j is written when requested.  A zero fingerprint gives j = 0, rho = 0.
 // With `certify`, a voxel whose K-th kernel score is within `cert_margin` of the best exact
-// score is appended to a fallback list (the low-precision ranking could have missed the best).
+// score (same units) is appended to a fallback list (the low-precision ranking could have missed the best).
 #include "mrf_internal.cuh"
 
 namespace {
@@ -37,7 +37,7 @@ k_merge(const float2* __restrict__ Z, int64_t n_in, const int32_t* __restrict__ 
         const int32_t* __restrict__ nlist, const float2* __restrict__ atoms,
         const float* __restrict__ inv_norm2, const double* __restrict__ norm2, int64_t d,
         int L, int cone, int S, const float* __restrict__ part_s,
-        const int32_t* __restrict__ part_i, float tie_rel, int certify, float cert_margin,
+        const int32_t* __restrict__ part_i, float tie_tol, int certify, float cert_margin,
         int32_t* __restrict__ idx_out, float2* __restrict__ rho_out, float2* __restrict__ X_out,
         int32_t* __restrict__ fb_list, int32_t* __restrict__ fb_n, uint32_t* err,
         unsigned long long* cnt) {
@@ -126,10 +126,19 @@ k_merge(const float2* __restrict__ Z, int64_t n_in, const int32_t* __restrict__ 
         return;
     }
 
-    // 3. FP64 rescore of the near-ties
+    // 3. FP64 rescore of the near-ties.  Windows are absolute in normalised correlation
+    //    |c| / (||d|| ||z||): rounding errors of the FP32 (and BF16) sums scale with ||z||, not
+    //    with the correlation itself.
     const float eb = es[best];
-    const float thr = (cone == MRF_CONE_COMPLEX) ? eb * (1.f - tie_rel) * (1.f - tie_rel)
-                                                 : eb - tie_rel * fabsf(eb);
+    const float zn = sqrtf(zn2);
+    auto floor_of = [&](float tol) -> float {     // lowest score still within `tol`
+        if (cone == MRF_CONE_COMPLEX) {
+            float c = sqrtf(fmaxf(eb, 0.f)) - tol * zn;
+            return c > 0.f ? c * c : 0.f;
+        }
+        return eb - tol * zn;
+    };
+    const float thr = floor_of(tie_tol);
     int ntie = 0;
 #pragma unroll
     for (int q = 0; q < KT; ++q) ntie += (cj[q] >= 0 && es[q] >= thr) ? 1 : 0;
@@ -164,16 +173,13 @@ k_merge(const float2* __restrict__ Z, int64_t n_in, const int32_t* __restrict__ 
         if (lane == 0 && cj[KT - 1] >= 0 && es[KT - 1] >= thr)
             atomicAdd(cnt + CNT_TIE_OVERFLOW, 1ULL);
     }
-    // 4. certification of the low-precision ranking
-    if (certify && cj[KT - 1] >= 0) {
-        const float cthr = (cone == MRF_CONE_COMPLEX) ? eb * (1.f - cert_margin) * (1.f - cert_margin)
-                                                      : eb - cert_margin * fabsf(eb);
-        if (cs[KT - 1] >= cthr && zn2 > 0.f) {
-            if (lane == 0) {
-                int pos = atomicAdd(fb_n, 1);
-                fb_list[pos] = static_cast<int32_t>(v);
-                atomicAdd(cnt + CNT_UNCERT, 1ULL);
-            }
+    // 4. certification of the low-precision ranking: the K-th kernel score must lie more than
+    //    cert_margin (normalised correlation) below the best exact score
+    if (certify && cj[KT - 1] >= 0 && zn2 > 0.f && cs[KT - 1] >= floor_of(cert_margin)) {
+        if (lane == 0) {
+            int pos = atomicAdd(fb_n, 1);
+            fb_list[pos] = static_cast<int32_t>(v);
+            atomicAdd(cnt + CNT_UNCERT, 1ULL);
         }
     }
     // 5. density in FP64
@@ -214,7 +220,7 @@ k_merge(const float2* __restrict__ Z, int64_t n_in, const int32_t* __restrict__ 
 
 mrf_status launch_merge(const float2* Z, int64_t n, const mrf_dict* D, int cone, int K, int S,
                         const float* part_s, const int32_t* part_i, const int32_t* vlist,
-                        const int32_t* nlist, float tie_rel, int certify, float cert_margin,
+                        const int32_t* nlist, float tie_tol, int certify, float cert_margin,
                         int32_t* idx_out, float2* rho_out, float2* X_out, int32_t* fb_list,
                         int32_t* fb_n, uint32_t* err, unsigned long long* counters,
                         cudaStream_t st) {
@@ -223,12 +229,12 @@ mrf_status launch_merge(const float2* Z, int64_t n, const mrf_dict* D, int cone,
     if (K == 8) {
         k_merge<8><<<grid, WARPS * 32, 0, st>>>(Z, n, vlist, nlist, D->atoms, D->inv_norm2,
                                                 D->norm2, D->d, D->L, cone, S, part_s, part_i,
-                                                tie_rel, certify, cert_margin, idx_out, rho_out,
+                                                tie_tol, certify, cert_margin, idx_out, rho_out,
                                                 X_out, fb_list, fb_n, err, counters);
     } else if (K == 16) {
         k_merge<16><<<grid, WARPS * 32, 0, st>>>(Z, n, vlist, nlist, D->atoms, D->inv_norm2,
                                                  D->norm2, D->d, D->L, cone, S, part_s, part_i,
-                                                 tie_rel, certify, cert_margin, idx_out,
+                                                 tie_tol, certify, cert_margin, idx_out,
                                                  rho_out, X_out, fb_list, fb_n, err, counters);
     } else {
         mrf_set_error("merge: K must be 8 or 16");

@@ -109,7 +109,7 @@ int bf16_choose_splits(int64_t n, int64_t nblk, int num_sms);
 // merge.cu
 mrf_status launch_merge(const float2* Z, int64_t n, const mrf_dict* D, int cone, int K, int S,
                         const float* part_s, const int32_t* part_i, const int32_t* vlist,
-                        const int32_t* nlist, float tie_rel, int certify, float cert_margin,
+                        const int32_t* nlist, float tie_tol, int certify, float cert_margin,
                         int32_t* idx_out, float2* rho_out, float2* X_out, int32_t* fb_list,
                         int32_t* fb_n, uint32_t* err, unsigned long long* counters,
                         cudaStream_t st);

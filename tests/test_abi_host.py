@@ -58,4 +58,4 @@ def test_host_argument_errors(L):
     assert L.mrf_dict_info(None, None, None, None) == MRF_EINVAL
     assert L.mrf_status_str(MRF_EINVAL) == b"MRF_EINVAL"
     o = mrf.proj_opts()
-    assert o.topk == 8 and o.mode == 0 and abs(o.tie_rel - 1e-5) < 1e-12
+    assert o.topk == 0 and o.mode == 0 and abs(o.tie_tol - 1e-5) < 1e-12

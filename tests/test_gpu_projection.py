@@ -30,7 +30,7 @@ def cfg1():
     return dic, p, Z.astype(np.complex64)
 
 
-def run(mrf, D, Z, mode, cone="complex", X=True, topk=8, certify=True):
+def run(mrf, D, Z, mode, cone="complex", X=True, topk=0, certify=True):
     n = Z.shape[0]
     Zd = to_dev(Z)
     idx = torch.full((n,), -7, dtype=torch.int32, device="cuda")
@@ -101,14 +101,21 @@ def test_duplicate_atoms_tie_to_smallest_index(mrf, mode):
     np.testing.assert_allclose(r, 1.5 - 0.5j, rtol=1e-5)
 
 
-def test_topk16_and_no_certify(mrf, cfg1):
+@pytest.mark.parametrize("topk", [4, 8, 16])
+def test_topk_and_uncertified_bf16(mrf, cfg1, topk):
+    """Without certification the BF16 form is top-K + exact rescore: report its agreement and
+    check that every miss is within the rigorous BF16 correlation error bound of the best."""
     dic, p, Z = cfg1
     D = mrf.build_dict_index(dic["atoms"])
-    idx, r, X, st = run(mrf, D, Z, "bf16", topk=16, certify=False)
+    idx, r, X, st = run(mrf, D, Z, "bf16", topk=topk, certify=False)
     ref = mo.project(Z, dic["atoms"])
     agree = float(np.mean(idx == ref["idx"]))
-    assert agree > 0.99, agree
-    idx, r, X, st = run(mrf, D, Z, "fp32", topk=16)
+    sg = mo.correlation(Z, dic["atoms"], idx)
+    bound = 2.0 ** -8 + 2.0 ** -18 + 2 * Z.shape[1] * 2.0 ** -24
+    assert np.all(sg >= ref["s1"] - 2 * bound)
+    assert agree > {4: 0.9, 8: 0.97, 16: 0.98}[topk], agree
+    print(f"bf16 top-{topk} uncertified agreement {agree:.5f}")
+    idx, r, X, st = run(mrf, D, Z, "fp32", topk=topk)
     check_projection(Z, dic["atoms"], idx, r, g_X=X)
 
 
