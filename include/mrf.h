@@ -206,6 +206,26 @@ mrf_status mrf_lut(const mrf_dict* dict, const int32_t* idx, int64_t n, float* p
                    void* stream);
 
 /*
+ * Launch-geometry tuning of the exhaustive kernels (read by the project's autotuner).  Zero
+ * fields select the library's defaults.  The `last_*` fields report the geometry of the most
+ * recent launch on this dictionary.
+ */
+typedef struct mrf_tune {
+    int32_t bf16_cluster;      /* CTAs per cluster sharing atom blocks by multicast: 1, 2, 4 */
+    int32_t bf16_live_tiles;   /* voxel tiles (128 rows) kept live per super-group, >= 1 */
+    int32_t bf16_splits;       /* atom splits of the BF16 search, >= 1 */
+    int32_t fp32_splits;       /* atom splits of the FP32 search, >= 1 */
+    int32_t last_bf16_ctas;    /* out: CTAs of the last BF16 search launch */
+    int32_t last_bf16_cluster; /* out: its cluster size */
+    int32_t last_bf16_splits;  /* out: its atom splits */
+    int32_t last_fp32_splits;  /* out: atom splits of the last FP32 search launch */
+    int32_t reserved[8];
+} mrf_tune;
+
+mrf_status mrf_get_tune(const mrf_dict* dict, mrf_tune* out);
+mrf_status mrf_set_tune(mrf_dict* dict, const mrf_tune* in);
+
+/*
  * Stage profiler (tracing aid; the paper reports search and total times, Tables 2-3).  While
  * enabled, every call records a CUDA event pair on its own stream around each stage and counts
  * the library's kernel launches.  mrf_profile_read synchronises on the recorded events, adds

@@ -10,7 +10,7 @@ from __future__ import annotations
 import ctypes as C
 
 from . import _lib
-from ._lib import MODES, CONES, MRFError, ProjOpts, ReconOpts, IndexOpts, Stats, Op
+from ._lib import MODES, CONES, MRFError, ProjOpts, ReconOpts, IndexOpts, Stats, Op, Tune
 
 _LIB = None
 
@@ -116,6 +116,18 @@ class Dictionary:
 
     def check(self, stream=None) -> None:
         _check(lib().mrf_dict_check(self.handle, _stream(stream)))
+
+    def get_tune(self) -> dict:
+        t = Tune()
+        _check(lib().mrf_get_tune(self.handle, C.byref(t)))
+        return t.as_dict()
+
+    def set_tune(self, **kw) -> None:
+        t = Tune()
+        _check(lib().mrf_get_tune(self.handle, C.byref(t)))
+        for k, v in kw.items():
+            setattr(t, k, int(v))
+        _check(lib().mrf_set_tune(self.handle, C.byref(t)))
 
 
 def build_dict_index(atoms, params=None, grid_shape=None, pack_bf16=True, stream=None):

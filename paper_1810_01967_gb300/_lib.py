@@ -49,6 +49,17 @@ class ReconOpts(C.Structure):
                 ("max_shrink", C.c_int32), ("reserved", C.c_int32 * 5), ("proj", ProjOpts)]
 
 
+class Tune(C.Structure):
+    _fields_ = [("bf16_cluster", C.c_int32), ("bf16_live_tiles", C.c_int32),
+                ("bf16_splits", C.c_int32), ("fp32_splits", C.c_int32),
+                ("last_bf16_ctas", C.c_int32), ("last_bf16_cluster", C.c_int32),
+                ("last_bf16_splits", C.c_int32), ("last_fp32_splits", C.c_int32),
+                ("reserved", C.c_int32 * 8)]
+
+    def as_dict(self) -> dict:
+        return {f: getattr(self, f) for f, _ in self._fields_ if f != "reserved"}
+
+
 SIGNATURES = {
     "mrf_default_index_opts": (None, [C.POINTER(IndexOpts)]),
     "mrf_default_proj_opts": (None, [C.POINTER(ProjOpts)]),
@@ -73,6 +84,8 @@ SIGNATURES = {
                                   C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
                                   C.POINTER(Stats), C.c_void_p]),
     "mrf_lut": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p]),
+    "mrf_get_tune": (C.c_int, [C.c_void_p, C.POINTER(Tune)]),
+    "mrf_set_tune": (C.c_int, [C.c_void_p, C.POINTER(Tune)]),
     "mrf_profile_enable": (C.c_int, [C.c_int32]),
     "mrf_profile_read": (C.c_int, [C.POINTER(C.c_double), C.POINTER(C.c_int64), C.c_int32]),
     "mrf_status_str": (C.c_char_p, [C.c_int]),

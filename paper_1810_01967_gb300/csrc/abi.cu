@@ -206,7 +206,9 @@ mrf_status project_core(mrf_dict* D, const float2* Z, int64_t n, const mrf_proj_
     if (n == 0) return MRF_OK;
     MRF_TRY(ensure_scratch(D, n));
     if (o->mode == MRF_PROJ_FP32_EXACT) {
-        const int S = fp32_choose_splits(n, D->d, D->num_sms);
+        const int S = D->tune.fp32_splits > 0 ? D->tune.fp32_splits
+                                              : fp32_choose_splits(n, D->d, D->num_sms);
+        D->tune.last_fp32_splits = S;
         MRF_TRY(ensure_part(D, n, S, K));
         float* ps = static_cast<float*>(D->part);
         int32_t* pi = reinterpret_cast<int32_t*>(ps + static_cast<size_t>(S) * n * K);
@@ -225,7 +227,7 @@ mrf_status project_core(mrf_dict* D, const float2* Z, int64_t n, const mrf_proj_
             ProfScope ps1(1, 1, st);
             MRF_TRY(launch_pack_queries(Z, n, D->L, D->Kp, D->zq, st));
         }
-        const int S = bf16_choose_splits(n, D->nblk, D->num_sms);
+        const int S = bf16_choose_splits(D, n);
         MRF_TRY(ensure_part(D, n, S, K));
         float* ps = static_cast<float*>(D->part);
         int32_t* pi = reinterpret_cast<int32_t*>(ps + static_cast<size_t>(S) * n * K);
@@ -520,6 +522,27 @@ mrf_status mrf_lut(const mrf_dict* D, const int32_t* idx, int64_t n, float* para
     if (n > 0 && (!idx || !params_out)) return fail(MRF_EINVAL, "idx and params_out required");
     ProfScope ps6(6, 1, S_(stream));
     return launch_lut(idx, n, D->params, D->P, D->d, params_out, D->err, S_(stream));
+}
+
+mrf_status mrf_get_tune(const mrf_dict* D, mrf_tune* out) {
+    if (!D || !out) return fail(MRF_EINVAL, "dict and out are required");
+    *out = D->tune;
+    return MRF_OK;
+}
+
+mrf_status mrf_set_tune(mrf_dict* D, const mrf_tune* in) {
+    if (!D || !in) return fail(MRF_EINVAL, "dict and in are required");
+    if (in->bf16_cluster != 0 && in->bf16_cluster != 1 && in->bf16_cluster != 2 &&
+        in->bf16_cluster != 4)
+        return fail(MRF_EINVAL, "bf16_cluster must be 0, 1, 2 or 4");
+    if (in->bf16_live_tiles < 0 || in->bf16_splits < 0 || in->fp32_splits < 0 ||
+        in->bf16_splits > 4096 || in->fp32_splits > 4096)
+        return fail(MRF_EINVAL, "tuning values out of range");
+    D->tune.bf16_cluster = in->bf16_cluster;
+    D->tune.bf16_live_tiles = in->bf16_live_tiles;
+    D->tune.bf16_splits = in->bf16_splits;
+    D->tune.fp32_splits = in->fp32_splits;
+    return MRF_OK;
 }
 
 mrf_status mrf_profile_enable(int32_t on) {

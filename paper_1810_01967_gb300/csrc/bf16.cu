@@ -9,8 +9,11 @@
 // same TMEM lane, so the epilogue thread that owns the row forms |c|^2 / ||D_j||^2 without any
 // data exchange and keeps a sorted top-K in registers.  Scores never reach global memory.
 //
-// Persistent CTAs (one per SM) walk work units (atom split s, voxel tile m), consecutive units
-// sharing s so that CTAs running together stream the same atom blocks through L2.
+// Clusters of C CTAs work on C consecutive voxel tiles against the same atom blocks: each CTA
+// loads 1/C of every atom block and multicasts it to the whole cluster, so a block crosses L2
+// once per cluster.  Persistent clusters walk work units (atom split s, voxel-tile group g); the
+// unit order keeps a few dozen voxel tiles live at a time (super-groups of PG groups, all splits)
+// so the query tiles being re-read stay resident in L2 while the atom blocks stream.
 // Warp roles: warp 0 = TMA producer, warp 1 = TMEM owner and MMA issuer, warps 2..5 = epilogue
 // (TMEM lanes 32 (w mod 4) ...).  4-stage shared-memory ring (48 KB per stage: A 128x64,
 // B 256x64 BF16, 128-byte swizzle), double-buffered 2 x 256-column FP32 accumulator.
@@ -42,6 +45,23 @@ struct Shared {
     volatile int abort;
 };
 
+// Work-unit schedule shared by all roles.  Cluster unit uc -> (split s, group g); the voxel
+// tile of CTA `rank` is g * C + rank.
+struct Sched {
+    int64_t NG;      // voxel-tile groups (ceil(Mt / C))
+    int64_t S;       // atom splits
+    int64_t PG;      // groups per super-group
+    __device__ __forceinline__ void map(int64_t uc, int64_t& s, int64_t& g) const {
+        const int64_t per_sg = PG * S;
+        const int64_t sg = uc / per_sg;
+        const int64_t l = uc - sg * per_sg;
+        const int64_t g0 = sg * PG;
+        const int64_t pe = min(PG, NG - g0);
+        s = l / pe;
+        g = g0 + (l - s * pe);
+    }
+};
+
 template <int KT>
 __device__ __forceinline__ void topk_insert(float (&ts)[KT], int32_t (&ti)[KT], float s,
                                             int32_t j) {
@@ -61,10 +81,10 @@ __device__ __forceinline__ void topk_insert(float (&ts)[KT], int32_t (&ti)[KT], 
     }
 }
 
-template <int KT>
+template <int KT, int C>
 __global__ void __launch_bounds__(NTHREADS, 1)
 k_bf16_topk(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
-            int64_t n, int64_t d, int64_t nblk, int Kp, int cone, int S, int blocks_per_split,
+            int64_t n, int64_t d, int64_t nblk, int Kp, int cone, Sched sc, int blocks_per_split,
             const float* __restrict__ inv_norm2, float* __restrict__ part_s,
             int32_t* __restrict__ part_i, uint32_t* err) {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
@@ -74,13 +94,24 @@ k_bf16_topk(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
 
     const int warp = threadIdx.x >> 5;
     const int lane = threadIdx.x & 31;
-    const int64_t Mt = (n + BM - 1) / BM;
-    const int64_t units = Mt * S;
+    const uint32_t rank = (C > 1) ? mrfk::cluster_ctarank() : 0u;
+    const int64_t cluster = blockIdx.x / C;
+    const int64_t nclusters = gridDim.x / C;
+    const int64_t units = sc.NG * sc.S;
     const int nk = (Kp + BK - 1) / BK;
+    constexpr uint16_t kMask = static_cast<uint16_t>((1u << C) - 1u);
+    constexpr int SLICE_ROWS = BN / C;
+    constexpr int SLICE_BYTES = B_BYTES / C;
 
     if (threadIdx.x == 0) {
-        for (int i = 0; i < STAGES; ++i) { mrfk::mbar_init(&sh->full[i], 1); mrfk::mbar_init(&sh->empty[i], 1); }
-        for (int i = 0; i < 2; ++i) { mrfk::mbar_init(&sh->tfull[i], 1); mrfk::mbar_init(&sh->tempty[i], 128); }
+        for (int i = 0; i < STAGES; ++i) {
+            mrfk::mbar_init(&sh->full[i], 1);
+            mrfk::mbar_init(&sh->empty[i], C);
+        }
+        for (int i = 0; i < 2; ++i) {
+            mrfk::mbar_init(&sh->tfull[i], 1);
+            mrfk::mbar_init(&sh->tempty[i], 128);
+        }
         mrfk::mbar_init(&sh->drain, 1);
         sh->abort = 0;
         mrfk::fence_mbar_init();
@@ -94,7 +125,7 @@ k_bf16_topk(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
         mrfk::tma_prefetch_desc(&tmB);
     }
     mrfk::tc_fence_before();
-    __syncthreads();
+    if (C > 1) mrfk::cluster_sync(); else __syncthreads();
     mrfk::tc_fence_after();
     const uint32_t tmem = sh->tmem_base;
 
@@ -111,9 +142,10 @@ k_bf16_topk(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
             uint32_t slot_phase[STAGES];
             bool slot_used[STAGES];
             for (int i = 0; i < STAGES; ++i) { slot_used[i] = false; slot_phase[i] = 0; }
-            for (int64_t u = blockIdx.x; u < units && !sh->abort; u += gridDim.x) {
-                const int64_t m = u % Mt;
-                const int64_t s = u / Mt;
+            for (int64_t uc = cluster; uc < units && !sh->abort; uc += nclusters) {
+                int64_t s, g;
+                sc.map(uc, s, g);
+                const int64_t m = g * C + rank;
                 const int64_t b0 = s * blocks_per_split;
                 const int64_t b1 = min(b0 + blocks_per_split, nblk);
                 for (int64_t b = b0; b < b1 && !sh->abort; ++b) {
@@ -121,19 +153,28 @@ k_bf16_topk(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
                         if (!mrfk::mbar_wait(&sh->empty[stage], phase ^ 1u)) { fail(); break; }
                         unsigned char* sa = base + stage * STAGE_BYTES;
                         mrfk::mbar_arrive_expect_tx(&sh->full[stage], STAGE_BYTES);
-                        mrfk::tma_load_2d(sa, &tmA, &sh->full[stage], kc * BK, static_cast<int32_t>(m * BM));
-                        mrfk::tma_load_2d(sa + A_BYTES, &tmB, &sh->full[stage], kc * BK,
-                                          static_cast<int32_t>(b * BN));
+                        mrfk::tma_load_2d(sa, &tmA, &sh->full[stage], kc * BK,
+                                          static_cast<int32_t>(m * BM));
+                        if (C > 1)
+                            mrfk::tma_load_2d_mc(sa + A_BYTES + rank * SLICE_BYTES, &tmB,
+                                                 &sh->full[stage], kc * BK,
+                                                 static_cast<int32_t>(b * BN + rank * SLICE_ROWS),
+                                                 kMask);
+                        else
+                            mrfk::tma_load_2d(sa + A_BYTES, &tmB, &sh->full[stage], kc * BK,
+                                              static_cast<int32_t>(b * BN));
                         slot_used[stage] = true;
                         slot_phase[stage] = phase;
                         if (++stage == STAGES) { stage = 0; phase ^= 1u; }
                     }
                 }
             }
-            if (sh->abort) {
-                // drain: every slot this thread filled must have landed before the CTA exits
-                for (int i = 0; i < STAGES; ++i)
-                    if (slot_used[i]) mrfk::mbar_wait(&sh->full[i], slot_phase[i]);
+            // Before the CTA may leave: every fill of its slots has landed, and every consumer
+            // of the cluster has released them (their commit arrivals target this CTA).
+            for (int i = 0; i < STAGES; ++i) {
+                if (!slot_used[i]) continue;
+                if (sh->abort) mrfk::mbar_wait(&sh->full[i], slot_phase[i]);
+                if (!mrfk::mbar_wait(&sh->empty[i], slot_phase[i])) atomicOr(err, MRF_DERR_TIMEOUT);
             }
         }
     } else if (warp == 1) {
@@ -144,8 +185,9 @@ k_bf16_topk(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
             int acc = 0;
             uint32_t aphase = 0;
             bool any = false;
-            for (int64_t u = blockIdx.x; u < units && !sh->abort; u += gridDim.x) {
-                const int64_t s = u / Mt;
+            for (int64_t uc = cluster; uc < units && !sh->abort; uc += nclusters) {
+                int64_t s, g;
+                sc.map(uc, s, g);
                 const int64_t b0 = s * blocks_per_split;
                 const int64_t b1 = min(b0 + blocks_per_split, nblk);
                 for (int64_t b = b0; b < b1 && !sh->abort; ++b) {
@@ -165,7 +207,8 @@ k_bf16_topk(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
                             const uint64_t db = mrfk::sdesc_k_sw128(sb + k * 32);
                             mrfk::mma_bf16(dt, da, db, IDESC, (kc > 0 || k > 0) ? 1u : 0u);
                         }
-                        mrfk::mma_commit(&sh->empty[stage]);
+                        if (C > 1) mrfk::mma_commit_mc(&sh->empty[stage], kMask);
+                        else mrfk::mma_commit(&sh->empty[stage]);
                         any = true;
                         if (++stage == STAGES) { stage = 0; phase ^= 1u; }
                     }
@@ -187,9 +230,10 @@ k_bf16_topk(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
         const uint32_t lane_base = static_cast<uint32_t>(quarter * 32) << 16;
         int acc = 0;
         uint32_t aphase = 0;
-        for (int64_t u = blockIdx.x; u < units && !sh->abort; u += gridDim.x) {
-            const int64_t m = u % Mt;
-            const int64_t s = u / Mt;
+        for (int64_t uc = cluster; uc < units && !sh->abort; uc += nclusters) {
+            int64_t s, g;
+            sc.map(uc, s, g);
+            const int64_t m = g * C + rank;
             const int64_t b0 = s * blocks_per_split;
             const int64_t b1 = min(b0 + blocks_per_split, nblk);
             float ts[KT];
@@ -216,9 +260,9 @@ k_bf16_topk(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
                         const int64_t j = b * 128 + c * 32 + i;
                         const float x = __uint_as_float(re[i]);
                         const float y = __uint_as_float(im[i]);
-                        const float sc = (cone == MRF_CONE_COMPLEX) ? (x * x + y * y) * w
-                                                                    : x * sqrtf(w);
-                        if (j < d) topk_insert<KT>(ts, ti, sc, static_cast<int32_t>(j));
+                        const float scv = (cone == MRF_CONE_COMPLEX) ? (x * x + y * y) * w
+                                                                     : x * sqrtf(w);
+                        if (j < d) topk_insert<KT>(ts, ti, scv, static_cast<int32_t>(j));
                     }
                 }
                 mrfk::tc_fence_before();
@@ -236,6 +280,7 @@ k_bf16_topk(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
     }
     mrfk::tc_fence_before();
     __syncthreads();
+    if (C > 1) mrfk::cluster_sync();
     mrfk::tc_fence_after();
     if (warp == 1) mrfk::tmem_dealloc(tmem, 512);
 }
@@ -281,62 +326,152 @@ mrf_status make_map(CUtensorMap* m, const void* ptr, int64_t rows, int Kp, int b
     return MRF_OK;
 }
 
-}  // namespace
-
-int bf16_choose_splits(int64_t n, int64_t nblk, int num_sms) {
-    // Pick the atom split S that minimises the makespan ceil(units / G) * ceil(nblk / S)
-    // of the static round-robin schedule, units = Mt * S, G = min(units, num_sms).
-    const int64_t Mt = (n + BM - 1) / BM;
-    int best = 1;
-    double best_t = 1e300;
-    for (int64_t S = 1; S <= nblk && S <= 1024; ++S) {
-        int64_t units = Mt * S;
-        int64_t G = units < num_sms ? units : num_sms;
-        int64_t waves = (units + G - 1) / G;
-        int64_t per = (nblk + S - 1) / S;
-        double t = static_cast<double>(waves * per) + 1e-3 * S;   // prefer fewer splits
-        if (t < best_t) { best_t = t; best = static_cast<int>(S); }
+template <int KT, int C>
+mrf_status launch_t(const CUtensorMap& ta, const CUtensorMap& tb, int64_t n, const mrf_dict* D,
+                    int cone, Sched sc, int bps, int nclusters, float* part_s, int32_t* part_i,
+                    cudaStream_t st) {
+    auto kern = k_bf16_topk<KT, C>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         static_cast<int>(kSmem));
+    if (e == cudaSuccess) {
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3(static_cast<unsigned>(nclusters * C));
+        cfg.blockDim = dim3(NTHREADS);
+        cfg.dynamicSmemBytes = kSmem;
+        cfg.stream = st;
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeClusterDimension;
+        attr[0].val.clusterDim.x = C;
+        attr[0].val.clusterDim.y = 1;
+        attr[0].val.clusterDim.z = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        e = cudaLaunchKernelEx(&cfg, kern, ta, tb, n, D->d, D->nblk, D->Kp, cone, sc, bps,
+                               static_cast<const float*>(D->inv_norm2), part_s, part_i, D->err);
     }
-    return best;
-}
-
-mrf_status launch_bf16_topk(const __nv_bfloat16* zq, int64_t n, const mrf_dict* D, int cone,
-                            int K, int S, float* part_s, int32_t* part_i, cudaStream_t st) {
-    if (n == 0) return MRF_OK;
-    if (!D->bop) {
-        mrf_set_error("BF16 operand was not packed (mrf_index_opts.pack_bf16 = 0)");
-        return MRF_EUNSUPPORTED;
-    }
-    CUtensorMap ta, tb;
-    MRF_TRY(make_map(&ta, zq, n, D->Kp, BM));
-    MRF_TRY(make_map(&tb, D->bop, D->nblk * 256, D->Kp, BN));
-    const int64_t Mt = (n + BM - 1) / BM;
-    const int64_t units = Mt * S;
-    const int bps = static_cast<int>((D->nblk + S - 1) / S);
-    const unsigned grid = static_cast<unsigned>(units < D->num_sms ? units : D->num_sms);
-    cudaError_t e;
-    if (K == 8) {
-        e = cudaFuncSetAttribute(k_bf16_topk<8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 static_cast<int>(kSmem));
-        if (e == cudaSuccess)
-            k_bf16_topk<8><<<grid, NTHREADS, kSmem, st>>>(ta, tb, n, D->d, D->nblk, D->Kp, cone,
-                                                          S, bps, D->inv_norm2, part_s, part_i,
-                                                          D->err);
-    } else if (K == 16) {
-        e = cudaFuncSetAttribute(k_bf16_topk<16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 static_cast<int>(kSmem));
-        if (e == cudaSuccess)
-            k_bf16_topk<16><<<grid, NTHREADS, kSmem, st>>>(ta, tb, n, D->d, D->nblk, D->Kp,
-                                                           cone, S, bps, D->inv_norm2, part_s,
-                                                           part_i, D->err);
-    } else {
-        mrf_set_error("bf16 kernel: K must be 8 or 16");
-        return MRF_EINVAL;
-    }
-    if (e == cudaSuccess) e = cudaGetLastError();
     if (e != cudaSuccess) {
         mrf_set_error(std::string("bf16 kernel launch: ") + cudaGetErrorString(e));
         return MRF_ECUDA;
     }
     return MRF_OK;
+}
+
+// Co-resident clusters of size C (persistent grid), from the occupancy calculator.
+template <int KT, int C>
+int max_clusters(cudaStream_t st) {
+    auto kern = k_bf16_topk<KT, C>;
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             static_cast<int>(kSmem)) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(C);
+    cfg.blockDim = dim3(NTHREADS);
+    cfg.dynamicSmemBytes = kSmem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = C;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    int nc = 0;
+    if (cudaOccupancyMaxActiveClusters(&nc, kern, &cfg) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    return nc;
+}
+
+// Pick the atom split S minimising the makespan ceil(units / G) * (ceil(nblk / S) + h) of the
+// static schedule (units = NG * S, G co-resident clusters), where h = 2 blocks models the cost of
+// starting a unit (pipeline refill on a new query tile, the candidates written per unit and
+// read again by the merge).  S * 16 candidates per voxel are kept below 1024.
+int choose_splits(int64_t NG, int64_t nblk, int64_t G) {
+    int best = 1;
+    double best_t = 1e300;
+    for (int64_t S = 1; S <= nblk && S <= 64; ++S) {
+        int64_t units = NG * S;
+        int64_t g = units < G ? units : G;
+        int64_t waves = (units + g - 1) / g;
+        int64_t per = (nblk + S - 1) / S;
+        double t = static_cast<double>(waves) * (per + 2) + 1e-3 * S;
+        if (t < best_t) { best_t = t; best = static_cast<int>(S); }
+    }
+    return best;
+}
+
+constexpr int kDefaultCluster = 2;     // CTAs sharing each atom block by multicast
+constexpr int64_t kDefaultLive = 32;   // voxel tiles kept live per super-group (~16 MB, L=1000)
+
+int cluster_of(const mrf_dict* D) {
+    int c = D->tune.bf16_cluster;
+    return (c == 1 || c == 2 || c == 4) ? c : kDefaultCluster;
+}
+
+template <int KT>
+int max_clusters_any(int C, cudaStream_t st) {
+    switch (C) {
+        case 1: return max_clusters<KT, 1>(st);
+        case 2: return max_clusters<KT, 2>(st);
+        default: return max_clusters<KT, 4>(st);
+    }
+}
+
+}  // namespace
+
+int bf16_choose_splits(const mrf_dict* D, int64_t n) {
+    if (D->tune.bf16_splits > 0) return static_cast<int>(D->tune.bf16_splits);
+    const int C = cluster_of(D);
+    const int64_t Mt = (n + BM - 1) / BM;
+    const int64_t NG = (Mt + C - 1) / C;
+    return choose_splits(NG, D->nblk, D->num_sms / C);
+}
+
+mrf_status launch_bf16_topk(const __nv_bfloat16* zq, int64_t n, mrf_dict* D, int cone, int K,
+                            int S, float* part_s, int32_t* part_i, cudaStream_t st) {
+    if (n == 0) return MRF_OK;
+    if (!D->bop) {
+        mrf_set_error("BF16 operand was not packed (mrf_index_opts.pack_bf16 = 0)");
+        return MRF_EUNSUPPORTED;
+    }
+    if (K != 8 && K != 16) {
+        mrf_set_error("bf16 kernel: K must be 8 or 16");
+        return MRF_EINVAL;
+    }
+    const int C = cluster_of(D);
+    CUtensorMap ta, tb;
+    MRF_TRY(make_map(&ta, zq, n, D->Kp, BM));
+    MRF_TRY(make_map(&tb, D->bop, D->nblk * 256, D->Kp, BN / C));
+    const int64_t Mt = (n + BM - 1) / BM;
+    const int64_t live = D->tune.bf16_live_tiles > 0 ? D->tune.bf16_live_tiles : kDefaultLive;
+    Sched sc;
+    sc.NG = (Mt + C - 1) / C;
+    sc.S = S;
+    sc.PG = (live + C - 1) / C;
+    const int bps = static_cast<int>((D->nblk + S - 1) / S);
+    const int64_t units = sc.NG * sc.S;
+    int nc = (K == 8) ? max_clusters_any<8>(C, st) : max_clusters_any<16>(C, st);
+    if (nc <= 0) {
+        mrf_set_error("bf16 kernel: no cluster of the requested size fits on this device");
+        return MRF_EUNSUPPORTED;
+    }
+    if (nc > units) nc = static_cast<int>(units);
+    D->tune.last_bf16_ctas = nc * C;
+    D->tune.last_bf16_cluster = C;
+    D->tune.last_bf16_splits = S;
+    if (K == 8) {
+        switch (C) {
+            case 1: return launch_t<8, 1>(ta, tb, n, D, cone, sc, bps, nc, part_s, part_i, st);
+            case 2: return launch_t<8, 2>(ta, tb, n, D, cone, sc, bps, nc, part_s, part_i, st);
+            default: return launch_t<8, 4>(ta, tb, n, D, cone, sc, bps, nc, part_s, part_i, st);
+        }
+    }
+    switch (C) {
+        case 1: return launch_t<16, 1>(ta, tb, n, D, cone, sc, bps, nc, part_s, part_i, st);
+        case 2: return launch_t<16, 2>(ta, tb, n, D, cone, sc, bps, nc, part_s, part_i, st);
+        default: return launch_t<16, 4>(ta, tb, n, D, cone, sc, bps, nc, part_s, part_i, st);
+    }
 }

@@ -195,6 +195,7 @@ constexpr size_t smem_bytes() {
 }  // namespace
 
 int fp32_choose_splits(int64_t n, int64_t d, int num_sms) {
+    // (callers apply mrf_tune.fp32_splits before falling back to this default)
     int64_t Mt = (n + TM - 1) / TM;
     int64_t tiles = (d + TN - 1) / TN;
     int64_t target = 4LL * num_sms;

@@ -58,6 +58,7 @@ struct mrf_dict {
     double* red = nullptr;          // [8] reductions (norms for the step rule / kappa)
     CoverTreeDev* tree = nullptr;
     int num_sms = 148;
+    mrf_tune tune = {};              // requested geometry (0 = default) and last launches
 };
 
 // thread-local error text
@@ -103,9 +104,9 @@ mrf_status launch_fp32_topk(const float2* Z, const int32_t* vlist, const int32_t
                             float* part_s, int32_t* part_i, cudaStream_t st);
 int fp32_choose_splits(int64_t n, int64_t d, int num_sms);
 // bf16.cu
-mrf_status launch_bf16_topk(const __nv_bfloat16* zq, int64_t n, const mrf_dict* D, int cone,
-                            int K, int S, float* part_s, int32_t* part_i, cudaStream_t st);
-int bf16_choose_splits(int64_t n, int64_t nblk, int num_sms);
+mrf_status launch_bf16_topk(const __nv_bfloat16* zq, int64_t n, mrf_dict* D, int cone, int K,
+                            int S, float* part_s, int32_t* part_i, cudaStream_t st);
+int bf16_choose_splits(const mrf_dict* D, int64_t n);
 // merge.cu
 mrf_status launch_merge(const float2* Z, int64_t n, const mrf_dict* D, int cone, int K, int S,
                         const float* part_s, const int32_t* part_i, const int32_t* vlist,
