@@ -200,6 +200,28 @@ mrf_status mrf_reconstruct(mrf_dict* dict, const mrf_op* op, const void* Y,
                            const mrf_recon_opts* opts, void* X_out, int32_t* idx_out,
                            void* rho_out, float* params_out, mrf_stats* stats, void* stream);
 
+/*
+ * Exhaustive FP32 projection that allocates no device memory (the paper has no counterpart:
+ * this is a deployment variant of mrf_project's FP32 mode).  For callers that must not
+ * allocate once running -- applications whose device memory belongs to their own pool or
+ * allocator, or real-time pipelines that forbid cudaMalloc/cudaFree after start-up.  The caller
+ * passes the dictionary and every input and output; the working memory is one file-scope device
+ * array of about 20 MB that every GPU loading the library holds until the process exits.
+ *   atoms    device complex64 [d][L], 1 <= d <= 1,048,576, 1 <= L <= 4096 (zero atoms rejected)
+ *   Z        device complex64 [n][L], 0 <= n <= 4096 voxels per call
+ *   cone     mrf_cone
+ *   idx_out  device int32 [n]; rho_out device complex64 [n] or NULL; X_out device [n][L] or NULL
+ * Results equal mrf_project's FP32 mode (top-8 candidates, FP64 near-tie rescore, FP64
+ * density).  Larger sizes return MRF_EINVAL with a message, before any launch.  The first call
+ * on a device looks up the array's device address (cudaGetSymbolAddress) with that device
+ * current; make that first call before any stream capture.  All calls share the one array, so
+ * calls that overlap on the GPU (other streams, other threads) race; serialise them.  The call
+ * synchronises `stream` before returning.
+ */
+mrf_status mrf_project_fp32_static(const void* atoms, int64_t d, int32_t L, const void* Z,
+                                   int64_t n, int32_t cone, int32_t* idx_out, void* rho_out,
+                                   void* X_out, void* stream);
+
 /* Look-up table Theta_v = params[idx_v] (Algorithm 2, last step): device int32 [n] ->
  * device float32 [n][P]. */
 mrf_status mrf_lut(const mrf_dict* dict, const int32_t* idx, int64_t n, float* params_out,

@@ -84,6 +84,9 @@ SIGNATURES = {
                                   C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
                                   C.POINTER(Stats), C.c_void_p]),
     "mrf_lut": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p]),
+    "mrf_project_fp32_static": (C.c_int, [C.c_void_p, C.c_int64, C.c_int32, C.c_void_p,
+                                          C.c_int64, C.c_int32, C.c_void_p, C.c_void_p,
+                                          C.c_void_p, C.c_void_p]),
     "mrf_get_tune": (C.c_int, [C.c_void_p, C.POINTER(Tune)]),
     "mrf_set_tune": (C.c_int, [C.c_void_p, C.POINTER(Tune)]),
     "mrf_profile_enable": (C.c_int, [C.c_int32]),
