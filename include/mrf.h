@@ -66,8 +66,13 @@ typedef struct mrf_dict mrf_dict;   /* opaque; owned by the library */
 typedef struct mrf_index_opts {
     int32_t pack_bf16;     /* build the BF16 tensor-core operand (default 1) */
     int32_t pack_fp8;      /* build the FP8 e4m3 operand (default 0) */
-    int32_t build_tree;    /* build the cover tree on the host (default 0) */
-    int32_t reserved[5];
+    int32_t build_tree;    /* build the cover tree on the host (default 0), §4.1 */
+    int32_t tree_cone;     /* metric of the tree: MRF_CONE_COMPLEX = phase-quotient distance
+                              min_phi ||x - e^{i phi} y|| (default), MRF_CONE_REAL_POS =
+                              Euclidean distance of the unit atoms */
+    float   tree_dup_tol;  /* atoms within this distance of an earlier node are represented by
+                              it (default 1e-5) */
+    int32_t reserved[3];
 } mrf_index_opts;
 
 typedef struct mrf_proj_opts {
@@ -85,7 +90,11 @@ typedef struct mrf_proj_opts {
                               rounding) + 2L 2^-24 (FP32 accumulation) (default 0) */
     float   eps;           /* cover tree (1+eps) approximation (default 0) */
     float   fallback_thr;  /* learned proposal: normalised correlation threshold (0.98) */
-    int32_t reserved[8];
+    float   tree_route;    /* cover tree: a voxel whose candidate list exceeds 64 entries while
+                              its best distance to z/||z|| is above this goes to the exhaustive
+                              search, where Algorithm 1 cannot prune (default 0.9; >= 2
+                              disables routing) */
+    int32_t reserved[7];
 } mrf_proj_opts;
 
 /* Filled by calls given a non-NULL pointer; such calls synchronise `stream` before return. */
@@ -147,6 +156,37 @@ void mrf_dict_free(mrf_dict* dict);
 /* d, L, P of a dict (any pointer may be NULL). */
 mrf_status mrf_dict_info(const mrf_dict* dict, int64_t* d, int32_t* L, int32_t* P);
 
+/* Cover tree built by mrf_build_dict_index (levels r_i = sigma 2^-i, §4.1). */
+typedef struct mrf_tree_info {
+    int64_t nodes;            /* distinct atoms in the tree */
+    int64_t explicit_nodes;   /* (node, level) pairs with children other than the node itself */
+    int32_t levels;           /* i_max */
+    int32_t metric;           /* mrf_cone the tree was built for */
+    double  sigma;            /* maximal distance from the root, the level-0 radius */
+    double  build_ms;         /* host construction + upload time */
+    int64_t device_bytes;     /* device memory of the flattened tree */
+} mrf_tree_info;
+
+mrf_status mrf_tree_get_info(const mrf_dict* dict, mrf_tree_info* info);
+
+/* Copy the tree structure to host arrays (any may be NULL): per atom [d] the level at which it
+ * first appears (-1 for a duplicate), its parent atom at the level above (-1 for the root and
+ * duplicates) and its representative node; per explicit node [explicit_nodes] its atom, its level
+ * i (its new children first appear at i + 1) and its maxdist, the largest distance from the node
+ * to its subtree (§4.1, eq. maxdistbound). */
+mrf_status mrf_tree_export(const mrf_dict* dict, int32_t* first_level, int32_t* parent,
+                           int32_t* rep, int32_t* en_atom, int32_t* en_level, float* en_maxdist);
+
+/* Build the cover tree of host atoms on the host alone (no GPU; offline use and tests), with
+ * the construction mrf_build_dict_index uses.  atoms: host complex64 [d][L]; cone: the metric.
+ * Outputs as mrf_tree_export, with the explicit-node arrays sized d (there are at most d - 1
+ * explicit nodes); *n_explicit, *sigma and *levels receive the counts and the root radius. */
+mrf_status mrf_tree_build_host(const void* atoms, int64_t d, int32_t L, int32_t cone,
+                               float dup_tol, int32_t* first_level, int32_t* parent,
+                               int32_t* rep, int32_t* en_atom, int32_t* en_level,
+                               float* en_maxdist, int64_t* n_explicit, double* sigma,
+                               int32_t* levels);
+
 /* Pre-allocate scratch for up to n_max voxels (so later calls allocate nothing). */
 mrf_status mrf_dict_reserve(mrf_dict* dict, int64_t n_max);
 
@@ -155,7 +195,11 @@ mrf_status mrf_dict_check(mrf_dict* dict, void* stream);
 
 /*
  * Matched-filtering projection of n fingerprints (§3.2, eqs. exactP / exactPs; with
- * MRF_PROJ_COVERTREE, Algorithm 2 lines "ANNS" and "rescaling" on Z_v / ||Z_v||).
+ * MRF_PROJ_COVERTREE, the (1+eps)-ANNS of Algorithm 1 on Z_v / ||Z_v|| warm-started at
+ * warm_idx (§4.3, eq. ANN1), then the exact rescore of the 8 best atoms it visited; voxels
+ * routed away by `tree_route` or whose candidate list would exceed 512 entries are projected by
+ * the exhaustive search instead: BF16 tensor cores (certified as `certify` says) when the
+ * dictionary has the BF16 operand, else FP32).
  *   Z         device complex64 [n][L]
  *   warm_idx  device int32 [n] or NULL: previous atoms, the warm start of the tree search
  *   idx_out   device int32 [n]: j*_v
@@ -254,8 +298,8 @@ mrf_status mrf_set_tune(mrf_dict* dict, const mrf_tune* in);
  * their elapsed times into ms[stage] and launches[stage] for stage < n_stages, and clears
  * them.  Stages: 0 gradient step (cuFFT + mask + combine; cuFFT's kernels are timed here but
  * not counted as launches), 1 BF16 query packing, 2 BF16 tensor-core search, 3 FP32 search,
- * 4 merge / rescore / density, 5 certification fallback (FP32 search + merge), 6 look-up
- * table, 7 other.  Enabling or disabling clears the tables.  Not thread-safe.
+ * 4 merge / rescore / density, 5 fallback to the exhaustive FP32 search (certification or
+ * cover-tree overflow: search + merge), 6 look-up table, 7 cover-tree search.  Enabling or disabling clears the tables.  Not thread-safe.
  */
 #define MRF_PROFILE_STAGES 8
 mrf_status mrf_profile_enable(int32_t on);

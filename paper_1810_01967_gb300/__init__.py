@@ -10,7 +10,8 @@ from __future__ import annotations
 import ctypes as C
 
 from . import _lib
-from ._lib import MODES, CONES, MRFError, ProjOpts, ReconOpts, IndexOpts, Stats, Op, Tune
+from ._lib import (MODES, CONES, MRFError, ProjOpts, ReconOpts, IndexOpts, Stats, Op, Tune,
+                   TreeInfo)
 
 _LIB = None
 
@@ -52,11 +53,12 @@ def _stream(stream) -> int | None:
 
 def proj_opts(mode: str = "fp32", cone: str = "complex", topk: int = 0, certify: bool = True,
               tie_tol: float = 1e-5, cert_margin: float = 0.0, eps: float = 0.0,
-              fallback_thr: float = 0.98) -> ProjOpts:
+              fallback_thr: float = 0.98, tree_route: float = 0.9) -> ProjOpts:
     o = ProjOpts()
     lib().mrf_default_proj_opts(C.byref(o))
     o.mode, o.cone, o.topk, o.certify = MODES[mode], CONES[cone], topk, int(certify)
     o.tie_tol, o.cert_margin, o.eps, o.fallback_thr = tie_tol, cert_margin, eps, fallback_thr
+    o.tree_route = tree_route
     return o
 
 
@@ -81,12 +83,16 @@ class Dictionary:
     """An mrf_dict: the dictionary copied to the GPU plus its packed operands."""
 
     def __init__(self, atoms, params=None, grid_shape=None, pack_bf16: bool = True,
-                 stream=None):
+                 build_tree: bool = False, tree_cone: str = "complex",
+                 tree_dup_tol: float = 1e-5, stream=None):
         import numpy as np
         d, L = atoms.shape
         o = IndexOpts()
         lib().mrf_default_index_opts(C.byref(o))
         o.pack_bf16 = int(pack_bf16)
+        o.build_tree = int(build_tree)
+        o.tree_cone = CONES[tree_cone]
+        o.tree_dup_tol = tree_dup_tol
         P = 0 if params is None else int(params.shape[1])
         gs = None
         if grid_shape is not None:
@@ -117,6 +123,25 @@ class Dictionary:
     def check(self, stream=None) -> None:
         _check(lib().mrf_dict_check(self.handle, _stream(stream)))
 
+    def tree_info(self) -> dict:
+        t = TreeInfo()
+        _check(lib().mrf_tree_get_info(self.handle, C.byref(t)))
+        return t.as_dict()
+
+    def tree_export(self) -> dict:
+        """Host copy of the cover tree (see mrf_tree_export)."""
+        import numpy as np
+        info = self.tree_info()
+        d, ne = self.d, info["explicit_nodes"]
+        out = {"first_level": np.empty(d, np.int32), "parent": np.empty(d, np.int32),
+               "rep": np.empty(d, np.int32), "en_atom": np.empty(ne, np.int32),
+               "en_level": np.empty(ne, np.int32), "en_maxdist": np.empty(ne, np.float32)}
+        _check(lib().mrf_tree_export(self.handle, *[_ptr(out[k]) for k in
+                                                    ("first_level", "parent", "rep", "en_atom",
+                                                     "en_level", "en_maxdist")]))
+        out.update(info)
+        return out
+
     def get_tune(self) -> dict:
         t = Tune()
         _check(lib().mrf_get_tune(self.handle, C.byref(t)))
@@ -130,8 +155,30 @@ class Dictionary:
         _check(lib().mrf_set_tune(self.handle, C.byref(t)))
 
 
-def build_dict_index(atoms, params=None, grid_shape=None, pack_bf16=True, stream=None):
-    return Dictionary(atoms, params, grid_shape, pack_bf16, stream)
+def build_dict_index(atoms, params=None, grid_shape=None, pack_bf16=True, build_tree=False,
+                     tree_cone="complex", tree_dup_tol=1e-5, stream=None):
+    return Dictionary(atoms, params, grid_shape, pack_bf16, build_tree, tree_cone, tree_dup_tol,
+                      stream)
+
+
+def tree_build_host(atoms, cone: str = "complex", dup_tol: float = 1e-5) -> dict:
+    """Cover tree of host atoms built on the host alone (mrf_tree_build_host)."""
+    import numpy as np
+    atoms = np.ascontiguousarray(atoms, dtype=np.complex64)
+    d, L = atoms.shape
+    out = {k: np.empty(d, np.int32) for k in ("first_level", "parent", "rep", "en_atom",
+                                              "en_level")}
+    out["en_maxdist"] = np.empty(d, np.float32)
+    ne, sig, lev = C.c_int64(), C.c_double(), C.c_int32()
+    _check(lib().mrf_tree_build_host(_ptr(atoms), d, L, CONES[cone], dup_tol,
+                                     *[_ptr(out[k]) for k in ("first_level", "parent", "rep",
+                                                              "en_atom", "en_level",
+                                                              "en_maxdist")],
+                                     C.byref(ne), C.byref(sig), C.byref(lev)))
+    for k in ("en_atom", "en_level", "en_maxdist"):
+        out[k] = out[k][:ne.value]
+    out.update(explicit_nodes=ne.value, sigma=sig.value, levels=lev.value)
+    return out
 
 
 def project(D: Dictionary, Z, idx_out, rho_out=None, X_out=None, warm_idx=None, opts=None,
@@ -178,7 +225,7 @@ def lut(D: Dictionary, idx, params_out, stream=None) -> None:
 
 
 PROFILE_STAGES = ["gradient", "pack_bf16", "search_bf16", "search_fp32", "merge", "fallback",
-                  "lut", "other"]
+                  "lut", "search_tree"]
 
 
 def profile_enable(on: bool = True) -> None:

@@ -20,13 +20,24 @@ CONES = {"complex": 0, "real_pos": 1}
 
 class IndexOpts(C.Structure):
     _fields_ = [("pack_bf16", C.c_int32), ("pack_fp8", C.c_int32), ("build_tree", C.c_int32),
-                ("reserved", C.c_int32 * 5)]
+                ("tree_cone", C.c_int32), ("tree_dup_tol", C.c_float),
+                ("reserved", C.c_int32 * 3)]
+
+
+class TreeInfo(C.Structure):
+    _fields_ = [("nodes", C.c_int64), ("explicit_nodes", C.c_int64), ("levels", C.c_int32),
+                ("metric", C.c_int32), ("sigma", C.c_double), ("build_ms", C.c_double),
+                ("device_bytes", C.c_int64)]
+
+    def as_dict(self) -> dict:
+        return {f: getattr(self, f) for f, _ in self._fields_}
 
 
 class ProjOpts(C.Structure):
     _fields_ = [("mode", C.c_int32), ("cone", C.c_int32), ("topk", C.c_int32),
                 ("certify", C.c_int32), ("tie_tol", C.c_float), ("cert_margin", C.c_float),
-                ("eps", C.c_float), ("fallback_thr", C.c_float), ("reserved", C.c_int32 * 8)]
+                ("eps", C.c_float), ("fallback_thr", C.c_float), ("tree_route", C.c_float),
+                ("reserved", C.c_int32 * 7)]
 
 
 class Stats(C.Structure):
@@ -71,6 +82,13 @@ SIGNATURES = {
     "mrf_dict_info": (C.c_int, [C.c_void_p, C.POINTER(C.c_int64), C.POINTER(C.c_int32),
                                 C.POINTER(C.c_int32)]),
     "mrf_dict_reserve": (C.c_int, [C.c_void_p, C.c_int64]),
+    "mrf_tree_build_host": (C.c_int, [C.c_void_p, C.c_int64, C.c_int32, C.c_int32, C.c_float,
+                                      C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
+                                      C.c_void_p, C.c_void_p, C.POINTER(C.c_int64),
+                                      C.POINTER(C.c_double), C.POINTER(C.c_int32)]),
+    "mrf_tree_get_info": (C.c_int, [C.c_void_p, C.POINTER(TreeInfo)]),
+    "mrf_tree_export": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
+                                  C.c_void_p, C.c_void_p]),
     "mrf_dict_check": (C.c_int, [C.c_void_p, C.c_void_p]),
     "mrf_project": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.POINTER(ProjOpts),
                               C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,

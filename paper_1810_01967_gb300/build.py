@@ -31,12 +31,13 @@ def cuda_home() -> str:
 
 
 def sources() -> list[str]:
-    return sorted(os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith(".cu"))
+    return sorted(os.path.join(CSRC, f) for f in os.listdir(CSRC)
+                  if f.endswith(".cu") or f.endswith(".cpp"))
 
 
 def _digest() -> str:
     h = hashlib.sha256()
-    for p in sorted(os.listdir(CSRC)) + ["../../include/mrf.h"]:
+    for p in sorted(os.listdir(CSRC)) + ["../../include/mrf.h", "../build.py"]:
         full = os.path.normpath(os.path.join(CSRC, p))
         if os.path.isfile(full):
             h.update(p.encode())
@@ -60,7 +61,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
         common += ["-Xptxas", "-v"]
 
     def compile_one(src: str) -> tuple[str, str]:
-        obj = os.path.join(BUILD, os.path.basename(src)[:-3] + ".o")
+        obj = os.path.join(BUILD, os.path.splitext(os.path.basename(src))[0] + ".o")
         cmd = [nvcc, "-c", src, "-o", obj] + common
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:

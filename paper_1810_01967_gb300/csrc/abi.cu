@@ -98,6 +98,7 @@ mrf_status ensure_scratch(mrf_dict* D, int64_t n) {
     MRF_TRY(dalloc(&D->zbuf, static_cast<size_t>(n * L)));
     MRF_TRY(dalloc(&D->wbuf, static_cast<size_t>(n * L)));
     MRF_TRY(dalloc(&D->vlist, static_cast<size_t>(n)));
+    MRF_TRY(dalloc(&D->vlist2, static_cast<size_t>(n)));
     if (D->bop) MRF_TRY(dalloc(&D->zq, static_cast<size_t>(n * D->Kp)));
     if (D->xprev) MRF_TRY(dalloc(&D->xprev, static_cast<size_t>(n * L)));
     D->cap_n = n;
@@ -130,8 +131,11 @@ mrf_status check_proj_opts(const mrf_dict* D, const mrf_proj_opts* o) {
         case MRF_PROJ_BF16:
             if (!D->bop) return fail(MRF_EUNSUPPORTED, "dictionary built without the BF16 operand");
             return MRF_OK;
-        case MRF_PROJ_FP8:
         case MRF_PROJ_COVERTREE:
+            if (!D->tree) return fail(MRF_EUNSUPPORTED, "dictionary built without a cover tree");
+            if (!(o->eps >= 0.f) || !std::isfinite(o->eps)) return fail(MRF_EINVAL, "eps must be >= 0");
+            return MRF_OK;
+        case MRF_PROJ_FP8:
         case MRF_PROJ_LEARNED:
             return fail(MRF_EUNSUPPORTED, "projection mode not available in this build");
         default: return fail(MRF_EINVAL, "unknown projection mode");
@@ -197,6 +201,57 @@ struct ProfScope {
     }
 };
 
+mrf_status bf16_margin(const mrf_dict* D, const mrf_proj_opts* o, float* m) {
+    // |c~ - c| <= (2u + u^2) ||d|| ||z|| for BF16 operand rounding (u = 2^-9) plus the FP32
+    // accumulation of 2L products; in normalised-correlation units
+    *m = o->cert_margin > 0.f ? o->cert_margin
+                              : static_cast<float>(std::ldexp(1.0, -8) + std::ldexp(1.0, -18) +
+                                                   2.0 * D->L * std::ldexp(1.0, -24));
+    return MRF_OK;
+}
+
+// Exhaustive projection of the voxels listed in D->vlist (cnt of them, length in D->nlist[0]):
+// BF16 tensor cores with certification (second list D->vlist2) when the operand exists, else
+// FP32.  Results go to the listed voxels' entries of the outputs.
+mrf_status exhaustive_on_list(mrf_dict* D, const float2* Z, int32_t cnt, const mrf_proj_opts* o,
+                              int32_t* idx_out, float2* rho_out, float2* X_out, cudaStream_t st) {
+    ProfScope ps5(5, 0, st);
+    if (D->bop) {
+        const int K = 16;
+        MRF_TRY(launch_pack_gather(Z, D->vlist, cnt, D->L, D->Kp, D->zq, st));
+        const int S = bf16_choose_splits(D, cnt);
+        MRF_TRY(ensure_part(D, cnt, S, K));
+        float* qs = static_cast<float*>(D->part);
+        int32_t* qi = reinterpret_cast<int32_t*>(qs + static_cast<size_t>(S) * cnt * K);
+        MRF_TRY(launch_bf16_topk(D->zq, cnt, D, o->cone, K, S, qs, qi, st));
+        float margin;
+        bf16_margin(D, o, &margin);
+        MRF_TRY(launch_merge(Z, cnt, D, o->cone, K, S, qs, qi, D->vlist, D->nlist, o->tie_tol,
+                             o->certify, margin, idx_out, rho_out, X_out, D->vlist2,
+                             D->nlist + 1, D->err, D->counters, st));
+        if (!o->certify) return MRF_OK;
+        int32_t c2 = 0;
+        MRF_CUDA_TRY(cudaMemcpyAsync(&c2, D->nlist + 1, sizeof(c2), cudaMemcpyDeviceToHost, st));
+        MRF_CUDA_TRY(cudaStreamSynchronize(st));
+        if (c2 == 0) return MRF_OK;
+        const int S2 = fp32_choose_splits(c2, D->d, D->num_sms);
+        MRF_TRY(ensure_part(D, c2, S2, 8));
+        float* rs = static_cast<float*>(D->part);
+        int32_t* ri = reinterpret_cast<int32_t*>(rs + static_cast<size_t>(S2) * c2 * 8);
+        MRF_TRY(launch_fp32_topk(Z, D->vlist2, D->nlist + 1, c2, D, o->cone, 8, S2, rs, ri, st));
+        return launch_merge(Z, c2, D, o->cone, 8, S2, rs, ri, D->vlist2, D->nlist + 1,
+                            o->tie_tol, 0, 0.f, idx_out, rho_out, X_out, nullptr, nullptr,
+                            D->err, D->counters, st);
+    }
+    const int S2 = fp32_choose_splits(cnt, D->d, D->num_sms);
+    MRF_TRY(ensure_part(D, cnt, S2, 8));
+    float* qs = static_cast<float*>(D->part);
+    int32_t* qi = reinterpret_cast<int32_t*>(qs + static_cast<size_t>(S2) * cnt * 8);
+    MRF_TRY(launch_fp32_topk(Z, D->vlist, D->nlist, cnt, D, o->cone, 8, S2, qs, qi, st));
+    return launch_merge(Z, cnt, D, o->cone, 8, S2, qs, qi, D->vlist, D->nlist, o->tie_tol, 0,
+                        0.f, idx_out, rho_out, X_out, nullptr, nullptr, D->err, D->counters, st);
+}
+
 // The projection proper.  `zq_ready` says the BF16 operand of Z is already in D->zq.
 mrf_status project_core(mrf_dict* D, const float2* Z, int64_t n, const mrf_proj_opts* o,
                         const int32_t* warm, int32_t* idx_out, float2* rho_out, float2* X_out,
@@ -236,12 +291,8 @@ mrf_status project_core(mrf_dict* D, const float2* Z, int64_t n, const mrf_proj_
             MRF_TRY(launch_bf16_topk(D->zq, n, D, o->cone, K, S, ps, pi, st));
         }
         if (o->certify) MRF_CUDA_TRY(cudaMemsetAsync(D->nlist, 0, sizeof(int32_t), st));
-        // |c~ - c| <= (2u + u^2) ||d|| ||z|| for BF16 operand rounding (u = 2^-9) plus the FP32
-        // accumulation of 2L products; in normalised-correlation units
-        const float margin = o->cert_margin > 0.f
-                                 ? o->cert_margin
-                                 : static_cast<float>(std::ldexp(1.0, -8) + std::ldexp(1.0, -18) +
-                                                      2.0 * D->L * std::ldexp(1.0, -24));
+        float margin;
+        bf16_margin(D, o, &margin);
         {
             ProfScope ps4(4, 1, st);
             MRF_TRY(launch_merge(Z, n, D, o->cone, K, S, ps, pi, nullptr, nullptr, o->tie_tol,
@@ -265,6 +316,28 @@ mrf_status project_core(mrf_dict* D, const float2* Z, int64_t n, const mrf_proj_
                                      nullptr, D->err, D->counters, st));
             }
         }
+        return MRF_OK;
+    }
+    if (o->mode == MRF_PROJ_COVERTREE) {
+        MRF_TRY(ensure_part(D, n, 1, 8));
+        float* ps = static_cast<float*>(D->part);
+        int32_t* pi = reinterpret_cast<int32_t*>(ps + static_cast<size_t>(n) * 8);
+        MRF_CUDA_TRY(cudaMemsetAsync(D->nlist, 0, 2 * sizeof(int32_t), st));
+        {
+            ProfScope ps7(7, 1, st);
+            MRF_TRY(launch_ct_search(Z, n, D, o->cone, warm, o->eps, o->tree_route, ps, pi,
+                                     D->vlist, D->nlist, st));
+        }
+        {
+            ProfScope ps4(4, 1, st);
+            MRF_TRY(launch_merge(Z, n, D, o->cone, 8, 1, ps, pi, nullptr, nullptr, o->tie_tol, 0,
+                                 0.f, idx_out, rho_out, X_out, nullptr, nullptr, D->err,
+                                 D->counters, st));
+        }
+        int32_t cnt = 0;
+        MRF_CUDA_TRY(cudaMemcpyAsync(&cnt, D->nlist, sizeof(cnt), cudaMemcpyDeviceToHost, st));
+        MRF_CUDA_TRY(cudaStreamSynchronize(st));
+        if (cnt > 0) MRF_TRY(exhaustive_on_list(D, Z, cnt, o, idx_out, rho_out, X_out, st));
         return MRF_OK;
     }
     return fail(MRF_EUNSUPPORTED, "projection mode not available in this build");
@@ -320,6 +393,8 @@ void mrf_default_index_opts(mrf_index_opts* o) {
     if (!o) return;
     std::memset(o, 0, sizeof(*o));
     o->pack_bf16 = 1;
+    o->tree_cone = MRF_CONE_COMPLEX;
+    o->tree_dup_tol = 1e-5f;
 }
 
 void mrf_default_proj_opts(mrf_proj_opts* o) {
@@ -333,6 +408,7 @@ void mrf_default_proj_opts(mrf_proj_opts* o) {
     o->cert_margin = 0.f;
     o->eps = 0.f;
     o->fallback_thr = 0.98f;
+    o->tree_route = 0.9f;
 }
 
 void mrf_default_recon_opts(mrf_recon_opts* o) {
@@ -347,8 +423,10 @@ void mrf_default_recon_opts(mrf_recon_opts* o) {
 
 void mrf_dict_free(mrf_dict* D) {
     if (!D) return;
+    if (D->tree) ct_free(D->tree);
     void* ptrs[] = {D->atoms, D->inv_norm2, D->norm2, D->params, D->bop, D->zq, D->zbuf,
-                    D->wbuf, D->xprev, D->vlist, D->nlist, D->part, D->err, D->counters, D->red};
+                    D->wbuf, D->xprev, D->vlist, D->vlist2, D->nlist, D->part, D->err,
+                    D->counters, D->red};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     delete D;
@@ -366,8 +444,10 @@ mrf_status mrf_build_dict_index(const void* atoms, int64_t d, int32_t L, const f
     if (grid_ndim < 0 || (grid_ndim > 0 && !grid_shape)) return fail(MRF_EINVAL, "grid_shape");
     mrf_index_opts o;
     if (opts) o = *opts; else mrf_default_index_opts(&o);
-    if (o.pack_fp8 || o.build_tree)
-        return fail(MRF_EUNSUPPORTED, "FP8 operand / cover tree not available in this build");
+    if (o.pack_fp8) return fail(MRF_EUNSUPPORTED, "FP8 operand not available in this build");
+    if (o.build_tree && o.tree_cone != MRF_CONE_COMPLEX && o.tree_cone != MRF_CONE_REAL_POS)
+        return fail(MRF_EINVAL, "tree_cone must be a mrf_cone");
+    if (o.build_tree && !(o.tree_dup_tol >= 0.f)) return fail(MRF_EINVAL, "tree_dup_tol < 0");
     cudaStream_t st = S_(stream);
     mrf_dict* D = new mrf_dict();
     D->d = d;
@@ -384,7 +464,7 @@ mrf_status mrf_build_dict_index(const void* atoms, int64_t d, int32_t L, const f
     if ((s = dalloc(&D->err, 1)) != MRF_OK) return bail(s);
     if ((s = dalloc(&D->counters, CNT_N)) != MRF_OK) return bail(s);
     if ((s = dalloc(&D->red, 8)) != MRF_OK) return bail(s);
-    if ((s = dalloc(&D->nlist, 1)) != MRF_OK) return bail(s);
+    if ((s = dalloc(&D->nlist, 2)) != MRF_OK) return bail(s);
     if (P > 0 && (s = dalloc(&D->params, static_cast<size_t>(d * P))) != MRF_OK) return bail(s);
     auto cuda_bail = [&](cudaError_t e, const char* what) {
         mrf_set_error(std::string(what) + ": " + cudaGetErrorString(e));
@@ -417,8 +497,23 @@ mrf_status mrf_build_dict_index(const void* atoms, int64_t d, int32_t L, const f
         mrf_dict_free(D);
         return MRF_ENONFINITE;
     }
+    if (o.build_tree) {
+        s = ct_build_upload(D, o.tree_cone == MRF_CONE_COMPLEX ? 0 : 1, o.tree_dup_tol);
+        if (s != MRF_OK) { mrf_dict_free(D); return s; }
+    }
     *out = D;
     return MRF_OK;
+}
+
+mrf_status mrf_tree_get_info(const mrf_dict* D, mrf_tree_info* info) {
+    if (!D || !info) return fail(MRF_EINVAL, "dict and info are required");
+    return ct_info(D, info);
+}
+
+mrf_status mrf_tree_export(const mrf_dict* D, int32_t* first_level, int32_t* parent,
+                           int32_t* rep, int32_t* en_atom, int32_t* en_level, float* en_maxdist) {
+    if (!D) return fail(MRF_EINVAL, "dict is NULL");
+    return ct_export(D, first_level, parent, rep, en_atom, en_level, en_maxdist);
 }
 
 mrf_status mrf_dict_info(const mrf_dict* D, int64_t* d, int32_t* L, int32_t* P) {

@@ -50,7 +50,8 @@ struct mrf_dict {
     float2* wbuf = nullptr;         // [cap_n][L] FFT workspace
     float2* xprev = nullptr;        // [cap_n][L] previous iterate (step rule)
     int32_t* vlist = nullptr;       // [cap_n] compacted voxel list (fallback)
-    int32_t* nlist = nullptr;       // [1] its length
+    int32_t* nlist = nullptr;       // [2] lengths of vlist and vlist2
+    int32_t* vlist2 = nullptr;      // [cap_n] second-level list (certification of a fallback)
     size_t part_bytes = 0;
     void* part = nullptr;           // partial top-k candidates (scores then indices)
     uint32_t* err = nullptr;        // device error word
@@ -85,6 +86,8 @@ mrf_status launch_atom_norms(mrf_dict* D, cudaStream_t st);
 mrf_status launch_pack_bop(mrf_dict* D, cudaStream_t st);
 mrf_status launch_pack_queries(const float2* Z, int64_t n, int L, int Kp, __nv_bfloat16* zq,
                                cudaStream_t st);
+mrf_status launch_pack_gather(const float2* Z, const int32_t* vlist, int64_t n, int L, int Kp,
+                              __nv_bfloat16* zq, cudaStream_t st);
 mrf_status launch_mask_ky(float2* W, const uint8_t* mask, int Ny, int Nx, int L,
                           cudaStream_t st);
 mrf_status launch_grad_combine(const float2* X, const float2* G, const float2* AHY, float2* Z,
@@ -107,6 +110,15 @@ int fp32_choose_splits(int64_t n, int64_t d, int num_sms);
 mrf_status launch_bf16_topk(const __nv_bfloat16* zq, int64_t n, mrf_dict* D, int cone, int K,
                             int S, float* part_s, int32_t* part_i, cudaStream_t st);
 int bf16_choose_splits(const mrf_dict* D, int64_t n);
+// covertree.cu
+mrf_status ct_build_upload(mrf_dict* D, int metric, double dup_tol);
+void ct_free(CoverTreeDev* t);
+mrf_status launch_ct_search(const float2* Z, int64_t n, const mrf_dict* D, int cone,
+                            const int32_t* warm, float eps, float route, float* part_s,
+                            int32_t* part_i, int32_t* fb_list, int32_t* fb_n, cudaStream_t st);
+mrf_status ct_info(const mrf_dict* D, mrf_tree_info* info);
+mrf_status ct_export(const mrf_dict* D, int32_t* first_level, int32_t* parent, int32_t* rep,
+                     int32_t* en_atom, int32_t* en_level, float* en_maxdist);
 // merge.cu
 mrf_status launch_merge(const float2* Z, int64_t n, const mrf_dict* D, int cone, int K, int S,
                         const float* part_s, const int32_t* part_i, const int32_t* vlist,

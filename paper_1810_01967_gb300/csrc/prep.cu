@@ -59,6 +59,18 @@ __global__ void k_pack_queries(const float2* __restrict__ Z, int64_t n, int L, i
     zq[i] = __floats2bfloat162_rn(z.x, z.y);
 }
 
+__global__ void k_pack_gather(const float2* __restrict__ Z, const int32_t* __restrict__ vlist,
+                              int64_t n, int L, int Kp, __nv_bfloat162* __restrict__ zq) {
+    int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+    int64_t half = Kp / 2;
+    if (i >= n * half) return;
+    int64_t k = i / half;
+    int t = static_cast<int>(i - k * half);
+    const int64_t v = vlist[k];
+    float2 z = (t < L) ? Z[v * L + t] : make_float2(0.f, 0.f);
+    zq[i] = __floats2bfloat162_rn(z.x, z.y);
+}
+
 __global__ void k_mask_ky(float2* __restrict__ W, const uint8_t* __restrict__ mask, int Ny,
                           int Nx, int L) {
     int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
@@ -191,6 +203,15 @@ mrf_status launch_pack_queries(const float2* Z, int64_t n, int L, int Kp, __nv_b
     if (n == 0) return MRF_OK;
     k_pack_queries<<<grid_for(n * (Kp / 2)), kThreads, 0, st>>>(
         Z, n, L, Kp, reinterpret_cast<__nv_bfloat162*>(zq));
+    LAUNCH_CHECK();
+    return MRF_OK;
+}
+
+mrf_status launch_pack_gather(const float2* Z, const int32_t* vlist, int64_t n, int L, int Kp,
+                              __nv_bfloat16* zq, cudaStream_t st) {
+    if (n == 0) return MRF_OK;
+    k_pack_gather<<<grid_for(n * (Kp / 2)), kThreads, 0, st>>>(
+        Z, vlist, n, L, Kp, reinterpret_cast<__nv_bfloat162*>(zq));
     LAUNCH_CHECK();
     return MRF_OK;
 }
