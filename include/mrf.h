@@ -219,6 +219,11 @@ mrf_status mrf_forward(const mrf_op* op, const void* X, void* Y, void* stream);
 /* A^H(Y) = F^H P_Omega^H Y: Y device [Ny][Nx][L] -> AHY device [n][L]. */
 mrf_status mrf_adjoint(const mrf_op* op, const void* Y, void* AHY, void* stream);
 
+/* Gradient step alone (§3.2, eq. blip; Algorithm 2 "gradient update"):
+ * Z = X - mu (A^H A X - AHY), all device complex64 [n][L]; X and Z may not alias. */
+mrf_status mrf_gradient(mrf_dict* dict, const mrf_op* op, const void* AHY, const void* X,
+                        float mu, void* Z, void* stream);
+
 /*
  * One BLIP iteration (§3.2, eq. blip): Z = X - mu (A^H A X - AHY), then the projection; X is
  * overwritten by rho_v D_j*.
@@ -266,6 +271,76 @@ mrf_status mrf_project_fp32_static(const void* atoms, int64_t d, int32_t L, cons
                                    int64_t n, int32_t cone, int32_t* idx_out, void* rho_out,
                                    void* X_out, void* stream);
 
+/*
+ * Learned proposal (the build's learned form of the projection; the paper keeps learned
+ * matching out of its comparisons, §2).  A network x (2L) -> hidden -> hidden -> 3 with GELU
+ * maps the canonical fingerprint -- z/||z|| rotated by exp(-i angle(v1^H z)), v1 the
+ * dictionary's dominant right singular vector -- to standardised (log T1, log T2, B0).  The
+ * nearest grid cell's (2 radius + 1)^k neighbourhood of valid atoms is rescored exactly, and a
+ * voxel whose best normalised correlation stays below mrf_proj_opts.fallback_thr is projected
+ * by the exhaustive search.  Training and inference run on this library's kernels.
+ */
+typedef struct mrf_mlp mrf_mlp;
+
+typedef struct mrf_mlp_opts {
+    int32_t  hidden;        /* hidden width (default 512) */
+    int32_t  radius;        /* neighbourhood radius per grid dimension (default 2: 5x5x5) */
+    int64_t  residue_pool;  /* capacity of the aliasing-residue pool, fingerprints (262144) */
+    uint64_t seed;          /* initialisation and sampling seed (default 5000) */
+    int32_t  reserved[8];
+} mrf_mlp_opts;
+
+typedef struct mrf_train_opts {
+    int32_t steps;          /* Adam steps */
+    int32_t batch;          /* fingerprints per step, <= 65536 */
+    float   lr;             /* Adam learning rate (beta1 0.9, beta2 0.999, eps 1e-8) */
+    float   snr_lo, snr_hi; /* noise SNR range, dB */
+    float   p_residue;      /* probability that a sample carries a residue from the pool */
+    int32_t reserved[6];
+} mrf_train_opts;
+
+void mrf_default_mlp_opts(mrf_mlp_opts* o);
+
+/* Create a model for `dict` (built with params (T1, T2[, B0]) and grid_shape (n1, n2[, nB0]) in
+ * that order).  grid_axes: host float32, the axis values concatenated (n1 T1 values, n2 T2
+ * values[, nB0 B0 values]), each ascending; cell_atom: host int32 [n1 n2 (nB0)], the atom of each
+ * grid cell or -1.  Initialises the weights (He normal, seed), the target standardisation from
+ * the dictionary's parameters, and v1 by power iteration.  Synchronises `stream`. */
+mrf_status mrf_mlp_create(mrf_dict* dict, const float* grid_axes, const int32_t* cell_atom,
+                          const mrf_mlp_opts* opts, mrf_mlp** out, void* stream);
+void mrf_mlp_free(mrf_mlp* mlp);
+
+/* Append aliasing residues (Z_v - X0_v) / ||X0_v|| of voxels with X0_v != 0 to the pool (Z: an
+ * IPG query, X0: the ground-truth image; device complex64 [n][L]); reservoir sampling once full. */
+mrf_status mrf_mlp_add_residues(mrf_mlp* mlp, const void* Z, const void* X0, int64_t n,
+                                void* stream);
+
+/* `steps` Adam steps on batches synthesised on the GPU: a random atom, a complex scale of
+ * modulus U[0.5, 1], a pool residue with probability p_residue, complex Gaussian noise at an SNR
+ * drawn from [snr_lo, snr_hi] dB.  loss_history: host float [steps] or NULL (if given, the
+ * call synchronises every step). */
+mrf_status mrf_mlp_train(mrf_mlp* mlp, const mrf_train_opts* opts, float* loss_history,
+                         void* stream);
+
+/* Read (set = 0) or write (set = 1) all parameters as one host float32 array in the order
+ * W1 [2L][H], b1 [H], W2 [H][H], b2 [H], W3 [H][3], b3 [3]; *count receives its length. */
+mrf_status mrf_mlp_params(mrf_mlp* mlp, float* host_params, int32_t set, int64_t* count);
+
+/* Forward pass on X (device float32 [B][2L]) into Y_out ([B][3], host or device, may be NULL);
+ * with targets T ([B][3]) also the MSE loss (host double) and the gradient of every parameter
+ * (grads_out, same layout as mrf_mlp_params, host or device).  Synchronises `stream`. */
+mrf_status mrf_mlp_grad(mrf_mlp* mlp, const float* X, const float* T, int64_t B, float* Y_out,
+                        float* grads_out, double* loss_out, void* stream);
+
+/* Canonical network inputs of Z (device complex64 [n][L]) into X (device float32 [n][2L]); also
+ * copies v1 (host complex64 [L]) and the target means and standard deviations (host float [6])
+ * when those pointers are not NULL.  Synchronises `stream`. */
+mrf_status mrf_mlp_canonical(mrf_mlp* mlp, const void* Z, int64_t n, float* X, float* v1_host,
+                             float* tstats_host, void* stream);
+
+/* Use `mlp` for MRF_PROJ_LEARNED projections of `dict` (NULL detaches). */
+mrf_status mrf_dict_attach_mlp(mrf_dict* dict, mrf_mlp* mlp);
+
 /* Look-up table Theta_v = params[idx_v] (Algorithm 2, last step): device int32 [n] ->
  * device float32 [n][P]. */
 mrf_status mrf_lut(const mrf_dict* dict, const int32_t* idx, int64_t n, float* params_out,
@@ -298,8 +373,9 @@ mrf_status mrf_set_tune(mrf_dict* dict, const mrf_tune* in);
  * their elapsed times into ms[stage] and launches[stage] for stage < n_stages, and clears
  * them.  Stages: 0 gradient step (cuFFT + mask + combine; cuFFT's kernels are timed here but
  * not counted as launches), 1 BF16 query packing, 2 BF16 tensor-core search, 3 FP32 search,
- * 4 merge / rescore / density, 5 fallback to the exhaustive FP32 search (certification or
- * cover-tree overflow: search + merge), 6 look-up table, 7 cover-tree search.  Enabling or disabling clears the tables.  Not thread-safe.
+ * 4 merge / rescore / density, 5 fallback to the exhaustive search (certification, cover-tree
+ * routing or overflow, learned-proposal fallback), 6 look-up table, 7 proposal search (cover
+ * tree traversal or learned network + neighbourhood rescore).  Enabling or disabling clears the tables.  Not thread-safe.
  */
 #define MRF_PROFILE_STAGES 8
 mrf_status mrf_profile_enable(int32_t on);

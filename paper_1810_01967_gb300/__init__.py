@@ -200,6 +200,11 @@ def adjoint(op: Op, Y, AHY, stream=None) -> None:
     _check(lib().mrf_adjoint(C.byref(op), _ptr(Y), _ptr(AHY), _stream(stream)))
 
 
+def gradient(D: Dictionary, op: Op, AHY, X, mu: float, Z_out, stream=None) -> None:
+    _check(lib().mrf_gradient(D.handle, C.byref(op), _ptr(AHY), _ptr(X), mu, _ptr(Z_out),
+                              _stream(stream)))
+
+
 def ipg_step(D: Dictionary, op: Op, AHY, X, mu: float, idx_io, rho_out=None, opts=None,
              stats: bool = False, stream=None):
     o = opts or proj_opts()
@@ -224,8 +229,94 @@ def lut(D: Dictionary, idx, params_out, stream=None) -> None:
     _check(lib().mrf_lut(D.handle, _ptr(idx), idx.shape[0], _ptr(params_out), _stream(stream)))
 
 
+class MLP:
+    """Learned proposal model (mrf_mlp) bound to a Dictionary."""
+
+    def __init__(self, D: Dictionary, grid_axes, cell_atom, hidden: int = 512, radius: int = 2,
+                 residue_pool: int = 262144, seed: int = 5000, stream=None):
+        import numpy as np
+        o = _lib.MlpOpts()
+        lib().mrf_default_mlp_opts(C.byref(o))
+        o.hidden, o.radius, o.residue_pool, o.seed = hidden, radius, residue_pool, seed
+        ax = np.ascontiguousarray(np.concatenate([np.asarray(a, np.float32) for a in grid_axes]))
+        ca = np.ascontiguousarray(np.asarray(cell_atom, np.int32).ravel())
+        h = C.c_void_p()
+        _check(lib().mrf_mlp_create(D.handle, _ptr(ax), _ptr(ca), C.byref(o), C.byref(h),
+                                    _stream(stream)))
+        self.handle, self.dict = h, D
+        self.hidden, self.L = hidden, D.L
+
+    def close(self):
+        if getattr(self, "handle", None):
+            lib().mrf_mlp_free(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def add_residues(self, Z, X0, stream=None):
+        _check(lib().mrf_mlp_add_residues(self.handle, _ptr(Z), _ptr(X0), Z.shape[0],
+                                          _stream(stream)))
+
+    def train(self, steps: int, batch: int = 1024, lr: float = 1e-3, snr=(30.0, 50.0),
+              p_residue: float = 0.5, history: bool = False, stream=None):
+        import numpy as np
+        o = _lib.TrainOpts(steps, batch, lr, snr[0], snr[1], p_residue)
+        h = np.zeros(steps, np.float32) if history else None
+        _check(lib().mrf_mlp_train(self.handle, C.byref(o), _ptr(h), _stream(stream)))
+        return h
+
+    def params(self, values=None):
+        """Get (values None) or set all parameters as one float32 host array."""
+        import numpy as np
+        n = C.c_int64()
+        _check(lib().mrf_mlp_params(self.handle, None, 0, C.byref(n)))
+        if values is None:
+            out = np.empty(n.value, np.float32)
+            _check(lib().mrf_mlp_params(self.handle, _ptr(out), 0, C.byref(n)))
+            return out
+        v = np.ascontiguousarray(values, np.float32)
+        assert v.size == n.value
+        _check(lib().mrf_mlp_params(self.handle, _ptr(v), 1, C.byref(n)))
+
+    def grad(self, X, T=None, stream=None):
+        """(Y, loss, grads) for device float32 inputs X [B][2L] and targets T [B][3]."""
+        import numpy as np
+        import torch
+        for t in (X, T):
+            if t is not None and t.dtype != torch.float32:
+                raise TypeError("MLP.grad expects float32 tensors")
+        if X.shape[1] != 2 * self.L:
+            raise ValueError("X must be [B][2L]")
+        B = X.shape[0]
+        Y = np.empty((B, 3), np.float32)
+        n = C.c_int64()
+        _check(lib().mrf_mlp_params(self.handle, None, 0, C.byref(n)))
+        g = np.empty(n.value, np.float32) if T is not None else None
+        loss = C.c_double()
+        _check(lib().mrf_mlp_grad(self.handle, _ptr(X), _ptr(T), B, _ptr(Y), _ptr(g),
+                                  C.byref(loss) if T is not None else None, _stream(stream)))
+        return Y, (loss.value if T is not None else None), g
+
+    def canonical(self, Z, X_out, stream=None):
+        import numpy as np
+        v1 = np.empty(self.L, np.complex64)
+        ts = np.empty(6, np.float32)
+        _check(lib().mrf_mlp_canonical(self.handle, _ptr(Z), Z.shape[0], _ptr(X_out), _ptr(v1),
+                                       _ptr(ts), _stream(stream)))
+        return v1, ts
+
+
+def attach_mlp(D: Dictionary, mlp) -> None:
+    _check(lib().mrf_dict_attach_mlp(D.handle, None if mlp is None else mlp.handle))
+    D._mlp = mlp
+
+
 PROFILE_STAGES = ["gradient", "pack_bf16", "search_bf16", "search_fp32", "merge", "fallback",
-                  "lut", "search_tree"]
+                  "lut", "search_proposal"]
 
 
 def profile_enable(on: bool = True) -> None:

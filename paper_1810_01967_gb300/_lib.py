@@ -71,6 +71,17 @@ class Tune(C.Structure):
         return {f: getattr(self, f) for f, _ in self._fields_ if f != "reserved"}
 
 
+class MlpOpts(C.Structure):
+    _fields_ = [("hidden", C.c_int32), ("radius", C.c_int32), ("residue_pool", C.c_int64),
+                ("seed", C.c_uint64), ("reserved", C.c_int32 * 8)]
+
+
+class TrainOpts(C.Structure):
+    _fields_ = [("steps", C.c_int32), ("batch", C.c_int32), ("lr", C.c_float),
+                ("snr_lo", C.c_float), ("snr_hi", C.c_float), ("p_residue", C.c_float),
+                ("reserved", C.c_int32 * 6)]
+
+
 SIGNATURES = {
     "mrf_default_index_opts": (None, [C.POINTER(IndexOpts)]),
     "mrf_default_proj_opts": (None, [C.POINTER(ProjOpts)]),
@@ -95,6 +106,8 @@ SIGNATURES = {
                               C.POINTER(Stats), C.c_void_p]),
     "mrf_forward": (C.c_int, [C.POINTER(Op), C.c_void_p, C.c_void_p, C.c_void_p]),
     "mrf_adjoint": (C.c_int, [C.POINTER(Op), C.c_void_p, C.c_void_p, C.c_void_p]),
+    "mrf_gradient": (C.c_int, [C.c_void_p, C.POINTER(Op), C.c_void_p, C.c_void_p, C.c_float,
+                               C.c_void_p, C.c_void_p]),
     "mrf_ipg_step": (C.c_int, [C.c_void_p, C.POINTER(Op), C.c_void_p, C.c_void_p, C.c_float,
                                C.POINTER(ProjOpts), C.c_void_p, C.c_void_p, C.POINTER(Stats),
                                C.c_void_p]),
@@ -109,6 +122,19 @@ SIGNATURES = {
     "mrf_set_tune": (C.c_int, [C.c_void_p, C.POINTER(Tune)]),
     "mrf_profile_enable": (C.c_int, [C.c_int32]),
     "mrf_profile_read": (C.c_int, [C.POINTER(C.c_double), C.POINTER(C.c_int64), C.c_int32]),
+    "mrf_default_mlp_opts": (None, [C.POINTER(MlpOpts)]),
+    "mrf_mlp_create": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(MlpOpts),
+                                 C.POINTER(C.c_void_p), C.c_void_p]),
+    "mrf_mlp_free": (None, [C.c_void_p]),
+    "mrf_mlp_add_residues": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64,
+                                       C.c_void_p]),
+    "mrf_mlp_train": (C.c_int, [C.c_void_p, C.POINTER(TrainOpts), C.c_void_p, C.c_void_p]),
+    "mrf_mlp_params": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int32, C.POINTER(C.c_int64)]),
+    "mrf_mlp_grad": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p,
+                               C.c_void_p, C.c_void_p, C.c_void_p]),
+    "mrf_mlp_canonical": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p,
+                                    C.c_void_p, C.c_void_p]),
+    "mrf_dict_attach_mlp": (C.c_int, [C.c_void_p, C.c_void_p]),
     "mrf_status_str": (C.c_char_p, [C.c_int]),
     "mrf_last_error": (C.c_char_p, []),
 }

@@ -135,8 +135,10 @@ mrf_status check_proj_opts(const mrf_dict* D, const mrf_proj_opts* o) {
             if (!D->tree) return fail(MRF_EUNSUPPORTED, "dictionary built without a cover tree");
             if (!(o->eps >= 0.f) || !std::isfinite(o->eps)) return fail(MRF_EINVAL, "eps must be >= 0");
             return MRF_OK;
-        case MRF_PROJ_FP8:
         case MRF_PROJ_LEARNED:
+            if (!D->mlp) return fail(MRF_EUNSUPPORTED, "no learned model attached to the dictionary");
+            return MRF_OK;
+        case MRF_PROJ_FP8:
             return fail(MRF_EUNSUPPORTED, "projection mode not available in this build");
         default: return fail(MRF_EINVAL, "unknown projection mode");
     }
@@ -340,6 +342,29 @@ mrf_status project_core(mrf_dict* D, const float2* Z, int64_t n, const mrf_proj_
         if (cnt > 0) MRF_TRY(exhaustive_on_list(D, Z, cnt, o, idx_out, rho_out, X_out, st));
         return MRF_OK;
     }
+    if (o->mode == MRF_PROJ_LEARNED) {
+        MRF_TRY(ensure_part(D, n, 1, 8));
+        float* ps = static_cast<float*>(D->part);
+        int32_t* pi = reinterpret_cast<int32_t*>(ps + static_cast<size_t>(n) * 8);
+        MRF_CUDA_TRY(cudaMemsetAsync(D->nlist, 0, 2 * sizeof(int32_t), st));
+        {
+            ProfScope ps7(7, 4, st);
+            MRF_TRY(learned_candidates(D, Z, n, o->cone, ps, pi, st));
+        }
+        {
+            ProfScope ps4(4, 2, st);
+            MRF_TRY(launch_merge(Z, n, D, o->cone, 8, 1, ps, pi, nullptr, nullptr, o->tie_tol, 0,
+                                 0.f, idx_out, rho_out, X_out, nullptr, nullptr, D->err,
+                                 D->counters, st));
+            MRF_TRY(learned_flag(D, Z, n, idx_out, o->fallback_thr, o->cone, D->vlist, D->nlist,
+                                 st));
+        }
+        int32_t cnt = 0;
+        MRF_CUDA_TRY(cudaMemcpyAsync(&cnt, D->nlist, sizeof(cnt), cudaMemcpyDeviceToHost, st));
+        MRF_CUDA_TRY(cudaStreamSynchronize(st));
+        if (cnt > 0) MRF_TRY(exhaustive_on_list(D, Z, cnt, o, idx_out, rho_out, X_out, st));
+        return MRF_OK;
+    }
     return fail(MRF_EUNSUPPORTED, "projection mode not available in this build");
 }
 
@@ -424,6 +449,7 @@ void mrf_default_recon_opts(mrf_recon_opts* o) {
 void mrf_dict_free(mrf_dict* D) {
     if (!D) return;
     if (D->tree) ct_free(D->tree);
+    if (D->mlp) mlp_detach(D->mlp);
     void* ptrs[] = {D->atoms, D->inv_norm2, D->norm2, D->params, D->bop, D->zq, D->zbuf,
                     D->wbuf, D->xprev, D->vlist, D->vlist2, D->nlist, D->part, D->err,
                     D->counters, D->red};
@@ -583,6 +609,23 @@ mrf_status mrf_adjoint(const mrf_op* op, const void* Y, void* AHY, void* stream)
     MRF_TRY(fft_exec(h2, static_cast<float2*>(AHY), static_cast<float2*>(AHY), CUFFT_INVERSE));
     MRF_TRY(launch_scale(static_cast<float2*>(AHY), cnt,
                          1.0f / std::sqrt(static_cast<float>(op->Ny) * op->Nx), st));
+    return MRF_OK;
+}
+
+mrf_status mrf_gradient(mrf_dict* D, const mrf_op* op, const void* AHY, const void* X,
+                        float mu, void* Z, void* stream) {
+    if (!D) return fail(MRF_EINVAL, "dict is NULL");
+    MRF_TRY(check_op(op));
+    if (op->L != D->L) return fail(MRF_EINVAL, "op->L differs from the dictionary's L");
+    if (!AHY || !X || !Z) return fail(MRF_EINVAL, "AHY, X and Z are required");
+    if (!std::isfinite(mu)) return fail(MRF_EINVAL, "mu must be finite");
+    cudaStream_t st = S_(stream);
+    const int64_t n = static_cast<int64_t>(op->Ny) * op->Nx;
+    MRF_TRY(ensure_scratch(D, n));
+    MRF_TRY(gradient(D, op, static_cast<const float2*>(AHY), static_cast<const float2*>(X), mu,
+                     false, st));
+    MRF_CUDA_TRY(cudaMemcpyAsync(Z, D->zbuf, sizeof(float2) * n * op->L, cudaMemcpyDeviceToDevice,
+                                 st));
     return MRF_OK;
 }
 

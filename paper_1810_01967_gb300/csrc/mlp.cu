@@ -1,0 +1,1004 @@
+// Learned proposal for the matched filter: a small MLP maps a fingerprint to (log T1, log T2,
+// B0), whose nearest grid cell's neighbourhood is rescored exactly, with the exhaustive search as
+// the fallback when the best rescored correlation is low.  The paper keeps learned matching out
+// of its comparisons (§2); this is the build's "learned proposal" form of the projection.
+//
+// Network: x (2L, the canonical unit fingerprint) -> 512 -> 512 -> 3, GELU (x Phi(x)), trained
+// with MSE on standardised targets and Adam, entirely with this file's kernels:
+//   * a tiled FP32 SIMT GEMM (64x64 tiles, 4x4 per thread) with the transposes the forward and
+//     backward passes need and a fused bias + GELU epilogue that keeps the pre-activation;
+//   * small kernels for the 3-wide output layer, the loss, bias gradients and Adam;
+//   * batch synthesis from the dictionary: random atom, complex scale, aliasing residue drawn
+//     from a pool collected from IPG iterates, and complex Gaussian noise at 30-50 dB, drawn with
+//     SplitMix64 (Steele, Lea, Flood 2014) as a counter-based generator and Box-Muller;
+//   * canonicalisation z^ = z/||z|| rotated by exp(-i angle(v1^H z^)), v1 the dictionary's
+//     dominant right singular vector (power iteration, phase fixed so its largest entry is real
+//     positive).
+// Inference (MRF_PROJ_LEARNED) runs the forward pass on the queries, maps the prediction to the
+// nearest grid cell and rescores the valid atoms of the (2r+1)^k neighbourhood in FP32; the merge
+// kernel then rescores its best 8 exactly (FP64 near-ties) and forms the density.
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include "mrf_internal.cuh"
+
+namespace {
+
+constexpr int kT = 256;
+
+// ------------------------------------------------------------------------------------ RNG
+__device__ __forceinline__ uint64_t splitmix64(uint64_t x) {
+    x += 0x9E3779B97F4A7C15ull;
+    x = (x ^ (x >> 30)) * 0xBF58476D1CE4E5B9ull;
+    x = (x ^ (x >> 27)) * 0x94D049BB133111EBull;
+    return x ^ (x >> 31);
+}
+// uniform in (0, 1) from stream `key`, counter `c`
+__device__ __forceinline__ float urand(uint64_t key, uint64_t c) {
+    const uint64_t r = splitmix64(key ^ splitmix64(c));
+    return (static_cast<float>(r >> 40) + 0.5f) * (1.0f / 16777216.0f);
+}
+
+// ------------------------------------------------------------------------------------ GEMM
+// C[M x N] = op(A)[M x K] op(B)[K x N] (+ bias[N]); element (m, k) of A is A[m lda + k], or
+// A[k lda + m] when TA; likewise B.  Epilogue: EP = 0 plain store, 1 bias, 2 bias + GELU with the
+// pre-activation stored in Hpre.
+constexpr int GB = 64, GK = 16;
+
+template <bool TA, bool TB, int EP>
+__global__ void __launch_bounds__(256)
+k_gemm(int M, int N, int K, const float* __restrict__ A, int lda, const float* __restrict__ B,
+       int ldb, float* __restrict__ C, int ldc, const float* __restrict__ bias,
+       float* __restrict__ Hpre) {
+    __shared__ float As[GK][GB + 4];
+    __shared__ float Bs[GK][GB + 4];
+    const int tid = threadIdx.x;
+    const int tx = tid & 15, ty = tid >> 4;
+    const int m0 = blockIdx.y * GB, n0 = blockIdx.x * GB;
+    float acc[4][4] = {};
+    for (int k0 = 0; k0 < K; k0 += GK) {
+        for (int e = tid; e < GB * GK; e += 256) {
+            int mm, kk;
+            if (TA) { mm = e % GB; kk = e / GB; } else { kk = e % GK; mm = e / GK; }
+            const int m = m0 + mm, k = k0 + kk;
+            float v = 0.f;
+            if (m < M && k < K) v = TA ? A[static_cast<int64_t>(k) * lda + m]
+                                       : A[static_cast<int64_t>(m) * lda + k];
+            As[kk][mm] = v;
+        }
+        for (int e = tid; e < GB * GK; e += 256) {
+            int nn, kk;
+            if (TB) { kk = e % GK; nn = e / GK; } else { nn = e % GB; kk = e / GB; }
+            const int n = n0 + nn, k = k0 + kk;
+            float v = 0.f;
+            if (n < N && k < K) v = TB ? B[static_cast<int64_t>(n) * ldb + k]
+                                       : B[static_cast<int64_t>(k) * ldb + n];
+            Bs[kk][nn] = v;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int kk = 0; kk < GK; ++kk) {
+            float a[4], b[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) a[i] = As[kk][ty * 4 + i];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) b[j] = Bs[kk][tx * 4 + j];
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(a[i], b[j], acc[i][j]);
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const int m = m0 + ty * 4 + i;
+        if (m >= M) continue;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int n = n0 + tx * 4 + j;
+            if (n >= N) continue;
+            float v = acc[i][j];
+            if (EP >= 1) v += bias[n];
+            if (EP == 2) {
+                Hpre[static_cast<int64_t>(m) * ldc + n] = v;
+                v = 0.5f * v * (1.f + erff(v * 0.70710678118654752f));
+            }
+            C[static_cast<int64_t>(m) * ldc + n] = v;
+        }
+    }
+}
+
+template <bool TA, bool TB, int EP>
+mrf_status gemm(int M, int N, int K, const float* A, int lda, const float* B, int ldb, float* C,
+                int ldc, const float* bias, float* Hpre, cudaStream_t st) {
+    dim3 grid((N + GB - 1) / GB, (M + GB - 1) / GB);
+    k_gemm<TA, TB, EP><<<grid, 256, 0, st>>>(M, N, K, A, lda, B, ldb, C, ldc, bias, Hpre);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) {
+        mrf_set_error(std::string("gemm launch: ") + cudaGetErrorString(e));
+        return MRF_ECUDA;
+    }
+    return MRF_OK;
+}
+
+// 3-wide output layer: Y[b][o] = A[b][:] W[:][o] + c[o] (warp per row)
+__global__ void k_out3(const float* __restrict__ A, int64_t Bn, int H, const float* __restrict__ W,
+                       const float* __restrict__ c, float* __restrict__ Y) {
+    const int64_t b = (static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (b >= Bn) return;
+    float s0 = 0.f, s1 = 0.f, s2 = 0.f;
+    for (int k = lane; k < H; k += 32) {
+        const float a = A[b * H + k];
+        s0 = fmaf(a, W[k * 3 + 0], s0);
+        s1 = fmaf(a, W[k * 3 + 1], s1);
+        s2 = fmaf(a, W[k * 3 + 2], s2);
+    }
+    for (int o = 16; o; o >>= 1) {
+        s0 += __shfl_xor_sync(0xffffffffu, s0, o);
+        s1 += __shfl_xor_sync(0xffffffffu, s1, o);
+        s2 += __shfl_xor_sync(0xffffffffu, s2, o);
+    }
+    if (lane == 0) {
+        Y[b * 3 + 0] = s0 + c[0];
+        Y[b * 3 + 1] = s1 + c[1];
+        Y[b * 3 + 2] = s2 + c[2];
+    }
+}
+
+// MSE loss and dY = 2 (Y - T) / (B 3); loss accumulated in FP64
+__global__ void k_mse(const float* __restrict__ Y, const float* __restrict__ T, int64_t count,
+                      float* __restrict__ dY, double* loss) {
+    double s = 0.0;
+    const float sc = 2.f / static_cast<float>(count);
+    for (int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; i < count;
+         i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+        const float r = Y[i] - T[i];
+        dY[i] = sc * r;
+        s += static_cast<double>(r) * r;
+    }
+    for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if ((threadIdx.x & 31) == 0) atomicAdd(loss, s / static_cast<double>(count));
+}
+
+// dW3[k][o] = sum_b A[b][k] dY[b][o];  dA[b][k] = sum_o dY[b][o] W3[k][o]
+__global__ void k_out3_back(const float* __restrict__ A, const float* __restrict__ dY,
+                            const float* __restrict__ W, int64_t Bn, int H,
+                            float* __restrict__ dW, float* __restrict__ dA) {
+    const int k = blockIdx.x;
+    float s0 = 0.f, s1 = 0.f, s2 = 0.f;
+    const float w0 = W[k * 3], w1 = W[k * 3 + 1], w2 = W[k * 3 + 2];
+    for (int64_t b = threadIdx.x; b < Bn; b += blockDim.x) {
+        const float a = A[b * H + k];
+        const float g0 = dY[b * 3], g1 = dY[b * 3 + 1], g2 = dY[b * 3 + 2];
+        s0 = fmaf(a, g0, s0);
+        s1 = fmaf(a, g1, s1);
+        s2 = fmaf(a, g2, s2);
+        dA[b * H + k] = g0 * w0 + g1 * w1 + g2 * w2;
+    }
+    __shared__ float red[3][32];
+    for (int o = 16; o; o >>= 1) {
+        s0 += __shfl_xor_sync(0xffffffffu, s0, o);
+        s1 += __shfl_xor_sync(0xffffffffu, s1, o);
+        s2 += __shfl_xor_sync(0xffffffffu, s2, o);
+    }
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (lane == 0) { red[0][w] = s0; red[1][w] = s1; red[2][w] = s2; }
+    __syncthreads();
+    if (threadIdx.x < 3) {
+        float t = 0.f;
+        for (int i = 0; i < static_cast<int>(blockDim.x >> 5); ++i) t += red[threadIdx.x][i];
+        dW[k * 3 + threadIdx.x] = t;
+    }
+}
+
+// dH = dA * gelu'(H), in place on dA
+__global__ void k_gelu_back(float* __restrict__ dA, const float* __restrict__ H, int64_t count) {
+    const int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (i >= count) return;
+    const float x = H[i];
+    const float cdf = 0.5f * (1.f + erff(x * 0.70710678118654752f));
+    const float pdf = 0.39894228040143268f * expf(-0.5f * x * x);
+    dA[i] *= cdf + x * pdf;
+}
+
+// column sums: out[n] = sum_m X[m][n]
+__global__ void k_colsum(const float* __restrict__ X, int64_t M, int N, float* __restrict__ out) {
+    const int n = blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= N) return;
+    float s = 0.f;
+    for (int64_t m = 0; m < M; ++m) s += X[m * N + n];
+    out[n] = s;
+}
+
+__global__ void k_adam(float* __restrict__ p, const float* __restrict__ g, float* __restrict__ m,
+                       float* __restrict__ v, int64_t count, float lr, float b1, float b2,
+                       float eps, float c1, float c2) {
+    const int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (i >= count) return;
+    const float gi = g[i];
+    const float mi = b1 * m[i] + (1.f - b1) * gi;
+    const float vi = b2 * v[i] + (1.f - b2) * gi * gi;
+    m[i] = mi;
+    v[i] = vi;
+    p[i] -= lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+}
+
+// ------------------------------------------------------------------ canonical input
+// row v of X (2L floats) = (Re, Im) of z^ exp(-i angle(v1^H z^)), z^ = Z_v / ||Z_v||
+__global__ void k_canon(const float2* __restrict__ Z, const int32_t* __restrict__ rows,
+                        int64_t n, int L, const float2* __restrict__ v1, float* __restrict__ X) {
+    const int64_t r = (static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (r >= n) return;
+    const int64_t v = rows ? rows[r] : r;
+    const float2* z = Z + v * L;
+    float s = 0.f, cr = 0.f, ci = 0.f;
+    for (int t = lane; t < L; t += 32) {
+        const float2 a = z[t], w = v1[t];
+        s = fmaf(a.x, a.x, fmaf(a.y, a.y, s));
+        cr = fmaf(w.x, a.x, fmaf(w.y, a.y, cr));      // v1^H z
+        ci = fmaf(w.x, a.y, fmaf(-w.y, a.x, ci));
+    }
+    for (int o = 16; o; o >>= 1) {
+        s += __shfl_xor_sync(0xffffffffu, s, o);
+        cr += __shfl_xor_sync(0xffffffffu, cr, o);
+        ci += __shfl_xor_sync(0xffffffffu, ci, o);
+    }
+    const float inv = s > 0.f ? rsqrtf(s) : 0.f;
+    const float mag = sqrtf(cr * cr + ci * ci);
+    const float ur = mag > 0.f ? cr / mag : 1.f, ui = mag > 0.f ? -ci / mag : 0.f;   // e^{-i phi}
+    float* x = X + r * 2 * L;
+    for (int t = lane; t < L; t += 32) {
+        const float2 a = z[t];
+        x[2 * t] = inv * (a.x * ur - a.y * ui);
+        x[2 * t + 1] = inv * (a.x * ui + a.y * ur);
+    }
+}
+
+// ------------------------------------------------------------------ power iteration for v1
+// u = D v (length d), then w = D^H u (length L)
+__global__ void k_dv(const float2* __restrict__ D, int64_t d, int L, const float2* __restrict__ v,
+                     float2* __restrict__ u) {
+    const int64_t j = (static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (j >= d) return;
+    float re = 0.f, im = 0.f;
+    for (int t = lane; t < L; t += 32) {
+        const float2 a = D[j * L + t], b = v[t];
+        re = fmaf(a.x, b.x, fmaf(-a.y, b.y, re));
+        im = fmaf(a.x, b.y, fmaf(a.y, b.x, im));
+    }
+    for (int o = 16; o; o >>= 1) {
+        re += __shfl_xor_sync(0xffffffffu, re, o);
+        im += __shfl_xor_sync(0xffffffffu, im, o);
+    }
+    if (lane == 0) u[j] = make_float2(re, im);
+}
+__global__ void k_dhu(const float2* __restrict__ D, int64_t d, int L, const float2* __restrict__ u,
+                      double* __restrict__ w) {
+    // grid-stride over atoms per frame t: w[t] += conj(D[j][t]) u[j]
+    const int t = blockIdx.x;
+    double re = 0.0, im = 0.0;
+    for (int64_t j = threadIdx.x; j < d; j += blockDim.x) {
+        const float2 a = D[j * L + t], b = u[j];
+        re += static_cast<double>(a.x) * b.x + static_cast<double>(a.y) * b.y;
+        im += static_cast<double>(a.x) * b.y - static_cast<double>(a.y) * b.x;
+    }
+    __shared__ double sr[32], si[32];
+    for (int o = 16; o; o >>= 1) {
+        re += __shfl_xor_sync(0xffffffffu, re, o);
+        im += __shfl_xor_sync(0xffffffffu, im, o);
+    }
+    const int wi = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (lane == 0) { sr[wi] = re; si[wi] = im; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double a = 0.0, b = 0.0;
+        for (int i = 0; i < static_cast<int>(blockDim.x >> 5); ++i) { a += sr[i]; b += si[i]; }
+        w[2 * t] = a;
+        w[2 * t + 1] = b;
+    }
+}
+
+// ------------------------------------------------------------------ batch synthesis
+struct SynthArgs {
+    const float2* atoms;
+    const float* inv_norm2;
+    const float* params;   // [d][P]
+    int P;
+    int64_t d;
+    int L;
+    const float2* residues;   // [R][L] relative residues
+    int64_t R;
+    float p_res;
+    float snr_lo, snr_hi;
+    int has_b0;
+    int b0_col;
+    float tmean[3], tstd[3];
+    uint64_t key;
+};
+
+// One warp per sample: fingerprint f = rho (d_j/||d_j|| + s r) + noise, stored as a complex row
+// of F (later canonicalised); target = standardised (log T1, log T2, B0) of atom j.
+__global__ void k_synth(SynthArgs a, int64_t B, uint64_t step, float2* __restrict__ F,
+                        float* __restrict__ T) {
+    const int64_t b = (static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (b >= B) return;
+    const uint64_t base = (step * static_cast<uint64_t>(B) + b) * 16ull;
+    const int64_t j = static_cast<int64_t>(urand(a.key, base) * a.d) % a.d;
+    const float amp = 0.5f + 0.5f * urand(a.key, base + 1);
+    const float ph = 6.283185307179586f * urand(a.key, base + 2);
+    const float rr = amp * cosf(ph), ri = amp * sinf(ph);
+    const bool use_res = a.R > 0 && urand(a.key, base + 3) < a.p_res;
+    const int64_t k = use_res ? static_cast<int64_t>(urand(a.key, base + 4) * a.R) % a.R : 0;
+    const float snr = a.snr_lo + (a.snr_hi - a.snr_lo) * urand(a.key, base + 5);
+    const float inrm = sqrtf(a.inv_norm2[j]);
+    // per-component noise sd for a unit-norm signal at this SNR (amplitude amp)
+    const float sd = amp * powf(10.f, -snr / 20.f) * rsqrtf(2.f * a.L);
+    const float2* d = a.atoms + j * a.L;
+    const float2* r = a.residues + k * a.L;
+    float2* f = F + b * a.L;
+    for (int t = lane; t < a.L; t += 32) {
+        float2 x = make_float2(d[t].x * inrm, d[t].y * inrm);
+        if (use_res) { x.x += r[t].x; x.y += r[t].y; }
+        const uint64_t c = base * 4096ull + 2ull * t + 1000000007ull;
+        const float u1 = urand(a.key, c), u2 = urand(a.key, c + 1);
+        const float g = sqrtf(-2.f * logf(u1));
+        const float n1 = g * cosf(6.283185307179586f * u2), n2 = g * sinf(6.283185307179586f * u2);
+        f[t] = make_float2(rr * x.x - ri * x.y + sd * n1, rr * x.y + ri * x.x + sd * n2);
+    }
+    if (lane == 0) {
+        const float* p = a.params + j * a.P;
+        const float y0 = logf(p[0]), y1 = logf(p[1]), y2 = a.has_b0 ? p[a.b0_col] : 0.f;
+        T[b * 3 + 0] = (y0 - a.tmean[0]) / a.tstd[0];
+        T[b * 3 + 1] = (y1 - a.tmean[1]) / a.tstd[1];
+        T[b * 3 + 2] = (y2 - a.tmean[2]) / a.tstd[2];
+    }
+}
+
+// residue pool entry: (Z_v - X0_v) / ||X0_v|| for voxels with a nonzero X0_v
+__global__ void k_residue(const float2* __restrict__ Z, const float2* __restrict__ X0, int64_t n,
+                          int L, int64_t cap, float2* __restrict__ pool,
+                          unsigned long long* __restrict__ count, uint64_t key) {
+    const int64_t v = (static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (v >= n) return;
+    const float2* x0 = X0 + v * L;
+    float s = 0.f;
+    for (int t = lane; t < L; t += 32) s = fmaf(x0[t].x, x0[t].x, fmaf(x0[t].y, x0[t].y, s));
+    for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (s == 0.f) return;
+    unsigned long long slot = 0;
+    if (lane == 0) slot = atomicAdd(count, 1ULL);
+    slot = __shfl_sync(0xffffffffu, slot, 0);
+    int64_t dst = static_cast<int64_t>(slot);
+    if (dst >= cap) {   // reservoir sampling once the pool is full
+        const int64_t k = static_cast<int64_t>(urand(key, slot) * static_cast<float>(slot + 1));
+        if (k >= cap) return;
+        dst = k;
+    }
+    const float inv = rsqrtf(s);
+    const float2* z = Z + v * L;
+    for (int t = lane; t < L; t += 32)
+        pool[dst * L + t] = make_float2((z[t].x - x0[t].x) * inv, (z[t].y - x0[t].y) * inv);
+}
+
+// ------------------------------------------------------------------ neighbourhood rescore
+struct GridArgs {
+    int ndim;                 // 2 or 3 (T1, T2[, B0])
+    int shape[3];
+    const float* axis[3];     // axis values (T1, T2 log-spaced; B0 linear)
+    const int32_t* cell_atom;
+    const int32_t* near_atom;   // atom of the nearest valid cell of every cell
+    int radius;
+    float tmean[3], tstd[3];
+};
+
+__device__ __forceinline__ int nearest_index(const float* ax, int n, float x, bool logscale) {
+    // axes are sorted ascending; compare in log space for T1/T2
+    int lo = 0, hi = n - 1;
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        const float a = logscale ? logf(ax[mid]) : ax[mid];
+        if (a <= x) lo = mid; else hi = mid;
+    }
+    const float a = logscale ? logf(ax[lo]) : ax[lo];
+    const float b = logscale ? logf(ax[hi]) : ax[hi];
+    return (fabsf(x - a) <= fabsf(b - x)) ? lo : hi;
+}
+
+// One warp per voxel: prediction -> nearest cell -> exact FP32 correlation of the valid atoms of
+// the neighbourhood; keeps the best 8 (score = |c|^2 / ||d||^2) for the merge.
+__global__ void k_nbhd(const float2* __restrict__ Z, int64_t n, int L, const float* __restrict__ Yp,
+                       GridArgs G, const float2* __restrict__ atoms, const float* __restrict__ inv_norm2,
+                       int cone, float* __restrict__ part_s, int32_t* __restrict__ part_i) {
+    const int64_t v = (static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (v >= n) return;
+    int c[3] = {0, 0, 0};
+    for (int k = 0; k < G.ndim; ++k) {
+        const float y = Yp[v * 3 + k] * G.tstd[k] + G.tmean[k];
+        c[k] = nearest_index(G.axis[k], G.shape[k], y, k < 2);
+    }
+    float bs[8];
+    int32_t bi[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) { bs[q] = -INFINITY; bi[q] = -1; }
+    const float2* z = Z + v * L;
+    const int r = G.radius;
+    const int r2 = G.ndim == 3 ? r : 0;
+    const int64_t center = (G.ndim == 3)
+        ? (static_cast<int64_t>(c[0]) * G.shape[1] + c[1]) * G.shape[2] + c[2]
+        : static_cast<int64_t>(c[0]) * G.shape[1] + c[1];
+    bool any = false;
+    for (int a0 = -r; a0 <= r + 1; ++a0)
+        for (int a1 = -r; a1 <= r; ++a1)
+            for (int a2 = -r2; a2 <= r2; ++a2) {
+                int32_t j;
+                if (a0 == r + 1) {        // pass after the neighbourhood: nearest valid atom
+                    if (any || a1 != -r || a2 != -r2) continue;
+                    j = G.near_atom[center];
+                } else {
+                    const int i0 = c[0] + a0, i1 = c[1] + a1, i2 = c[2] + a2;
+                    if (i0 < 0 || i0 >= G.shape[0] || i1 < 0 || i1 >= G.shape[1]) continue;
+                    if (G.ndim == 3 && (i2 < 0 || i2 >= G.shape[2])) continue;
+                    const int64_t cell = (G.ndim == 3)
+                        ? (static_cast<int64_t>(i0) * G.shape[1] + i1) * G.shape[2] + i2
+                        : static_cast<int64_t>(i0) * G.shape[1] + i1;
+                    j = G.cell_atom[cell];
+                }
+                if (j < 0) continue;
+                any = true;
+                const float2* d = atoms + static_cast<int64_t>(j) * L;
+                float re = 0.f, im = 0.f;
+                for (int t = lane; t < L; t += 32) {
+                    const float2 a = d[t], b = z[t];
+                    re = fmaf(a.x, b.x, fmaf(a.y, b.y, re));
+                    im = fmaf(a.x, b.y, fmaf(-a.y, b.x, im));
+                }
+                for (int o = 16; o; o >>= 1) {
+                    re += __shfl_xor_sync(0xffffffffu, re, o);
+                    im += __shfl_xor_sync(0xffffffffu, im, o);
+                }
+                const float w = inv_norm2[j];
+                const float s = (cone == MRF_CONE_COMPLEX) ? (re * re + im * im) * w : re * sqrtf(w);
+                if (s > bs[7]) {
+                    bs[7] = s;
+                    bi[7] = j;
+#pragma unroll
+                    for (int q = 7; q > 0; --q) {
+                        const bool up = bs[q] > bs[q - 1];
+                        const float x = bs[q], y = bs[q - 1];
+                        const int32_t ix = bi[q], iy = bi[q - 1];
+                        bs[q - 1] = up ? x : y;
+                        bs[q] = up ? y : x;
+                        bi[q - 1] = up ? ix : iy;
+                        bi[q] = up ? iy : ix;
+                    }
+                }
+            }
+    if (lane < 8) {
+        float sv = bs[0];
+        int32_t iv = bi[0];
+#pragma unroll
+        for (int q = 1; q < 8; ++q)
+            if (lane == q) { sv = bs[q]; iv = bi[q]; }
+        part_s[v * 8 + lane] = sv;
+        part_i[v * 8 + lane] = iv;
+    }
+}
+
+// voxels whose chosen atom's normalised correlation is below thr go to the fallback list
+__global__ void k_flag_low(const float2* __restrict__ Z, int64_t n, int L,
+                           const int32_t* __restrict__ idx, const float2* __restrict__ atoms,
+                           const float* __restrict__ inv_norm2, float thr, int cone,
+                           int32_t* __restrict__ list, int32_t* __restrict__ cnt_list,
+                           unsigned long long* __restrict__ cnt) {
+    const int64_t v = (static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (v >= n) return;
+    const int32_t j = idx[v];
+    const float2* z = Z + v * L;
+    const float2* d = atoms + static_cast<int64_t>(j) * L;
+    float re = 0.f, im = 0.f, s = 0.f;
+    for (int t = lane; t < L; t += 32) {
+        const float2 a = d[t], b = z[t];
+        re = fmaf(a.x, b.x, fmaf(a.y, b.y, re));
+        im = fmaf(a.x, b.y, fmaf(-a.y, b.x, im));
+        s = fmaf(b.x, b.x, fmaf(b.y, b.y, s));
+    }
+    for (int o = 16; o; o >>= 1) {
+        re += __shfl_xor_sync(0xffffffffu, re, o);
+        im += __shfl_xor_sync(0xffffffffu, im, o);
+        s += __shfl_xor_sync(0xffffffffu, s, o);
+    }
+    if (lane != 0 || s == 0.f) return;
+    const float corr = ((cone == MRF_CONE_COMPLEX) ? sqrtf(re * re + im * im) : re) *
+                       sqrtf(inv_norm2[j]) * rsqrtf(s);
+    if (corr < thr) {
+        const int p = atomicAdd(cnt_list, 1);
+        list[p] = static_cast<int32_t>(v);
+        atomicAdd(cnt + CNT_FALLBACK, 1ULL);
+    }
+}
+
+unsigned gridw(int64_t rows) { return static_cast<unsigned>((rows * 32 + kT - 1) / kT); }
+unsigned grid1(int64_t count) { return static_cast<unsigned>((count + kT - 1) / kT); }
+
+}  // namespace
+
+// ====================================================================================== model
+struct mrf_mlp {
+    mrf_dict* dict = nullptr;
+    int L = 0, H = 512, I = 0;      // I = 2L inputs
+    // parameters (FP32 master copies) in one block: W1 [I][H], b1 [H], W2 [H][H], b2 [H],
+    // W3 [H][3], b3 [3]
+    float* par = nullptr;
+    float* grad = nullptr;
+    float* m = nullptr;
+    float* v = nullptr;
+    int64_t np = 0;
+    int64_t off[6] = {};
+    float tmean[3] = {0, 0, 0}, tstd[3] = {1, 1, 1};
+    int has_b0 = 0, b0_col = 2;
+    float2* v1 = nullptr;           // [L]
+    // grid
+    int ndim = 0;
+    int shape[3] = {1, 1, 1};
+    float* axes = nullptr;          // concatenated axis values
+    int32_t* cell_atom = nullptr;
+    int32_t* near_atom = nullptr;   // atom of the nearest valid cell (grid index distance)
+    int radius = 2;
+    // residues
+    float2* pool = nullptr;
+    int64_t pool_cap = 0;
+    unsigned long long* pool_count = nullptr;
+    // workspaces for a batch of up to cap_b rows
+    int64_t cap_b = 0;
+    float2* F = nullptr;            // [B][L] raw fingerprints
+    float* X = nullptr;             // [B][I]
+    float* H1 = nullptr, *A1 = nullptr, *H2 = nullptr, *A2 = nullptr;   // [B][H]
+    float* Y = nullptr, *T = nullptr, *dY = nullptr;                  // [B][3]
+    float* dA1 = nullptr, *dA2 = nullptr;                              // [B][H]
+    double* loss = nullptr;
+    int64_t step = 0;
+    uint64_t seed = 5000;
+};
+
+namespace {
+
+template <typename T>
+mrf_status alloc(T** p, size_t count) {
+    if (*p) { cudaFree(*p); *p = nullptr; }
+    if (!count) return MRF_OK;
+    if (cudaMalloc(reinterpret_cast<void**>(p), count * sizeof(T)) != cudaSuccess) {
+        cudaGetLastError();
+        mrf_set_error("cudaMalloc failed in the learned proposal");
+        return MRF_ENOMEM;
+    }
+    return MRF_OK;
+}
+
+mrf_status ensure_batch(mrf_mlp* M, int64_t B) {
+    if (B <= M->cap_b) return MRF_OK;
+    MRF_TRY(alloc(&M->F, B * M->L));
+    MRF_TRY(alloc(&M->X, B * M->I));
+    MRF_TRY(alloc(&M->H1, B * M->H));
+    MRF_TRY(alloc(&M->A1, B * M->H));
+    MRF_TRY(alloc(&M->H2, B * M->H));
+    MRF_TRY(alloc(&M->A2, B * M->H));
+    MRF_TRY(alloc(&M->dA1, B * M->H));
+    MRF_TRY(alloc(&M->dA2, B * M->H));
+    MRF_TRY(alloc(&M->Y, B * 3));
+    MRF_TRY(alloc(&M->T, B * 3));
+    MRF_TRY(alloc(&M->dY, B * 3));
+    M->cap_b = B;
+    return MRF_OK;
+}
+
+float* P(mrf_mlp* M, int k) { return M->par + M->off[k]; }
+float* G(mrf_mlp* M, int k) { return M->grad + M->off[k]; }
+
+mrf_status forward(mrf_mlp* M, const float* X, int64_t B, cudaStream_t st) {
+    const int I = M->I, H = M->H;
+    MRF_TRY((gemm<false, false, 2>(static_cast<int>(B), H, I, X, I, P(M, 0), H, M->A1, H, P(M, 1),
+                                   M->H1, st)));
+    MRF_TRY((gemm<false, false, 2>(static_cast<int>(B), H, H, M->A1, H, P(M, 2), H, M->A2, H,
+                                   P(M, 3), M->H2, st)));
+    k_out3<<<gridw(B), kT, 0, st>>>(M->A2, B, H, P(M, 4), P(M, 5), M->Y);
+    return cudaGetLastError() == cudaSuccess ? MRF_OK : MRF_ECUDA;
+}
+
+// gradients of the MSE of (Y, T) for the batch in X; requires a forward pass on X first
+mrf_status backward(mrf_mlp* M, const float* X, int64_t B, cudaStream_t st) {
+    const int I = M->I, H = M->H;
+    MRF_CUDA_TRY(cudaMemsetAsync(M->loss, 0, sizeof(double), st));
+    k_mse<<<128, kT, 0, st>>>(M->Y, M->T, B * 3, M->dY, M->loss);
+    k_out3_back<<<H, 256, 0, st>>>(M->A2, M->dY, P(M, 4), B, H, G(M, 4), M->dA2);
+    k_colsum<<<1, 32, 0, st>>>(M->dY, B, 3, G(M, 5));
+    k_gelu_back<<<grid1(B * H), kT, 0, st>>>(M->dA2, M->H2, B * H);            // dH2
+    MRF_TRY((gemm<true, false, 0>(H, H, static_cast<int>(B), M->A1, H, M->dA2, H, G(M, 2), H,
+                                  nullptr, nullptr, st)));                       // dW2
+    k_colsum<<<(H + kT - 1) / kT, kT, 0, st>>>(M->dA2, B, H, G(M, 3));
+    MRF_TRY((gemm<false, true, 0>(static_cast<int>(B), H, H, M->dA2, H, P(M, 2), H, M->dA1, H,
+                                  nullptr, nullptr, st)));                       // dA1
+    k_gelu_back<<<grid1(B * H), kT, 0, st>>>(M->dA1, M->H1, B * H);            // dH1
+    MRF_TRY((gemm<true, false, 0>(I, H, static_cast<int>(B), X, I, M->dA1, H, G(M, 0), H, nullptr,
+                                  nullptr, st)));                                // dW1
+    k_colsum<<<(H + kT - 1) / kT, kT, 0, st>>>(M->dA1, B, H, G(M, 1));
+    return cudaGetLastError() == cudaSuccess ? MRF_OK : MRF_ECUDA;
+}
+
+mrf_status power_v1(mrf_mlp* M, cudaStream_t st) {
+    const mrf_dict* D = M->dict;
+    const int L = M->L;
+    float2* u = nullptr;
+    double* w = nullptr;
+    MRF_TRY(alloc(&u, static_cast<size_t>(D->d)));
+    mrf_status s = alloc(&w, static_cast<size_t>(2 * L));
+    if (s != MRF_OK) { cudaFree(u); return s; }
+    std::vector<float2> hv(L);
+    std::vector<double> hw(2 * L);
+    for (int t = 0; t < L; ++t) hv[t] = make_float2(1.f / std::sqrt(static_cast<float>(L)), 0.f);
+    for (int it = 0; it < 60 && s == MRF_OK; ++it) {
+        if (cudaMemcpyAsync(M->v1, hv.data(), L * sizeof(float2), cudaMemcpyHostToDevice, st) !=
+            cudaSuccess) { s = MRF_ECUDA; break; }
+        k_dv<<<gridw(D->d), kT, 0, st>>>(D->atoms, D->d, L, M->v1, u);
+        k_dhu<<<L, 256, 0, st>>>(D->atoms, D->d, L, u, w);
+        if (cudaMemcpyAsync(hw.data(), w, 2 * L * sizeof(double), cudaMemcpyDeviceToHost, st) !=
+                cudaSuccess ||
+            cudaStreamSynchronize(st) != cudaSuccess) { s = MRF_ECUDA; break; }
+        double nrm = 0.0;
+        for (int t = 0; t < 2 * L; ++t) nrm += hw[t] * hw[t];
+        nrm = std::sqrt(nrm);
+        if (!(nrm > 0.0)) { s = MRF_EINTERNAL; break; }
+        for (int t = 0; t < L; ++t)
+            hv[t] = make_float2(static_cast<float>(hw[2 * t] / nrm), static_cast<float>(hw[2 * t + 1] / nrm));
+    }
+    if (s == MRF_OK) {
+        // phase: largest-magnitude entry real and positive
+        int k = 0;
+        for (int t = 1; t < L; ++t)
+            if (std::hypot(hv[t].x, hv[t].y) > std::hypot(hv[k].x, hv[k].y)) k = t;
+        const double a = std::atan2(hv[k].y, hv[k].x), c = std::cos(-a), sn = std::sin(-a);
+        for (int t = 0; t < L; ++t) {
+            const double x = hv[t].x, y = hv[t].y;
+            hv[t] = make_float2(static_cast<float>(x * c - y * sn), static_cast<float>(x * sn + y * c));
+        }
+        if (cudaMemcpyAsync(M->v1, hv.data(), L * sizeof(float2), cudaMemcpyHostToDevice, st) !=
+                cudaSuccess ||
+            cudaStreamSynchronize(st) != cudaSuccess) s = MRF_ECUDA;
+    }
+    cudaFree(u);
+    cudaFree(w);
+    if (s != MRF_OK) mrf_set_error("power iteration for the dominant singular vector failed");
+    return s;
+}
+
+}  // namespace
+
+// ====================================================================================== ABI
+extern "C" {
+
+void mrf_default_mlp_opts(mrf_mlp_opts* o) {
+    if (!o) return;
+    std::memset(o, 0, sizeof(*o));
+    o->hidden = 512;
+    o->radius = 2;
+    o->residue_pool = 262144;
+    o->seed = 5000;
+}
+
+mrf_status mrf_mlp_create(mrf_dict* D, const float* grid_axes, const int32_t* cell_atom,
+                          const mrf_mlp_opts* opts, mrf_mlp** out, void* stream) {
+    if (!D || !out) { mrf_set_error("dict and out are required"); return MRF_EINVAL; }
+    *out = nullptr;
+    const int nd = static_cast<int>(D->grid_shape.size());
+    if (nd < 2 || nd > 3 || D->P < nd || !D->params) {
+        mrf_set_error("the learned proposal needs a dictionary built with params (T1, T2[, B0]) "
+                      "and a grid_shape of 2 or 3 dimensions in that order");
+        return MRF_EINVAL;
+    }
+    if (!grid_axes || !cell_atom) { mrf_set_error("grid_axes and cell_atom are required"); return MRF_EINVAL; }
+    mrf_mlp_opts o;
+    if (opts) o = *opts; else mrf_default_mlp_opts(&o);
+    if (o.hidden < 8 || o.hidden > 4096 || o.radius < 0 || o.radius > 8 || o.residue_pool < 0) {
+        mrf_set_error("bad mlp options");
+        return MRF_EINVAL;
+    }
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    mrf_mlp* M = new mrf_mlp();
+    M->dict = D;
+    M->L = D->L;
+    M->I = 2 * D->L;
+    M->H = o.hidden;
+    M->radius = o.radius;
+    M->seed = o.seed;
+    M->ndim = nd;
+    int64_t cells = 1, naxis = 0;
+    for (int k = 0; k < nd; ++k) { M->shape[k] = D->grid_shape[k]; cells *= M->shape[k]; naxis += M->shape[k]; }
+    M->has_b0 = nd == 3;
+    M->b0_col = 2;
+    const int I = M->I, H = M->H;
+    const int64_t sizes[6] = {static_cast<int64_t>(I) * H, H, static_cast<int64_t>(H) * H, H, H * 3, 3};
+    M->np = 0;
+    for (int k = 0; k < 6; ++k) { M->off[k] = M->np; M->np += sizes[k]; }
+    mrf_status s = MRF_OK;
+    auto bail = [&](mrf_status e) { mrf_mlp_free(M); return e; };
+    if ((s = alloc(&M->par, M->np)) || (s = alloc(&M->grad, M->np)) || (s = alloc(&M->m, M->np)) ||
+        (s = alloc(&M->v, M->np)) || (s = alloc(&M->v1, static_cast<size_t>(M->L))) ||
+        (s = alloc(&M->axes, static_cast<size_t>(naxis))) ||
+        (s = alloc(&M->cell_atom, static_cast<size_t>(cells))) ||
+        (s = alloc(&M->near_atom, static_cast<size_t>(cells))) || (s = alloc(&M->loss, 1)) ||
+        (s = alloc(&M->pool_count, 1)))
+        return bail(s);
+    if (o.residue_pool > 0 && (s = alloc(&M->pool, static_cast<size_t>(o.residue_pool) * M->L)))
+        return bail(s);
+    M->pool_cap = o.residue_pool;
+    // He-normal initialisation (SplitMix64 + Box-Muller on the host), zero biases
+    std::vector<float> hp(M->np, 0.f);
+    uint64_t state = o.seed;
+    auto next = [&]() {
+        state += 0x9E3779B97F4A7C15ull;
+        uint64_t z = state;
+        z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+        z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+        z ^= z >> 31;
+        return (static_cast<double>(z >> 11) + 0.5) * (1.0 / 9007199254740992.0);
+    };
+    const int fan[3] = {I, H, H};
+    const int wk[3] = {0, 2, 4};
+    for (int l = 0; l < 3; ++l) {
+        const double sd = std::sqrt(2.0 / fan[l]);
+        for (int64_t i = 0; i < sizes[wk[l]]; ++i) {
+            const double u1 = next(), u2 = next();
+            hp[M->off[wk[l]] + i] = static_cast<float>(sd * std::sqrt(-2.0 * std::log(u1)) *
+                                                       std::cos(6.283185307179586 * u2));
+        }
+    }
+    // target standardisation from the dictionary's parameters
+    std::vector<float> prm(static_cast<size_t>(D->d) * D->P);
+    if (cudaMemcpy(prm.data(), D->params, prm.size() * sizeof(float), cudaMemcpyDeviceToHost) !=
+        cudaSuccess) return bail(MRF_ECUDA);
+    for (int k = 0; k < 3; ++k) {
+        if (k == 2 && !M->has_b0) { M->tmean[k] = 0.f; M->tstd[k] = 1.f; continue; }
+        double s1 = 0.0, s2 = 0.0;
+        for (int64_t j = 0; j < D->d; ++j) {
+            const double y = (k < 2) ? std::log(prm[j * D->P + k]) : prm[j * D->P + M->b0_col];
+            s1 += y;
+            s2 += y * y;
+        }
+        const double mu = s1 / D->d, var = s2 / D->d - mu * mu;
+        M->tmean[k] = static_cast<float>(mu);
+        M->tstd[k] = static_cast<float>(var > 1e-12 ? std::sqrt(var) : 1.0);
+    }
+    // nearest valid cell of every cell: multi-source breadth-first search over the grid
+    std::vector<int32_t> near(cell_atom, cell_atom + cells);
+    {
+        std::vector<int64_t> frontier;
+        for (int64_t c = 0; c < cells; ++c)
+            if (near[c] >= 0) frontier.push_back(c);
+        if (frontier.empty()) {
+            mrf_set_error("cell_atom has no valid cell");
+            return bail(MRF_EINVAL);
+        }
+        const int64_t st1 = (nd == 3) ? M->shape[2] : 1;
+        const int64_t st0 = st1 * M->shape[1];
+        const int64_t strides[3] = {st0, st1, 1};
+        while (!frontier.empty()) {
+            std::vector<int64_t> next;
+            for (int64_t c : frontier) {
+                int64_t rem = c;
+                for (int k = 0; k < nd; ++k) {
+                    const int64_t ik = rem / strides[k];
+                    rem -= ik * strides[k];
+                    for (int dlt = -1; dlt <= 1; dlt += 2) {
+                        const int64_t jk = ik + dlt;
+                        if (jk < 0 || jk >= M->shape[k]) continue;
+                        const int64_t nb = c + dlt * strides[k];
+                        if (near[nb] < 0) { near[nb] = near[c]; next.push_back(nb); }
+                    }
+                }
+            }
+            frontier.swap(next);
+        }
+    }
+    if (cudaMemcpyAsync(M->par, hp.data(), M->np * sizeof(float), cudaMemcpyHostToDevice, st) ||
+        cudaMemcpyAsync(M->near_atom, near.data(), cells * sizeof(int32_t), cudaMemcpyHostToDevice, st) ||
+        cudaMemsetAsync(M->m, 0, M->np * sizeof(float), st) ||
+        cudaMemsetAsync(M->v, 0, M->np * sizeof(float), st) ||
+        cudaMemsetAsync(M->pool_count, 0, sizeof(unsigned long long), st) ||
+        cudaMemcpyAsync(M->axes, grid_axes, naxis * sizeof(float), cudaMemcpyHostToDevice, st) ||
+        cudaMemcpyAsync(M->cell_atom, cell_atom, cells * sizeof(int32_t), cudaMemcpyHostToDevice, st))
+        return bail(MRF_ECUDA);
+    if ((s = power_v1(M, st)) != MRF_OK) return bail(s);
+    *out = M;
+    return MRF_OK;
+}
+
+void mrf_mlp_free(mrf_mlp* M) {
+    if (!M) return;
+    if (M->dict && M->dict->mlp == M) M->dict->mlp = nullptr;
+    void* ptrs[] = {M->par, M->grad, M->m, M->v, M->v1, M->axes, M->cell_atom, M->near_atom, M->pool,
+                    M->pool_count, M->F, M->X, M->H1, M->A1, M->H2, M->A2, M->Y, M->T, M->dY,
+                    M->dA1, M->dA2, M->loss};
+    for (void* p : ptrs)
+        if (p) cudaFree(p);
+    delete M;
+}
+
+mrf_status mrf_mlp_add_residues(mrf_mlp* M, const void* Z, const void* X0, int64_t n,
+                                void* stream) {
+    if (!M || !M->dict || (n > 0 && (!Z || !X0)) || n < 0) {
+        mrf_set_error("bad arguments (or the model's dictionary was freed)");
+        return MRF_EINVAL;
+    }
+    if (!M->pool || n == 0) return MRF_OK;
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    k_residue<<<gridw(n), kT, 0, st>>>(static_cast<const float2*>(Z), static_cast<const float2*>(X0),
+                                       n, M->L, M->pool_cap, M->pool, M->pool_count,
+                                       M->seed ^ 0x5eedull);
+    MRF_CUDA_TRY(cudaGetLastError());
+    return MRF_OK;
+}
+
+mrf_status mrf_mlp_train(mrf_mlp* M, const mrf_train_opts* opts, float* loss_history,
+                         void* stream) {
+    if (!M || !opts || !M->dict) {
+        mrf_set_error("mlp and opts are required (and the model's dictionary must be alive)");
+        return MRF_EINVAL;
+    }
+    const mrf_train_opts& o = *opts;
+    if (o.steps < 0 || o.batch < 1 || o.batch > 65536 || !(o.lr > 0.f) || o.snr_lo > o.snr_hi ||
+        o.p_residue < 0.f || o.p_residue > 1.f) {
+        mrf_set_error("bad training options");
+        return MRF_EINVAL;
+    }
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    const int64_t B = o.batch;
+    MRF_TRY(ensure_batch(M, B));
+    unsigned long long pc = 0;
+    MRF_CUDA_TRY(cudaMemcpyAsync(&pc, M->pool_count, sizeof(pc), cudaMemcpyDeviceToHost, st));
+    MRF_CUDA_TRY(cudaStreamSynchronize(st));
+    const mrf_dict* D = M->dict;
+    SynthArgs a;
+    a.atoms = D->atoms;
+    a.inv_norm2 = D->inv_norm2;
+    a.params = D->params;
+    a.P = D->P;
+    a.d = D->d;
+    a.L = M->L;
+    a.residues = M->pool;
+    a.R = static_cast<int64_t>(pc < static_cast<unsigned long long>(M->pool_cap) ? pc : M->pool_cap);
+    a.p_res = o.p_residue;
+    a.snr_lo = o.snr_lo;
+    a.snr_hi = o.snr_hi;
+    a.has_b0 = M->has_b0;
+    a.b0_col = M->b0_col;
+    for (int k = 0; k < 3; ++k) { a.tmean[k] = M->tmean[k]; a.tstd[k] = M->tstd[k]; }
+    a.key = M->seed * 0x100000001B3ull + 17ull;
+    const float b1 = 0.9f, b2 = 0.999f, eps = 1e-8f;
+    for (int s = 0; s < o.steps; ++s) {
+        k_synth<<<gridw(B), kT, 0, st>>>(a, B, static_cast<uint64_t>(M->step), M->F, M->T);
+        k_canon<<<gridw(B), kT, 0, st>>>(M->F, nullptr, B, M->L, M->v1, M->X);
+        MRF_TRY(forward(M, M->X, B, st));
+        MRF_TRY(backward(M, M->X, B, st));
+        ++M->step;
+        const float c1 = 1.f - std::pow(b1, static_cast<float>(M->step));
+        const float c2 = 1.f - std::pow(b2, static_cast<float>(M->step));
+        k_adam<<<grid1(M->np), kT, 0, st>>>(M->par, M->grad, M->m, M->v, M->np, o.lr, b1, b2, eps,
+                                            c1, c2);
+        if (loss_history) {
+            double l = 0.0;
+            MRF_CUDA_TRY(cudaMemcpyAsync(&l, M->loss, sizeof(l), cudaMemcpyDeviceToHost, st));
+            MRF_CUDA_TRY(cudaStreamSynchronize(st));
+            loss_history[s] = static_cast<float>(l);
+        }
+    }
+    MRF_CUDA_TRY(cudaGetLastError());
+    return MRF_OK;
+}
+
+mrf_status mrf_mlp_params(mrf_mlp* M, float* host_params, int32_t set, int64_t* count) {
+    if (!M) { mrf_set_error("mlp is NULL"); return MRF_EINVAL; }
+    if (count) *count = M->np;
+    if (!host_params) return MRF_OK;
+    cudaError_t e = set ? cudaMemcpy(M->par, host_params, M->np * sizeof(float), cudaMemcpyHostToDevice)
+                        : cudaMemcpy(host_params, M->par, M->np * sizeof(float), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) { mrf_set_error(cudaGetErrorString(e)); return MRF_ECUDA; }
+    return MRF_OK;
+}
+
+mrf_status mrf_mlp_grad(mrf_mlp* M, const float* X, const float* T, int64_t B, float* Y_out,
+                        float* grads_out, double* loss_out, void* stream) {
+    if (!M || !X || B < 1 || B > 65536) { mrf_set_error("bad arguments"); return MRF_EINVAL; }
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    MRF_TRY(ensure_batch(M, B));
+    MRF_TRY(forward(M, X, B, st));
+    if (Y_out) MRF_CUDA_TRY(cudaMemcpyAsync(Y_out, M->Y, B * 3 * sizeof(float), cudaMemcpyDefault, st));
+    if (T) {
+        MRF_CUDA_TRY(cudaMemcpyAsync(M->T, T, B * 3 * sizeof(float), cudaMemcpyDefault, st));
+        MRF_TRY(backward(M, X, B, st));
+        if (grads_out)
+            MRF_CUDA_TRY(cudaMemcpyAsync(grads_out, M->grad, M->np * sizeof(float), cudaMemcpyDefault, st));
+        if (loss_out) MRF_CUDA_TRY(cudaMemcpyAsync(loss_out, M->loss, sizeof(double), cudaMemcpyDefault, st));
+    }
+    MRF_CUDA_TRY(cudaStreamSynchronize(st));
+    return MRF_OK;
+}
+
+mrf_status mrf_mlp_canonical(mrf_mlp* M, const void* Z, int64_t n, float* X, float* v1_host,
+                             float* tstats_host, void* stream) {
+    if (!M || n < 0 || (n > 0 && (!Z || !X))) { mrf_set_error("bad arguments"); return MRF_EINVAL; }
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    if (n > 0) {
+        k_canon<<<gridw(n), kT, 0, st>>>(static_cast<const float2*>(Z), nullptr, n, M->L, M->v1, X);
+        MRF_CUDA_TRY(cudaGetLastError());
+    }
+    if (v1_host) MRF_CUDA_TRY(cudaMemcpyAsync(v1_host, M->v1, M->L * sizeof(float2), cudaMemcpyDeviceToHost, st));
+    if (tstats_host) {
+        for (int k = 0; k < 3; ++k) { tstats_host[k] = M->tmean[k]; tstats_host[3 + k] = M->tstd[k]; }
+    }
+    MRF_CUDA_TRY(cudaStreamSynchronize(st));
+    return MRF_OK;
+}
+
+mrf_status mrf_dict_attach_mlp(mrf_dict* D, mrf_mlp* M) {
+    if (!D) { mrf_set_error("dict is NULL"); return MRF_EINVAL; }
+    if (M && M->dict != D) { mrf_set_error("the model was created for another dictionary"); return MRF_EINVAL; }
+    D->mlp = M;
+    return MRF_OK;
+}
+
+}  // extern "C"
+
+void mlp_detach(mrf_mlp* M) {
+    if (M) M->dict = nullptr;
+}
+
+// Learned projection of n queries: candidates into part (S = 1, K = 8) for the merge; voxels below
+// the threshold are listed afterwards by learned_flag (needs the merged indices).
+mrf_status learned_candidates(mrf_dict* D, const float2* Z, int64_t n, int cone, float* part_s,
+                              int32_t* part_i, cudaStream_t st) {
+    mrf_mlp* M = D->mlp;
+    if (!M) {
+        mrf_set_error("no learned model attached (mrf_dict_attach_mlp)");
+        return MRF_EUNSUPPORTED;
+    }
+    const int64_t chunk = 16384;
+    MRF_TRY(ensure_batch(M, std::min<int64_t>(chunk, n)));
+    GridArgs G;
+    G.ndim = M->ndim;
+    int64_t o = 0;
+    for (int k = 0; k < 3; ++k) {
+        G.shape[k] = M->shape[k];
+        G.axis[k] = M->axes + o;
+        if (k < M->ndim) o += M->shape[k];
+        G.tmean[k] = M->tmean[k];
+        G.tstd[k] = M->tstd[k];
+    }
+    G.cell_atom = M->cell_atom;
+    G.near_atom = M->near_atom;
+    G.radius = M->radius;
+    for (int64_t s = 0; s < n; s += chunk) {
+        const int64_t b = std::min(chunk, n - s);
+        k_canon<<<gridw(b), kT, 0, st>>>(Z + s * M->L, nullptr, b, M->L, M->v1, M->X);
+        MRF_TRY(forward(M, M->X, b, st));
+        k_nbhd<<<gridw(b), kT, 0, st>>>(Z + s * M->L, b, M->L, M->Y, G, D->atoms, D->inv_norm2,
+                                       cone, part_s + s * 8, part_i + s * 8);
+    }
+    MRF_CUDA_TRY(cudaGetLastError());
+    return MRF_OK;
+}
+
+mrf_status learned_flag(mrf_dict* D, const float2* Z, int64_t n, const int32_t* idx, float thr,
+                        int cone, int32_t* list, int32_t* cnt_list, cudaStream_t st) {
+    k_flag_low<<<gridw(n), kT, 0, st>>>(Z, n, D->L, idx, D->atoms, D->inv_norm2, thr, cone, list,
+                                        cnt_list, D->counters);
+    MRF_CUDA_TRY(cudaGetLastError());
+    return MRF_OK;
+}

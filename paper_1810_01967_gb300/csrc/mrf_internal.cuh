@@ -58,6 +58,7 @@ struct mrf_dict {
     unsigned long long* counters = nullptr;   // [CNT_N]
     double* red = nullptr;          // [8] reductions (norms for the step rule / kappa)
     CoverTreeDev* tree = nullptr;
+    mrf_mlp* mlp = nullptr;          // attached learned proposal (not owned)
     int num_sms = 148;
     mrf_tune tune = {};              // requested geometry (0 = default) and last launches
 };
@@ -119,6 +120,12 @@ mrf_status launch_ct_search(const float2* Z, int64_t n, const mrf_dict* D, int c
 mrf_status ct_info(const mrf_dict* D, mrf_tree_info* info);
 mrf_status ct_export(const mrf_dict* D, int32_t* first_level, int32_t* parent, int32_t* rep,
                      int32_t* en_atom, int32_t* en_level, float* en_maxdist);
+// mlp.cu
+void mlp_detach(mrf_mlp* M);
+mrf_status learned_candidates(mrf_dict* D, const float2* Z, int64_t n, int cone, float* part_s,
+                              int32_t* part_i, cudaStream_t st);
+mrf_status learned_flag(mrf_dict* D, const float2* Z, int64_t n, const int32_t* idx, float thr,
+                        int cone, int32_t* list, int32_t* cnt_list, cudaStream_t st);
 // merge.cu
 mrf_status launch_merge(const float2* Z, int64_t n, const mrf_dict* D, int cone, int K, int S,
                         const float* part_s, const int32_t* part_i, const int32_t* vlist,
