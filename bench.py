@@ -154,10 +154,42 @@ def make_workload(slice_idx: int):
     return dic, p
 
 
-def reconstruction_quality(mrf, D, op, p, dic, dev, stream, iters: int) -> dict:
-    """Whole reconstructions (iters BLIP iterations) with the BF16 and the FP32 exhaustive
-    projections: time per slice, matches/s, T1/T2 accuracy against the phantom (mask rho != 0),
-    their atom agreement, and the first iteration's agreement with the FP64 oracle on a voxel
+def train_learned(mrf, D, dic, dev, phantoms: int = 64, steps: int = 2000):
+    """Learned proposal for the workload's dictionary: aliasing residues from 4 IPG iterates of
+    `phantoms` seeded 96x96 training phantoms, then `steps` Adam steps of 1024 synthetic
+    fingerprints (2M at the defaults).  Returns (model, seconds of GPU training)."""
+    import torch
+    import mrfgen
+    M = mrf.MLP(D, dic["axes"], dic["cell_atom"], hidden=512)
+    for k in range(phantoms):
+        pk = mrfgen.make_problem(2, i=1000 + k, dic=dic, N=96)
+        Ny, Nx, L = pk["Ny"], pk["Nx"], pk["L"]
+        n = Ny * Nx
+        opk = mrf.make_op(Ny, Nx, L, torch.from_numpy(pk["masks"]).to(dev))
+        AHY = torch.empty((n, L), dtype=torch.complex64, device=dev)
+        mrf.adjoint(opk, torch.from_numpy(pk["Y"]).to(dev), AHY)
+        X0 = torch.from_numpy(pk["X0"]).to(dev)
+        X = torch.zeros((n, L), dtype=torch.complex64, device=dev)
+        idx = torch.zeros(n, dtype=torch.int32, device=dev)
+        Zk = torch.empty_like(X)
+        for _ in range(4):
+            mrf.gradient(D, opk, AHY, X, 1.0, Zk)
+            M.add_residues(Zk, X0)
+            mrf.ipg_step(D, opk, AHY, X, 1.0, idx, opts=mrf.proj_opts(mode="bf16", certify=False))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    hist = M.train(steps=steps, batch=1024, lr=1e-3, history=True)
+    torch.cuda.synchronize()
+    return M, time.perf_counter() - t0, hist
+
+
+def reconstruction_quality(mrf, D, op, p, dic, dev, stream, iters: int, fp32: bool = True,
+                           forms: bool = True) -> dict:
+    """Whole reconstructions (iters BLIP / CoverBLIP iterations) of the slice with every form of
+    the projection -- BF16 exhaustive, FP32 exhaustive (the plain comparator), cover tree
+    (eps = 0.4, CoverBLIP) and the learned proposal (threshold 0.98) -- reporting time per slice,
+    matches/s, T1/T2 accuracy against the phantom (mask rho != 0), B0 error, atom agreement with
+    FP32, the search work, and the first iteration's agreement with the FP64 oracle on a voxel
     sample (both sides start from the generator's k-space)."""
     import torch
     from oracle import mrf_oracle as mo
@@ -167,15 +199,31 @@ def reconstruction_quality(mrf, D, op, p, dic, dev, stream, iters: int) -> dict:
     fg = ph["labels"] >= 0
     Yd = torch.from_numpy(p["Y"]).to(dev)
     out, idxs = {}, {}
-    for mode in ("bf16", "fp32"):
+    runs = [("bf16", {})]
+    if fp32:
+        runs.append(("fp32", {}))
+    if forms:
+        t0 = time.perf_counter()
+        D.close()
+        D2 = mrf.build_dict_index(dic["atoms"], dic["params"], grid_shape=dic["grid_shape"],
+                                  build_tree=True)
+        out["tree_build_s"] = time.perf_counter() - t0
+        M, tsec, hist = train_learned(mrf, D2, dic, dev)
+        mrf.attach_mlp(D2, M)
+        out["learned_train"] = {"gpu_s": tsec, "fingerprints": 2000 * 1024,
+                                "loss_first": float(hist[:20].mean()),
+                                "loss_last": float(hist[-100:].mean())}
+        D = D2
+        runs += [("covertree", {"eps": 0.4}), ("learned", {"fallback_thr": 0.98})]
+    for mode, kw in runs:
         X = torch.empty((n, L), dtype=torch.complex64, device=dev)
         idx = torch.empty(n, dtype=torch.int32, device=dev)
         prm = torch.empty((n, dic["params"].shape[1]), dtype=torch.float32, device=dev)
-        ro = mrf.recon_opts(iters=iters, mode=mode, certify=False)
+        ro = mrf.recon_opts(iters=iters, mode=mode, certify=False, **kw)
         a = torch.cuda.Event(enable_timing=True)
         b = torch.cuda.Event(enable_timing=True)
         a.record(stream)
-        mrf.reconstruct(D, op, Yd, X, idx, None, prm, opts=ro)
+        st = mrf.reconstruct(D, op, Yd, X, idx, None, prm, opts=ro, stats=True)
         b.record(stream)
         torch.cuda.synchronize()
         s = a.elapsed_time(b) / 1e3
@@ -184,8 +232,12 @@ def reconstruction_quality(mrf, D, op, p, dic, dev, stream, iters: int) -> dict:
         out[mode] = {"s_per_slice": s, "iters": iters, "matches_per_s": n * d * iters / s,
                      "T1_acc": mo.accuracy(pr[:, 0], ph["T1"], fg),
                      "T2_acc": mo.accuracy(pr[:, 1], ph["T2"], fg),
-                     "B0_mae_hz": float(np.mean(np.abs(pr[fg, 2] - ph["B0"][fg])))}
-    out["bf16_vs_fp32_atom_agreement"] = float(np.mean(idxs["bf16"] == idxs["fp32"]))
+                     "B0_mae_hz": float(np.mean(np.abs(pr[fg, 2] - ph["B0"][fg]))),
+                     "exhaustive_fallback_voxel_iters": st["n_fallback"],
+                     "tree_distance_evals": st["n_dist_evals"], **kw}
+    for mode in idxs:
+        if "fp32" in idxs:
+            out[mode]["atom_agreement_vs_fp32"] = float(np.mean(idxs[mode] == idxs["fp32"]))
     # first iteration (template matching) against the oracle on a seeded sample
     g = np.random.Generator(np.random.PCG64(99))
     sel = np.sort(g.choice(np.flatnonzero(fg), 192, replace=False))
@@ -194,6 +246,8 @@ def reconstruction_quality(mrf, D, op, p, dic, dev, stream, iters: int) -> dict:
     AHY = torch.empty((n, L), dtype=torch.complex64, device=dev)
     mrf.adjoint(op, Yd, AHY)
     for mode in ("bf16", "fp32"):
+        if mode not in out:
+            continue
         idx = torch.empty(n, dtype=torch.int32, device=dev)
         rho = torch.empty(n, dtype=torch.complex64, device=dev)
         mrf.project(D, AHY, idx, rho, opts=mrf.proj_opts(mode=mode, certify=False))
@@ -382,7 +436,8 @@ def run_ours(args) -> None:
     # ------------------------------------------------------------- quality (rank 0)
     quality = None
     if rank == 0 and not args.no_quality:
-        quality = reconstruction_quality(mrf, D, op, p, dic, dev, stream, args.iters)
+        quality = reconstruction_quality(mrf, D, op, p, dic, dev, stream, args.iters,
+                                         fp32=not args.no_fp32, forms=not args.no_forms)
     if world > 1:
         dist.barrier()
     if rank != 0:
@@ -416,7 +471,7 @@ def run_ours(args) -> None:
             "dtype": "bf16" if args.mode == "bf16" else "f32", "data": "synthetic",
             "config": {"workload": WORKLOAD, "n_voxels": n, "L": L, "d": d,
                        "step": "one BLIP iteration (ipg_step) + look-up table",
-                       "projection": args.mode, "topk": 8, "certify": True,
+                       "projection": args.mode, "topk": 16 if args.mode == "bf16" else 8, "certify": False,
                        "l2": "inputs larger than L2 (BF16 dictionary operand 800 MB)"},
             "roofline": roof, "cpu_baseline": cpu,
             "e2e": {"value": world * n * d * e2e_steps / e2e_s, "unit": UNIT,
@@ -439,10 +494,12 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--iters", type=int, default=20)
     ap.add_argument("--no-quality", action="store_true")
+    ap.add_argument("--no-fp32", action="store_true", help="skip the 25 s FP32 reconstruction")
+    ap.add_argument("--no-forms", action="store_true", help="skip the cover tree and learned forms")
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--mode", default="bf16", choices=["bf16", "fp32"])
-    ap.add_argument("--fp32-sample", type=int, default=512)
+    ap.add_argument("--fp32-sample", type=int, default=0)
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--profile-case", type=int, default=0,
                     help="projection-only small case with N voxels (for ncu captures)")

@@ -341,6 +341,38 @@ mrf_status mrf_mlp_canonical(mrf_mlp* mlp, const void* Z, int64_t n, float* X, f
 /* Use `mlp` for MRF_PROJ_LEARNED projections of `dict` (NULL detaches). */
 mrf_status mrf_dict_attach_mlp(mrf_dict* dict, mrf_mlp* mlp);
 
+/*
+ * Batches of slices (the batching form: many slices of different sizes through whole BLIP
+ * iterations).  The slices share the dictionary; all of them stay resident, stacked voxel-major,
+ * and each iteration is every slice's gradient step followed by one projection of all stacked
+ * voxels (one persistent launch of the search).  With use_graph the iteration is captured once
+ * into a CUDA graph and replayed (projections without host synchronisation only: FP32 or BF16,
+ * with certify = 0).  The masks of `ops` are read at every iteration and must stay alive.
+ */
+typedef struct mrf_batch mrf_batch;
+
+/* n_slices operators (their L must be the dictionary's).  Allocates the stacked buffers and the
+ * dictionary's scratch for the total voxel count. */
+mrf_status mrf_batch_create(mrf_dict* dict, int32_t n_slices, const mrf_op* ops,
+                            mrf_batch** out);
+void mrf_batch_free(mrf_batch* batch);
+
+/* A^H Y of every slice (Y: host array of n_slices device pointers to complex64 [Ny][Nx][L])
+ * into the batch; X = 0 and the warm-start atoms = 0. */
+mrf_status mrf_batch_load(mrf_batch* batch, const void* const* Y, void* stream);
+
+/* `iters` iterations (step mu, projection `opts`) over all slices, asynchronous on `stream`. */
+mrf_status mrf_batch_run(mrf_batch* batch, int32_t iters, float mu, const mrf_proj_opts* opts,
+                         int32_t use_graph, void* stream);
+
+/* Device pointers to slice s's rows of the stacked image, atoms and densities; its voxel count
+ * and offset (any output may be NULL). */
+mrf_status mrf_batch_slice(mrf_batch* batch, int32_t s, void** X, int32_t** idx, void** rho,
+                           int64_t* n, int64_t* offset);
+
+/* Look-up table of all stacked voxels: params_out device float32 [sum n_s][P]. */
+mrf_status mrf_batch_lut(mrf_batch* batch, float* params_out, void* stream);
+
 /* Look-up table Theta_v = params[idx_v] (Algorithm 2, last step): device int32 [n] ->
  * device float32 [n][P]. */
 mrf_status mrf_lut(const mrf_dict* dict, const int32_t* idx, int64_t n, float* params_out,

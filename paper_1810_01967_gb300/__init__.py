@@ -310,6 +310,66 @@ class MLP:
         return v1, ts
 
 
+class Batch:
+    """Slices of different sizes reconstructed together (mrf_batch)."""
+
+    def __init__(self, D: Dictionary, ops):
+        arr = (Op * len(ops))(*ops)
+        h = C.c_void_p()
+        _check(lib().mrf_batch_create(D.handle, len(ops), arr, C.byref(h)))
+        self.handle, self.dict, self._ops = h, D, list(ops)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            lib().mrf_batch_free(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def load(self, Ys, stream=None):
+        ptrs = (C.c_void_p * len(Ys))(*[_ptr(y) for y in Ys])
+        self._Ys = list(Ys)
+        _check(lib().mrf_batch_load(self.handle, ptrs, _stream(stream)))
+
+    def run(self, iters: int, mu: float = 1.0, opts=None, use_graph: bool = False, stream=None):
+        o = opts or proj_opts()
+        _check(lib().mrf_batch_run(self.handle, iters, mu, C.byref(o), int(use_graph),
+                                   _stream(stream)))
+
+    def slice(self, s: int) -> dict:
+        X, idx, rho = C.c_void_p(), C.c_void_p(), C.c_void_p()
+        n, off = C.c_int64(), C.c_int64()
+        _check(lib().mrf_batch_slice(self.handle, s, C.byref(X), C.byref(idx), C.byref(rho),
+                                     C.byref(n), C.byref(off)))
+        return {"X": X.value, "idx": idx.value, "rho": rho.value, "n": n.value,
+                "offset": off.value}
+
+    def views(self, s: int) -> dict:
+        """Zero-copy torch views of slice s's rows: X complex64 [n, L], idx int32 [n],
+        rho complex64 [n] (valid while the batch lives)."""
+        import torch
+        v = self.slice(s)
+        n, L = v["n"], self._ops[0].L
+
+        class _Dev:
+            def __init__(self, ptr, shape, typestr):
+                self.__cuda_array_interface__ = {"data": (ptr, False), "shape": shape,
+                                                 "typestr": typestr, "version": 2}
+
+        X = torch.as_tensor(_Dev(v["X"], (n, 2 * L), "<f4"), device="cuda")
+        rho = torch.as_tensor(_Dev(v["rho"], (n, 2), "<f4"), device="cuda")
+        idx = torch.as_tensor(_Dev(v["idx"], (n,), "<i4"), device="cuda")
+        return {"X": X.view(torch.complex64), "idx": idx, "rho": rho.view(torch.complex64)[:, 0],
+                "n": n, "offset": v["offset"]}
+
+    def lut(self, params_out, stream=None):
+        _check(lib().mrf_batch_lut(self.handle, _ptr(params_out), _stream(stream)))
+
+
 def attach_mlp(D: Dictionary, mlp) -> None:
     _check(lib().mrf_dict_attach_mlp(D.handle, None if mlp is None else mlp.handle))
     D._mlp = mlp

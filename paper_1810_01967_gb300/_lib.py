@@ -135,6 +135,15 @@ SIGNATURES = {
     "mrf_mlp_canonical": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p,
                                     C.c_void_p, C.c_void_p]),
     "mrf_dict_attach_mlp": (C.c_int, [C.c_void_p, C.c_void_p]),
+    "mrf_batch_create": (C.c_int, [C.c_void_p, C.c_int32, C.c_void_p, C.POINTER(C.c_void_p)]),
+    "mrf_batch_free": (None, [C.c_void_p]),
+    "mrf_batch_load": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
+    "mrf_batch_run": (C.c_int, [C.c_void_p, C.c_int32, C.c_float, C.POINTER(ProjOpts), C.c_int32,
+                                C.c_void_p]),
+    "mrf_batch_slice": (C.c_int, [C.c_void_p, C.c_int32, C.POINTER(C.c_void_p),
+                                  C.POINTER(C.c_void_p), C.POINTER(C.c_void_p),
+                                  C.POINTER(C.c_int64), C.POINTER(C.c_int64)]),
+    "mrf_batch_lut": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
     "mrf_status_str": (C.c_char_p, [C.c_int]),
     "mrf_last_error": (C.c_char_p, []),
 }

@@ -41,6 +41,8 @@ mrf_status dalloc(T** p, size_t count) {
 std::mutex g_plan_mu;
 std::map<std::tuple<int, int, int, int>, cufftHandle> g_plans;
 
+}  // namespace
+
 mrf_status get_plan(int kind, int Ny, int Nx, int L, cudaStream_t st, cufftHandle* out) {
     std::lock_guard<std::mutex> lk(g_plan_mu);
     auto key = std::make_tuple(kind, Ny, Nx, L);
@@ -77,6 +79,8 @@ mrf_status fft_exec(cufftHandle h, const float2* in, float2* out, int dir) {
         return fail(MRF_ECUDA, "cufftExecC2C failed: " + std::to_string(static_cast<int>(r)));
     return MRF_OK;
 }
+
+namespace {
 
 mrf_status check_op(const mrf_op* op) {
     if (!op || !op->mask) return fail(MRF_EINVAL, "op or op->mask is NULL");
@@ -166,7 +170,10 @@ mrf_status read_stats(mrf_dict* D, int64_t n, mrf_stats* stats, cudaStream_t st)
     return MRF_OK;
 }
 
+}  // namespace
+
 // ------------------------------------------------------------------------------ profiler
+namespace {
 struct ProfEntry {
     int stage;
     int launches;
@@ -182,6 +189,8 @@ void prof_clear() {
     g_prof_pending.clear();
     for (int i = 0; i < MRF_PROFILE_STAGES; ++i) { g_prof_ms[i] = 0.0; g_prof_launch[i] = 0; }
 }
+
+}  // namespace
 
 // Records an event pair around a stage on `st` while profiling is enabled.
 struct ProfScope {
@@ -203,6 +212,7 @@ struct ProfScope {
     }
 };
 
+namespace {
 mrf_status bf16_margin(const mrf_dict* D, const mrf_proj_opts* o, float* m) {
     // |c~ - c| <= (2u + u^2) ||d|| ||z|| for BF16 operand rounding (u = 2^-9) plus the FP32
     // accumulation of 2L products; in normalised-correlation units
@@ -210,6 +220,22 @@ mrf_status bf16_margin(const mrf_dict* D, const mrf_proj_opts* o, float* m) {
                               : static_cast<float>(std::ldexp(1.0, -8) + std::ldexp(1.0, -18) +
                                                    2.0 * D->L * std::ldexp(1.0, -24));
     return MRF_OK;
+}
+
+}  // namespace
+
+mrf_status dict_ensure_scratch(mrf_dict* D, int64_t n) { return ensure_scratch(D, n); }
+
+bool profiler_suspend() {
+    const bool was = g_prof_on;
+    g_prof_on = false;
+    return was;
+}
+void profiler_resume(bool was) { g_prof_on = was; }
+
+mrf_status check_op_public(const mrf_op* op) { return check_op(op); }
+mrf_status check_proj_public(const mrf_dict* D, const mrf_proj_opts* o) {
+    return check_proj_opts(D, o);
 }
 
 // Exhaustive projection of the voxels listed in D->vlist (cnt of them, length in D->nlist[0]):
@@ -368,20 +394,29 @@ mrf_status project_core(mrf_dict* D, const float2* Z, int64_t n, const mrf_proj_
     return fail(MRF_EUNSUPPORTED, "projection mode not available in this build");
 }
 
-// Z = X - mu (A^H A X - AHY) into D->zbuf (and its BF16 operand when `want_zq`).
-mrf_status gradient(mrf_dict* D, const mrf_op* op, const float2* AHY, const float2* X, float mu,
-                    bool want_zq, cudaStream_t st) {
+// Z = X - mu (A^H A X - AHY) for one slice: W is an n x L FFT workspace, zq (optional) receives
+// the BF16 query operand of Z.
+mrf_status gradient_to(const mrf_op* op, const float2* AHY, const float2* X, float mu, float2* Z,
+                       float2* W, __nv_bfloat16* zq, int Kp, uint32_t* err, cudaStream_t st) {
     const int64_t n = static_cast<int64_t>(op->Ny) * op->Nx;
     cufftHandle hy;
     MRF_TRY(get_plan(0, op->Ny, op->Nx, op->L, st, &hy));
     ProfScope ps0(0, 2, st);
-    MRF_TRY(fft_exec(hy, X, D->wbuf, CUFFT_FORWARD));
-    MRF_TRY(launch_mask_ky(D->wbuf, op->mask, op->Ny, op->Nx, op->L, st));
-    MRF_TRY(fft_exec(hy, D->wbuf, D->wbuf, CUFFT_INVERSE));
-    MRF_TRY(launch_grad_combine(X, D->wbuf, AHY, D->zbuf, n, op->L, mu,
-                                1.0f / static_cast<float>(op->Ny), want_zq ? D->zq : nullptr,
-                                D->Kp, D->err, st));
+    MRF_TRY(fft_exec(hy, X, W, CUFFT_FORWARD));
+    MRF_TRY(launch_mask_ky(W, op->mask, op->Ny, op->Nx, op->L, st));
+    MRF_TRY(fft_exec(hy, W, W, CUFFT_INVERSE));
+    MRF_TRY(launch_grad_combine(X, W, AHY, Z, n, op->L, mu, 1.0f / static_cast<float>(op->Ny), zq,
+                                Kp, err, st));
     return MRF_OK;
+}
+
+namespace {
+
+// Z = X - mu (A^H A X - AHY) into D->zbuf (and its BF16 operand when `want_zq`).
+mrf_status gradient(mrf_dict* D, const mrf_op* op, const float2* AHY, const float2* X, float mu,
+                    bool want_zq, cudaStream_t st) {
+    return gradient_to(op, AHY, X, mu, D->zbuf, D->wbuf, want_zq ? D->zq : nullptr, D->Kp,
+                       D->err, st);
 }
 
 double read_red(mrf_dict* D, int i, cudaStream_t st, mrf_status* s) {

@@ -81,6 +81,18 @@ void mrf_set_error(const std::string& msg);
         if (s_ != MRF_OK) return s_;                                                    \
     } while (0)
 
+// ----- host helpers shared across translation units (abi.cu)
+mrf_status project_core(mrf_dict* D, const float2* Z, int64_t n, const mrf_proj_opts* o,
+                        const int32_t* warm, int32_t* idx_out, float2* rho_out, float2* X_out,
+                        bool zq_ready, cudaStream_t st);
+mrf_status gradient_to(const mrf_op* op, const float2* AHY, const float2* X, float mu, float2* Z,
+                       float2* W, __nv_bfloat16* zq, int Kp, uint32_t* err, cudaStream_t st);
+mrf_status dict_ensure_scratch(mrf_dict* D, int64_t n);
+bool profiler_suspend();
+void profiler_resume(bool was);
+mrf_status check_op_public(const mrf_op* op);
+mrf_status check_proj_public(const mrf_dict* D, const mrf_proj_opts* o);
+
 // ----- kernels (launch wrappers); all asynchronous on `st`
 // prep.cu
 mrf_status launch_atom_norms(mrf_dict* D, cudaStream_t st);

@@ -57,5 +57,9 @@ def test_host_argument_errors(L):
     assert L.mrf_adjoint(C.byref(op), 1, 1, None) == MRF_EINVAL
     assert L.mrf_dict_info(None, None, None, None) == MRF_EINVAL
     assert L.mrf_status_str(MRF_EINVAL) == b"MRF_EINVAL"
+    assert L.mrf_batch_create(None, 2, None, C.byref(h)) == MRF_EINVAL
+    assert L.mrf_batch_run(None, 1, 1.0, None, 0, None) == MRF_EINVAL
+    assert L.mrf_batch_slice(None, 0, None, None, None, None, None) == MRF_EINVAL
+    L.mrf_batch_free(None)
     o = mrf.proj_opts()
     assert o.topk == 0 and o.mode == 0 and abs(o.tie_tol - 1e-5) < 1e-12
