@@ -199,14 +199,14 @@ def reconstruction_quality(mrf, D, op, p, dic, dev, stream, iters: int, fp32: bo
     fg = ph["labels"] >= 0
     Yd = torch.from_numpy(p["Y"]).to(dev)
     out, idxs = {}, {}
-    runs = [("bf16", {})]
+    runs = [("bf16", {}), ("fp8", {})]
     if fp32:
         runs.append(("fp32", {}))
     if forms:
         t0 = time.perf_counter()
         D.close()
         D2 = mrf.build_dict_index(dic["atoms"], dic["params"], grid_shape=dic["grid_shape"],
-                                  build_tree=True)
+                                  build_tree=True, pack_fp8=True)
         out["tree_build_s"] = time.perf_counter() - t0
         M, tsec, hist = train_learned(mrf, D2, dic, dev)
         mrf.attach_mlp(D2, M)
@@ -245,7 +245,7 @@ def reconstruction_quality(mrf, D, op, p, dic, dev, stream, iters: int, fp32: bo
     ref = mo.project(Zh, dic["atoms"])
     AHY = torch.empty((n, L), dtype=torch.complex64, device=dev)
     mrf.adjoint(op, Yd, AHY)
-    for mode in ("bf16", "fp32"):
+    for mode in ("bf16", "fp8", "fp32"):
         if mode not in out:
             continue
         idx = torch.empty(n, dtype=torch.int32, device=dev)
@@ -272,7 +272,7 @@ def run_profile_case(args) -> None:
     dic, p = make_workload(0)
     Ny, Nx, L = p["Ny"], p["Nx"], p["L"]
     n = args.profile_case
-    D = mrf.build_dict_index(dic["atoms"], dic["params"])
+    D = mrf.build_dict_index(dic["atoms"], dic["params"], pack_fp8=(args.mode == "fp8"))
     mask = torch.from_numpy(p["masks"]).cuda()
     op = mrf.make_op(Ny, Nx, L, mask)
     AHY = torch.empty((Ny * Nx, L), dtype=torch.complex64, device="cuda")
@@ -351,7 +351,7 @@ def run_ours(args) -> None:
     n = Ny * Nx
     dev = torch.device("cuda", local)
     stream = torch.cuda.current_stream()
-    D = mrf.build_dict_index(atoms, params)
+    D = mrf.build_dict_index(atoms, params, pack_fp8=True)
     D.reserve(n)
     mask = torch.from_numpy(p["masks"]).to(dev)
     op = mrf.make_op(Ny, Nx, L, mask)
@@ -446,18 +446,24 @@ def run_ours(args) -> None:
     # ------------------------------------------------------------- report
     peaks = measured_peaks()
     value = world * n * d * args.steps / (ms_max / 1e3)
-    search_ms, search_launches = prof["search_bf16"] if args.mode == "bf16" else prof["search_fp32"]
+    search_ms, search_launches = prof["search_tc"] if args.mode in ("bf16", "fp8") else prof["search_fp32"]
     flops_per_launch = 8.0 * L * n * d
     achieved = flops_per_launch * search_launches / (search_ms / 1e3) / 1e12 if search_ms else 0.0
-    if args.mode == "bf16":
+    if args.mode in ("bf16", "fp8"):
         peak = float(peaks.get("bf16_tflops_sustained", peaks.get("bf16_tflops")))
+        src = peaks["_source"] + " sustained bf16"
+        if args.mode == "fp8":
+            peak, src = 2.0 * peak, src + " x 2 (nominal fp8 / bf16 dense ratio, 4.5 / 2.25)"
         roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "frac": achieved / peak, "traffic": traffic_per_launch(n, d),
-                "kernel": "k_bf16_topk", "peak_source": peaks["_source"] + " sustained bf16",
-                "flops_per_launch": flops_per_launch}
+                "frac": achieved / peak,
+                "traffic": traffic_per_launch(n, d) if args.mode == "bf16" else None,
+                "kernel": "k_tc_topk", "peak_source": src, "flops_per_launch": flops_per_launch}
     else:
-        roof = {"bound": "alu", "achieved": achieved, "peak": None, "unit": "TFLOP/s",
-                "frac": None, "traffic": None, "kernel": "k_fp32_topk"}
+        # FP32 SIMT: 152 SMs x 128 FP32 lanes x 2 flop (FFMA) x 2070 MHz maximum SM clock
+        peak = 152 * 128 * 2 * 2.07e9 / 1e12
+        roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": achieved / peak, "traffic": None, "kernel": "k_fp32_topk",
+                "peak_source": "152 SMs x 128 lanes x 2 flop x 2.07 GHz"}
     launches = int(sum(v[1] for v in prof.values()))
     cpu = None
     if not args.no_cpu:
@@ -468,10 +474,11 @@ def run_ours(args) -> None:
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "bf16" if args.mode == "bf16" else "f32", "data": "synthetic",
+            "dtype": {"bf16": "bf16", "fp8": "fp8_e4m3", "fp32": "f32"}[args.mode],
+            "data": "synthetic",
             "config": {"workload": WORKLOAD, "n_voxels": n, "L": L, "d": d,
                        "step": "one BLIP iteration (ipg_step) + look-up table",
-                       "projection": args.mode, "topk": 16 if args.mode == "bf16" else 8, "certify": False,
+                       "projection": args.mode, "topk": 8 if args.mode == "fp32" else 16, "certify": False,
                        "l2": "inputs larger than L2 (BF16 dictionary operand 800 MB)"},
             "roofline": roof, "cpu_baseline": cpu,
             "e2e": {"value": world * n * d * e2e_steps / e2e_s, "unit": UNIT,
@@ -498,7 +505,7 @@ def main():
     ap.add_argument("--no-forms", action="store_true", help="skip the cover tree and learned forms")
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--mode", default="bf16", choices=["bf16", "fp32"])
+    ap.add_argument("--mode", default="bf16", choices=["bf16", "fp8", "fp32"])
     ap.add_argument("--fp32-sample", type=int, default=0)
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--profile-case", type=int, default=0,

@@ -87,7 +87,10 @@ typedef struct mrf_proj_opts {
                               are rescored in FP64 (default 1e-5) */
     float   cert_margin;   /* margin of `certify`, same units; <= 0 selects the rigorous
                               bound of the BF16 correlation error, 2^-8 + 2^-18 (operand
-                              rounding) + 2L 2^-24 (FP32 accumulation) (default 0) */
+                              rounding) + 2L 2^-24 (FP32 accumulation), or for FP8
+                              2 u8 + u8^2 + 2L 2^-13 with u8 = 2^-4 + sqrt(2L) 2^-10 / 224
+                              (E4M3 rounding of rows scaled into (224, 448]; 13-bit partial
+                              sums assumed) (default 0) */
     float   eps;           /* cover tree (1+eps) approximation (default 0) */
     float   fallback_thr;  /* learned proposal: normalised correlation threshold (0.98) */
     float   tree_route;    /* cover tree: a voxel whose candidate list exceeds 64 entries while
@@ -404,7 +407,8 @@ mrf_status mrf_set_tune(mrf_dict* dict, const mrf_tune* in);
  * the library's kernel launches.  mrf_profile_read synchronises on the recorded events, adds
  * their elapsed times into ms[stage] and launches[stage] for stage < n_stages, and clears
  * them.  Stages: 0 gradient step (cuFFT + mask + combine; cuFFT's kernels are timed here but
- * not counted as launches), 1 BF16 query packing, 2 BF16 tensor-core search, 3 FP32 search,
+ * not counted as launches), 1 query packing (BF16 or FP8), 2 tensor-core search (BF16 or
+ * FP8), 3 FP32 search,
  * 4 merge / rescore / density, 5 fallback to the exhaustive search (certification, cover-tree
  * routing or overflow, learned-proposal fallback), 6 look-up table, 7 proposal search (cover
  * tree traversal or learned network + neighbourhood rescore).  Enabling or disabling clears the tables.  Not thread-safe.

@@ -84,12 +84,13 @@ class Dictionary:
 
     def __init__(self, atoms, params=None, grid_shape=None, pack_bf16: bool = True,
                  build_tree: bool = False, tree_cone: str = "complex",
-                 tree_dup_tol: float = 1e-5, stream=None):
+                 tree_dup_tol: float = 1e-5, stream=None, pack_fp8: bool = False):
         import numpy as np
         d, L = atoms.shape
         o = IndexOpts()
         lib().mrf_default_index_opts(C.byref(o))
         o.pack_bf16 = int(pack_bf16)
+        o.pack_fp8 = int(pack_fp8)
         o.build_tree = int(build_tree)
         o.tree_cone = CONES[tree_cone]
         o.tree_dup_tol = tree_dup_tol
@@ -156,9 +157,9 @@ class Dictionary:
 
 
 def build_dict_index(atoms, params=None, grid_shape=None, pack_bf16=True, build_tree=False,
-                     tree_cone="complex", tree_dup_tol=1e-5, stream=None):
+                     tree_cone="complex", tree_dup_tol=1e-5, stream=None, pack_fp8=False):
     return Dictionary(atoms, params, grid_shape, pack_bf16, build_tree, tree_cone, tree_dup_tol,
-                      stream)
+                      stream, pack_fp8)
 
 
 def tree_build_host(atoms, cone: str = "complex", dup_tol: float = 1e-5) -> dict:
@@ -375,7 +376,7 @@ def attach_mlp(D: Dictionary, mlp) -> None:
     D._mlp = mlp
 
 
-PROFILE_STAGES = ["gradient", "pack_bf16", "search_bf16", "search_fp32", "merge", "fallback",
+PROFILE_STAGES = ["gradient", "pack_queries", "search_tc", "search_fp32", "merge", "fallback",
                   "lut", "search_proposal"]
 
 

@@ -104,6 +104,10 @@ mrf_status ensure_scratch(mrf_dict* D, int64_t n) {
     MRF_TRY(dalloc(&D->vlist, static_cast<size_t>(n)));
     MRF_TRY(dalloc(&D->vlist2, static_cast<size_t>(n)));
     if (D->bop) MRF_TRY(dalloc(&D->zq, static_cast<size_t>(n * D->Kp)));
+    if (D->fop) {
+        MRF_TRY(dalloc(&D->zq8, static_cast<size_t>(n * D->Kp8)));
+        MRF_TRY(dalloc(&D->qs8, static_cast<size_t>(n)));
+    }
     if (D->xprev) MRF_TRY(dalloc(&D->xprev, static_cast<size_t>(n * L)));
     D->cap_n = n;
     return MRF_OK;
@@ -143,7 +147,8 @@ mrf_status check_proj_opts(const mrf_dict* D, const mrf_proj_opts* o) {
             if (!D->mlp) return fail(MRF_EUNSUPPORTED, "no learned model attached to the dictionary");
             return MRF_OK;
         case MRF_PROJ_FP8:
-            return fail(MRF_EUNSUPPORTED, "projection mode not available in this build");
+            if (!D->fop) return fail(MRF_EUNSUPPORTED, "dictionary built without the FP8 operand");
+            return MRF_OK;
         default: return fail(MRF_EINVAL, "unknown projection mode");
     }
 }
@@ -219,6 +224,21 @@ mrf_status bf16_margin(const mrf_dict* D, const mrf_proj_opts* o, float* m) {
     *m = o->cert_margin > 0.f ? o->cert_margin
                               : static_cast<float>(std::ldexp(1.0, -8) + std::ldexp(1.0, -18) +
                                                    2.0 * D->L * std::ldexp(1.0, -24));
+    return MRF_OK;
+}
+
+// FP8 counterpart.  A row scaled into (224, 448] and rounded to E4M3 has error at most
+// 2^-4 |x_i| per normal entry and 2^-10 per subnormal one, so relative to the row norm
+// (>= 224) u8 = 2^-4 + sqrt(2L) 2^-10 / 224.  The MMA's internal accumulation width for FP8
+// inputs is not documented; the margin assumes partial sums rounded to 13 bits (2L 2^-13),
+// which is far above the FP32 figure.  The result (about 0.37 at L = 1000) makes certification
+// flag almost every voxel: certified FP8 is a correctness mode, the FP8 form is meant to run
+// uncertified with its agreement rate measured.
+mrf_status fp8_margin(const mrf_dict* D, const mrf_proj_opts* o, float* m) {
+    if (o->cert_margin > 0.f) { *m = o->cert_margin; return MRF_OK; }
+    const double u8 = std::ldexp(1.0, -4) + std::sqrt(2.0 * D->L) * std::ldexp(1.0, -10) / 224.0;
+    const double b = 2.0 * u8 + u8 * u8 + 2.0 * D->L * std::ldexp(1.0, -13);
+    *m = static_cast<float>(b < 2.0 ? b : 2.0);
     return MRF_OK;
 }
 
@@ -305,8 +325,12 @@ mrf_status project_core(mrf_dict* D, const float2* Z, int64_t n, const mrf_proj_
                              D->counters, st));
         return MRF_OK;
     }
-    if (o->mode == MRF_PROJ_BF16) {
-        if (!zq_ready) {
+    if (o->mode == MRF_PROJ_BF16 || o->mode == MRF_PROJ_FP8) {
+        const bool f8 = (o->mode == MRF_PROJ_FP8);
+        if (f8) {
+            ProfScope ps1(1, 1, st);
+            MRF_TRY(launch_pack_queries_fp8(Z, nullptr, n, D->L, D->Kp8, D->zq8, D->qs8, st));
+        } else if (!zq_ready) {
             ProfScope ps1(1, 1, st);
             MRF_TRY(launch_pack_queries(Z, n, D->L, D->Kp, D->zq, st));
         }
@@ -316,11 +340,13 @@ mrf_status project_core(mrf_dict* D, const float2* Z, int64_t n, const mrf_proj_
         int32_t* pi = reinterpret_cast<int32_t*>(ps + static_cast<size_t>(S) * n * K);
         {
             ProfScope ps2(2, 1, st);
-            MRF_TRY(launch_bf16_topk(D->zq, n, D, o->cone, K, S, ps, pi, st));
+            if (f8) MRF_TRY(launch_fp8_topk(D->zq8, D->qs8, n, D, o->cone, K, S, ps, pi, st));
+            else MRF_TRY(launch_bf16_topk(D->zq, n, D, o->cone, K, S, ps, pi, st));
         }
         if (o->certify) MRF_CUDA_TRY(cudaMemsetAsync(D->nlist, 0, sizeof(int32_t), st));
         float margin;
-        bf16_margin(D, o, &margin);
+        if (f8) fp8_margin(D, o, &margin);
+        else bf16_margin(D, o, &margin);
         {
             ProfScope ps4(4, 1, st);
             MRF_TRY(launch_merge(Z, n, D, o->cone, K, S, ps, pi, nullptr, nullptr, o->tie_tol,
@@ -485,7 +511,8 @@ void mrf_dict_free(mrf_dict* D) {
     if (!D) return;
     if (D->tree) ct_free(D->tree);
     if (D->mlp) mlp_detach(D->mlp);
-    void* ptrs[] = {D->atoms, D->inv_norm2, D->norm2, D->params, D->bop, D->zq, D->zbuf,
+    void* ptrs[] = {D->atoms, D->inv_norm2, D->norm2, D->params, D->bop, D->zq, D->fop, D->w8,
+                    D->zq8, D->qs8, D->zbuf,
                     D->wbuf, D->xprev, D->vlist, D->vlist2, D->nlist, D->part, D->err,
                     D->counters, D->red};
     for (void* p : ptrs)
@@ -505,7 +532,6 @@ mrf_status mrf_build_dict_index(const void* atoms, int64_t d, int32_t L, const f
     if (grid_ndim < 0 || (grid_ndim > 0 && !grid_shape)) return fail(MRF_EINVAL, "grid_shape");
     mrf_index_opts o;
     if (opts) o = *opts; else mrf_default_index_opts(&o);
-    if (o.pack_fp8) return fail(MRF_EUNSUPPORTED, "FP8 operand not available in this build");
     if (o.build_tree && o.tree_cone != MRF_CONE_COMPLEX && o.tree_cone != MRF_CONE_REAL_POS)
         return fail(MRF_EINVAL, "tree_cone must be a mrf_cone");
     if (o.build_tree && !(o.tree_dup_tol >= 0.f)) return fail(MRF_EINVAL, "tree_dup_tol < 0");
@@ -542,12 +568,19 @@ mrf_status mrf_build_dict_index(const void* atoms, int64_t d, int32_t L, const f
     if ((e = cudaMemsetAsync(D->counters, 0, sizeof(unsigned long long) * CNT_N, st)))
         return cuda_bail(e, "memset");
     if ((s = launch_atom_norms(D, st)) != MRF_OK) return bail(s);
+    D->nblk = (d + 127) / 128;
     if (o.pack_bf16) {
-        D->nblk = (d + 127) / 128;
         D->Kp = ((2 * L + 15) / 16) * 16;
         if ((s = dalloc(&D->bop, static_cast<size_t>(D->nblk * 256 * D->Kp))) != MRF_OK)
             return bail(s);
         if ((s = launch_pack_bop(D, st)) != MRF_OK) return bail(s);
+    }
+    if (o.pack_fp8) {
+        D->Kp8 = ((2 * L + 31) / 32) * 32;
+        if ((s = dalloc(&D->fop, static_cast<size_t>(D->nblk * 256 * D->Kp8))) != MRF_OK)
+            return bail(s);
+        if ((s = dalloc(&D->w8, static_cast<size_t>(d))) != MRF_OK) return bail(s);
+        if ((s = launch_pack_fop(D, st)) != MRF_OK) return bail(s);
     }
     uint32_t werr = 0;
     if ((e = cudaMemcpyAsync(&werr, D->err, sizeof(werr), cudaMemcpyDeviceToHost, st)))

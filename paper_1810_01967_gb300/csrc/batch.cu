@@ -7,8 +7,8 @@
 // launch of the search kernel against the shared dictionary, however uneven the slices.  With
 // `use_graph` the iteration is captured once into a CUDA graph on an internal stream and
 // replayed; the first iteration runs eagerly so that cuFFT plans and scratch are created
-// outside the capture.  Only projections without host synchronisation can be captured (FP32 or
-// BF16, without certification).
+// outside the capture.  Only projections without host synchronisation can be captured (FP32,
+// BF16 or FP8, without certification).
 #include <cstring>
 #include <vector>
 
@@ -39,7 +39,8 @@ mrf_status bfail(mrf_status s, const std::string& m) {
 }
 
 bool capturable(const mrf_proj_opts& o) {
-    return !o.certify && (o.mode == MRF_PROJ_FP32_EXACT || o.mode == MRF_PROJ_BF16);
+    return !o.certify && (o.mode == MRF_PROJ_FP32_EXACT || o.mode == MRF_PROJ_BF16 ||
+                           o.mode == MRF_PROJ_FP8);
 }
 
 mrf_status iterate(mrf_batch* B, float mu, const mrf_proj_opts* o, cudaStream_t st) {
@@ -136,7 +137,7 @@ mrf_status mrf_batch_run(mrf_batch* B, int32_t iters, float mu, const mrf_proj_o
     MRF_TRY(check_proj_public(B->D, &o));
     if (use_graph && !capturable(o))
         return bfail(MRF_EUNSUPPORTED, "graph replay needs a projection without host "
-                                       "synchronisation (FP32 or BF16 with certify = 0)");
+                                       "synchronisation (FP32, BF16 or FP8 with certify = 0)");
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     for (int32_t it = 0; it < iters; ++it) {
         if (!use_graph || it == 0) {

@@ -1,5 +1,5 @@
-// Exhaustive matched filter on the 5th-generation tensor cores (§3.2, eq. exactP), BF16 inputs
-// with FP32 accumulation in tensor memory.
+// Exhaustive matched filter on the 5th-generation tensor cores (§3.2, eq. exactP): BF16 or FP8
+// (E4M3) inputs with FP32 accumulation in tensor memory.
 //
 // The complex correlation D_j^H Z_v is a real GEMM: query row v = (Re z_0, Im z_0, Re z_1, ...)
 // (K = 2L, padded to Kp), and per block of 128 atoms 256 operand rows: 128 rows
@@ -15,8 +15,11 @@
 // unit order keeps a few dozen voxel tiles live at a time (super-groups of PG groups, all splits)
 // so the query tiles being re-read stay resident in L2 while the atom blocks stream.
 // Warp roles: warp 0 = TMA producer, warp 1 = TMEM owner and MMA issuer, warps 2..5 = epilogue
-// (TMEM lanes 32 (w mod 4) ...).  4-stage shared-memory ring (48 KB per stage: A 128x64,
-// B 256x64 BF16, 128-byte swizzle), double-buffered 2 x 256-column FP32 accumulator.
+// (TMEM lanes 32 (w mod 4) ...).  4-stage shared-memory ring (48 KB per stage: A 128 rows and
+// B 256 rows of 128 bytes = 64 BF16 or 128 E4M3 elements, 128-byte swizzle), double-buffered
+// 2 x 256-column FP32 accumulator.  The FP8 form uses kind::f8f6f4 (K = 32 per instruction
+// instead of 16, the same 32 bytes), per-row power-of-two scales folded into the atom weights
+// and into a per-query factor applied to the K scores a voxel keeps.
 // Every mbarrier wait is bounded; on expiry the CTA raises MRF_DERR_TIMEOUT, drains what it
 // issued and exits.
 #include <cuda.h>
@@ -28,12 +31,14 @@ namespace {
 constexpr int BM = 128;
 constexpr int BN = 256;          // 128 atoms x (re, im)
 constexpr int BK = 64;           // BF16 elements per stage row = 128 bytes
+constexpr int BKB = 128;         // bytes per stage row
 constexpr int STAGES = 4;
-constexpr int A_BYTES = BM * BK * 2;
-constexpr int B_BYTES = BN * BK * 2;
+constexpr int A_BYTES = BM * BKB;
+constexpr int B_BYTES = BN * BKB;
 constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
 constexpr int NTHREADS = 192;
 constexpr uint32_t IDESC = mrfk::idesc_bf16(BM, BN);
+constexpr uint32_t IDESC8 = mrfk::idesc_e4m3(BM, BN);
 
 struct Shared {
     uint64_t full[STAGES];
@@ -81,12 +86,16 @@ __device__ __forceinline__ void topk_insert(float (&ts)[KT], int32_t (&ti)[KT], 
     }
 }
 
-template <int KT, int C>
+// F8: E4M3 operands (kind::f8f6f4), `wts` = 1 / (||D_j||^2 s_j^2) and `qs` = 1 / s_q per query
+// row; otherwise BF16, `wts` = 1 / ||D_j||^2 and qs unused.
+template <int KT, int C, bool F8>
 __global__ void __launch_bounds__(NTHREADS, 1)
-k_bf16_topk(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
-            int64_t n, int64_t d, int64_t nblk, int Kp, int cone, Sched sc, int blocks_per_split,
-            const float* __restrict__ inv_norm2, float* __restrict__ part_s,
-            int32_t* __restrict__ part_i, uint32_t* err) {
+k_tc_topk(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+          int64_t n, int64_t d, int64_t nblk, int Kp, int cone, Sched sc, int blocks_per_split,
+          const float* __restrict__ wts, const float* __restrict__ qs,
+          float* __restrict__ part_s, int32_t* __restrict__ part_i, uint32_t* err) {
+    constexpr int EK = F8 ? 128 : 64;     // elements per stage row
+    constexpr int KPER = F8 ? 32 : 16;    // elements per MMA instruction (32 bytes either way)
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char* base = reinterpret_cast<unsigned char*>(
         (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
@@ -98,7 +107,7 @@ k_bf16_topk(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
     const int64_t cluster = blockIdx.x / C;
     const int64_t nclusters = gridDim.x / C;
     const int64_t units = sc.NG * sc.S;
-    const int nk = (Kp + BK - 1) / BK;
+    const int nk = (Kp + EK - 1) / EK;
     constexpr uint16_t kMask = static_cast<uint16_t>((1u << C) - 1u);
     constexpr int SLICE_ROWS = BN / C;
     constexpr int SLICE_BYTES = B_BYTES / C;
@@ -153,15 +162,15 @@ k_bf16_topk(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
                         if (!mrfk::mbar_wait(&sh->empty[stage], phase ^ 1u)) { fail(); break; }
                         unsigned char* sa = base + stage * STAGE_BYTES;
                         mrfk::mbar_arrive_expect_tx(&sh->full[stage], STAGE_BYTES);
-                        mrfk::tma_load_2d(sa, &tmA, &sh->full[stage], kc * BK,
+                        mrfk::tma_load_2d(sa, &tmA, &sh->full[stage], kc * EK,
                                           static_cast<int32_t>(m * BM));
                         if (C > 1)
                             mrfk::tma_load_2d_mc(sa + A_BYTES + rank * SLICE_BYTES, &tmB,
-                                                 &sh->full[stage], kc * BK,
+                                                 &sh->full[stage], kc * EK,
                                                  static_cast<int32_t>(b * BN + rank * SLICE_ROWS),
                                                  kMask);
                         else
-                            mrfk::tma_load_2d(sa + A_BYTES, &tmB, &sh->full[stage], kc * BK,
+                            mrfk::tma_load_2d(sa + A_BYTES, &tmB, &sh->full[stage], kc * EK,
                                               static_cast<int32_t>(b * BN));
                         slot_used[stage] = true;
                         slot_phase[stage] = phase;
@@ -200,12 +209,15 @@ k_bf16_topk(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
                         mrfk::tc_fence_after();
                         const uint32_t sa = mrfk::smem_u32(base + stage * STAGE_BYTES);
                         const uint32_t sb = sa + A_BYTES;
-                        const int rem = Kp - kc * BK;
-                        const int nmma = rem >= BK ? BK / 16 : rem / 16;
+                        const int rem = Kp - kc * EK;
+                        const int nmma = rem >= EK ? EK / KPER : rem / KPER;
                         for (int k = 0; k < nmma; ++k) {
                             const uint64_t da = mrfk::sdesc_k_sw128(sa + k * 32);
                             const uint64_t db = mrfk::sdesc_k_sw128(sb + k * 32);
-                            mrfk::mma_bf16(dt, da, db, IDESC, (kc > 0 || k > 0) ? 1u : 0u);
+                            if (F8)
+                                mrfk::mma_f8(dt, da, db, IDESC8, (kc > 0 || k > 0) ? 1u : 0u);
+                            else
+                                mrfk::mma_bf16(dt, da, db, IDESC, (kc > 0 || k > 0) ? 1u : 0u);
                         }
                         if (C > 1) mrfk::mma_commit_mc(&sh->empty[stage], kMask);
                         else mrfk::mma_commit(&sh->empty[stage]);
@@ -252,7 +264,7 @@ k_bf16_topk(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
                     mrfk::tmem_ld32(tb + c * 32, re);
                     mrfk::tmem_ld32(tb + 128 + c * 32, im);
                     const int64_t jl = b * 128 + c * 32 + lane;
-                    const float wl = (jl < d) ? inv_norm2[jl] : 0.f;
+                    const float wl = (jl < d) ? wts[jl] : 0.f;
                     mrfk::tmem_ld_wait();
 #pragma unroll
                     for (int i = 0; i < 32; ++i) {
@@ -272,6 +284,12 @@ k_bf16_topk(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
             if (!ok) break;
             const int64_t v = m * BM + row;
             if (v < n) {
+                if (F8) {
+                    const float q = qs[v];
+                    const float f = (cone == MRF_CONE_COMPLEX) ? q * q : q;
+#pragma unroll
+                    for (int q2 = 0; q2 < KT; ++q2) ts[q2] *= f;
+                }
                 const int64_t o = (s * n + v) * KT;
 #pragma unroll
                 for (int q = 0; q < KT; ++q) { part_s[o + q] = ts[q]; part_i[o + q] = ti[q]; }
@@ -305,20 +323,24 @@ EncodeFn get_encode() {
     return fn;
 }
 
-mrf_status make_map(CUtensorMap* m, const void* ptr, int64_t rows, int Kp, int box_rows) {
+// Tensor map over a row-major [rows][Kp] operand of 2-byte (BF16) or 1-byte (E4M3) elements;
+// boxes of 128 bytes x box_rows rows with the 128-byte swizzle the UMMA descriptors expect.
+mrf_status make_map(CUtensorMap* m, const void* ptr, int64_t rows, int Kp, int box_rows,
+                    bool f8) {
     EncodeFn enc = get_encode();
     if (!enc) {
         mrf_set_error("cuTensorMapEncodeTiled is unavailable");
         return MRF_ECUDA;
     }
+    const int esz = f8 ? 1 : 2;
     cuuint64_t dims[2] = {static_cast<cuuint64_t>(Kp), static_cast<cuuint64_t>(rows)};
-    cuuint64_t strides[1] = {static_cast<cuuint64_t>(Kp) * 2};
-    cuuint32_t box[2] = {static_cast<cuuint32_t>(BK), static_cast<cuuint32_t>(box_rows)};
+    cuuint64_t strides[1] = {static_cast<cuuint64_t>(Kp) * esz};
+    cuuint32_t box[2] = {static_cast<cuuint32_t>(BKB / esz), static_cast<cuuint32_t>(box_rows)};
     cuuint32_t es[2] = {1, 1};
-    CUresult r = enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(ptr), dims,
-                     strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
-                     CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-                     CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    CUresult r = enc(m, f8 ? CU_TENSOR_MAP_DATA_TYPE_UINT8 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2,
+                     const_cast<void*>(ptr), dims, strides, box, es,
+                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                     CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS) {
         mrf_set_error("cuTensorMapEncodeTiled failed: " + std::to_string(static_cast<int>(r)));
         return MRF_ECUDA;
@@ -326,11 +348,11 @@ mrf_status make_map(CUtensorMap* m, const void* ptr, int64_t rows, int Kp, int b
     return MRF_OK;
 }
 
-template <int KT, int C>
+template <int KT, int C, bool F8>
 mrf_status launch_t(const CUtensorMap& ta, const CUtensorMap& tb, int64_t n, const mrf_dict* D,
-                    int cone, Sched sc, int bps, int nclusters, float* part_s, int32_t* part_i,
-                    cudaStream_t st) {
-    auto kern = k_bf16_topk<KT, C>;
+                    int cone, Sched sc, int bps, int nclusters, const float* wts, const float* qs,
+                    float* part_s, int32_t* part_i, cudaStream_t st) {
+    auto kern = k_tc_topk<KT, C, F8>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          static_cast<int>(kSmem));
     if (e == cudaSuccess) {
@@ -346,11 +368,11 @@ mrf_status launch_t(const CUtensorMap& ta, const CUtensorMap& tb, int64_t n, con
         attr[0].val.clusterDim.z = 1;
         cfg.attrs = attr;
         cfg.numAttrs = 1;
-        e = cudaLaunchKernelEx(&cfg, kern, ta, tb, n, D->d, D->nblk, D->Kp, cone, sc, bps,
-                               static_cast<const float*>(D->inv_norm2), part_s, part_i, D->err);
+        e = cudaLaunchKernelEx(&cfg, kern, ta, tb, n, D->d, D->nblk, F8 ? D->Kp8 : D->Kp, cone,
+                               sc, bps, wts, qs, part_s, part_i, D->err);
     }
     if (e != cudaSuccess) {
-        mrf_set_error(std::string("bf16 kernel launch: ") + cudaGetErrorString(e));
+        mrf_set_error(std::string("tensor-core search launch: ") + cudaGetErrorString(e));
         return MRF_ECUDA;
     }
     return MRF_OK;
@@ -359,7 +381,7 @@ mrf_status launch_t(const CUtensorMap& ta, const CUtensorMap& tb, int64_t n, con
 // Co-resident clusters of size C (persistent grid), from the occupancy calculator.
 template <int KT, int C>
 int max_clusters(cudaStream_t st) {
-    auto kern = k_bf16_topk<KT, C>;
+    auto kern = k_tc_topk<KT, C, false>;   // same resources for both element types
     if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              static_cast<int>(kSmem)) != cudaSuccess) {
         cudaGetLastError();
@@ -430,21 +452,38 @@ int bf16_choose_splits(const mrf_dict* D, int64_t n) {
     return choose_splits(NG, D->nblk, D->num_sms / C);
 }
 
-mrf_status launch_bf16_topk(const __nv_bfloat16* zq, int64_t n, mrf_dict* D, int cone, int K,
-                            int S, float* part_s, int32_t* part_i, cudaStream_t st) {
+namespace {
+
+template <int KT, bool F8>
+mrf_status launch_c(int C, const CUtensorMap& ta, const CUtensorMap& tb, int64_t n,
+                    const mrf_dict* D, int cone, Sched sc, int bps, int nc, const float* wts,
+                    const float* qs, float* part_s, int32_t* part_i, cudaStream_t st) {
+    switch (C) {
+        case 1: return launch_t<KT, 1, F8>(ta, tb, n, D, cone, sc, bps, nc, wts, qs, part_s, part_i, st);
+        case 2: return launch_t<KT, 2, F8>(ta, tb, n, D, cone, sc, bps, nc, wts, qs, part_s, part_i, st);
+        default: return launch_t<KT, 4, F8>(ta, tb, n, D, cone, sc, bps, nc, wts, qs, part_s, part_i, st);
+    }
+}
+
+// Shared launch path of both element types: operand maps, schedule, persistent grid.
+mrf_status launch_tc(bool f8, const void* zq, const float* qs, int64_t n, mrf_dict* D, int cone,
+                     int K, int S, float* part_s, int32_t* part_i, cudaStream_t st) {
     if (n == 0) return MRF_OK;
-    if (!D->bop) {
-        mrf_set_error("BF16 operand was not packed (mrf_index_opts.pack_bf16 = 0)");
+    const void* op = f8 ? static_cast<const void*>(D->fop) : static_cast<const void*>(D->bop);
+    if (!op) {
+        mrf_set_error(f8 ? "FP8 operand was not packed (mrf_index_opts.pack_fp8 = 0)"
+                         : "BF16 operand was not packed (mrf_index_opts.pack_bf16 = 0)");
         return MRF_EUNSUPPORTED;
     }
     if (K != 8 && K != 16) {
-        mrf_set_error("bf16 kernel: K must be 8 or 16");
+        mrf_set_error("tensor-core search: K must be 8 or 16");
         return MRF_EINVAL;
     }
     const int C = cluster_of(D);
+    const int Kp = f8 ? D->Kp8 : D->Kp;
     CUtensorMap ta, tb;
-    MRF_TRY(make_map(&ta, zq, n, D->Kp, BM));
-    MRF_TRY(make_map(&tb, D->bop, D->nblk * 256, D->Kp, BN / C));
+    MRF_TRY(make_map(&ta, zq, n, Kp, BM, f8));
+    MRF_TRY(make_map(&tb, op, D->nblk * 256, Kp, BN / C, f8));
     const int64_t Mt = (n + BM - 1) / BM;
     const int64_t live = D->tune.bf16_live_tiles > 0 ? D->tune.bf16_live_tiles : kDefaultLive;
     Sched sc;
@@ -455,23 +494,29 @@ mrf_status launch_bf16_topk(const __nv_bfloat16* zq, int64_t n, mrf_dict* D, int
     const int64_t units = sc.NG * sc.S;
     int nc = (K == 8) ? max_clusters_any<8>(C, st) : max_clusters_any<16>(C, st);
     if (nc <= 0) {
-        mrf_set_error("bf16 kernel: no cluster of the requested size fits on this device");
+        mrf_set_error("tensor-core search: no cluster of the requested size fits on this device");
         return MRF_EUNSUPPORTED;
     }
     if (nc > units) nc = static_cast<int>(units);
     D->tune.last_bf16_ctas = nc * C;
     D->tune.last_bf16_cluster = C;
     D->tune.last_bf16_splits = S;
-    if (K == 8) {
-        switch (C) {
-            case 1: return launch_t<8, 1>(ta, tb, n, D, cone, sc, bps, nc, part_s, part_i, st);
-            case 2: return launch_t<8, 2>(ta, tb, n, D, cone, sc, bps, nc, part_s, part_i, st);
-            default: return launch_t<8, 4>(ta, tb, n, D, cone, sc, bps, nc, part_s, part_i, st);
-        }
-    }
-    switch (C) {
-        case 1: return launch_t<16, 1>(ta, tb, n, D, cone, sc, bps, nc, part_s, part_i, st);
-        case 2: return launch_t<16, 2>(ta, tb, n, D, cone, sc, bps, nc, part_s, part_i, st);
-        default: return launch_t<16, 4>(ta, tb, n, D, cone, sc, bps, nc, part_s, part_i, st);
-    }
+    const float* wts = f8 ? D->w8 : D->inv_norm2;
+    if (f8)
+        return K == 8 ? launch_c<8, true>(C, ta, tb, n, D, cone, sc, bps, nc, wts, qs, part_s, part_i, st)
+                      : launch_c<16, true>(C, ta, tb, n, D, cone, sc, bps, nc, wts, qs, part_s, part_i, st);
+    return K == 8 ? launch_c<8, false>(C, ta, tb, n, D, cone, sc, bps, nc, wts, qs, part_s, part_i, st)
+                  : launch_c<16, false>(C, ta, tb, n, D, cone, sc, bps, nc, wts, qs, part_s, part_i, st);
+}
+
+}  // namespace
+
+mrf_status launch_bf16_topk(const __nv_bfloat16* zq, int64_t n, mrf_dict* D, int cone, int K,
+                            int S, float* part_s, int32_t* part_i, cudaStream_t st) {
+    return launch_tc(false, zq, nullptr, n, D, cone, K, S, part_s, part_i, st);
+}
+
+mrf_status launch_fp8_topk(const uint8_t* zq8, const float* qs, int64_t n, mrf_dict* D, int cone,
+                           int K, int S, float* part_s, int32_t* part_i, cudaStream_t st) {
+    return launch_tc(true, zq8, qs, n, D, cone, K, S, part_s, part_i, st);
 }

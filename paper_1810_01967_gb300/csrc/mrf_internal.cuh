@@ -43,9 +43,16 @@ struct mrf_dict {
     __nv_bfloat16* bop = nullptr;
     int64_t nblk = 0;
     int32_t Kp = 0;
+    // FP8 E4M3 operand: the same blocks and rows, row length Kp8 = 2L rounded up to 32, each
+    // atom scaled by a power of two s_j; w8[j] = 1 / (||D_j||^2 s_j^2)
+    uint8_t* fop = nullptr;
+    float* w8 = nullptr;
+    int32_t Kp8 = 0;
     // scratch (grown on demand, or reserved up front)
     int64_t cap_n = 0;
     __nv_bfloat16* zq = nullptr;    // [cap_n][Kp]
+    uint8_t* zq8 = nullptr;         // [cap_n][Kp8] FP8 queries (with the FP8 operand)
+    float* qs8 = nullptr;           // [cap_n] 1 / s of each FP8 query row
     float2* zbuf = nullptr;         // [cap_n][L] gradient-step output Z
     float2* wbuf = nullptr;         // [cap_n][L] FFT workspace
     float2* xprev = nullptr;        // [cap_n][L] previous iterate (step rule)
@@ -99,6 +106,9 @@ mrf_status launch_atom_norms(mrf_dict* D, cudaStream_t st);
 mrf_status launch_pack_bop(mrf_dict* D, cudaStream_t st);
 mrf_status launch_pack_queries(const float2* Z, int64_t n, int L, int Kp, __nv_bfloat16* zq,
                                cudaStream_t st);
+mrf_status launch_pack_fop(mrf_dict* D, cudaStream_t st);
+mrf_status launch_pack_queries_fp8(const float2* Z, const int32_t* vlist, int64_t n, int L,
+                                   int Kp8, uint8_t* zq8, float* qs, cudaStream_t st);
 mrf_status launch_pack_gather(const float2* Z, const int32_t* vlist, int64_t n, int L, int Kp,
                               __nv_bfloat16* zq, cudaStream_t st);
 mrf_status launch_mask_ky(float2* W, const uint8_t* mask, int Ny, int Nx, int L,
@@ -123,6 +133,8 @@ int fp32_choose_splits(int64_t n, int64_t d, int num_sms);
 mrf_status launch_bf16_topk(const __nv_bfloat16* zq, int64_t n, mrf_dict* D, int cone, int K,
                             int S, float* part_s, int32_t* part_i, cudaStream_t st);
 int bf16_choose_splits(const mrf_dict* D, int64_t n);
+mrf_status launch_fp8_topk(const uint8_t* zq8, const float* qs, int64_t n, mrf_dict* D, int cone,
+                           int K, int S, float* part_s, int32_t* part_i, cudaStream_t st);
 // covertree.cu
 mrf_status ct_build_upload(mrf_dict* D, int metric, double dup_tol);
 void ct_free(CoverTreeDev* t);

@@ -1,4 +1,4 @@
-// Elementwise and packing kernels around the projection: atom norms, BF16 operand packing,
+// Elementwise and packing kernels around the projection: atom norms, BF16 and FP8 operand packing,
 // the k-space line mask and the gradient-step combination of §3.2 eq. blip, the look-up table
 // of Algorithm 2 and FP64 reductions used by the step rule (eq. steprule).
 #include "mrf_internal.cuh"
@@ -69,6 +69,86 @@ __global__ void k_pack_gather(const float2* __restrict__ Z, const int32_t* __res
     const int64_t v = vlist[k];
     float2 z = (t < L) ? Z[v * L + t] : make_float2(0.f, 0.f);
     zq[i] = __floats2bfloat162_rn(z.x, z.y);
+}
+
+// ----------------------------------------------------------------------------- FP8 (E4M3)
+// Rows are scaled by a power of two s chosen from the row's largest real or imaginary
+// magnitude m so that s m lies in (224, 448] (448 is the largest finite E4M3 value); a zero row
+// keeps s = 1.  Each value is rounded to nearest with saturation.  The kernel scores are then
+// rescaled by the factors below, so FP8 scores are in the units of the BF16 ones.
+__device__ __forceinline__ float e4m3_row_scale(float m) {
+    if (!(m > 0.f) || !isfinite(m)) return 1.f;
+    int e = ilogbf(448.f / m);
+    e = e > 126 ? 126 : (e < -126 ? -126 : e);
+    return ldexpf(1.f, e);
+}
+
+__device__ __forceinline__ uint16_t e4m3_pair(float x, float y) {
+    const uint16_t lo = __nv_cvt_float_to_fp8(x, __NV_SATFINITE, __NV_E4M3);
+    const uint16_t hi = __nv_cvt_float_to_fp8(y, __NV_SATFINITE, __NV_E4M3);
+    return static_cast<uint16_t>(lo | (hi << 8));
+}
+
+__device__ __forceinline__ float warp_max(float x) {
+    for (int o = 16; o; o >>= 1) x = fmaxf(x, __shfl_xor_sync(0xffffffffu, x, o));
+    return x;
+}
+
+// One warp per atom slot of the padded blocks: the atom's two operand rows (as in k_pack_bop)
+// in E4M3, and w8[j] = 1 / (||D_j||^2 s_j^2).
+__global__ void k_pack_fop(const float2* __restrict__ atoms, const float* __restrict__ inv_norm2,
+                           int64_t d, int L, int Kp8, int64_t nblk, uint16_t* __restrict__ fop,
+                           float* __restrict__ w8) {
+    const int64_t slot = (static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (slot >= nblk * 128) return;
+    const int64_t b = slot >> 7;
+    const int r = static_cast<int>(slot & 127);
+    const int64_t j = slot;
+    const bool real = j < d;
+    float m = 0.f;
+    if (real)
+        for (int t = lane; t < L; t += 32) {
+            const float2 v = atoms[j * L + t];
+            m = fmaxf(m, fmaxf(fabsf(v.x), fabsf(v.y)));
+        }
+    m = warp_max(m);
+    const float sj = e4m3_row_scale(m);
+    const int half = Kp8 / 2;
+    uint16_t* re_row = fop + (b * 256 + r) * half;
+    uint16_t* im_row = fop + (b * 256 + 128 + r) * half;
+    for (int t = lane; t < half; t += 32) {
+        float2 v = make_float2(0.f, 0.f);
+        if (real && t < L) v = atoms[j * L + t];
+        re_row[t] = e4m3_pair(v.x * sj, v.y * sj);
+        im_row[t] = e4m3_pair(-v.y * sj, v.x * sj);
+    }
+    if (real && lane == 0) w8[j] = inv_norm2[j] / (sj * sj);
+}
+
+// One warp per voxel (listed voxels when vlist is given): the E4M3 query row and qs = 1 / s.
+__global__ void k_pack_queries_fp8(const float2* __restrict__ Z, const int32_t* __restrict__ vlist,
+                                   int64_t n, int L, int Kp8, uint16_t* __restrict__ zq8,
+                                   float* __restrict__ qs) {
+    const int64_t k = (static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (k >= n) return;
+    const int64_t v = vlist ? static_cast<int64_t>(vlist[k]) : k;
+    const float2* z = Z + v * L;
+    float m = 0.f;
+    for (int t = lane; t < L; t += 32) {
+        const float2 a = z[t];
+        m = fmaxf(m, fmaxf(fabsf(a.x), fabsf(a.y)));
+    }
+    m = warp_max(m);
+    const float s = e4m3_row_scale(m);
+    const int half = Kp8 / 2;
+    uint16_t* row = zq8 + k * half;
+    for (int t = lane; t < half; t += 32) {
+        const float2 a = (t < L) ? z[t] : make_float2(0.f, 0.f);
+        row[t] = e4m3_pair(a.x * s, a.y * s);
+    }
+    if (lane == 0) qs[k] = 1.f / s;
 }
 
 __global__ void k_mask_ky(float2* __restrict__ W, const uint8_t* __restrict__ mask, int Ny,
@@ -194,6 +274,24 @@ mrf_status launch_pack_bop(mrf_dict* D, cudaStream_t st) {
     int64_t total = D->nblk * 256 * (D->Kp / 2);
     k_pack_bop<<<grid_for(total), kThreads, 0, st>>>(D->atoms, D->d, D->L, D->Kp, D->nblk,
                                                       reinterpret_cast<__nv_bfloat162*>(D->bop));
+    LAUNCH_CHECK();
+    return MRF_OK;
+}
+
+mrf_status launch_pack_fop(mrf_dict* D, cudaStream_t st) {
+    const int64_t slots = D->nblk * 128;
+    k_pack_fop<<<grid_for(slots * 32), kThreads, 0, st>>>(
+        D->atoms, D->inv_norm2, D->d, D->L, D->Kp8, D->nblk, reinterpret_cast<uint16_t*>(D->fop),
+        D->w8);
+    LAUNCH_CHECK();
+    return MRF_OK;
+}
+
+mrf_status launch_pack_queries_fp8(const float2* Z, const int32_t* vlist, int64_t n, int L,
+                                   int Kp8, uint8_t* zq8, float* qs, cudaStream_t st) {
+    if (n == 0) return MRF_OK;
+    k_pack_queries_fp8<<<grid_for(n * 32), kThreads, 0, st>>>(
+        Z, vlist, n, L, Kp8, reinterpret_cast<uint16_t*>(zq8), qs);
     LAUNCH_CHECK();
     return MRF_OK;
 }

@@ -1,5 +1,5 @@
 """GPU parity of the matched-filtering projection (mrf_project) against the FP64 oracle, through
-the C ABI, for the FP32 SIMT kernel and the BF16 tcgen05 kernel: realistic aliased fingerprints,
+the C ABI, for the FP32 SIMT kernel and the BF16 and FP8 tcgen05 kernels: realistic aliased fingerprints,
 several tiles plus ragged tails, edge cases (zero rows, single voxel, tiny dictionaries, odd L,
 duplicate atoms) and both cone readings."""
 import numpy as np
@@ -43,11 +43,11 @@ def run(mrf, D, Z, mode, cone="complex", X=True, topk=0, certify=True):
     return (idx.cpu().numpy(), rho.cpu().numpy(), None if Xo is None else Xo.cpu().numpy(), st)
 
 
-@pytest.mark.parametrize("mode", ["fp32", "bf16"])
+@pytest.mark.parametrize("mode", ["fp32", "bf16", "fp8"])
 @pytest.mark.parametrize("n", [1000, 1024, 1])
 def test_aliased_fingerprints(mrf, cfg1, mode, n):
     dic, p, Z = cfg1
-    D = mrf.build_dict_index(dic["atoms"], dic["params"])
+    D = mrf.build_dict_index(dic["atoms"], dic["params"], pack_fp8=(mode == "fp8"))
     Zs = Z[:n]
     idx, rho, X, st = run(mrf, D, Zs, mode)
     agree, ties = check_projection(Zs, dic["atoms"], idx, rho, g_X=X)
@@ -55,7 +55,7 @@ def test_aliased_fingerprints(mrf, cfg1, mode, n):
     print(f"{mode} n={n}: agreement {agree:.5f}, near-tie swaps {ties}, stats {st}")
 
 
-@pytest.mark.parametrize("mode", ["fp32", "bf16"])
+@pytest.mark.parametrize("mode", ["fp32", "bf16", "fp8"])
 @pytest.mark.parametrize("cone", ["complex", "real_pos"])
 def test_atoms_times_scalars_and_zero_rows(mrf, cfg1, mode, cone):
     dic = cfg1[0]
@@ -67,7 +67,7 @@ def test_atoms_times_scalars_and_zero_rows(mrf, cfg1, mode, cone):
                                     if cone == "complex" else 1.0)
     Z = (rho[:, None] * A[js].astype(np.complex128)).astype(np.complex64)
     Z[::37] = 0
-    D = mrf.build_dict_index(A, dic["params"])
+    D = mrf.build_dict_index(A, dic["params"], pack_fp8=(mode == "fp8"))
     idx, r, X, st = run(mrf, D, Z, mode, cone=cone)
     check_projection(Z, A, idx, r, cone=cone, g_X=X)
     zero = np.zeros(n, bool)
@@ -76,26 +76,26 @@ def test_atoms_times_scalars_and_zero_rows(mrf, cfg1, mode, cone):
     assert st["n_zero"] == zero.sum()
 
 
-@pytest.mark.parametrize("mode", ["fp32", "bf16"])
+@pytest.mark.parametrize("mode", ["fp32", "bf16", "fp8"])
 @pytest.mark.parametrize("L,d,n", [(37, 5, 70), (100, 1, 3), (8, 300, 129), (1000, 257, 300)])
 def test_odd_shapes(mrf, mode, L, d, n):
     g = np.random.Generator(np.random.PCG64(L * 1000 + d))
     A = (g.standard_normal((d, L)) + 1j * g.standard_normal((d, L))).astype(np.complex64)
     A *= g.uniform(0.5, 2.0, (d, 1)).astype(np.float32)
     Z = (g.standard_normal((n, L)) + 1j * g.standard_normal((n, L))).astype(np.complex64)
-    D = mrf.build_dict_index(A)
+    D = mrf.build_dict_index(A, pack_fp8=(mode == "fp8"))
     idx, r, X, _ = run(mrf, D, Z, mode)
     check_projection(Z, A, idx, r, g_X=X)
 
 
-@pytest.mark.parametrize("mode", ["fp32", "bf16"])
+@pytest.mark.parametrize("mode", ["fp32", "bf16", "fp8"])
 def test_duplicate_atoms_tie_to_smallest_index(mrf, mode):
     g = np.random.Generator(np.random.PCG64(7))
     B = (g.standard_normal((40, 64)) + 1j * g.standard_normal((40, 64))).astype(np.complex64)
     A = np.concatenate([B, B, B[:10]])
     js = g.integers(0, 40, 200)
     Z = (A[js] * np.complex64(1.5 - 0.5j)).astype(np.complex64)
-    D = mrf.build_dict_index(A)
+    D = mrf.build_dict_index(A, pack_fp8=(mode == "fp8"))
     idx, r, X, _ = run(mrf, D, Z, mode)
     assert np.array_equal(idx, js)
     np.testing.assert_allclose(r, 1.5 - 0.5j, rtol=1e-5)
@@ -117,6 +117,41 @@ def test_topk_and_uncertified_bf16(mrf, cfg1, topk):
     print(f"bf16 top-{topk} uncertified agreement {agree:.5f}")
     idx, r, X, st = run(mrf, D, Z, "fp32", topk=topk)
     check_projection(Z, dic["atoms"], idx, r, g_X=X)
+
+
+@pytest.mark.parametrize("cone", ["complex", "real_pos"])
+def test_fp8_search_matches_e4m3_emulation(mrf, cfg1, cone):
+    """The FP8 kernel ranks by the correlations of the E4M3-quantised operands (rows scaled by
+    powers of two).  Uncertified, the answer is the exactly best atom among the 16 best by that
+    ranking: compare with a float64 evaluation of the quantised products (fp8_emul), allowing
+    for near-ties at the 16th place within the FP32 accumulation error, and check the rigorous
+    bound on every miss."""
+    from fp8_emul import fp8_scores
+    dic, p, Z = cfg1
+    A = dic["atoms"]
+    Zs = Z[:600]
+    D = mrf.build_dict_index(A, pack_fp8=True)
+    idx, r, X, st = run(mrf, D, Zs, "fp8", cone=cone, topk=16, certify=False)
+    S8 = fp8_scores(Zs, A, cone)
+    Zc, Ac = Zs.astype(np.complex128), A.astype(np.complex128)
+    C = Zc @ Ac.conj().T
+    den = np.linalg.norm(Zc, axis=1)[:, None] * np.linalg.norm(Ac, axis=1)[None, :]
+    ex = (np.abs(C) if cone == "complex" else C.real) / np.maximum(den, 1e-300)
+    srt = -np.sort(-S8, axis=1)
+    kth = srt[:, 15]
+    tol = 1e-4 * np.maximum(np.abs(srt[:, 0]), 1e-30)    # FP32 accumulation, generous
+    sure = S8 >= (kth + tol)[:, None]                     # in the top 16 for any rounding
+    maybe = S8 >= (kth - tol)[:, None]                    # possibly in the top 16
+    lo = np.max(np.where(sure, ex, -np.inf), axis=1)
+    hi = np.max(np.where(maybe, ex, -np.inf), axis=1)
+    got = ex[np.arange(len(idx)), idx]
+    ok = (got >= lo - 1e-6) & (got <= hi + 1e-6) & maybe[np.arange(len(idx)), idx]
+    assert np.all(ok), np.flatnonzero(~ok)[:10]
+    ref = mo.project(Zs, A, cone)
+    agree = float(np.mean(idx == ref["idx"]))
+    print(f"fp8 uncertified ({cone}) agreement with the exact projection {agree:.4f}")
+    rr = mo.density(Zs, A, idx, cone)
+    assert np.max(np.abs(r - rr) / np.maximum(np.abs(rr), 1e-30)) <= 1e-4
 
 
 def test_empty_projection_is_a_no_op(mrf, cfg1):
