@@ -511,7 +511,7 @@ void mrf_dict_free(mrf_dict* D) {
     if (!D) return;
     if (D->tree) ct_free(D->tree);
     if (D->mlp) mlp_detach(D->mlp);
-    void* ptrs[] = {D->atoms, D->inv_norm2, D->norm2, D->params, D->bop, D->zq, D->fop, D->w8,
+    void* ptrs[] = {D->atoms, D->inv_norm2, D->norm2, D->params, D->bop, D->zq, D->fop,
                     D->zq8, D->qs8, D->zbuf,
                     D->wbuf, D->xprev, D->vlist, D->vlist2, D->nlist, D->part, D->err,
                     D->counters, D->red};
@@ -579,8 +579,25 @@ mrf_status mrf_build_dict_index(const void* atoms, int64_t d, int32_t L, const f
         D->Kp8 = ((2 * L + 31) / 32) * 32;
         if ((s = dalloc(&D->fop, static_cast<size_t>(D->nblk * 256 * D->Kp8))) != MRF_OK)
             return bail(s);
-        if ((s = dalloc(&D->w8, static_cast<size_t>(d))) != MRF_OK) return bail(s);
-        if ((s = launch_pack_fop(D, st)) != MRF_OK) return bail(s);
+        // one power of two for the whole normalised dictionary: its largest magnitude m goes to
+        // (224, 448]
+        unsigned int mb = 0;
+        unsigned int* dmb = reinterpret_cast<unsigned int*>(D->red);
+        if ((e = cudaMemsetAsync(dmb, 0, sizeof(unsigned int), st))) return cuda_bail(e, "memset");
+        if ((s = launch_atoms_absmax(D, dmb, st)) != MRF_OK) return bail(s);
+        if ((e = cudaMemcpyAsync(&mb, dmb, sizeof(mb), cudaMemcpyDeviceToHost, st)))
+            return cuda_bail(e, "read atom maximum");
+        if ((e = cudaStreamSynchronize(st))) return cuda_bail(e, "atom maximum");
+        float m;
+        std::memcpy(&m, &mb, sizeof(m));
+        float sg = 1.f;
+        if (m > 0.f && std::isfinite(m)) {
+            int ex = std::ilogb(448.f / m);
+            ex = ex > 126 ? 126 : (ex < -126 ? -126 : ex);
+            sg = std::ldexp(1.f, ex);
+        }
+        D->g8 = 1.f / sg;
+        if ((s = launch_pack_fop(D, sg, st)) != MRF_OK) return bail(s);
     }
     uint32_t werr = 0;
     if ((e = cudaMemcpyAsync(&werr, D->err, sizeof(werr), cudaMemcpyDeviceToHost, st)))

@@ -86,13 +86,14 @@ __device__ __forceinline__ void topk_insert(float (&ts)[KT], int32_t (&ti)[KT], 
     }
 }
 
-// F8: E4M3 operands (kind::f8f6f4), `wts` = 1 / (||D_j||^2 s_j^2) and `qs` = 1 / s_q per query
-// row; otherwise BF16, `wts` = 1 / ||D_j||^2 and qs unused.
+// F8: E4M3 operands (kind::f8f6f4); the K kept scores of voxel v are multiplied by
+// (qs[v] gsc)^2 (complex cone) or qs[v] gsc (real cone), qs = 1 / (the query row's scale) and
+// gsc = 1 / (the dictionary's scale).  BF16: scores are used as computed.
 template <int KT, int C, bool F8>
 __global__ void __launch_bounds__(NTHREADS, 1)
 k_tc_topk(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
           int64_t n, int64_t d, int64_t nblk, int Kp, int cone, Sched sc, int blocks_per_split,
-          const float* __restrict__ wts, const float* __restrict__ qs,
+          float gsc, const float* __restrict__ qs,
           float* __restrict__ part_s, int32_t* __restrict__ part_i, uint32_t* err) {
     constexpr int EK = F8 ? 128 : 64;     // elements per stage row
     constexpr int KPER = F8 ? 32 : 16;    // elements per MMA instruction (32 bytes either way)
@@ -237,9 +238,14 @@ k_tc_topk(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
         }
     } else {
         // ------------------------------------------------------------ epilogue (4 warps)
+        // Per 32-atom chunk: scores |c|^2 (complex cone) or Re c (real cone) of the normalised
+        // atoms, their maximum against the thread's K-th best, and only when it is beaten the
+        // slow path: the chunk's scores go to this thread's column of shared memory and the
+        // beating atoms are inserted one by one (one copy of the insertion code).
         const int quarter = warp & 3;
         const int row = quarter * 32 + lane;
         const uint32_t lane_base = static_cast<uint32_t>(quarter * 32) << 16;
+        float* col = reinterpret_cast<float*>(base + STAGES * STAGE_BYTES + sizeof(Shared)) + row;
         int acc = 0;
         uint32_t aphase = 0;
         for (int64_t uc = cluster; uc < units && !sh->abort; uc += nclusters) {
@@ -263,18 +269,32 @@ k_tc_topk(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
                     __syncwarp();
                     mrfk::tmem_ld32(tb + c * 32, re);
                     mrfk::tmem_ld32(tb + 128 + c * 32, im);
-                    const int64_t jl = b * 128 + c * 32 + lane;
-                    const float wl = (jl < d) ? wts[jl] : 0.f;
                     mrfk::tmem_ld_wait();
+                    float mx = -INFINITY;
 #pragma unroll
                     for (int i = 0; i < 32; ++i) {
-                        const float w = __shfl_sync(0xffffffffu, wl, i);
-                        const int64_t j = b * 128 + c * 32 + i;
                         const float x = __uint_as_float(re[i]);
                         const float y = __uint_as_float(im[i]);
-                        const float scv = (cone == MRF_CONE_COMPLEX) ? (x * x + y * y) * w
-                                                                     : x * sqrtf(w);
-                        if (j < d) topk_insert<KT>(ts, ti, scv, static_cast<int32_t>(j));
+                        const float v = (cone == MRF_CONE_COMPLEX) ? fmaf(x, x, y * y) : x;
+                        re[i] = __float_as_uint(v);
+                        mx = fmaxf(mx, v);
+                    }
+                    if (mx > ts[KT - 1]) {
+                        const float thr = ts[KT - 1];
+                        uint32_t hits = 0;
+#pragma unroll
+                        for (int i = 0; i < 32; ++i) {
+                            const float v = __uint_as_float(re[i]);
+                            col[i * BM] = v;
+                            hits |= (v > thr) ? (1u << i) : 0u;
+                        }
+                        const int64_t jb = b * 128 + c * 32;
+                        while (hits) {
+                            const int i = __ffs(hits) - 1;
+                            hits &= hits - 1;
+                            const int64_t j = jb + i;
+                            if (j < d) topk_insert<KT>(ts, ti, col[i * BM], static_cast<int32_t>(j));
+                        }
                     }
                 }
                 mrfk::tc_fence_before();
@@ -285,7 +305,7 @@ k_tc_topk(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
             const int64_t v = m * BM + row;
             if (v < n) {
                 if (F8) {
-                    const float q = qs[v];
+                    const float q = qs[v] * gsc;
                     const float f = (cone == MRF_CONE_COMPLEX) ? q * q : q;
 #pragma unroll
                     for (int q2 = 0; q2 < KT; ++q2) ts[q2] *= f;
@@ -303,7 +323,8 @@ k_tc_topk(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
     if (warp == 1) mrfk::tmem_dealloc(tmem, 512);
 }
 
-constexpr size_t kSmem = STAGES * STAGE_BYTES + sizeof(Shared) + 1024;
+// ring + barriers + the epilogue's score columns (32 x 128 floats) + alignment slack
+constexpr size_t kSmem = STAGES * STAGE_BYTES + sizeof(Shared) + 32 * BM * sizeof(float) + 1024;
 
 using EncodeFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
                               const cuuint64_t*, const cuuint64_t*, const cuuint32_t*,
@@ -350,7 +371,7 @@ mrf_status make_map(CUtensorMap* m, const void* ptr, int64_t rows, int Kp, int b
 
 template <int KT, int C, bool F8>
 mrf_status launch_t(const CUtensorMap& ta, const CUtensorMap& tb, int64_t n, const mrf_dict* D,
-                    int cone, Sched sc, int bps, int nclusters, const float* wts, const float* qs,
+                    int cone, Sched sc, int bps, int nclusters, float gsc, const float* qs,
                     float* part_s, int32_t* part_i, cudaStream_t st) {
     auto kern = k_tc_topk<KT, C, F8>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -369,7 +390,7 @@ mrf_status launch_t(const CUtensorMap& ta, const CUtensorMap& tb, int64_t n, con
         cfg.attrs = attr;
         cfg.numAttrs = 1;
         e = cudaLaunchKernelEx(&cfg, kern, ta, tb, n, D->d, D->nblk, F8 ? D->Kp8 : D->Kp, cone,
-                               sc, bps, wts, qs, part_s, part_i, D->err);
+                               sc, bps, gsc, qs, part_s, part_i, D->err);
     }
     if (e != cudaSuccess) {
         mrf_set_error(std::string("tensor-core search launch: ") + cudaGetErrorString(e));
@@ -456,7 +477,7 @@ namespace {
 
 template <int KT, bool F8>
 mrf_status launch_c(int C, const CUtensorMap& ta, const CUtensorMap& tb, int64_t n,
-                    const mrf_dict* D, int cone, Sched sc, int bps, int nc, const float* wts,
+                    const mrf_dict* D, int cone, Sched sc, int bps, int nc, float wts,
                     const float* qs, float* part_s, int32_t* part_i, cudaStream_t st) {
     switch (C) {
         case 1: return launch_t<KT, 1, F8>(ta, tb, n, D, cone, sc, bps, nc, wts, qs, part_s, part_i, st);
@@ -501,7 +522,7 @@ mrf_status launch_tc(bool f8, const void* zq, const float* qs, int64_t n, mrf_di
     D->tune.last_bf16_ctas = nc * C;
     D->tune.last_bf16_cluster = C;
     D->tune.last_bf16_splits = S;
-    const float* wts = f8 ? D->w8 : D->inv_norm2;
+    const float wts = f8 ? D->g8 : 1.f;
     if (f8)
         return K == 8 ? launch_c<8, true>(C, ta, tb, n, D, cone, sc, bps, nc, wts, qs, part_s, part_i, st)
                       : launch_c<16, true>(C, ta, tb, n, D, cone, sc, bps, nc, wts, qs, part_s, part_i, st);

@@ -38,15 +38,16 @@ struct mrf_dict {
     float* inv_norm2 = nullptr;     // [d] 1 / ||D_j||^2 (from an FP64 sum)
     double* norm2 = nullptr;        // [d] ||D_j||^2 in FP64
     float* params = nullptr;        // [d][P]
-    // BF16 tensor-core operand: blocks of 128 atoms, 256 rows each (128 real-part rows, then
-    // 128 imaginary-part rows), row length Kp = 2L rounded up to 16, interleaved (re, im).
+    // BF16 tensor-core operand of the normalised atoms D_j / ||D_j||: blocks of 128 atoms, 256
+    // rows each (128 real-part rows, then 128 imaginary-part rows), row length Kp = 2L rounded
+    // up to 16, interleaved (re, im).
     __nv_bfloat16* bop = nullptr;
     int64_t nblk = 0;
     int32_t Kp = 0;
-    // FP8 E4M3 operand: the same blocks and rows, row length Kp8 = 2L rounded up to 32, each
-    // atom scaled by a power of two s_j; w8[j] = 1 / (||D_j||^2 s_j^2)
+    // FP8 E4M3 operand: the same blocks and rows of normalised atoms, row length Kp8 = 2L
+    // rounded up to 32, all scaled by one power of two 1 / g8
     uint8_t* fop = nullptr;
-    float* w8 = nullptr;
+    float g8 = 1.f;
     int32_t Kp8 = 0;
     // scratch (grown on demand, or reserved up front)
     int64_t cap_n = 0;
@@ -106,7 +107,8 @@ mrf_status launch_atom_norms(mrf_dict* D, cudaStream_t st);
 mrf_status launch_pack_bop(mrf_dict* D, cudaStream_t st);
 mrf_status launch_pack_queries(const float2* Z, int64_t n, int L, int Kp, __nv_bfloat16* zq,
                                cudaStream_t st);
-mrf_status launch_pack_fop(mrf_dict* D, cudaStream_t st);
+mrf_status launch_atoms_absmax(const mrf_dict* D, unsigned int* m_bits, cudaStream_t st);
+mrf_status launch_pack_fop(mrf_dict* D, float s, cudaStream_t st);
 mrf_status launch_pack_queries_fp8(const float2* Z, const int32_t* vlist, int64_t n, int L,
                                    int Kp8, uint8_t* zq8, float* qs, cudaStream_t st);
 mrf_status launch_pack_gather(const float2* Z, const int32_t* vlist, int64_t n, int L, int Kp,

@@ -30,8 +30,11 @@ __global__ void k_atom_norms(const float2* __restrict__ atoms, int64_t d, int L,
 
 // Row r of block b: atom j = 128 b + (r mod 128); r < 128 holds (Re d, Im d) per frame,
 // r >= 128 holds (-Im d, Re d), so that a query row (Re z, Im z) gives Re(d^H z) and Im(d^H z).
-__global__ void k_pack_bop(const float2* __restrict__ atoms, int64_t d, int L, int Kp,
-                           int64_t nblk, __nv_bfloat162* __restrict__ bop) {
+// Atom rows are normalised (D_j / ||D_j||, the FP64 norm) before rounding, so the kernels' scores
+// need no per-atom weight.
+__global__ void k_pack_bop(const float2* __restrict__ atoms, const double* __restrict__ norm2,
+                           int64_t d, int L, int Kp, int64_t nblk,
+                           __nv_bfloat162* __restrict__ bop) {
     int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
     int64_t half = Kp / 2;
     int64_t total = nblk * 256 * half;
@@ -42,7 +45,12 @@ __global__ void k_pack_bop(const float2* __restrict__ atoms, int64_t d, int L, i
     int r = static_cast<int>(row & 255);
     int64_t j = b * 128 + (r & 127);
     float2 v = make_float2(0.f, 0.f);
-    if (j < d && t < L) v = atoms[j * L + t];
+    if (j < d && t < L) {
+        const float inv = static_cast<float>(1.0 / sqrt(norm2[j]));
+        v = atoms[j * L + t];
+        v.x *= inv;
+        v.y *= inv;
+    }
     float x = (r < 128) ? v.x : -v.y;
     float y = (r < 128) ? v.y : v.x;
     bop[i] = __floats2bfloat162_rn(x, y);
@@ -72,10 +80,11 @@ __global__ void k_pack_gather(const float2* __restrict__ Z, const int32_t* __res
 }
 
 // ----------------------------------------------------------------------------- FP8 (E4M3)
-// Rows are scaled by a power of two s chosen from the row's largest real or imaginary
+// Query rows are scaled by a power of two s chosen from the row's largest real or imaginary
 // magnitude m so that s m lies in (224, 448] (448 is the largest finite E4M3 value); a zero row
-// keeps s = 1.  Each value is rounded to nearest with saturation.  The kernel scores are then
-// rescaled by the factors below, so FP8 scores are in the units of the BF16 ones.
+// keeps s = 1.  Atoms use one such power of two for the whole (normalised) dictionary.  Each
+// value is rounded to nearest with saturation.  The kernel multiplies the scores it keeps by
+// the inverse factors, so FP8 scores are in the units of the BF16 ones.
 __device__ __forceinline__ float e4m3_row_scale(float m) {
     if (!(m > 0.f) || !isfinite(m)) return 1.f;
     int e = ilogbf(448.f / m);
@@ -94,11 +103,30 @@ __device__ __forceinline__ float warp_max(float x) {
     return x;
 }
 
-// One warp per atom slot of the padded blocks: the atom's two operand rows (as in k_pack_bop)
-// in E4M3, and w8[j] = 1 / (||D_j||^2 s_j^2).
-__global__ void k_pack_fop(const float2* __restrict__ atoms, const float* __restrict__ inv_norm2,
-                           int64_t d, int L, int Kp8, int64_t nblk, uint16_t* __restrict__ fop,
-                           float* __restrict__ w8) {
+// Largest real or imaginary magnitude of the normalised atoms (one warp per atom), as float
+// bits in *m_bits (non-negative floats order like their bit patterns).
+__global__ void k_atoms_absmax(const float2* __restrict__ atoms, const double* __restrict__ norm2,
+                               int64_t d, int L, unsigned int* m_bits) {
+    const int64_t j = (static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (j >= d) return;
+    const float inv = static_cast<float>(1.0 / sqrt(norm2[j]));
+    float m = 0.f;
+    for (int t = lane; t < L; t += 32) {
+        float2 v = atoms[j * L + t];
+        m = fmaxf(m, fmaxf(fabsf(v.x * inv), fabsf(v.y * inv)));
+    }
+    m = warp_max(m);
+    if (lane == 0 && isfinite(m)) atomicMax(m_bits, __float_as_uint(m));
+}
+
+// One warp per atom slot of the padded blocks: the two operand rows of the normalised atom (as
+// in k_pack_bop) times the dictionary-wide power of two `s`, in E4M3.  With unit atoms the
+// rows' norms are s >= 224 ... so every row keeps the relative accuracy of a per-row scale,
+// and the kernel needs no per-atom weight.
+__global__ void k_pack_fop(const float2* __restrict__ atoms, const double* __restrict__ norm2,
+                           int64_t d, int L, int Kp8, int64_t nblk, float s,
+                           uint16_t* __restrict__ fop) {
     const int64_t slot = (static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
     if (slot >= nblk * 128) return;
@@ -106,24 +134,20 @@ __global__ void k_pack_fop(const float2* __restrict__ atoms, const float* __rest
     const int r = static_cast<int>(slot & 127);
     const int64_t j = slot;
     const bool real = j < d;
-    float m = 0.f;
-    if (real)
-        for (int t = lane; t < L; t += 32) {
-            const float2 v = atoms[j * L + t];
-            m = fmaxf(m, fmaxf(fabsf(v.x), fabsf(v.y)));
-        }
-    m = warp_max(m);
-    const float sj = e4m3_row_scale(m);
+    const float inv = real ? static_cast<float>(1.0 / sqrt(norm2[j])) : 0.f;
     const int half = Kp8 / 2;
     uint16_t* re_row = fop + (b * 256 + r) * half;
     uint16_t* im_row = fop + (b * 256 + 128 + r) * half;
     for (int t = lane; t < half; t += 32) {
         float2 v = make_float2(0.f, 0.f);
-        if (real && t < L) v = atoms[j * L + t];
-        re_row[t] = e4m3_pair(v.x * sj, v.y * sj);
-        im_row[t] = e4m3_pair(-v.y * sj, v.x * sj);
+        if (real && t < L) {
+            v = atoms[j * L + t];
+            v.x = (v.x * inv) * s;
+            v.y = (v.y * inv) * s;
+        }
+        re_row[t] = e4m3_pair(v.x, v.y);
+        im_row[t] = e4m3_pair(-v.y, v.x);
     }
-    if (real && lane == 0) w8[j] = inv_norm2[j] / (sj * sj);
 }
 
 // One warp per voxel (listed voxels when vlist is given): the E4M3 query row and qs = 1 / s.
@@ -272,17 +296,23 @@ mrf_status launch_atom_norms(mrf_dict* D, cudaStream_t st) {
 
 mrf_status launch_pack_bop(mrf_dict* D, cudaStream_t st) {
     int64_t total = D->nblk * 256 * (D->Kp / 2);
-    k_pack_bop<<<grid_for(total), kThreads, 0, st>>>(D->atoms, D->d, D->L, D->Kp, D->nblk,
+    k_pack_bop<<<grid_for(total), kThreads, 0, st>>>(D->atoms, D->norm2, D->d, D->L, D->Kp, D->nblk,
                                                       reinterpret_cast<__nv_bfloat162*>(D->bop));
     LAUNCH_CHECK();
     return MRF_OK;
 }
 
-mrf_status launch_pack_fop(mrf_dict* D, cudaStream_t st) {
+mrf_status launch_atoms_absmax(const mrf_dict* D, unsigned int* m_bits, cudaStream_t st) {
+    k_atoms_absmax<<<grid_for(D->d * 32), kThreads, 0, st>>>(D->atoms, D->norm2, D->d, D->L,
+                                                              m_bits);
+    LAUNCH_CHECK();
+    return MRF_OK;
+}
+
+mrf_status launch_pack_fop(mrf_dict* D, float s, cudaStream_t st) {
     const int64_t slots = D->nblk * 128;
     k_pack_fop<<<grid_for(slots * 32), kThreads, 0, st>>>(
-        D->atoms, D->inv_norm2, D->d, D->L, D->Kp8, D->nblk, reinterpret_cast<uint16_t*>(D->fop),
-        D->w8);
+        D->atoms, D->norm2, D->d, D->L, D->Kp8, D->nblk, s, reinterpret_cast<uint16_t*>(D->fop));
     LAUNCH_CHECK();
     return MRF_OK;
 }

@@ -3,9 +3,10 @@
 E4M3 (the OCP 8-bit floating-point format used by the tensor cores): 1 sign, 4 exponent
 (bias 7) and 3 mantissa bits; normal numbers 2^-6 <= |x| <= 448 with spacing 2^(e-3) in the
 binade [2^e, 2^(e+1)), subnormals with spacing 2^-9 below 2^-6; no infinities.  Rounding is to
-nearest, ties to even, with saturation at 448.  Rows are scaled by the power of two
+nearest, ties to even, with saturation at 448.  A query row is scaled by the power of two
 s = 2^floor(log2(448 / m)), m the row's largest real or imaginary magnitude (float32
-arithmetic), s = 1 for a zero row.
+arithmetic), s = 1 for a zero row; the atoms are first normalised in float32 by the FP64 norm
+and then share one such power of two, from the largest magnitude of the whole dictionary.
 """
 import numpy as np
 
@@ -40,14 +41,26 @@ def quantise_rows(V: np.ndarray):
     return e4m3_round(Vs.real) + 1j * e4m3_round(Vs.imag), s
 
 
+def normalised_atoms(D: np.ndarray) -> np.ndarray:
+    """float32 D_j * (1 / ||D_j||) with the reciprocal of the FP64 norm rounded to float32."""
+    D = np.asarray(D, np.complex64)
+    n2 = np.sum(np.abs(D.astype(np.complex128)) ** 2, axis=1)
+    inv = (1.0 / np.sqrt(n2)).astype(np.float32)
+    re = (D.real.astype(np.float32) * inv[:, None]).astype(np.float32)
+    im = (D.imag.astype(np.float32) * inv[:, None]).astype(np.float32)
+    return re, im
+
+
 def fp8_scores(Z: np.ndarray, D: np.ndarray, cone: str = "complex") -> np.ndarray:
-    """Scores the FP8 search ranks by: |q(D_j)^H q(z)|^2 / (s_z^2 s_j^2 ||D_j||^2) (complex
-    cone; Re(.) / (s_z s_j ||D_j||) for the real cone), with the products of quantised values
-    summed exactly (float64)."""
+    """Scores the FP8 search ranks by: |q(D_j)^H q(z)|^2 / (s_z s)^2 (complex cone;
+    Re(.) / (s_z s) for the real cone), with the products of quantised values summed exactly
+    (float64)."""
     Qz, sz = quantise_rows(Z)
-    Qd, sd = quantise_rows(D)
-    n2 = np.sum(np.abs(np.asarray(D, np.complex128)) ** 2, axis=1)
+    re, im = normalised_atoms(D)
+    m = np.float32(max(np.abs(re).max(), np.abs(im).max()))
+    sg = row_scale(np.array([m]))[0]
+    Qd = e4m3_round(re.astype(np.float64) * sg) + 1j * e4m3_round(im.astype(np.float64) * sg)
     C = Qz @ Qd.conj().T                       # [n][d] = q(D_j)^H q(z_v)
     if cone == "complex":
-        return np.abs(C) ** 2 / (sz[:, None] ** 2 * (sd ** 2 * n2)[None, :])
-    return C.real / (sz[:, None] * (sd * np.sqrt(n2))[None, :])
+        return np.abs(C) ** 2 / (sz[:, None] * sg) ** 2
+    return C.real / (sz[:, None] * sg)
