@@ -102,6 +102,21 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def max_over_ranks(x: float, world: int, device) -> float:
+    """x of the slowest rank (max over the process group; x itself for one process)."""
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def rank_slices(n_slices: int, rank: int, world: int) -> list[int]:
+    """Slices of this rank: dealt round-robin, so every slice goes to exactly one rank."""
+    return list(range(rank, n_slices, world))
+
+
 def measured_peaks() -> dict:
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -292,6 +307,225 @@ def run_profile_case(args) -> None:
                       "stage_launches": {k: v[1] for k, v in prof.items()}}))
 
 
+SLICES_WORKLOAD = ("64 slices of {128,192,256,320}^2 (seeded draw), L=1000, d=100011 shared "
+                   "(T1,T2,B0) IR-bSSFP, R in [8,24], 20 BLIP iterations")
+
+
+def run_slices(args) -> None:
+    """The batching form on the 64-slice workload: every slice's 20 BLIP iterations through
+    mrf_batch.  Two schedules, all slices submitted at t = 0: one batch of all slices (one
+    projection launch per iteration covers every slice; latency = the makespan), and groups of
+    `--group` slices, shortest first (per-slice latency = its group's completion).  Forms: BF16
+    and FP8 replayed as CUDA graphs, and the learned proposal with fallback (eager; its
+    fallback sizes the exhaustive search on the host).  Inputs: one seeded slice per matrix size
+    is generated (k-space, masks), and the 64 slices of the seeded draw use the generated slice
+    of their size.  Under torchrun the slices are dealt to ranks round-robin."""
+    import torch
+    import torch.distributed as dist
+    import mrfgen
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    import paper_1810_01967_gb300 as mrf
+    from paper_1810_01967_gb300 import build as b
+    if rank == 0 or world == 1:
+        b.build()
+    if world > 1:
+        dist.barrier()
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream()
+    dic = mrfgen.make_dictionary(5)
+    atoms, params = dic["atoms"], dic["params"]
+    d, L = atoms.shape
+    geo = [mrfgen.slice_geometry(5, i) for i in range(64)]
+    mine = rank_slices(64, rank, world)
+    first = {}
+    for i in mine:
+        first.setdefault(geo[i][0], i)
+    probs = {N: mrfgen.make_problem(5, i, dic=dic) for N, i in first.items()}
+    D = mrf.build_dict_index(atoms, params, grid_shape=dic["grid_shape"], pack_fp8=True)
+    masks = {N: torch.from_numpy(p["masks"]).to(dev) for N, p in probs.items()}
+    Ys = {N: torch.from_numpy(p["Y"]).to(dev) for N, p in probs.items()}
+    iters = args.iters
+    forms = [("bf16", True), ("fp8", True)]
+    if not args.no_forms:
+        forms.append(("learned", False))
+
+    def sync():
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+
+    out = {}
+    mlp_s = None
+    for mode, graph in forms:
+        kw = {}
+        if mode == "learned":
+            M, mlp_s, _ = train_learned(mrf, D, dic, dev)
+            mrf.attach_mlp(D, M)
+            kw = {"fallback_thr": 0.98}
+        o = mrf.proj_opts(mode=mode, certify=False, **kw)
+        # --- all slices in one batch
+        ops = [mrf.make_op(geo[i][0], geo[i][0], L, masks[geo[i][0]]) for i in mine]
+        B = mrf.Batch(D, ops)
+        B.load([Ys[geo[i][0]] for i in mine])
+        B.run(2, 1.0, o, use_graph=graph)            # warm-up: plans, scratch, graph capture
+        sync()
+        a = torch.cuda.Event(enable_timing=True)
+        e = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        B.load([Ys[geo[i][0]] for i in mine])
+        B.run(iters, 1.0, o, use_graph=graph)
+        e.record(stream)
+        sync()
+        t_all = max_over_ranks(a.elapsed_time(e) / 1e3, world, dev)
+        B.close()
+        del B
+        # --- groups of `group` slices, shortest first
+        order = sorted(mine, key=lambda i: (geo[i][0], i))
+        groups = [order[k:k + args.group] for k in range(0, len(order), args.group)]
+        Bs = []
+        for gi in groups:
+            og = [mrf.make_op(geo[i][0], geo[i][0], L, masks[geo[i][0]]) for i in gi]
+            Bg = mrf.Batch(D, og)
+            Bg.load([Ys[geo[i][0]] for i in gi])
+            Bg.run(2, 1.0, o, use_graph=graph)
+            Bs.append(Bg)
+        sync()
+        a = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        ends = []
+        for gi, Bg in zip(groups, Bs):
+            Bg.load([Ys[geo[i][0]] for i in gi])
+            Bg.run(iters, 1.0, o, use_graph=graph)
+            ev = torch.cuda.Event(enable_timing=True)
+            ev.record(stream)
+            ends.append(ev)
+        sync()
+        lat = []
+        for gi, ev in zip(groups, ends):
+            lat += [a.elapsed_time(ev) / 1e3] * len(gi)
+        t_grp = max_over_ranks(max(lat), world, dev)
+        for Bg in Bs:
+            Bg.close()
+        del Bs
+        lat_all = lat
+        if world > 1:
+            g = [None] * world
+            dist.all_gather_object(g, lat)
+            lat_all = [x for part in g for x in part]
+        out[mode] = {"graph": graph, "one_batch": {"s": t_all, "slices_per_s": 64 / t_all,
+                                                   "p50_s": t_all, "p99_s": t_all},
+                     "groups": {"group": args.group, "s": t_grp, "slices_per_s": 64 / t_grp,
+                                "p50_s": float(np.percentile(lat_all, 50)),
+                                "p99_s": float(np.percentile(lat_all, 99))}, **kw}
+    if world > 1:
+        dist.barrier()
+    if rank != 0:
+        dist.destroy_process_group()
+        return
+    best = out["bf16"]["one_batch"]
+    line = {"metric": "slices/s (64 uneven slices, 20 BLIP iterations each)",
+            "value": best["slices_per_s"], "unit": "slices/s", "n_gpus": world, "steps": 1,
+            "warmup": 1, "ms_per_step": 1e3 * best["s"], "higher_is_better": True,
+            "scaling": "strong", "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
+            "config": {"workload": SLICES_WORKLOAD, "voxels": int(sum(geo[i][0] ** 2 for i in range(64))),
+                       "inputs": "one generated slice per matrix size, reused by the slices of that size"},
+            "forms": out, "learned_train_gpu_s": mlp_s}
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+TREE_WORKLOAD = ("256x256, L=500, d=999,702 (T1,T2,B1,B0) IR-bSSFP, smooth B0/B1 fields, R=16, "
+                 "20 iterations: CoverBLIP eps in {0, 0.2, 0.5, 1.0} vs BF16 brute force")
+
+
+def run_tree(args) -> None:
+    """The cover-tree workload: the million-atom dictionary, the tree built on the host, then
+    whole reconstructions of one slice with the BF16 tensor-core brute force and with CoverBLIP
+    (Algorithm 2, warm-started searches) at several eps, plus one cold tree projection of
+    A^H Y per eps for the search kernel's own rate (distance evaluations, unique bytes)."""
+    import torch
+    import mrfgen
+    from oracle import mrf_oracle as mo
+    import paper_1810_01967_gb300 as mrf
+    from paper_1810_01967_gb300 import build as b
+    b.build()
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.current_stream()
+    t0 = time.perf_counter()
+    dic = mrfgen.make_dictionary(3)
+    p = mrfgen.make_problem(3, dic=dic)
+    gen_s = time.perf_counter() - t0
+    atoms, params = dic["atoms"], dic["params"]
+    d, L = atoms.shape
+    Ny, Nx = p["Ny"], p["Nx"]
+    n = Ny * Nx
+    t0 = time.perf_counter()
+    D = mrf.build_dict_index(atoms, params, build_tree=True)
+    build_s = time.perf_counter() - t0
+    info = D.tree_info()
+    op = mrf.make_op(Ny, Nx, L, torch.from_numpy(p["masks"]).to(dev))
+    Yd = torch.from_numpy(p["Y"]).to(dev)
+    ph = p["phantom"]
+    fg = ph["labels"] >= 0
+    AHY = torch.empty((n, L), dtype=torch.complex64, device=dev)
+    mrf.adjoint(op, Yd, AHY)
+    runs = [("bf16", {})] + [("covertree", {"eps": e}) for e in (0.0, 0.2, 0.5, 1.0)]
+    out = {}
+    ref_idx = None
+    for mode, kw in runs:
+        X = torch.empty((n, L), dtype=torch.complex64, device=dev)
+        idx = torch.empty(n, dtype=torch.int32, device=dev)
+        prm = torch.empty((n, params.shape[1]), dtype=torch.float32, device=dev)
+        ro = mrf.recon_opts(iters=args.iters, mode=mode, certify=False, **kw)
+        a = torch.cuda.Event(enable_timing=True)
+        e = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        st = mrf.reconstruct(D, op, Yd, X, idx, None, prm, opts=ro, stats=True)
+        e.record(stream)
+        torch.cuda.synchronize()
+        sec = a.elapsed_time(e) / 1e3
+        pr = prm.cpu().numpy()
+        gi = idx.cpu().numpy()
+        if mode == "bf16":
+            ref_idx = gi
+        r = {"s_per_slice": sec, "matches_per_s_bruteforce_equiv": n * d * args.iters / sec,
+             "T1_acc": mo.accuracy(pr[:, 0], ph["T1"], fg),
+             "T2_acc": mo.accuracy(pr[:, 1], ph["T2"], fg),
+             "atom_agreement_vs_bf16": float(np.mean(gi == ref_idx)),
+             "distance_evals": st["n_dist_evals"],
+             "exhaustive_voxel_iters": st["n_fallback"], **kw}
+        if mode == "covertree":
+            # one cold projection of A^H Y: the tree search kernel's own rate
+            ii = torch.empty(n, dtype=torch.int32, device=dev)
+            mrf.profile_enable(True)
+            s2 = mrf.project(D, AHY, ii, opts=mrf.proj_opts(mode="covertree", eps=kw["eps"],
+                                                           certify=False), stats=True)
+            prof = mrf.profile_read()
+            mrf.profile_enable(False)
+            ms = prof["search_proposal"][0]
+            r["first_projection"] = {
+                "tree_ms": ms, "fallback_ms": prof["fallback"][0], "merge_ms": prof["merge"][0],
+                "evals_per_voxel": s2["n_dist_evals"] / n,
+                "bruteforce_ratio": d * n / max(s2["n_dist_evals"], 1),
+                "routed_voxels": s2["n_fallback"],
+                "unique_GBps": s2["n_dist_evals"] * L * 8 / (ms / 1e3) / 1e9 if ms else None}
+        out[f"{mode}" + (f"_eps{kw['eps']}" if kw else "")] = r
+    line = {"metric": "recon s/slice at fixed T1/T2 error (cover tree vs brute force)",
+            "value": out["covertree_eps0.5"]["s_per_slice"], "unit": "s/slice", "n_gpus": 1,
+            "steps": 1, "warmup": 0, "ms_per_step": 1e3 * out["covertree_eps0.5"]["s_per_slice"],
+            "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": TREE_WORKLOAD, "n_voxels": n, "L": L, "d": d},
+            "tree": {"build_s_host": build_s, **info}, "generate_s": gen_s, "forms": out}
+    print(json.dumps(line), flush=True)
+
+
 def run_reference(args) -> None:
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -388,10 +622,7 @@ def run_ours(args) -> None:
     prof = mrf.profile_read()
     mrf.profile_enable(False)
     clocks = clk.stop()
-    t = torch.tensor([ms], dtype=torch.float64, device=dev)
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    ms_max = float(t.item())
+    ms_max = max_over_ranks(ms, world, dev)
     D.check()
     # ------------------------------------------------------------- end to end (host buffers)
     Xh = X.cpu().pin_memory()
@@ -411,10 +642,7 @@ def run_ours(args) -> None:
         prm_h.copy_(prm, non_blocking=True)
     barrier()
     e2e_s = time.perf_counter() - t0
-    te = torch.tensor([e2e_s], dtype=torch.float64, device=dev)
-    if world > 1:
-        dist.all_reduce(te, op=dist.ReduceOp.MAX)
-    e2e_s = float(te.item())
+    e2e_s = max_over_ranks(e2e_s, world, dev)
     h2d = Xh.numel() * 8 + AHYh.numel() * 8
     d2h = n * 4 + n * 8 + n * params.shape[1] * 4
     # ------------------------------------------------------------- FP32 exact comparator
@@ -508,11 +736,19 @@ def main():
     ap.add_argument("--mode", default="bf16", choices=["bf16", "fp8", "fp32"])
     ap.add_argument("--fp32-sample", type=int, default=0)
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--workload", default="slice", choices=["slice", "slices64", "tree1m"],
+                    help="slice: the BLIP-iteration bench; slices64: the batching form; "
+                         "tree1m: the cover tree on the million-atom dictionary")
+    ap.add_argument("--group", type=int, default=8, help="slices per group (slices64)")
     ap.add_argument("--profile-case", type=int, default=0,
                     help="projection-only small case with N voxels (for ncu captures)")
     args = ap.parse_args()
     if args.profile_case > 0:
         run_profile_case(args)
+    elif args.workload == "slices64" and args.impl == "ours":
+        run_slices(args)
+    elif args.workload == "tree1m" and args.impl == "ours":
+        run_tree(args)
     elif args.impl == "reference":
         run_reference(args)
     else:

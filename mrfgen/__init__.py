@@ -10,9 +10,10 @@ Every random draw uses ``numpy.random.Generator(PCG64(seed))`` with the fixed se
 from .sequence import flip_train, param_grid
 from .bloch import epg_fisp, bssfp, simulate_dictionary
 from .phantom import ellipse_phantom, line_masks, acquire
-from .configs import CONFIGS, make_problem, make_dictionary
+from .configs import CONFIGS, make_problem, make_dictionary, slice_geometry
 
 __all__ = [
     "flip_train", "param_grid", "epg_fisp", "bssfp", "simulate_dictionary",
     "ellipse_phantom", "line_masks", "acquire", "CONFIGS", "make_problem", "make_dictionary",
+    "slice_geometry",
 ]

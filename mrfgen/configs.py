@@ -81,6 +81,18 @@ def _snap(ph: dict, dic: dict) -> np.ndarray:
     return idx
 
 
+def slice_geometry(cfg: int, i: int = 0, **over) -> tuple[int, float]:
+    """(N, R) of slice i: fixed for workloads 1-4; for workload 5 a seeded draw of the matrix
+    size from `sizes` and of the acceleration from `R_range`."""
+    c = config(cfg, **over)
+    N, R = c["N"], c["R"]
+    if cfg == 5 and N is None:
+        g = rng(2000 + 100 * cfg + i + 77)
+        N = int(g.choice(np.asarray(c["sizes"])))
+        R = float(g.uniform(*c["R_range"]))
+    return N, R
+
+
 def make_problem(cfg: int, i: int = 0, dic: dict | None = None, snap: bool = False,
                  full_sampling: bool = False, noiseless: bool = False, **over) -> dict:
     """Phantom, masks, ground truth X0 and k-space Y for slice ``i`` of workload ``cfg``.
@@ -89,12 +101,8 @@ def make_problem(cfg: int, i: int = 0, dic: dict | None = None, snap: bool = Fal
     uses the stored atom (requires ``dic``); ``full_sampling`` keeps every line.
     """
     c = config(cfg, **over)
-    N, L = c["N"], c["L"]
-    R = c["R"]
-    if cfg == 5 and N is None:
-        g = rng(2000 + 100 * cfg + i + 77)
-        N = int(g.choice(np.asarray(c["sizes"])))
-        R = float(g.uniform(*c["R_range"]))
+    L = c["L"]
+    N, R = slice_geometry(cfg, i, **over)
     ph = ellipse_phantom(N, 2000 + 100 * cfg + i, b0=c["phantom_b0"], smooth_b1=c["smooth_b1"])
     masks = (np.ones((L, N), np.uint8) if full_sampling
              else line_masks(N, L, R, 3000 + 100 * cfg + i))

@@ -218,6 +218,14 @@ struct ProfScope {
 };
 
 namespace {
+// Options whose cert_margin selects the rigorous bound (for the merge's rescore window).
+const mrf_proj_opts kRigorous = [] {
+    mrf_proj_opts o;
+    mrf_default_proj_opts(&o);
+    o.cert_margin = 0.f;
+    return o;
+}();
+
 mrf_status bf16_margin(const mrf_dict* D, const mrf_proj_opts* o, float* m) {
     // |c~ - c| <= (2u + u^2) ||d|| ||z|| for BF16 operand rounding (u = 2^-9) plus the FP32
     // accumulation of 2L products; in normalised-correlation units
@@ -274,9 +282,12 @@ mrf_status exhaustive_on_list(mrf_dict* D, const float2* Z, int32_t cnt, const m
         MRF_TRY(launch_bf16_topk(D->zq, cnt, D, o->cone, K, S, qs, qi, st));
         float margin;
         bf16_margin(D, o, &margin);
+        float bound;
+        bf16_margin(D, &kRigorous, &bound);
         MRF_TRY(launch_merge(Z, cnt, D, o->cone, K, S, qs, qi, D->vlist, D->nlist, o->tie_tol,
                              o->certify, margin, idx_out, rho_out, X_out, D->vlist2,
-                             D->nlist + 1, D->err, D->counters, st));
+                             D->nlist + 1, D->err, D->counters, st,
+                             2.f * bound + o->tie_tol));
         if (!o->certify) return MRF_OK;
         int32_t c2 = 0;
         MRF_CUDA_TRY(cudaMemcpyAsync(&c2, D->nlist + 1, sizeof(c2), cudaMemcpyDeviceToHost, st));
@@ -349,9 +360,13 @@ mrf_status project_core(mrf_dict* D, const float2* Z, int64_t n, const mrf_proj_
         else bf16_margin(D, o, &margin);
         {
             ProfScope ps4(4, 1, st);
+            // rescore window: twice the rigorous bound of the kernel's error, plus tie_tol
+            float bound;
+            if (f8) fp8_margin(D, &kRigorous, &bound);
+            else bf16_margin(D, &kRigorous, &bound);
             MRF_TRY(launch_merge(Z, n, D, o->cone, K, S, ps, pi, nullptr, nullptr, o->tie_tol,
                                  o->certify, margin, idx_out, rho_out, X_out, D->vlist,
-                                 D->nlist, D->err, D->counters, st));
+                                 D->nlist, D->err, D->counters, st, 2.f * bound + o->tie_tol));
         }
         if (o->certify) {
             int32_t cnt = 0;

@@ -158,4 +158,4 @@ mrf_status launch_merge(const float2* Z, int64_t n, const mrf_dict* D, int cone,
                         const int32_t* nlist, float tie_tol, int certify, float cert_margin,
                         int32_t* idx_out, float2* rho_out, float2* X_out, int32_t* fb_list,
                         int32_t* fb_n, uint32_t* err, unsigned long long* counters,
-                        cudaStream_t st);
+                        cudaStream_t st, float window = -1.f);   // window < 0: rescore all K

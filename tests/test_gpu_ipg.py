@@ -69,13 +69,16 @@ def test_one_iteration_from_a_phantom_iterate(mrf, cfg1, mode):
     print(f"{mode}: one-step agreement {agree:.5f} ({ties} near-tie swaps)")
 
 
-@pytest.mark.parametrize("mode", ["fp32", "bf16"])
-def test_reconstruct_workload1(mrf, cfg1, mode):
+@pytest.mark.parametrize("mode,cone", [("fp32", "complex"), ("bf16", "complex"),
+                                       ("fp32", "real_pos"), ("bf16", "real_pos")])
+def test_reconstruct_workload1(mrf, cfg1, mode, cone):
+    """Whole BLIP reconstructions against the oracle's, for both readings of the cone (the
+    paper's real positive gamma and the complex density)."""
     dic, p = cfg1
     Ny, Nx, L = p["Ny"], p["Nx"], p["L"]
     n = Ny * Nx
     iters = p["iters"]
-    ref = mo.blip(p["Y"], p["masks"], dic["atoms"], Ny, Nx, iters=iters)
+    ref = mo.blip(p["Y"], p["masks"], dic["atoms"], Ny, Nx, iters=iters, cone=cone)
     D = mrf.build_dict_index(dic["atoms"], dic["params"])
     op = mrf.make_op(Ny, Nx, L, to_dev(p["masks"]))
     X = torch.empty((n, L), dtype=torch.complex64, device="cuda")
@@ -83,14 +86,15 @@ def test_reconstruct_workload1(mrf, cfg1, mode):
     rho = torch.empty(n, dtype=torch.complex64, device="cuda")
     prm = torch.empty((n, dic["params"].shape[1]), dtype=torch.float32, device="cuda")
     st = mrf.reconstruct(D, op, to_dev(p["Y"]), X, idx, rho, prm,
-                         opts=mrf.recon_opts(iters=iters, mode=mode), stats=True)
+                         opts=mrf.recon_opts(iters=iters, mode=mode, cone=cone), stats=True)
     gi = idx.cpu().numpy()
     agree = float(np.mean(gi == ref["idx"]))
     relX = np.linalg.norm(X.cpu().numpy() - ref["X"]) / np.linalg.norm(ref["X"])
     fg = p["phantom"]["labels"] >= 0
     t1g = mo.accuracy(prm.cpu().numpy()[:, 0], p["phantom"]["T1"], fg)
     t1r = mo.accuracy(mo.lut(ref["idx"], dic["params"])[:, 0], p["phantom"]["T1"], fg)
-    print(f"{mode}: agreement {agree:.5f} relX {relX:.2e} T1 acc gpu {t1g:.4f} oracle {t1r:.4f}")
+    print(f"{mode} {cone}: agreement {agree:.5f} relX {relX:.2e} T1 acc gpu {t1g:.4f} "
+          f"oracle {t1r:.4f}")
     assert agree >= 0.995
     assert relX < 1e-3
     assert abs(t1g - t1r) < 2e-3
