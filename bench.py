@@ -162,6 +162,33 @@ def oracle_baseline(Zs: np.ndarray, atoms: np.ndarray, target_s: float = 12.0) -
                       f"projection (numpy complex128), {dt:.1f} s"}
 
 
+def oracle_baseline_1thread(Zs: np.ndarray, atoms: np.ndarray, target_s: float = 6.0) -> dict:
+    """The same oracle timing with one thread (BLAS pinned to one thread in a child process)."""
+    import tempfile
+    with tempfile.TemporaryDirectory() as tmp:
+        np.save(os.path.join(tmp, "z.npy"), Zs)
+        np.save(os.path.join(tmp, "a.npy"), atoms)
+        code = (
+            "import sys, time, json, numpy as np\n"
+            f"sys.path.insert(0, {ROOT!r})\n"
+            "from oracle import mrf_oracle as mo\n"
+            f"Z = np.load({os.path.join(tmp, 'z.npy')!r}); A = np.load({os.path.join(tmp, 'a.npy')!r})\n"
+            "t0 = time.perf_counter(); mo.project(Z[:4], A); t4 = time.perf_counter() - t0\n"
+            f"m = int(min(len(Z), max(4, 4 * {target_s} / max(t4, 1e-3))))\n"
+            "t0 = time.perf_counter(); mo.project(Z[:m], A); dt = time.perf_counter() - t0\n"
+            "print(json.dumps({'m': m, 'dt': dt}))\n")
+        env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1",
+                   MKL_NUM_THREADS="1")
+        r = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True,
+                           timeout=600)
+    if r.returncode != 0:
+        return {"error": r.stderr[-300:]}
+    o = json.loads(r.stdout.strip().splitlines()[-1])
+    d = atoms.shape[0]
+    return {"value": o["m"] * d / o["dt"], "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{o['m']} voxels x {d} atoms, one BLAS thread, {o['dt']:.1f} s"}
+
+
 def make_workload(slice_idx: int):
     import mrfgen
     dic = mrfgen.make_dictionary(2)
@@ -693,12 +720,14 @@ def run_ours(args) -> None:
                 "frac": achieved / peak, "traffic": None, "kernel": "k_fp32_topk",
                 "peak_source": "152 SMs x 128 lanes x 2 flop x 2.07 GHz"}
     launches = int(sum(v[1] for v in prof.values()))
-    cpu = None
+    cpu = cpu1 = None
     if not args.no_cpu:
         from oracle import mrf_oracle as mo
         Zh = mo.adjoint(p["Y"], p["masks"], Ny, Nx)
         g = np.random.Generator(np.random.PCG64(77))
-        cpu = oracle_baseline(Zh[g.permutation(n)[:4096]], atoms)
+        sample = Zh[g.permutation(n)[:4096]]
+        cpu = oracle_baseline(sample, atoms)
+        cpu1 = oracle_baseline_1thread(sample[:256], atoms)
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
@@ -716,6 +745,7 @@ def run_ours(args) -> None:
                       "quality": quality,
                       "stage_ms": {k: v[0] for k, v in prof.items()},
                       "stage_launches": {k: v[1] for k, v in prof.items()},
+                      "cpu_baseline_1thread": cpu1,
                       "fp32_exact_matches_per_s": fp32_rate,
                       "fp32_sample_voxels": args.fp32_sample}}
     print(json.dumps(line), flush=True)
