@@ -86,7 +86,7 @@ typedef struct mrf_proj_opts {
                               (||D_j|| ||Z_v||) is within this absolute distance of the best
                               are rescored in FP64 (default 1e-5) */
     float   cert_margin;   /* margin of `certify`, same units; <= 0 selects the rigorous
-                              bound of the BF16 correlation error, 2^-8 + 2^-18 (operand
+                              bound of the BF16 correlation error, 2^-7 + 2^-16 (operand
                               rounding) + 2L 2^-24 (FP32 accumulation), or for FP8
                               2 u8 + u8^2 + 2L 2^-13 with u8 = 2^-4 + sqrt(2L) 2^-10 / 224
                               (E4M3 rounding of rows scaled into (224, 448]; 13-bit partial
@@ -375,6 +375,52 @@ mrf_status mrf_batch_slice(mrf_batch* batch, int32_t s, void** X, int32_t** idx,
 
 /* Look-up table of all stacked voxels: params_out device float32 [sum n_s][P]. */
 mrf_status mrf_batch_lut(mrf_batch* batch, float* params_out, void* stream);
+
+/*
+ * Temporal subspace compression (§3.3, eqs. CS1, gradupdate and gradcompression; the option of
+ * §4.3 and §6).  V_s (device complex64 [L][s], row t = frame t) spans the s dominant eigenvectors
+ * of the frame Gram matrix sum_j D_j D_j^H.  A fingerprint row x compresses to x conj(V_s)
+ * (= V_s^H x) and a compressed row expands to xc V_s^T.  BLIP then runs on compressed images
+ * [n][s] against a dictionary index built from the compressed atoms (mrf_svd_compress of the
+ * atoms, then mrf_build_dict_index); only V_s V_s^H enters the results, so any orthonormal
+ * basis of the same subspace gives the same reconstruction.
+ */
+typedef struct mrf_svd_op mrf_svd_op;
+
+/* V_out (device complex64 [L][s]) = the s dominant eigenvectors of sum_j D_j D_j^H, each with
+ * its largest-magnitude entry real positive; eig_out (host, may be NULL) = their eigenvalues,
+ * largest first.  Subspace iteration in FP64 with Rayleigh-Ritz; synchronous. */
+mrf_status mrf_svd_basis(const mrf_dict* dict, int32_t s, void* V_out, double* eig_out,
+                         void* stream);
+
+/* Compression operator for V (host or device complex64 [L][s], copied).  With a sampling op
+ * (op->L == L) it also holds, per phase-encode line ky, the s x s matrix
+ * V_s^H diag(mask[., ky]) V_s of the compressed normal operator; op may be NULL for
+ * compression only.  The op's mask must stay alive. */
+mrf_status mrf_svd_op_create(const mrf_op* op, const void* V, int32_t L, int32_t s,
+                             mrf_svd_op** out, void* stream);
+void mrf_svd_op_free(mrf_svd_op* so);
+
+/* Xc [n][s] = X [n][L] conj(V_s) and X [n][L] = Xc V_s^T (device complex64, row-major). */
+mrf_status mrf_svd_compress(const mrf_svd_op* so, const void* X, int64_t n, void* Xc,
+                            void* stream);
+mrf_status mrf_svd_expand(const mrf_svd_op* so, const void* Xc, int64_t n, void* X,
+                          void* stream);
+
+/* One compressed iteration (eq. gradupdate + projection onto cone(D conj(V_s))): dict_c is the
+ * index of the compressed atoms (its L must be s), AHYc = compress(A^H Y), Xc [n][s] in/out,
+ * idx_io the warm start / result.  Same projection options as mrf_project. */
+mrf_status mrf_svd_ipg_step(mrf_dict* dict_c, mrf_svd_op* so, const void* AHYc, void* Xc,
+                            float mu, const mrf_proj_opts* opts, int32_t* idx_io,
+                            void* rho_out, void* stream);
+
+/* Whole compressed BLIP from Xc = 0 with a fixed step: A^H Y, compression, `iters` iterations,
+ * optionally the expanded image X_out [n][L] and the look-up table params_out [n][P].
+ * Synchronous; reports device errors. */
+mrf_status mrf_svd_reconstruct(mrf_dict* dict_c, mrf_svd_op* so, const void* Y, int32_t iters,
+                               float mu, const mrf_proj_opts* opts, void* Xc_out, void* X_out,
+                               int32_t* idx_out, void* rho_out, float* params_out,
+                               void* stream);
 
 /* Look-up table Theta_v = params[idx_v] (Algorithm 2, last step): device int32 [n] ->
  * device float32 [n][P]. */

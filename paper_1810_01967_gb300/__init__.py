@@ -371,6 +371,58 @@ class Batch:
         _check(lib().mrf_batch_lut(self.handle, _ptr(params_out), _stream(stream)))
 
 
+def svd_basis(D: Dictionary, s: int, stream=None):
+    """(V [L, s] complex64 on the GPU, eigenvalues [s] float64) of sum_j D_j D_j^H."""
+    import numpy as np
+    import torch
+    V = torch.empty((D.L, s), dtype=torch.complex64, device="cuda")
+    eig = np.empty(s, np.float64)
+    _check(lib().mrf_svd_basis(D.handle, s, _ptr(V), eig.ctypes.data, _stream(stream)))
+    return V, eig
+
+
+class SvdOp:
+    """Temporal compression with basis V [L, s] (mrf_svd_op); `op` adds the compressed normal
+    operator of that sampling pattern."""
+
+    def __init__(self, V, op: Op | None = None, stream=None):
+        L, s = V.shape
+        h = C.c_void_p()
+        _check(lib().mrf_svd_op_create(None if op is None else C.byref(op), _ptr(V), L, s,
+                                       C.byref(h), _stream(stream)))
+        self.handle, self.L, self.s, self._op, self._V = h, L, s, op, V
+
+    def close(self):
+        if getattr(self, "handle", None):
+            lib().mrf_svd_op_free(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def compress(self, X, Xc, stream=None):
+        _check(lib().mrf_svd_compress(self.handle, _ptr(X), X.shape[0], _ptr(Xc), _stream(stream)))
+
+    def expand(self, Xc, X, stream=None):
+        _check(lib().mrf_svd_expand(self.handle, _ptr(Xc), Xc.shape[0], _ptr(X), _stream(stream)))
+
+    def ipg_step(self, Dc: Dictionary, AHYc, Xc, mu: float, idx_io, rho_out=None, opts=None,
+                 stream=None):
+        o = opts or proj_opts()
+        _check(lib().mrf_svd_ipg_step(Dc.handle, self.handle, _ptr(AHYc), _ptr(Xc), mu, C.byref(o),
+                                      _ptr(idx_io), _ptr(rho_out), _stream(stream)))
+
+    def reconstruct(self, Dc: Dictionary, Y, iters: int, Xc_out, idx_out, X_out=None,
+                    rho_out=None, params_out=None, mu: float = 1.0, opts=None, stream=None):
+        o = opts or proj_opts()
+        _check(lib().mrf_svd_reconstruct(Dc.handle, self.handle, _ptr(Y), iters, mu, C.byref(o),
+                                         _ptr(Xc_out), _ptr(X_out), _ptr(idx_out), _ptr(rho_out),
+                                         _ptr(params_out), _stream(stream)))
+
+
 def attach_mlp(D: Dictionary, mlp) -> None:
     _check(lib().mrf_dict_attach_mlp(D.handle, None if mlp is None else mlp.handle))
     D._mlp = mlp

@@ -144,6 +144,17 @@ SIGNATURES = {
                                   C.POINTER(C.c_void_p), C.POINTER(C.c_void_p),
                                   C.POINTER(C.c_int64), C.POINTER(C.c_int64)]),
     "mrf_batch_lut": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
+    "mrf_svd_basis": (C.c_int, [C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "mrf_svd_op_create": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int32, C.c_int32,
+                                    C.POINTER(C.c_void_p), C.c_void_p]),
+    "mrf_svd_op_free": (None, [C.c_void_p]),
+    "mrf_svd_compress": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p]),
+    "mrf_svd_expand": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p]),
+    "mrf_svd_ipg_step": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_float,
+                                   C.POINTER(ProjOpts), C.c_void_p, C.c_void_p, C.c_void_p]),
+    "mrf_svd_reconstruct": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32, C.c_float,
+                                      C.POINTER(ProjOpts), C.c_void_p, C.c_void_p, C.c_void_p,
+                                      C.c_void_p, C.c_void_p, C.c_void_p]),
     "mrf_status_str": (C.c_char_p, [C.c_int]),
     "mrf_last_error": (C.c_char_p, []),
 }

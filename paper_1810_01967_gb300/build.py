@@ -77,7 +77,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
     objs = [o for o, _ in results]
     tmp = LIB + ".tmp"
     cmd = [nvcc, "-shared", "-o", tmp] + objs + ARCH + [
-        "-cudart", "shared", "-lcufft", "-L", os.path.join(home, "lib64"),
+        "-cudart", "shared", "-lcufft", "-lcublas", "-L", os.path.join(home, "lib64"),
         "-Xlinker", "-rpath," + os.path.join(home, "lib64")]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:

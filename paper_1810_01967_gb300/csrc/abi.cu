@@ -197,25 +197,20 @@ void prof_clear() {
 
 }  // namespace
 
-// Records an event pair around a stage on `st` while profiling is enabled.
-struct ProfScope {
-    bool on;
-    ProfEntry e;
-    cudaStream_t st;
-    ProfScope(int stage, int launches, cudaStream_t s) : on(g_prof_on), st(s) {
-        if (!on) return;
-        e.stage = stage;
-        e.launches = launches;
-        cudaEventCreate(&e.a);
-        cudaEventCreate(&e.b);
-        cudaEventRecord(e.a, st);
-    }
-    ~ProfScope() {
-        if (!on) return;
-        cudaEventRecord(e.b, st);
-        g_prof_pending.push_back(e);
-    }
-};
+ProfScope::ProfScope(int stage, int launches, cudaStream_t s) : on(g_prof_on), st(s) {
+    if (!on) return;
+    stage_ = stage;
+    launches_ = launches;
+    cudaEventCreate(&a_);
+    cudaEventCreate(&b_);
+    cudaEventRecord(a_, st);
+}
+
+ProfScope::~ProfScope() {
+    if (!on) return;
+    cudaEventRecord(b_, st);
+    g_prof_pending.push_back(ProfEntry{stage_, launches_, a_, b_});
+}
 
 namespace {
 // Options whose cert_margin selects the rigorous bound (for the merge's rescore window).
@@ -227,10 +222,10 @@ const mrf_proj_opts kRigorous = [] {
 }();
 
 mrf_status bf16_margin(const mrf_dict* D, const mrf_proj_opts* o, float* m) {
-    // |c~ - c| <= (2u + u^2) ||d|| ||z|| for BF16 operand rounding (u = 2^-9) plus the FP32
-    // accumulation of 2L products; in normalised-correlation units
+    // |c~ - c| <= (2u + u^2) ||d|| ||z|| for BF16 operand rounding (8 significant bits:
+    // u = 2^-8) plus the FP32 accumulation of 2L products; in normalised-correlation units
     *m = o->cert_margin > 0.f ? o->cert_margin
-                              : static_cast<float>(std::ldexp(1.0, -8) + std::ldexp(1.0, -18) +
+                              : static_cast<float>(std::ldexp(1.0, -7) + std::ldexp(1.0, -16) +
                                                    2.0 * D->L * std::ldexp(1.0, -24));
     return MRF_OK;
 }

@@ -89,6 +89,18 @@ void mrf_set_error(const std::string& msg);
         if (s_ != MRF_OK) return s_;                                                    \
     } while (0)
 
+// Records an event pair around a stage on `st` while the stage profiler is enabled (abi.cu).
+struct ProfScope {
+    ProfScope(int stage, int launches, cudaStream_t s);
+    ~ProfScope();
+    ProfScope(const ProfScope&) = delete;
+    ProfScope& operator=(const ProfScope&) = delete;
+    bool on;
+    cudaStream_t st;
+    int stage_ = 0, launches_ = 0;
+    cudaEvent_t a_ = nullptr, b_ = nullptr;
+};
+
 // ----- host helpers shared across translation units (abi.cu)
 mrf_status project_core(mrf_dict* D, const float2* Z, int64_t n, const mrf_proj_opts* o,
                         const int32_t* warm, int32_t* idx_out, float2* rho_out, float2* X_out,

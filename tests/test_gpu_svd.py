@@ -1,0 +1,142 @@
+"""GPU parity of the subspace-compressed BLIP (§3.3: eqs. CS1, gradupdate, gradcompression)
+against the float64 oracle (oracle/svd.py): the basis spans the dominant eigenvectors of the
+frame Gram matrix, compression and expansion, one compressed iteration from a common iterate,
+whole compressed reconstructions in FP32 and BF16, and the full basis reproducing BLIP."""
+import numpy as np
+import pytest
+
+import mrfgen
+from oracle import mrf_oracle as mo
+from oracle import svd as osvd
+from gpu_util import to_dev, check_projection
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def mrf():
+    import paper_1810_01967_gb300 as m
+    from paper_1810_01967_gb300 import build as b
+    b.build()
+    return m
+
+
+@pytest.fixture(scope="module")
+def cfg1():
+    dic = mrfgen.make_dictionary(1)
+    p = mrfgen.make_problem(1, dic=dic)
+    return dic, p
+
+
+@pytest.mark.parametrize("s", [10, 25])
+def test_basis_matches_oracle(mrf, cfg1, s):
+    dic, _ = cfg1
+    A = dic["atoms"]
+    D = mrf.build_dict_index(A)
+    V, eig = mrf.svd_basis(D, s)
+    Vg = V.cpu().numpy().astype(np.complex128)
+    Vo, wo = osvd.svd_basis(A, s)
+    assert np.max(np.abs(Vg.conj().T @ Vg - np.eye(s))) < 1e-5
+    # FP64 Gram matrix: eigenvalues to rounding of the largest
+    np.testing.assert_allclose(eig, wo, rtol=1e-6, atol=1e-9 * wo[0])
+    # same subspace: the principal cosines are all ~1
+    cos = np.linalg.svd(Vo.conj().T @ Vg, compute_uv=False)
+    assert cos.min() > 0.9999, cos.min()
+    # energy kept by the GPU basis equals the oracle's optimum
+    kg = np.sum(np.abs(osvd.compress(A, Vg)) ** 2)
+    assert abs(kg - wo.sum()) <= 2e-4 * wo.sum()
+
+
+def test_compress_expand(mrf, cfg1):
+    dic, p = cfg1
+    L = p["L"]
+    Vo, _ = osvd.svd_basis(dic["atoms"], 16)
+    V = to_dev(Vo.astype(np.complex64))
+    so = mrf.SvdOp(V)
+    g = np.random.Generator(np.random.PCG64(5))
+    X = (g.standard_normal((333, L)) + 1j * g.standard_normal((333, L))).astype(np.complex64)
+    Xc = torch.empty((333, 16), dtype=torch.complex64, device="cuda")
+    so.compress(to_dev(X), Xc)
+    ref = osvd.compress(X, Vo.astype(np.complex64))
+    np.testing.assert_allclose(Xc.cpu().numpy(), ref, atol=1e-5 * np.abs(ref).max())
+    Xe = torch.empty((333, L), dtype=torch.complex64, device="cuda")
+    so.expand(Xc, Xe)
+    refe = osvd.expand(Xc.cpu().numpy(), Vo.astype(np.complex64))
+    np.testing.assert_allclose(Xe.cpu().numpy(), refe, atol=1e-5 * np.abs(refe).max())
+
+
+def _setup(mrf, dic, p, s):
+    Vo, _ = osvd.svd_basis(dic["atoms"], s)
+    V64 = Vo.astype(np.complex64)
+    Vd = to_dev(V64)
+    op = mrf.make_op(p["Ny"], p["Nx"], p["L"], to_dev(p["masks"]))
+    so = mrf.SvdOp(Vd, op)
+    Ac = osvd.compress(dic["atoms"], V64).astype(np.complex64)
+    Dc = mrf.build_dict_index(Ac, dic["params"])
+    return V64, so, Dc, Ac
+
+
+def test_one_compressed_iteration(mrf, cfg1):
+    dic, p = cfg1
+    Ny, Nx = p["Ny"], p["Nx"]
+    n, s = Ny * Nx, 20
+    V64, so, Dc, Ac = _setup(mrf, dic, p, s)
+    r1 = osvd.blip_svd(p["Y"], p["masks"], dic["atoms"], V64, Ny, Nx, iters=1)
+    Xc1 = r1["Xc"].astype(np.complex64)
+    # oracle's second gradient step from the same (rounded) iterate
+    Zc = osvd.gradient_step_c(Xc1, p["Y"], p["masks"], Ny, Nx, 1.0, V64)
+    AHYc = to_dev(osvd.compress(mo.adjoint(p["Y"], p["masks"], Ny, Nx), V64).astype(np.complex64))
+    Xd = to_dev(Xc1)
+    idx = to_dev(r1["idx"].astype(np.int32))
+    rho = torch.empty(n, dtype=torch.complex64, device="cuda")
+    so.ipg_step(Dc, AHYc, Xd, 1.0, idx, rho, opts=mrf.proj_opts(mode="fp32"))
+    torch.cuda.synchronize()
+    agree, ties = check_projection(Zc, Ac, idx.cpu().numpy(), rho.cpu().numpy(),
+                                   g_X=Xd.cpu().numpy(), tie=1e-5)
+    print(f"compressed step: agreement {agree:.5f} ({ties} near-tie swaps)")
+
+
+@pytest.mark.parametrize("mode", ["fp32", "bf16"])
+def test_compressed_reconstruction(mrf, cfg1, mode):
+    dic, p = cfg1
+    Ny, Nx, L = p["Ny"], p["Nx"], p["L"]
+    n, s, iters = Ny * Nx, 20, p["iters"]
+    V64, so, Dc, Ac = _setup(mrf, dic, p, s)
+    ref = osvd.blip_svd(p["Y"], p["masks"], dic["atoms"], V64, Ny, Nx, iters=iters)
+    Xc = torch.empty((n, s), dtype=torch.complex64, device="cuda")
+    X = torch.empty((n, L), dtype=torch.complex64, device="cuda")
+    idx = torch.empty(n, dtype=torch.int32, device="cuda")
+    prm = torch.empty((n, dic["params"].shape[1]), dtype=torch.float32, device="cuda")
+    so.reconstruct(Dc, to_dev(p["Y"]), iters, Xc, idx, X, None, prm,
+                   opts=mrf.proj_opts(mode=mode, certify=(mode == "bf16")))
+    gi = idx.cpu().numpy()
+    agree = float(np.mean(gi == ref["idx"]))
+    relX = np.linalg.norm(X.cpu().numpy() - ref["X"]) / np.linalg.norm(ref["X"])
+    print(f"svd s={s} {mode}: agreement {agree:.5f} relX {relX:.2e}")
+    assert agree >= 0.995
+    assert relX < 1e-3
+    assert np.array_equal(prm.cpu().numpy(), dic["params"][gi])
+
+
+def test_full_basis_reproduces_blip(mrf, cfg1):
+    dic, p = cfg1
+    Ny, Nx, L = p["Ny"], p["Nx"], p["L"]
+    n, iters = Ny * Nx, 4
+    D = mrf.build_dict_index(dic["atoms"], dic["params"])
+    V, _ = mrf.svd_basis(D, L)
+    op = mrf.make_op(Ny, Nx, L, to_dev(p["masks"]))
+    so = mrf.SvdOp(V, op)
+    Ac = torch.empty((dic["atoms"].shape[0], L), dtype=torch.complex64, device="cuda")
+    mrf.SvdOp(V).compress(to_dev(dic["atoms"]), Ac)
+    Dc = mrf.build_dict_index(Ac, dic["params"])
+    Xc = torch.empty((n, L), dtype=torch.complex64, device="cuda")
+    X = torch.empty((n, L), dtype=torch.complex64, device="cuda")
+    idx = torch.empty(n, dtype=torch.int32, device="cuda")
+    so.reconstruct(Dc, to_dev(p["Y"]), iters, Xc, idx, X, opts=mrf.proj_opts(mode="fp32"))
+    ref = mo.blip(p["Y"], p["masks"], dic["atoms"], Ny, Nx, iters=iters)
+    agree = float(np.mean(idx.cpu().numpy() == ref["idx"]))
+    relX = np.linalg.norm(X.cpu().numpy() - ref["X"]) / np.linalg.norm(ref["X"])
+    print(f"full basis: agreement with BLIP {agree:.5f} relX {relX:.2e}")
+    assert agree >= 0.995 and relX < 1e-3
