@@ -277,6 +277,42 @@ def reconstruction_quality(mrf, D, op, p, dic, dev, stream, iters: int, fp32: bo
                      "B0_mae_hz": float(np.mean(np.abs(pr[fg, 2] - ph["B0"][fg]))),
                      "exhaustive_fallback_voxel_iters": st["n_fallback"],
                      "tree_distance_evals": st["n_dist_evals"], **kw}
+    if forms:
+        # temporal subspace compression (§3.3): BF16 BLIP on s-dimensional proxies
+        A_dev = torch.from_numpy(dic["atoms"]).to(dev)
+        energy = float(np.sum(np.abs(dic["atoms"].astype(np.complex128)) ** 2))
+        for s in (50, 200):
+            t0 = time.perf_counter()
+            V, eig = mrf.svd_basis(D, s)
+            basis_s = time.perf_counter() - t0
+            so = mrf.SvdOp(V, op)
+            Ac = torch.empty((d, s), dtype=torch.complex64, device=dev)
+            so.compress(A_dev, Ac)
+            Dc = mrf.build_dict_index(Ac, dic["params"])
+            Xc = torch.empty((n, s), dtype=torch.complex64, device=dev)
+            idx = torch.empty(n, dtype=torch.int32, device=dev)
+            prm = torch.empty((n, dic["params"].shape[1]), dtype=torch.float32, device=dev)
+            o = mrf.proj_opts(mode="bf16", certify=False)
+            so.reconstruct(Dc, Yd, 1, Xc, idx, opts=o)        # warm-up (plans, scratch)
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            so.reconstruct(Dc, Yd, iters, Xc, idx, None, None, prm, opts=o)
+            b.record(stream)
+            torch.cuda.synchronize()
+            sec = a.elapsed_time(b) / 1e3
+            pr = prm.cpu().numpy()
+            key = f"bf16_svd{s}"
+            idxs[key] = idx.cpu().numpy()
+            out[key] = {"s_per_slice": sec, "iters": iters, "s": s,
+                        "matches_per_s": n * d * iters / sec,
+                        "T1_acc": mo.accuracy(pr[:, 0], ph["T1"], fg),
+                        "T2_acc": mo.accuracy(pr[:, 1], ph["T2"], fg),
+                        "B0_mae_hz": float(np.mean(np.abs(pr[fg, 2] - ph["B0"][fg]))),
+                        "energy_kept": float(eig.sum() / energy), "basis_s": basis_s}
+            so.close()
+            Dc.close()
+        del A_dev
     for mode in idxs:
         if "fp32" in idxs:
             out[mode]["atom_agreement_vs_fp32"] = float(np.mean(idxs[mode] == idxs["fp32"]))
