@@ -72,7 +72,13 @@ typedef struct mrf_index_opts {
                               Euclidean distance of the unit atoms */
     float   tree_dup_tol;  /* atoms within this distance of an earlier node are represented by
                               it (default 1e-5) */
-    int32_t reserved[3];
+    int32_t phase_align;   /* §4.3 phase alignment (default 0): atoms are stored rotated so that
+                              v1^H D_j is real positive (v1 = dominant eigenvector of
+                              sum_j D_j D_j^H); projections with MRF_CONE_REAL_POS rotate each
+                              query the same way, project with the real positive density and
+                              restore the query's phase, so rho = gamma e^{i(beta_v - alpha_j)}.
+                              Densities are always reported relative to the atoms as given. */
+    int32_t reserved[2];
 } mrf_index_opts;
 
 typedef struct mrf_proj_opts {

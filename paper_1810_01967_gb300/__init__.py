@@ -84,13 +84,15 @@ class Dictionary:
 
     def __init__(self, atoms, params=None, grid_shape=None, pack_bf16: bool = True,
                  build_tree: bool = False, tree_cone: str = "complex",
-                 tree_dup_tol: float = 1e-5, stream=None, pack_fp8: bool = False):
+                 tree_dup_tol: float = 1e-5, stream=None, pack_fp8: bool = False,
+                 phase_align: bool = False):
         import numpy as np
         d, L = atoms.shape
         o = IndexOpts()
         lib().mrf_default_index_opts(C.byref(o))
         o.pack_bf16 = int(pack_bf16)
         o.pack_fp8 = int(pack_fp8)
+        o.phase_align = int(phase_align)
         o.build_tree = int(build_tree)
         o.tree_cone = CONES[tree_cone]
         o.tree_dup_tol = tree_dup_tol
@@ -157,9 +159,10 @@ class Dictionary:
 
 
 def build_dict_index(atoms, params=None, grid_shape=None, pack_bf16=True, build_tree=False,
-                     tree_cone="complex", tree_dup_tol=1e-5, stream=None, pack_fp8=False):
+                     tree_cone="complex", tree_dup_tol=1e-5, stream=None, pack_fp8=False,
+                     phase_align=False):
     return Dictionary(atoms, params, grid_shape, pack_bf16, build_tree, tree_cone, tree_dup_tol,
-                      stream, pack_fp8)
+                      stream, pack_fp8, phase_align)
 
 
 def tree_build_host(atoms, cone: str = "complex", dup_tol: float = 1e-5) -> dict:

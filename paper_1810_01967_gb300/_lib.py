@@ -21,7 +21,7 @@ CONES = {"complex": 0, "real_pos": 1}
 class IndexOpts(C.Structure):
     _fields_ = [("pack_bf16", C.c_int32), ("pack_fp8", C.c_int32), ("build_tree", C.c_int32),
                 ("tree_cone", C.c_int32), ("tree_dup_tol", C.c_float),
-                ("reserved", C.c_int32 * 3)]
+                ("phase_align", C.c_int32), ("reserved", C.c_int32 * 2)]
 
 
 class TreeInfo(C.Structure):

@@ -109,6 +109,7 @@ mrf_status ensure_scratch(mrf_dict* D, int64_t n) {
         MRF_TRY(dalloc(&D->qs8, static_cast<size_t>(n)));
     }
     if (D->xprev) MRF_TRY(dalloc(&D->xprev, static_cast<size_t>(n * L)));
+    if (D->aligned) MRF_TRY(dalloc(&D->qph, static_cast<size_t>(n)));
     D->cap_n = n;
     return MRF_OK;
 }
@@ -306,8 +307,9 @@ mrf_status exhaustive_on_list(mrf_dict* D, const float2* Z, int32_t cnt, const m
                         0.f, idx_out, rho_out, X_out, nullptr, nullptr, D->err, D->counters, st);
 }
 
+namespace {
 // The projection proper.  `zq_ready` says the BF16 operand of Z is already in D->zq.
-mrf_status project_core(mrf_dict* D, const float2* Z, int64_t n, const mrf_proj_opts* o,
+mrf_status project_impl(mrf_dict* D, const float2* Z, int64_t n, const mrf_proj_opts* o,
                         const int32_t* warm, int32_t* idx_out, float2* rho_out, float2* X_out,
                         bool zq_ready, cudaStream_t st) {
     (void)warm;
@@ -429,6 +431,28 @@ mrf_status project_core(mrf_dict* D, const float2* Z, int64_t n, const mrf_proj_
     }
     return fail(MRF_EUNSUPPORTED, "projection mode not available in this build");
 }
+}  // namespace
+
+// Projection with the dictionary's phase alignment applied when it has one: queries rotated by
+// their v1 phase for the real cone (into the FFT workspace), densities mapped back to the atoms
+// as given, and the voxel phase restored in X.
+mrf_status project_core(mrf_dict* D, const float2* Z, int64_t n, const mrf_proj_opts* o,
+                        const int32_t* warm, int32_t* idx_out, float2* rho_out, float2* X_out,
+                        bool zq_ready, cudaStream_t st) {
+    if (!D->aligned || n == 0)
+        return project_impl(D, Z, n, o, warm, idx_out, rho_out, X_out, zq_ready, st);
+    MRF_TRY(ensure_scratch(D, n));
+    const bool realc = (o->cone == MRF_CONE_REAL_POS);
+    const float2* Zs = Z;
+    if (realc) {
+        MRF_TRY(launch_align_queries(D, Z, n, D->wbuf, D->qph, st));
+        Zs = D->wbuf;
+        zq_ready = false;
+    }
+    MRF_TRY(project_impl(D, Zs, n, o, warm, idx_out, rho_out, X_out, zq_ready, st));
+    return launch_align_post(D, n, idx_out, realc ? D->qph : nullptr, rho_out,
+                             realc ? X_out : nullptr, st);
+}
 
 // Z = X - mu (A^H A X - AHY) for one slice: W is an n x L FFT workspace, zq (optional) receives
 // the BF16 query operand of Z.
@@ -522,7 +546,7 @@ void mrf_dict_free(mrf_dict* D) {
     if (D->tree) ct_free(D->tree);
     if (D->mlp) mlp_detach(D->mlp);
     void* ptrs[] = {D->atoms, D->inv_norm2, D->norm2, D->params, D->bop, D->zq, D->fop,
-                    D->zq8, D->qs8, D->zbuf,
+                    D->zq8, D->qs8, D->v1, D->ealign, D->qph, D->zbuf,
                     D->wbuf, D->xprev, D->vlist, D->vlist2, D->nlist, D->part, D->err,
                     D->counters, D->red};
     for (void* p : ptrs)
@@ -578,6 +602,7 @@ mrf_status mrf_build_dict_index(const void* atoms, int64_t d, int32_t L, const f
     if ((e = cudaMemsetAsync(D->counters, 0, sizeof(unsigned long long) * CNT_N, st)))
         return cuda_bail(e, "memset");
     if ((s = launch_atom_norms(D, st)) != MRF_OK) return bail(s);
+    if (o.phase_align && (s = phase_align_dictionary(D, st)) != MRF_OK) return bail(s);
     D->nblk = (d + 127) / 128;
     if (o.pack_bf16) {
         D->Kp = ((2 * L + 15) / 16) * 16;

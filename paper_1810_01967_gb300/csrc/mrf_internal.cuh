@@ -67,6 +67,11 @@ struct mrf_dict {
     double* red = nullptr;          // [8] reductions (norms for the step rule / kappa)
     CoverTreeDev* tree = nullptr;
     mrf_mlp* mlp = nullptr;          // attached learned proposal (not owned)
+    // phase alignment (real positive cone on complex data): atoms stored as D_j e^{-i alpha_j}
+    bool aligned = false;
+    float2* v1 = nullptr;            // [L] dominant eigenvector of sum_j D_j D_j^H
+    float2* ealign = nullptr;        // [d] e^{i alpha_j}
+    float2* qph = nullptr;           // [cap_n] e^{i beta_v} of the last aligned queries
     int num_sms = 148;
     mrf_tune tune = {};              // requested geometry (0 = default) and last launches
 };
@@ -158,6 +163,12 @@ mrf_status launch_ct_search(const float2* Z, int64_t n, const mrf_dict* D, int c
 mrf_status ct_info(const mrf_dict* D, mrf_tree_info* info);
 mrf_status ct_export(const mrf_dict* D, int32_t* first_level, int32_t* parent, int32_t* rep,
                      int32_t* en_atom, int32_t* en_level, float* en_maxdist);
+// phase.cu
+mrf_status phase_align_dictionary(mrf_dict* D, cudaStream_t st);
+mrf_status launch_align_queries(const mrf_dict* D, const float2* Z, int64_t n, float2* Zout,
+                                float2* eb, cudaStream_t st);
+mrf_status launch_align_post(const mrf_dict* D, int64_t n, const int32_t* idx, const float2* eb,
+                             float2* rho, float2* X, cudaStream_t st);
 // mlp.cu
 void mlp_detach(mrf_mlp* M);
 mrf_status learned_candidates(mrf_dict* D, const float2* Z, int64_t n, int cone, float* part_s,
