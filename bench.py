@@ -362,8 +362,11 @@ def reconstruction_quality(mrf, D, op, p, dic, dev, stream, iters: int, fp32: bo
 
 
 def run_profile_case(args) -> None:
-    """Projection only (mrf_project, BF16) on the first N voxels of A^H Y of the workload's
-    slice: the small case for kernel-level ncu captures (about 2 GB on the device)."""
+    """Projection only (mrf_project) on N voxels of the workload's slice: the small case for
+    kernel-level ncu captures (about 2 GB on the device).  Exhaustive modes project the first
+    N rows of A^H Y; the cover tree (eps 0.4) projects the phantom's object fingerprints with
+    the slice's noise level, i.e. queries near the dictionary, where the tree search does its
+    work instead of routing far queries to the exhaustive search."""
     import torch
     import paper_1810_01967_gb300 as mrf
     from paper_1810_01967_gb300 import build as b
@@ -371,16 +374,26 @@ def run_profile_case(args) -> None:
     dic, p = make_workload(0)
     Ny, Nx, L = p["Ny"], p["Nx"], p["L"]
     n = args.profile_case
-    D = mrf.build_dict_index(dic["atoms"], dic["params"], pack_fp8=(args.mode == "fp8"))
-    mask = torch.from_numpy(p["masks"]).cuda()
-    op = mrf.make_op(Ny, Nx, L, mask)
-    AHY = torch.empty((Ny * Nx, L), dtype=torch.complex64, device="cuda")
-    mrf.adjoint(op, torch.from_numpy(p["Y"]).cuda(), AHY)
-    Z = AHY[:n].contiguous()
-    del AHY
+    tree = args.mode == "covertree"
+    D = mrf.build_dict_index(dic["atoms"], dic["params"], pack_fp8=(args.mode == "fp8"),
+                             build_tree=tree)
+    if tree:
+        fg = np.flatnonzero(p["phantom"]["labels"] >= 0)
+        g = np.random.Generator(np.random.PCG64(123))
+        X0 = p["X0"][fg[g.integers(0, fg.size, n)]].astype(np.complex128)
+        sig = 0.01 * np.linalg.norm(X0, axis=1, keepdims=True) / np.sqrt(2 * L)
+        X0 += sig * (g.standard_normal(X0.shape) + 1j * g.standard_normal(X0.shape))
+        Z = torch.from_numpy(X0.astype(np.complex64)).cuda()
+    else:
+        mask = torch.from_numpy(p["masks"]).cuda()
+        op = mrf.make_op(Ny, Nx, L, mask)
+        AHY = torch.empty((Ny * Nx, L), dtype=torch.complex64, device="cuda")
+        mrf.adjoint(op, torch.from_numpy(p["Y"]).cuda(), AHY)
+        Z = AHY[:n].contiguous()
+        del AHY
     idx = torch.empty(n, dtype=torch.int32, device="cuda")
     rho = torch.empty(n, dtype=torch.complex64, device="cuda")
-    o = mrf.proj_opts(mode=args.mode, certify=False)
+    o = mrf.proj_opts(mode=args.mode, certify=False, eps=0.4 if tree else 0.0)
     mrf.profile_enable(True)
     for _ in range(args.steps):
         mrf.project(D, Z, idx, rho, opts=o)
@@ -682,6 +695,12 @@ def run_ours(args) -> None:
     rho = torch.empty(n, dtype=torch.complex64, device=dev)
     prm = torch.empty((n, params.shape[1]), dtype=torch.float32, device=dev)
     opts = mrf.proj_opts(mode=args.mode, certify=False)
+    tuned = None
+    if args.autotune and args.mode in ("bf16", "fp8"):
+        from paper_1810_01967_gb300 import autotune
+        tuned = autotune.tune(D, AHY, args.mode,
+                              grid={"bf16_cluster": (1, 2, 4), "bf16_live_tiles": (16, 32, 64, 128),
+                                    "bf16_splits": (0,)}, reps=2)
 
     def step(Xb, AHYb, idxb, rhob, prmb):
         mrf.ipg_step(D, op, AHYb, Xb, 1.0, idxb, rhob, opts=opts)
@@ -803,6 +822,7 @@ def run_ours(args) -> None:
                       "stage_ms": {k: v[0] for k, v in prof.items()},
                       "stage_launches": {k: v[1] for k, v in prof.items()},
                       "cpu_baseline_1thread": cpu1,
+                      "autotune": tuned,
                       "fp32_exact_matches_per_s": fp32_rate,
                       "fp32_sample_voxels": args.fp32_sample}}
     print(json.dumps(line), flush=True)
@@ -820,7 +840,10 @@ def main():
     ap.add_argument("--no-forms", action="store_true", help="skip the cover tree and learned forms")
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--mode", default="bf16", choices=["bf16", "fp8", "fp32"])
+    ap.add_argument("--mode", default="bf16", choices=["bf16", "fp8", "fp32", "covertree"],
+                    help="projection of the timed step (covertree: --profile-case only)")
+    ap.add_argument("--autotune", action="store_true",
+                    help="time the search geometries on the workload first and use the fastest")
     ap.add_argument("--fp32-sample", type=int, default=0)
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--workload", default="slice", choices=["slice", "slices64", "tree1m"],

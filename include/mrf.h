@@ -447,7 +447,10 @@ typedef struct mrf_tune {
     int32_t last_bf16_cluster; /* out: its cluster size */
     int32_t last_bf16_splits;  /* out: its atom splits */
     int32_t last_fp32_splits;  /* out: atom splits of the last FP32 search launch */
-    int32_t reserved[8];
+    int32_t tree_list_cap;     /* cover-tree candidate list capacity per voxel, 64..512 (0 = 256);
+                                  smaller lists fit more warps per SM, longer lists route fewer
+                                  voxels to the exhaustive search */
+    int32_t reserved[7];
 } mrf_tune;
 
 mrf_status mrf_get_tune(const mrf_dict* dict, mrf_tune* out);

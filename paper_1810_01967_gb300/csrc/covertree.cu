@@ -2,7 +2,8 @@
 // §4.3 eq. ANN1 and Algorithm 2: the search runs on Z_v / ||Z_v||, warm-started at the previous
 // atom).
 //
-// One warp per voxel.  The tree lives flat in HBM: unit atoms in BFS order (the children of a
+// One warp per voxel; the children a level adds are evaluated eight at a time (one pass over
+// the frames with eight independent accumulations per lane).  The tree lives flat in HBM: unit atoms in BFS order (the children of a
 // node at a level are contiguous rows), and per node a CSR list of its "explicit" levels -- the
 // levels at which it has children other than itself -- with the children's position range and
 // the exact maxdist of the node at that level.  The candidate sets Q_i of Algorithm 1 are two
@@ -40,10 +41,13 @@ struct CoverTreeDev {
 
 namespace {
 
-constexpr int CAP = 512;          // candidates per list per warp
+constexpr int CAP = 256;          // candidate list per warp unless mrf_tune.tree_list_cap says
+                                  // otherwise: 256 keeps 12 warps per SM resident and routes
+                                  // only a few more voxels to the exhaustive search than 512
 constexpr int WARPS = 4;          // warps (queries) per CTA
 constexpr int TOPC = 8;           // candidates handed to the merge
 constexpr int kRouteList = 64;    // list size from which far queries are routed away
+constexpr int kBatch = 8;         // candidate distances evaluated together
 
 struct TreeArgs {
     const float2* tatoms;
@@ -111,6 +115,64 @@ __device__ __forceinline__ float tree_dist(const TreeArgs& T, const float2* q, i
     return sqrtf(d2);
 }
 
+// The same distances for up to B candidates at once: one pass over the frames with B
+// independent accumulations per lane (B loads in flight instead of one), then the accurate
+// second pass for the few close ones.  nb (<= B) is uniform across the warp.
+template <int B>
+__device__ __forceinline__ void tree_dist_batch(const TreeArgs& T, const float2* q, int L,
+                                                const int32_t (&pos)[B], int nb, int lane,
+                                                float (&dist)[B], float (&corr)[B]) {
+    float re[B], im[B];
+    const float2* u[B];
+#pragma unroll
+    for (int b = 0; b < B; ++b) {
+        re[b] = 0.f;
+        im[b] = 0.f;
+        u[b] = T.tatoms + static_cast<int64_t>(b < nb ? pos[b] : pos[0]) * L;
+    }
+#pragma unroll 2
+    for (int t = lane; t < L; t += 32) {
+        const float2 z = q[t];
+#pragma unroll
+        for (int b = 0; b < B; ++b) {
+            if (b < nb) {
+                const float2 a = u[b][t];
+                re[b] = fmaf(a.x, z.x, fmaf(a.y, z.y, re[b]));
+                im[b] = fmaf(a.x, z.y, fmaf(-a.y, z.x, im[b]));
+            }
+        }
+    }
+#pragma unroll
+    for (int b = 0; b < B; ++b) {
+        if (b >= nb) continue;
+        const float r = warp_sum(re[b]);
+        const float m = warp_sum(im[b]);
+        float c, wr, wi;
+        if (T.metric == 0) {
+            c = sqrtf(r * r + m * m);
+            wr = c > 0.f ? r / c : 1.f;
+            wi = c > 0.f ? m / c : 0.f;
+        } else {
+            c = r;
+            wr = 1.f;
+            wi = 0.f;
+        }
+        corr[b] = c;
+        float d2 = fmaxf(0.f, 2.f - 2.f * c);
+        if (d2 < 0.04f) {   // accurate small distances: ||z^ - w u||^2
+            float sacc = 0.f;
+            for (int t = lane; t < L; t += 32) {
+                const float2 a = u[b][t], z = q[t];
+                const float xr = z.x - (wr * a.x - wi * a.y);
+                const float xi = z.y - (wr * a.y + wi * a.x);
+                sacc = fmaf(xr, xr, fmaf(xi, xi, sacc));
+            }
+            d2 = warp_sum(sacc);
+        }
+        dist[b] = sqrtf(d2);
+    }
+}
+
 __device__ __forceinline__ void top_insert(float (&cs)[TOPC], int32_t (&ci)[TOPC], float c,
                                            int32_t a) {
     if (c > cs[TOPC - 1]) {
@@ -130,7 +192,7 @@ __device__ __forceinline__ void top_insert(float (&cs)[TOPC], int32_t (&ci)[TOPC
 }
 
 __global__ void __launch_bounds__(WARPS * 32)
-k_ct_search(const float2* __restrict__ Z, int64_t n, int L, TreeArgs T,
+k_ct_search(const float2* __restrict__ Z, int64_t n, int L, TreeArgs T, int cap,
             const int32_t* __restrict__ warm, float eps, float route,
             float* __restrict__ part_s,
             int32_t* __restrict__ part_i, int32_t* __restrict__ fb_list,
@@ -139,11 +201,11 @@ k_ct_search(const float2* __restrict__ Z, int64_t n, int L, TreeArgs T,
     const int w = threadIdx.x >> 5;
     const int lane = threadIdx.x & 31;
     const int64_t v = static_cast<int64_t>(blockIdx.x) * WARPS + w;
-    const size_t per_warp = static_cast<size_t>(L) * sizeof(float2) + 2 * CAP * sizeof(Entry);
+    const size_t per_warp = static_cast<size_t>(L) * sizeof(float2) + 2 * cap * sizeof(Entry);
     unsigned char* mine = smem + per_warp * w;
     float2* q = reinterpret_cast<float2*>(mine);
     Entry* QA = reinterpret_cast<Entry*>(mine + static_cast<size_t>(L) * sizeof(float2));
-    Entry* QB = QA + CAP;
+    Entry* QB = QA + cap;
     if (v >= n) return;
     // unit query
     const float2* z = Z + v * L;
@@ -195,6 +257,8 @@ k_ct_search(const float2* __restrict__ Z, int64_t n, int L, TreeArgs T,
     const float inv_eps = eps > 0.f ? 1.f / eps : 0.f;
     for (int i = 0; i < T.imax && nq > 0; ++i) {
         if (eps > 0.f && T.sigma * exp2f(static_cast<float>(1 - i)) * (1.f + inv_eps) <= dmin) break;
+        // expand: new children enter the list with their distance pending (< 0), the parents
+        // carry theirs
         int nn = 0;
         for (int e = 0; e < nq && !overflow; ++e) {
             const Entry E = Q[e];
@@ -203,24 +267,42 @@ k_ct_search(const float2* __restrict__ Z, int64_t n, int L, TreeArgs T,
             if (cur < cend && T.en_level[cur] == i) {
                 const int32_t cb = T.en_cb[cur], ce = T.en_ce[cur];
                 for (int32_t c = cb; c < ce; ++c) {
-                    if (nn >= CAP) { overflow = true; break; }
-                    const float dc = tree_dist(T, q, L, c, lane, &corr);
-                    ++evals;
-                    top_insert(cs, ci, corr, T.order[c]);
+                    if (nn >= cap) { overflow = true; break; }
                     const int32_t cc = T.node_first[c];
                     const float mdc = (cc < T.node_first[c + 1]) ? T.en_maxdist[cc] : 0.f;
-                    if (lane == 0) N[nn] = {c, dc, cc, mdc};
+                    if (lane == 0) N[nn] = {c, -1.f, cc, mdc};
                     ++nn;
                 }
                 ++cur;
             }
             if (overflow) break;
-            if (nn >= CAP) { overflow = true; break; }
+            if (nn >= cap) { overflow = true; break; }
             if (lane == 0) N[nn] = {E.pos, E.dist, cur, (cur < cend) ? T.en_maxdist[cur] : 0.f};
             ++nn;
         }
         __syncwarp();
         if (overflow) break;
+        // distances of the new children, kBatch at a time
+        for (int e0 = 0; e0 < nn;) {
+            int32_t pos[kBatch], slot[kBatch];
+            int nb = 0;
+            while (e0 < nn && nb < kBatch) {
+                if (N[e0].dist < 0.f) { slot[nb] = e0; pos[nb] = N[e0].pos; ++nb; }
+                ++e0;
+            }
+            if (nb == 0) break;
+            float db[kBatch], cb[kBatch];
+            tree_dist_batch<kBatch>(T, q, L, pos, nb, lane, db, cb);
+            evals += nb;
+#pragma unroll
+            for (int b = 0; b < kBatch; ++b) {
+                if (b < nb) {
+                    top_insert(cs, ci, cb[b], T.order[pos[b]]);
+                    if (lane == 0) N[slot[b]].dist = db[b];
+                }
+            }
+        }
+        __syncwarp();
         // nearest new candidate
         float bmin = INFINITY;
         for (int e = lane; e < nn; e += 32) bmin = fminf(bmin, N[e].dist);
@@ -367,13 +449,14 @@ mrf_status launch_ct_search(const float2* Z, int64_t n, const mrf_dict* D, int c
     T.imax = t->host.imax;
     T.sigma = static_cast<float>(t->host.sigma);
     T.metric = t->host.metric;
-    const size_t per_warp = static_cast<size_t>(D->L) * sizeof(float2) + 2 * CAP * sizeof(Entry);
+    const int cap = D->tune.tree_list_cap > 0 ? D->tune.tree_list_cap : CAP;
+    const size_t per_warp = static_cast<size_t>(D->L) * sizeof(float2) + 2 * cap * sizeof(Entry);
     const size_t sm = per_warp * WARPS;
     cudaError_t e = cudaFuncSetAttribute(k_ct_search, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          static_cast<int>(sm));
     if (e == cudaSuccess) {
         k_ct_search<<<static_cast<unsigned>((n + WARPS - 1) / WARPS), WARPS * 32, sm, st>>>(
-            Z, n, D->L, T, warm, eps, route, part_s, part_i, fb_list, fb_n, D->counters);
+            Z, n, D->L, T, cap, warm, eps, route, part_s, part_i, fb_list, fb_n, D->counters);
         e = cudaGetLastError();
     }
     if (e != cudaSuccess) {
