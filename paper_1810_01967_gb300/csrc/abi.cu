@@ -545,7 +545,7 @@ void mrf_dict_free(mrf_dict* D) {
     if (!D) return;
     if (D->tree) ct_free(D->tree);
     if (D->mlp) mlp_detach(D->mlp);
-    void* ptrs[] = {D->atoms, D->inv_norm2, D->norm2, D->params, D->bop, D->zq, D->fop,
+    void* ptrs[] = {D->atoms, D->inv_norm2, D->inv_norm, D->norm2, D->params, D->bop, D->zq, D->fop,
                     D->zq8, D->qs8, D->v1, D->ealign, D->qph, D->zbuf,
                     D->wbuf, D->xprev, D->vlist, D->vlist2, D->nlist, D->part, D->err,
                     D->counters, D->red};
@@ -581,6 +581,7 @@ mrf_status mrf_build_dict_index(const void* atoms, int64_t d, int32_t L, const f
     auto bail = [&](mrf_status e) { mrf_dict_free(D); return e; };
     if ((s = dalloc(&D->atoms, static_cast<size_t>(d * L))) != MRF_OK) return bail(s);
     if ((s = dalloc(&D->inv_norm2, static_cast<size_t>(d))) != MRF_OK) return bail(s);
+    if ((s = dalloc(&D->inv_norm, static_cast<size_t>(d))) != MRF_OK) return bail(s);
     if ((s = dalloc(&D->norm2, static_cast<size_t>(d))) != MRF_OK) return bail(s);
     if ((s = dalloc(&D->err, 1)) != MRF_OK) return bail(s);
     if ((s = dalloc(&D->counters, CNT_N)) != MRF_OK) return bail(s);

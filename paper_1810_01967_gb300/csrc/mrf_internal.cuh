@@ -36,6 +36,7 @@ struct mrf_dict {
     std::vector<int32_t> grid_shape;
     float2* atoms = nullptr;        // [d][L] complex64 as given
     float* inv_norm2 = nullptr;     // [d] 1 / ||D_j||^2 (from an FP64 sum)
+    float* inv_norm = nullptr;      // [d] 1 / ||D_j|| (same sum; operand normalisation)
     double* norm2 = nullptr;        // [d] ||D_j||^2 in FP64
     float* params = nullptr;        // [d][P]
     // BF16 tensor-core operand of the normalised atoms D_j / ||D_j||: blocks of 128 atoms, 256

@@ -9,7 +9,7 @@ constexpr int kThreads = 256;
 
 __global__ void k_atom_norms(const float2* __restrict__ atoms, int64_t d, int L,
                              double* __restrict__ norm2, float* __restrict__ inv_norm2,
-                             uint32_t* err) {
+                             float* __restrict__ inv_norm, uint32_t* err) {
     int64_t j = (static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
     int lane = threadIdx.x & 31;
     if (j >= d) return;
@@ -25,6 +25,7 @@ __global__ void k_atom_norms(const float2* __restrict__ atoms, int64_t d, int L,
         if (bad) atomicOr(err, MRF_DERR_NONFINITE);
         norm2[j] = s;
         inv_norm2[j] = bad ? 0.f : static_cast<float>(1.0 / s);
+        if (inv_norm) inv_norm[j] = bad ? 0.f : static_cast<float>(1.0 / sqrt(s));
     }
 }
 
@@ -32,7 +33,7 @@ __global__ void k_atom_norms(const float2* __restrict__ atoms, int64_t d, int L,
 // r >= 128 holds (-Im d, Re d), so that a query row (Re z, Im z) gives Re(d^H z) and Im(d^H z).
 // Atom rows are normalised (D_j / ||D_j||, the FP64 norm) before rounding, so the kernels' scores
 // need no per-atom weight.
-__global__ void k_pack_bop(const float2* __restrict__ atoms, const double* __restrict__ norm2,
+__global__ void k_pack_bop(const float2* __restrict__ atoms, const float* __restrict__ inv_norm,
                            int64_t d, int L, int Kp, int64_t nblk,
                            __nv_bfloat162* __restrict__ bop) {
     int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
@@ -46,7 +47,7 @@ __global__ void k_pack_bop(const float2* __restrict__ atoms, const double* __res
     int64_t j = b * 128 + (r & 127);
     float2 v = make_float2(0.f, 0.f);
     if (j < d && t < L) {
-        const float inv = static_cast<float>(1.0 / sqrt(norm2[j]));
+        const float inv = inv_norm[j];
         v = atoms[j * L + t];
         v.x *= inv;
         v.y *= inv;
@@ -105,12 +106,12 @@ __device__ __forceinline__ float warp_max(float x) {
 
 // Largest real or imaginary magnitude of the normalised atoms (one warp per atom), as float
 // bits in *m_bits (non-negative floats order like their bit patterns).
-__global__ void k_atoms_absmax(const float2* __restrict__ atoms, const double* __restrict__ norm2,
+__global__ void k_atoms_absmax(const float2* __restrict__ atoms, const float* __restrict__ inv_norm,
                                int64_t d, int L, unsigned int* m_bits) {
     const int64_t j = (static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
     if (j >= d) return;
-    const float inv = static_cast<float>(1.0 / sqrt(norm2[j]));
+    const float inv = inv_norm[j];
     float m = 0.f;
     for (int t = lane; t < L; t += 32) {
         float2 v = atoms[j * L + t];
@@ -124,7 +125,7 @@ __global__ void k_atoms_absmax(const float2* __restrict__ atoms, const double* _
 // in k_pack_bop) times the dictionary-wide power of two `s`, in E4M3.  With unit atoms the
 // rows' norms are s >= 224 ... so every row keeps the relative accuracy of a per-row scale,
 // and the kernel needs no per-atom weight.
-__global__ void k_pack_fop(const float2* __restrict__ atoms, const double* __restrict__ norm2,
+__global__ void k_pack_fop(const float2* __restrict__ atoms, const float* __restrict__ inv_norm,
                            int64_t d, int L, int Kp8, int64_t nblk, float s,
                            uint16_t* __restrict__ fop) {
     const int64_t slot = (static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
@@ -134,7 +135,7 @@ __global__ void k_pack_fop(const float2* __restrict__ atoms, const double* __res
     const int r = static_cast<int>(slot & 127);
     const int64_t j = slot;
     const bool real = j < d;
-    const float inv = real ? static_cast<float>(1.0 / sqrt(norm2[j])) : 0.f;
+    const float inv = real ? inv_norm[j] : 0.f;
     const int half = Kp8 / 2;
     uint16_t* re_row = fop + (b * 256 + r) * half;
     uint16_t* im_row = fop + (b * 256 + 128 + r) * half;
@@ -289,21 +290,21 @@ inline unsigned grid_for(int64_t work) {
 
 mrf_status launch_atom_norms(mrf_dict* D, cudaStream_t st) {
     k_atom_norms<<<grid_for(D->d * 32), kThreads, 0, st>>>(D->atoms, D->d, D->L, D->norm2,
-                                                            D->inv_norm2, D->err);
+                                                            D->inv_norm2, D->inv_norm, D->err);
     LAUNCH_CHECK();
     return MRF_OK;
 }
 
 mrf_status launch_pack_bop(mrf_dict* D, cudaStream_t st) {
     int64_t total = D->nblk * 256 * (D->Kp / 2);
-    k_pack_bop<<<grid_for(total), kThreads, 0, st>>>(D->atoms, D->norm2, D->d, D->L, D->Kp, D->nblk,
+    k_pack_bop<<<grid_for(total), kThreads, 0, st>>>(D->atoms, D->inv_norm, D->d, D->L, D->Kp, D->nblk,
                                                       reinterpret_cast<__nv_bfloat162*>(D->bop));
     LAUNCH_CHECK();
     return MRF_OK;
 }
 
 mrf_status launch_atoms_absmax(const mrf_dict* D, unsigned int* m_bits, cudaStream_t st) {
-    k_atoms_absmax<<<grid_for(D->d * 32), kThreads, 0, st>>>(D->atoms, D->norm2, D->d, D->L,
+    k_atoms_absmax<<<grid_for(D->d * 32), kThreads, 0, st>>>(D->atoms, D->inv_norm, D->d, D->L,
                                                               m_bits);
     LAUNCH_CHECK();
     return MRF_OK;
@@ -312,7 +313,7 @@ mrf_status launch_atoms_absmax(const mrf_dict* D, unsigned int* m_bits, cudaStre
 mrf_status launch_pack_fop(mrf_dict* D, float s, cudaStream_t st) {
     const int64_t slots = D->nblk * 128;
     k_pack_fop<<<grid_for(slots * 32), kThreads, 0, st>>>(
-        D->atoms, D->norm2, D->d, D->L, D->Kp8, D->nblk, s, reinterpret_cast<uint16_t*>(D->fop));
+        D->atoms, D->inv_norm, D->d, D->L, D->Kp8, D->nblk, s, reinterpret_cast<uint16_t*>(D->fop));
     LAUNCH_CHECK();
     return MRF_OK;
 }
