@@ -450,7 +450,11 @@ typedef struct mrf_tune {
     int32_t tree_list_cap;     /* cover-tree candidate list capacity per voxel, 64..512 (0 = 256);
                                   smaller lists fit more warps per SM, longer lists route fewer
                                   voxels to the exhaustive search */
-    int32_t reserved[7];
+    int32_t bf16_pair;         /* 1: the tensor-core search on CTA pairs (2-SM MMA, M = 256,
+                                  each CTA staging half of every atom block) instead of clusters
+                                  sharing atom blocks by multicast (bf16_cluster is then ignored);
+                                  0 = the library's default */
+    int32_t reserved[6];
 } mrf_tune;
 
 mrf_status mrf_get_tune(const mrf_dict* dict, mrf_tune* out);

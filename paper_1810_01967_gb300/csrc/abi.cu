@@ -800,6 +800,8 @@ mrf_status mrf_set_tune(mrf_dict* D, const mrf_tune* in) {
     if (in->tree_list_cap != 0 && (in->tree_list_cap < 64 || in->tree_list_cap > 512))
         return fail(MRF_EINVAL, "tree_list_cap must be 0 or in 64..512");
     D->tune.tree_list_cap = in->tree_list_cap;
+    if (in->bf16_pair < 0 || in->bf16_pair > 1) return fail(MRF_EINVAL, "bf16_pair must be 0 or 1");
+    D->tune.bf16_pair = in->bf16_pair;
     D->tune.bf16_cluster = in->bf16_cluster;
     D->tune.bf16_live_tiles = in->bf16_live_tiles;
     D->tune.bf16_splits = in->bf16_splits;

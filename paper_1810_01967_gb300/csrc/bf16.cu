@@ -30,7 +30,6 @@ namespace {
 
 constexpr int BM = 128;
 constexpr int BN = 256;          // 128 atoms x (re, im)
-constexpr int BK = 64;           // BF16 elements per stage row = 128 bytes
 constexpr int BKB = 128;         // bytes per stage row
 constexpr int STAGES = 4;
 constexpr int A_BYTES = BM * BKB;
@@ -82,6 +81,49 @@ __device__ __forceinline__ void topk_insert(float (&ts)[KT], int32_t (&ti)[KT], 
             ts[q] = up ? b : a;
             ti[q - 1] = up ? ia : ib;
             ti[q] = up ? ib : ia;
+        }
+    }
+}
+
+// One 128-atom block of the accumulator (TMEM columns tb .. tb + 255: real parts, then
+// imaginary parts) into the thread's running top-KT: per 32-atom chunk the scores of the
+// normalised atoms, their maximum against the K-th best, and only when it is beaten the slow
+// path through the thread's shared-memory column `col` (stride BM floats).
+template <int KT>
+__device__ __forceinline__ void epilogue_block(uint32_t tb, int cone, int64_t b, int64_t d,
+                                               float* col, float (&ts)[KT], int32_t (&ti)[KT]) {
+#pragma unroll 1
+    for (int c = 0; c < 4; ++c) {
+        uint32_t re[32], im[32];
+        __syncwarp();
+        mrfk::tmem_ld32(tb + c * 32, re);
+        mrfk::tmem_ld32(tb + 128 + c * 32, im);
+        mrfk::tmem_ld_wait();
+        float mx = -INFINITY;
+#pragma unroll
+        for (int i = 0; i < 32; ++i) {
+            const float x = __uint_as_float(re[i]);
+            const float y = __uint_as_float(im[i]);
+            const float v = (cone == MRF_CONE_COMPLEX) ? fmaf(x, x, y * y) : x;
+            re[i] = __float_as_uint(v);
+            mx = fmaxf(mx, v);
+        }
+        if (mx > ts[KT - 1]) {
+            const float thr = ts[KT - 1];
+            uint32_t hits = 0;
+#pragma unroll
+            for (int i = 0; i < 32; ++i) {
+                const float v = __uint_as_float(re[i]);
+                col[i * BM] = v;
+                hits |= (v > thr) ? (1u << i) : 0u;
+            }
+            const int64_t jb = b * 128 + c * 32;
+            while (hits) {
+                const int i = __ffs(hits) - 1;
+                hits &= hits - 1;
+                const int64_t j = jb + i;
+                if (j < d) topk_insert<KT>(ts, ti, col[i * BM], static_cast<int32_t>(j));
+            }
         }
     }
 }
@@ -263,40 +305,7 @@ k_tc_topk(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
                 if (!mrfk::mbar_wait(&sh->tfull[acc], aphase)) { fail(); ok = false; break; }
                 mrfk::tc_fence_after();
                 const uint32_t tb = tmem + lane_base + static_cast<uint32_t>(acc * BN);
-#pragma unroll 1
-                for (int c = 0; c < 4; ++c) {
-                    uint32_t re[32], im[32];
-                    __syncwarp();
-                    mrfk::tmem_ld32(tb + c * 32, re);
-                    mrfk::tmem_ld32(tb + 128 + c * 32, im);
-                    mrfk::tmem_ld_wait();
-                    float mx = -INFINITY;
-#pragma unroll
-                    for (int i = 0; i < 32; ++i) {
-                        const float x = __uint_as_float(re[i]);
-                        const float y = __uint_as_float(im[i]);
-                        const float v = (cone == MRF_CONE_COMPLEX) ? fmaf(x, x, y * y) : x;
-                        re[i] = __float_as_uint(v);
-                        mx = fmaxf(mx, v);
-                    }
-                    if (mx > ts[KT - 1]) {
-                        const float thr = ts[KT - 1];
-                        uint32_t hits = 0;
-#pragma unroll
-                        for (int i = 0; i < 32; ++i) {
-                            const float v = __uint_as_float(re[i]);
-                            col[i * BM] = v;
-                            hits |= (v > thr) ? (1u << i) : 0u;
-                        }
-                        const int64_t jb = b * 128 + c * 32;
-                        while (hits) {
-                            const int i = __ffs(hits) - 1;
-                            hits &= hits - 1;
-                            const int64_t j = jb + i;
-                            if (j < d) topk_insert<KT>(ts, ti, col[i * BM], static_cast<int32_t>(j));
-                        }
-                    }
-                }
+                epilogue_block<KT>(tb, cone, b, d, col, ts, ti);
                 mrfk::tc_fence_before();
                 mrfk::mbar_arrive(&sh->tempty[acc]);
                 if (++acc == 2) { acc = 0; aphase ^= 1u; }
@@ -322,6 +331,224 @@ k_tc_topk(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
     mrfk::tc_fence_after();
     if (warp == 1) mrfk::tmem_dealloc(tmem, 512);
 }
+
+// ------------------------------------------------------------------------- CTA-pair kernel
+// The same search with the 2-SM MMA (cta_group::2): a cluster of two CTAs on one TPC computes
+// a 256-voxel x 256-column tile per instruction; each CTA stages its own 128 query rows and one
+// half of the atom block (CTA 0 the 128 real-part rows, CTA 1 the 128 imaginary-part rows), so
+// a stage is 32 KB instead of 48 KB and six stages fit.  Both CTAs' loads report to CTA 0's
+// `full` barrier; the even CTA issues every MMA and its commits arrive in both CTAs; both
+// epilogues report a drained accumulator to CTA 0.  Each CTA's tensor memory holds its own
+// 128 rows x 256 columns, so the epilogue is unchanged.
+constexpr int P_STAGES = 6;
+constexpr int P_A_BYTES = BM * BKB;
+constexpr int P_B_BYTES = 128 * BKB;
+constexpr int P_STAGE_BYTES = P_A_BYTES + P_B_BYTES;
+constexpr uint32_t IDESC_P = mrfk::idesc_bf16(2 * BM, BN);
+constexpr uint32_t IDESC8_P = mrfk::idesc_e4m3(2 * BM, BN);
+
+struct SharedP {
+    uint64_t full[P_STAGES];    // CTA 0: both CTAs' halves of the stage landed
+    uint64_t empty[P_STAGES];   // both CTAs: the pair's MMAs finished reading the stage
+    uint64_t tfull[2];          // both CTAs: accumulator ready
+    uint64_t tempty[2];         // CTA 0: drained by the 4 + 4 epilogue warps
+    uint64_t drain;
+    uint32_t tmem_base;
+    volatile int abort;
+};
+
+template <int KT, bool F8>
+__global__ void __launch_bounds__(NTHREADS, 1)
+k_tc_topk_pair(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+               int64_t n, int64_t d, int64_t nblk, int Kp, int cone, Sched sc,
+               int blocks_per_split, float gsc, const float* __restrict__ qs,
+               float* __restrict__ part_s, int32_t* __restrict__ part_i, uint32_t* err) {
+    constexpr int EK = F8 ? 128 : 64;
+    constexpr int KPER = F8 ? 32 : 16;
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    unsigned char* base = reinterpret_cast<unsigned char*>(
+        (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
+    SharedP* sh = reinterpret_cast<SharedP*>(base + P_STAGES * P_STAGE_BYTES);
+
+    const int warp = threadIdx.x >> 5;
+    const int lane = threadIdx.x & 31;
+    const uint32_t rank = mrfk::cluster_ctarank();      // 0 = issues the MMAs
+    const int64_t cluster = blockIdx.x / 2;
+    const int64_t nclusters = gridDim.x / 2;
+    const int64_t units = sc.NG * sc.S;
+    const int nk = (Kp + EK - 1) / EK;
+
+    if (threadIdx.x == 0) {
+        for (int i = 0; i < P_STAGES; ++i) {
+            mrfk::mbar_init(&sh->full[i], 1);
+            mrfk::mbar_init(&sh->empty[i], 1);
+        }
+        for (int i = 0; i < 2; ++i) {
+            mrfk::mbar_init(&sh->tfull[i], 1);
+            mrfk::mbar_init(&sh->tempty[i], 8);
+        }
+        mrfk::mbar_init(&sh->drain, 1);
+        sh->abort = 0;
+        mrfk::fence_mbar_init();
+    }
+    if (warp == 1) {
+        mrfk::tmem_alloc_pair(&sh->tmem_base, 512);
+        mrfk::tmem_relinquish_pair();
+    }
+    if (warp == 0 && lane == 0) {
+        mrfk::tma_prefetch_desc(&tmA);
+        mrfk::tma_prefetch_desc(&tmB);
+    }
+    mrfk::tc_fence_before();
+    mrfk::cluster_sync();
+    mrfk::tc_fence_after();
+    const uint32_t tmem = sh->tmem_base;
+
+    auto fail = [&]() {
+        atomicOr(err, MRF_DERR_TIMEOUT);
+        sh->abort = 1;
+    };
+
+    if (warp == 0) {
+        // ------------------------------------------------------------ TMA producer (both CTAs)
+        if (lane == 0) {
+            const uint32_t full0 = mrfk::mapa_shared(mrfk::smem_u32(&sh->full[0]), 0);
+            int stage = 0;
+            uint32_t phase = 0;
+            uint32_t slot_phase[P_STAGES];
+            bool slot_used[P_STAGES];
+            for (int i = 0; i < P_STAGES; ++i) { slot_used[i] = false; slot_phase[i] = 0; }
+            for (int64_t uc = cluster; uc < units && !sh->abort; uc += nclusters) {
+                int64_t s, g;
+                sc.map(uc, s, g);
+                const int64_t m = g * 2 + rank;
+                const int64_t b0 = s * blocks_per_split;
+                const int64_t b1 = min(b0 + blocks_per_split, nblk);
+                for (int64_t b = b0; b < b1 && !sh->abort; ++b) {
+                    for (int kc = 0; kc < nk; ++kc) {
+                        if (!mrfk::mbar_wait(&sh->empty[stage], phase ^ 1u)) { fail(); break; }
+                        unsigned char* sa = base + stage * P_STAGE_BYTES;
+                        const uint32_t fb = full0 + static_cast<uint32_t>(stage * sizeof(uint64_t));
+                        if (rank == 0) mrfk::mbar_arrive_expect_tx(&sh->full[stage], 2 * P_STAGE_BYTES);
+                        mrfk::tma_load_2d_pair(sa, &tmA, fb, kc * EK, static_cast<int32_t>(m * BM));
+                        mrfk::tma_load_2d_pair(sa + P_A_BYTES, &tmB, fb, kc * EK,
+                                               static_cast<int32_t>(b * BN + rank * 128));
+                        slot_used[stage] = true;
+                        slot_phase[stage] = phase;
+                        if (++stage == P_STAGES) { stage = 0; phase ^= 1u; }
+                    }
+                }
+            }
+            // before leaving: the pair's last MMAs released every slot this CTA filled (their
+            // commit arrivals target this CTA, and they imply that its loads had landed)
+            for (int i = 0; i < P_STAGES; ++i) {
+                if (!slot_used[i]) continue;
+                if (rank == 0 && sh->abort) mrfk::mbar_wait(&sh->full[i], slot_phase[i]);
+                if (!mrfk::mbar_wait(&sh->empty[i], slot_phase[i])) atomicOr(err, MRF_DERR_TIMEOUT);
+            }
+        }
+    } else if (warp == 1) {
+        if (lane == 0 && rank == 0) {
+            // -------------------------------------------------------- CTA 0: MMA issuer
+            int stage = 0;
+            uint32_t phase = 0;
+            int acc = 0;
+            uint32_t aphase = 0;
+            bool any = false;
+            for (int64_t uc = cluster; uc < units && !sh->abort; uc += nclusters) {
+                int64_t s, g;
+                sc.map(uc, s, g);
+                const int64_t b0 = s * blocks_per_split;
+                const int64_t b1 = min(b0 + blocks_per_split, nblk);
+                for (int64_t b = b0; b < b1 && !sh->abort; ++b) {
+                    if (!mrfk::mbar_wait_cluster(&sh->tempty[acc], aphase ^ 1u)) { fail(); break; }
+                    mrfk::tc_fence_after();
+                    const uint32_t dt = tmem + static_cast<uint32_t>(acc * BN);
+                    bool ok = true;
+                    for (int kc = 0; kc < nk; ++kc) {
+                        if (!mrfk::mbar_wait(&sh->full[stage], phase)) { fail(); ok = false; break; }
+                        mrfk::tc_fence_after();
+                        const uint32_t sa = mrfk::smem_u32(base + stage * P_STAGE_BYTES);
+                        const uint32_t sb = sa + P_A_BYTES;
+                        const int rem = Kp - kc * EK;
+                        const int nmma = rem >= EK ? EK / KPER : rem / KPER;
+                        for (int k = 0; k < nmma; ++k) {
+                            const uint64_t da = mrfk::sdesc_k_sw128(sa + k * 32);
+                            const uint64_t db = mrfk::sdesc_k_sw128(sb + k * 32);
+                            if (F8)
+                                mrfk::mma_f8_pair(dt, da, db, IDESC8_P, (kc > 0 || k > 0) ? 1u : 0u);
+                            else
+                                mrfk::mma_bf16_pair(dt, da, db, IDESC_P, (kc > 0 || k > 0) ? 1u : 0u);
+                        }
+                        mrfk::mma_commit_pair_mc(&sh->empty[stage], 3);
+                        any = true;
+                        if (++stage == P_STAGES) { stage = 0; phase ^= 1u; }
+                    }
+                    if (!ok) break;
+                    mrfk::mma_commit_pair_mc(&sh->tfull[acc], 3);
+                    if (++acc == 2) { acc = 0; aphase ^= 1u; }
+                }
+            }
+            if (any) {
+                mrfk::mma_commit_pair_mc(&sh->drain, 1);
+                if (!mrfk::mbar_wait(&sh->drain, 0)) atomicOr(err, MRF_DERR_TIMEOUT);
+            }
+        }
+    } else {
+        // ------------------------------------------------------------ epilogue (both CTAs)
+        const int quarter = warp & 3;
+        const int row = quarter * 32 + lane;
+        const uint32_t lane_base = static_cast<uint32_t>(quarter * 32) << 16;
+        float* col = reinterpret_cast<float*>(base + P_STAGES * P_STAGE_BYTES + sizeof(SharedP)) + row;
+        const uint32_t remote_tempty0 = mrfk::mapa_shared(mrfk::smem_u32(&sh->tempty[0]), 0);
+        int acc = 0;
+        uint32_t aphase = 0;
+        for (int64_t uc = cluster; uc < units && !sh->abort; uc += nclusters) {
+            int64_t s, g;
+            sc.map(uc, s, g);
+            const int64_t m = g * 2 + rank;
+            const int64_t b0 = s * blocks_per_split;
+            const int64_t b1 = min(b0 + blocks_per_split, nblk);
+            float ts[KT];
+            int32_t ti[KT];
+#pragma unroll
+            for (int q = 0; q < KT; ++q) { ts[q] = -INFINITY; ti[q] = -1; }
+            bool ok = true;
+            for (int64_t b = b0; b < b1; ++b) {
+                if (!mrfk::mbar_wait(&sh->tfull[acc], aphase)) { fail(); ok = false; break; }
+                mrfk::tc_fence_after();
+                const uint32_t tb = tmem + lane_base + static_cast<uint32_t>(acc * BN);
+                epilogue_block<KT>(tb, cone, b, d, col, ts, ti);
+                mrfk::tc_fence_before();
+                __syncwarp();
+                if (lane == 0)
+                    mrfk::mbar_arrive_cluster(remote_tempty0 +
+                                              static_cast<uint32_t>(acc * sizeof(uint64_t)));
+                if (++acc == 2) { acc = 0; aphase ^= 1u; }
+            }
+            if (!ok) break;
+            const int64_t v = m * BM + row;
+            if (v < n) {
+                if (F8) {
+                    const float q = qs[v] * gsc;
+                    const float f = (cone == MRF_CONE_COMPLEX) ? q * q : q;
+#pragma unroll
+                    for (int q2 = 0; q2 < KT; ++q2) ts[q2] *= f;
+                }
+                const int64_t o = (s * n + v) * KT;
+#pragma unroll
+                for (int q = 0; q < KT; ++q) { part_s[o + q] = ts[q]; part_i[o + q] = ti[q]; }
+            }
+        }
+    }
+    mrfk::tc_fence_before();
+    __syncthreads();
+    mrfk::cluster_sync();
+    mrfk::tc_fence_after();
+    if (warp == 1) mrfk::tmem_dealloc_pair(tmem, 512);
+}
+
+constexpr size_t kSmemP = P_STAGES * P_STAGE_BYTES + sizeof(SharedP) + 32 * BM * sizeof(float) + 1024;
 
 // ring + barriers + the epilogue's score columns (32 x 128 floats) + alignment slack
 constexpr size_t kSmem = STAGES * STAGE_BYTES + sizeof(Shared) + 32 * BM * sizeof(float) + 1024;
@@ -399,6 +626,64 @@ mrf_status launch_t(const CUtensorMap& ta, const CUtensorMap& tb, int64_t n, con
     return MRF_OK;
 }
 
+template <int KT, bool F8>
+mrf_status launch_pair(const CUtensorMap& ta, const CUtensorMap& tb, int64_t n, const mrf_dict* D,
+                       int cone, Sched sc, int bps, int nclusters, float gsc, const float* qs,
+                       float* part_s, int32_t* part_i, cudaStream_t st) {
+    auto kern = k_tc_topk_pair<KT, F8>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         static_cast<int>(kSmemP));
+    if (e == cudaSuccess) {
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3(static_cast<unsigned>(nclusters * 2));
+        cfg.blockDim = dim3(NTHREADS);
+        cfg.dynamicSmemBytes = kSmemP;
+        cfg.stream = st;
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeClusterDimension;
+        attr[0].val.clusterDim.x = 2;
+        attr[0].val.clusterDim.y = 1;
+        attr[0].val.clusterDim.z = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        e = cudaLaunchKernelEx(&cfg, kern, ta, tb, n, D->d, D->nblk, F8 ? D->Kp8 : D->Kp, cone,
+                               sc, bps, gsc, qs, part_s, part_i, D->err);
+    }
+    if (e != cudaSuccess) {
+        mrf_set_error(std::string("tensor-core search (CTA pairs) launch: ") + cudaGetErrorString(e));
+        return MRF_ECUDA;
+    }
+    return MRF_OK;
+}
+
+template <int KT>
+int max_pairs(cudaStream_t st) {
+    auto kern = k_tc_topk_pair<KT, false>;   // same resources for both element types
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             static_cast<int>(kSmemP)) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(2);
+    cfg.blockDim = dim3(NTHREADS);
+    cfg.dynamicSmemBytes = kSmemP;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = 2;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    int nc = 0;
+    if (cudaOccupancyMaxActiveClusters(&nc, kern, &cfg) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    return nc;
+}
+
 // Co-resident clusters of size C (persistent grid), from the occupancy calculator.
 template <int KT, int C>
 int max_clusters(cudaStream_t st) {
@@ -467,7 +752,7 @@ int max_clusters_any(int C, cudaStream_t st) {
 
 int bf16_choose_splits(const mrf_dict* D, int64_t n) {
     if (D->tune.bf16_splits > 0) return static_cast<int>(D->tune.bf16_splits);
-    const int C = cluster_of(D);
+    const int C = D->tune.bf16_pair > 0 ? 2 : cluster_of(D);
     const int64_t Mt = (n + BM - 1) / BM;
     const int64_t NG = (Mt + C - 1) / C;
     return choose_splits(NG, D->nblk, D->num_sms / C);
@@ -500,7 +785,8 @@ mrf_status launch_tc(bool f8, const void* zq, const float* qs, int64_t n, mrf_di
         mrf_set_error("tensor-core search: K must be 8 or 16");
         return MRF_EINVAL;
     }
-    const int C = cluster_of(D);
+    const bool pair = D->tune.bf16_pair > 0;
+    const int C = pair ? 2 : cluster_of(D);
     const int Kp = f8 ? D->Kp8 : D->Kp;
     CUtensorMap ta, tb;
     MRF_TRY(make_map(&ta, zq, n, Kp, BM, f8));
@@ -513,7 +799,8 @@ mrf_status launch_tc(bool f8, const void* zq, const float* qs, int64_t n, mrf_di
     sc.PG = (live + C - 1) / C;
     const int bps = static_cast<int>((D->nblk + S - 1) / S);
     const int64_t units = sc.NG * sc.S;
-    int nc = (K == 8) ? max_clusters_any<8>(C, st) : max_clusters_any<16>(C, st);
+    int nc = pair ? ((K == 8) ? max_pairs<8>(st) : max_pairs<16>(st))
+                  : ((K == 8) ? max_clusters_any<8>(C, st) : max_clusters_any<16>(C, st));
     if (nc <= 0) {
         mrf_set_error("tensor-core search: no cluster of the requested size fits on this device");
         return MRF_EUNSUPPORTED;
@@ -523,6 +810,13 @@ mrf_status launch_tc(bool f8, const void* zq, const float* qs, int64_t n, mrf_di
     D->tune.last_bf16_cluster = C;
     D->tune.last_bf16_splits = S;
     const float wts = f8 ? D->g8 : 1.f;
+    if (pair) {
+        if (f8)
+            return K == 8 ? launch_pair<8, true>(ta, tb, n, D, cone, sc, bps, nc, wts, qs, part_s, part_i, st)
+                          : launch_pair<16, true>(ta, tb, n, D, cone, sc, bps, nc, wts, qs, part_s, part_i, st);
+        return K == 8 ? launch_pair<8, false>(ta, tb, n, D, cone, sc, bps, nc, wts, qs, part_s, part_i, st)
+                      : launch_pair<16, false>(ta, tb, n, D, cone, sc, bps, nc, wts, qs, part_s, part_i, st);
+    }
     if (f8)
         return K == 8 ? launch_c<8, true>(C, ta, tb, n, D, cone, sc, bps, nc, wts, qs, part_s, part_i, st)
                       : launch_c<16, true>(C, ta, tb, n, D, cone, sc, bps, nc, wts, qs, part_s, part_i, st);

@@ -70,3 +70,33 @@ def test_tune_applies_and_caches(mrf, cfg1, tmp_path):
     t2 = D2.get_tune()
     for k, v in res["tune"].items():
         assert t2[k] == v
+
+
+@pytest.mark.parametrize("mode", ["bf16", "fp8"])
+def test_cta_pair_kernel_is_exact(mrf, cfg1, mode):
+    """The 2-SM (CTA pair) variant of the search under several schedules: certified results
+    equal the oracle's, uncertified ones stay within the rigorous bound."""
+    dic, Z = cfg1
+    A = dic["atoms"]
+    D = mrf.build_dict_index(A, pack_fp8=True)
+    ref = mo.project(Z, A)
+    Zd = to_dev(Z)
+    n = Z.shape[0]
+    for live in (1, 8, 64):
+        for S in (0, 1, 5):
+            D.set_tune(bf16_pair=1, bf16_live_tiles=live, bf16_splits=S)
+            idx = torch.empty(n, dtype=torch.int32, device="cuda")
+            rho = torch.empty(n, dtype=torch.complex64, device="cuda")
+            mrf.project(D, Zd, idx, rho, opts=mrf.proj_opts(mode=mode, certify=True))
+            t = D.get_tune()
+            assert t["last_bf16_cluster"] == 2
+            check_projection(Z, A, idx.cpu().numpy(), rho.cpu().numpy(), ref=ref)
+    # uncertified BF16 on the pair kernel: top-16 + exact rescore within 2 x the BF16 bound
+    if mode == "bf16":
+        D.set_tune(bf16_pair=1, bf16_live_tiles=0, bf16_splits=0)
+        idx = torch.empty(n, dtype=torch.int32, device="cuda")
+        mrf.project(D, Zd, idx, opts=mrf.proj_opts(mode="bf16", certify=False))
+        gi = idx.cpu().numpy()
+        bound = 2.0 ** -7 + 2.0 ** -16 + 2 * Z.shape[1] * 2.0 ** -24
+        assert np.all(mo.correlation(Z, A, gi) >= ref["s1"] - 2 * bound)
+        assert np.mean(gi == ref["idx"]) > 0.98
