@@ -458,6 +458,16 @@ def run_slices(args) -> None:
 
     out = {}
     mlp_s = None
+    tuned = None
+    if args.autotune:
+        # search geometry from the autotuner, timed on the largest slice's A^H Y
+        from paper_1810_01967_gb300 import autotune
+        Nb = max(first)
+        opb = mrf.make_op(Nb, Nb, L, masks[Nb])
+        Zt = torch.empty((Nb * Nb, L), dtype=torch.complex64, device=dev)
+        mrf.adjoint(opb, Ys[Nb], Zt)
+        tuned = autotune.tune(D, Zt, "bf16", reps=2)
+        del Zt
     for mode, graph in forms:
         kw = {}
         if mode == "learned":
@@ -531,7 +541,8 @@ def run_slices(args) -> None:
             "scaling": "strong", "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
             "config": {"workload": SLICES_WORKLOAD, "voxels": int(sum(geo[i][0] ** 2 for i in range(64))),
                        "inputs": "one generated slice per matrix size, reused by the slices of that size"},
-            "forms": out, "learned_train_gpu_s": mlp_s}
+            "forms": out, "learned_train_gpu_s": mlp_s,
+            "autotune": None if tuned is None else {"tune": tuned["tune"], "ms": tuned["ms"]}}
     print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
