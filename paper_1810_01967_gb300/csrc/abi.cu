@@ -459,6 +459,10 @@ mrf_status project_core(mrf_dict* D, const float2* Z, int64_t n, const mrf_proj_
 mrf_status gradient_to(const mrf_op* op, const float2* AHY, const float2* X, float mu, float2* Z,
                        float2* W, __nv_bfloat16* zq, int Kp, uint32_t* err, cudaStream_t st) {
     const int64_t n = static_cast<int64_t>(op->Ny) * op->Nx;
+    if (grad_fused_supported(op->Ny)) {          // one pass: y-transforms, mask, combine
+        ProfScope ps0(0, 1, st);
+        return launch_grad_fused(op, AHY, X, mu, Z, zq, Kp, err, st);
+    }
     cufftHandle hy;
     MRF_TRY(get_plan(0, op->Ny, op->Nx, op->L, st, &hy));
     ProfScope ps0(0, 2, st);

@@ -164,6 +164,10 @@ mrf_status launch_ct_search(const float2* Z, int64_t n, const mrf_dict* D, int c
 mrf_status ct_info(const mrf_dict* D, mrf_tree_info* info);
 mrf_status ct_export(const mrf_dict* D, int32_t* first_level, int32_t* parent, int32_t* rep,
                      int32_t* en_atom, int32_t* en_level, float* en_maxdist);
+// gradfft.cu
+bool grad_fused_supported(int Ny);
+mrf_status launch_grad_fused(const mrf_op* op, const float2* AHY, const float2* X, float mu,
+                             float2* Z, __nv_bfloat16* zq, int Kp, uint32_t* err, cudaStream_t st);
 // phase.cu
 mrf_status phase_align_dictionary(mrf_dict* D, cudaStream_t st);
 mrf_status launch_align_queries(const mrf_dict* D, const float2* Z, int64_t n, float2* Zout,

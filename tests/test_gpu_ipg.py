@@ -136,3 +136,24 @@ def test_adaptive_step_and_kappa(mrf, cfg1):
     mrf.reconstruct(D, op, to_dev(p["Y"]), X, idx,
                     opts=mrf.recon_opts(iters=2, kappa=True, mode="fp32"))
     assert torch.isfinite(torch.view_as_real(X)).all()
+
+
+@pytest.mark.parametrize("N", [16, 24, 32, 64, 40])
+def test_gradient_step_both_paths(mrf, cfg1, N):
+    """Z = X - mu A^H(A X - Y) against the oracle for power-of-two Ny (the one-pass kernel:
+    y-transforms, mask and combine in shared memory) and other Ny (cuFFT path)."""
+    dic, _ = cfg1
+    p = mrfgen.make_problem(1, dic=dic, N=N)
+    Ny, Nx, L = p["Ny"], p["Nx"], p["L"]
+    n = Ny * Nx
+    g = np.random.Generator(np.random.PCG64(N))
+    X = (g.standard_normal((n, L)) + 1j * g.standard_normal((n, L))).astype(np.complex64)
+    D = mrf.build_dict_index(dic["atoms"])
+    op = mrf.make_op(Ny, Nx, L, to_dev(p["masks"]))
+    AHY = torch.empty((n, L), dtype=torch.complex64, device="cuda")
+    mrf.adjoint(op, to_dev(p["Y"]), AHY)
+    Z = torch.empty((n, L), dtype=torch.complex64, device="cuda")
+    mrf.gradient(D, op, AHY, to_dev(X), 0.7, Z)
+    ref = mo.gradient_step(X, p["Y"], p["masks"], Ny, Nx, 0.7)
+    err = np.linalg.norm(Z.cpu().numpy() - ref) / np.linalg.norm(ref)
+    assert err < 2e-6, err
