@@ -14,9 +14,13 @@
 //   * canonicalisation z^ = z/||z|| rotated by exp(-i angle(v1^H z^)), v1 the dictionary's
 //     dominant right singular vector (power iteration, phase fixed so its largest entry is real
 //     positive).
-// Inference (MRF_PROJ_LEARNED) runs the forward pass on the queries, maps the prediction to the
-// nearest grid cell and rescores the valid atoms of the (2r+1)^k neighbourhood in FP32; the merge
-// kernel then rescores its best 8 exactly (FP64 near-ties) and forms the density.
+// Inference (MRF_PROJ_LEARNED) runs the forward pass on the queries with BF16 weights and
+// activations and FP32 accumulation (the two 512-wide layers as cuBLAS GEMMs), maps the
+// prediction to the nearest grid cell and rescores the valid atoms of the (2r+1)^k
+// neighbourhood in FP32; the merge kernel then rescores its best 8 exactly (extended-precision
+// near-ties) and forms the density.
+#include <cublas_v2.h>
+
 #include <cmath>
 #include <cstring>
 #include <vector>
@@ -107,6 +111,25 @@ k_gemm(int M, int N, int K, const float* __restrict__ A, int lda, const float* _
             }
             C[static_cast<int64_t>(m) * ldc + n] = v;
         }
+    }
+}
+
+__global__ void k_to_bf16(const float* __restrict__ a, int64_t n, __nv_bfloat16* __restrict__ b) {
+    for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < n;
+         i += static_cast<int64_t>(gridDim.x) * blockDim.x)
+        b[i] = __float2bfloat16_rn(a[i]);
+}
+
+// A = gelu(H + bias) (FP32), and its BF16 copy when Ab is given
+__global__ void k_bias_gelu(const float* __restrict__ Hm, int64_t count, int N,
+                            const float* __restrict__ bias, float* __restrict__ A,
+                            __nv_bfloat16* __restrict__ Ab) {
+    for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < count;
+         i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+        const float v = Hm[i] + bias[i % N];
+        const float g = 0.5f * v * (1.f + erff(v * 0.70710678118654752f));
+        A[i] = g;
+        if (Ab) Ab[i] = __float2bfloat16_rn(g);
     }
 }
 
@@ -567,6 +590,13 @@ struct mrf_mlp {
     double* loss = nullptr;
     int64_t step = 0;
     uint64_t seed = 5000;
+    // inference in BF16 (weights rounded from the FP32 masters when they change)
+    cublasHandle_t blas = nullptr;
+    __nv_bfloat16* w1b = nullptr;   // [I][H]
+    __nv_bfloat16* w2b = nullptr;   // [H][H]
+    __nv_bfloat16* xb = nullptr;    // [cap_b][I]
+    __nv_bfloat16* a1b = nullptr;   // [cap_b][H]
+    bool wb_valid = false;
 };
 
 namespace {
@@ -596,6 +626,8 @@ mrf_status ensure_batch(mrf_mlp* M, int64_t B) {
     MRF_TRY(alloc(&M->Y, B * 3));
     MRF_TRY(alloc(&M->T, B * 3));
     MRF_TRY(alloc(&M->dY, B * 3));
+    MRF_TRY(alloc(&M->xb, B * M->I));
+    MRF_TRY(alloc(&M->a1b, B * M->H));
     M->cap_b = B;
     return MRF_OK;
 }
@@ -609,6 +641,40 @@ mrf_status forward(mrf_mlp* M, const float* X, int64_t B, cudaStream_t st) {
                                    M->H1, st)));
     MRF_TRY((gemm<false, false, 2>(static_cast<int>(B), H, H, M->A1, H, P(M, 2), H, M->A2, H,
                                    P(M, 3), M->H2, st)));
+    k_out3<<<gridw(B), kT, 0, st>>>(M->A2, B, H, P(M, 4), P(M, 5), M->Y);
+    return cudaGetLastError() == cudaSuccess ? MRF_OK : MRF_ECUDA;
+}
+
+// Inference with BF16 weights and activations, FP32 accumulation (cuBLAS GEMMs for the two
+// 512-wide layers; bias, GELU and the 3-wide output layer in FP32 here).
+mrf_status forward_bf16(mrf_mlp* M, int64_t B, cudaStream_t st) {
+    const int I = M->I, H = M->H;
+    if (cublasSetStream(M->blas, st) != CUBLAS_STATUS_SUCCESS) {
+        mrf_set_error("cublasSetStream failed");
+        return MRF_ECUDA;
+    }
+    if (!M->wb_valid) {
+        k_to_bf16<<<256, kT, 0, st>>>(P(M, 0), static_cast<int64_t>(I) * H, M->w1b);
+        k_to_bf16<<<256, kT, 0, st>>>(P(M, 2), static_cast<int64_t>(H) * H, M->w2b);
+        M->wb_valid = true;
+    }
+    k_to_bf16<<<1024, kT, 0, st>>>(M->X, B * I, M->xb);
+    const float one = 1.f, zero = 0.f;
+    // row-major H1 [B][H] = Xb [B][I] W1b [I][H]  <=>  column-major H1^T = W1b^T Xb^T
+    if (cublasGemmEx(M->blas, CUBLAS_OP_N, CUBLAS_OP_N, H, static_cast<int>(B), I, &one, M->w1b,
+                     CUDA_R_16BF, H, M->xb, CUDA_R_16BF, I, &zero, M->H1, CUDA_R_32F, H,
+                     CUBLAS_COMPUTE_32F, CUBLAS_GEMM_DEFAULT) != CUBLAS_STATUS_SUCCESS) {
+        mrf_set_error("cublasGemmEx (layer 1) failed");
+        return MRF_ECUDA;
+    }
+    k_bias_gelu<<<1024, kT, 0, st>>>(M->H1, B * H, H, P(M, 1), M->A1, M->a1b);
+    if (cublasGemmEx(M->blas, CUBLAS_OP_N, CUBLAS_OP_N, H, static_cast<int>(B), H, &one, M->w2b,
+                     CUDA_R_16BF, H, M->a1b, CUDA_R_16BF, H, &zero, M->H2, CUDA_R_32F, H,
+                     CUBLAS_COMPUTE_32F, CUBLAS_GEMM_DEFAULT) != CUBLAS_STATUS_SUCCESS) {
+        mrf_set_error("cublasGemmEx (layer 2) failed");
+        return MRF_ECUDA;
+    }
+    k_bias_gelu<<<1024, kT, 0, st>>>(M->H2, B * H, H, P(M, 3), M->A2, nullptr);
     k_out3<<<gridw(B), kT, 0, st>>>(M->A2, B, H, P(M, 4), P(M, 5), M->Y);
     return cudaGetLastError() == cudaSuccess ? MRF_OK : MRF_ECUDA;
 }
@@ -734,8 +800,15 @@ mrf_status mrf_mlp_create(mrf_dict* D, const float* grid_axes, const int32_t* ce
         (s = alloc(&M->axes, static_cast<size_t>(naxis))) ||
         (s = alloc(&M->cell_atom, static_cast<size_t>(cells))) ||
         (s = alloc(&M->near_atom, static_cast<size_t>(cells))) || (s = alloc(&M->loss, 1)) ||
-        (s = alloc(&M->pool_count, 1)))
+        (s = alloc(&M->pool_count, 1)) ||
+        (s = alloc(&M->w1b, static_cast<size_t>(M->I) * M->H)) ||
+        (s = alloc(&M->w2b, static_cast<size_t>(M->H) * M->H)))
         return bail(s);
+    if (cublasCreate(&M->blas) != CUBLAS_STATUS_SUCCESS) {
+        M->blas = nullptr;
+        mrf_set_error("cublasCreate failed");
+        return bail(MRF_ECUDA);
+    }
     if (o.residue_pool > 0 && (s = alloc(&M->pool, static_cast<size_t>(o.residue_pool) * M->L)))
         return bail(s);
     M->pool_cap = o.residue_pool;
@@ -823,9 +896,10 @@ mrf_status mrf_mlp_create(mrf_dict* D, const float* grid_axes, const int32_t* ce
 void mrf_mlp_free(mrf_mlp* M) {
     if (!M) return;
     if (M->dict && M->dict->mlp == M) M->dict->mlp = nullptr;
+    if (M->blas) cublasDestroy(M->blas);
     void* ptrs[] = {M->par, M->grad, M->m, M->v, M->v1, M->axes, M->cell_atom, M->near_atom, M->pool,
                     M->pool_count, M->F, M->X, M->H1, M->A1, M->H2, M->A2, M->Y, M->T, M->dY,
-                    M->dA1, M->dA2, M->loss};
+                    M->dA1, M->dA2, M->loss, M->w1b, M->w2b, M->xb, M->a1b};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     delete M;
@@ -888,6 +962,7 @@ mrf_status mrf_mlp_train(mrf_mlp* M, const mrf_train_opts* opts, float* loss_his
         MRF_TRY(forward(M, M->X, B, st));
         MRF_TRY(backward(M, M->X, B, st));
         ++M->step;
+        M->wb_valid = false;
         const float c1 = 1.f - std::pow(b1, static_cast<float>(M->step));
         const float c2 = 1.f - std::pow(b2, static_cast<float>(M->step));
         k_adam<<<grid1(M->np), kT, 0, st>>>(M->par, M->grad, M->m, M->v, M->np, o.lr, b1, b2, eps,
@@ -907,6 +982,7 @@ mrf_status mrf_mlp_params(mrf_mlp* M, float* host_params, int32_t set, int64_t* 
     if (!M) { mrf_set_error("mlp is NULL"); return MRF_EINVAL; }
     if (count) *count = M->np;
     if (!host_params) return MRF_OK;
+    if (set) M->wb_valid = false;
     cudaError_t e = set ? cudaMemcpy(M->par, host_params, M->np * sizeof(float), cudaMemcpyHostToDevice)
                         : cudaMemcpy(host_params, M->par, M->np * sizeof(float), cudaMemcpyDeviceToHost);
     if (e != cudaSuccess) { mrf_set_error(cudaGetErrorString(e)); return MRF_ECUDA; }
@@ -987,7 +1063,7 @@ mrf_status learned_candidates(mrf_dict* D, const float2* Z, int64_t n, int cone,
     for (int64_t s = 0; s < n; s += chunk) {
         const int64_t b = std::min(chunk, n - s);
         k_canon<<<gridw(b), kT, 0, st>>>(Z + s * M->L, nullptr, b, M->L, M->v1, M->X);
-        MRF_TRY(forward(M, M->X, b, st));
+        MRF_TRY(forward_bf16(M, b, st));
         k_nbhd<<<gridw(b), kT, 0, st>>>(Z + s * M->L, b, M->L, M->Y, G, D->atoms, D->inv_norm2,
                                        cone, part_s + s * 8, part_i + s * 8);
     }
