@@ -84,8 +84,10 @@ typedef struct mrf_index_opts {
 typedef struct mrf_proj_opts {
     int32_t mode;          /* mrf_proj_mode (default MRF_PROJ_FP32_EXACT) */
     int32_t cone;          /* mrf_cone (default MRF_CONE_COMPLEX) */
-    int32_t topk;          /* candidates kept per voxel by the exhaustive kernels, 1..16;
-                              0 = mode default (8 for FP32, 16 for BF16 / FP8) */
+    int32_t topk;          /* candidates kept per voxel by the exhaustive kernels, 1..32
+                              (rounded up to 8, 16 or 32; FP32 at most 16); 0 = mode default
+                              (8 for FP32, 16 for BF16, 32 for FP8, whose coarser scores need
+                              the longer list to hold the best atom) */
     int32_t certify;       /* BF16/FP8: recompute voxels whose k-th candidate is within
                               cert_margin of the best with the FP32 exact kernel (default 1) */
     float   tie_tol;       /* candidates whose normalised correlation |D_j^H Z_v| /

@@ -92,8 +92,10 @@ mrf_status check_op(const mrf_op* op) {
 
 // ------------------------------------------------------------------------------ scratch
 int topk_slots(const mrf_proj_opts* o) {
-    int k = o->topk > 0 ? o->topk : (o->mode == MRF_PROJ_FP32_EXACT ? 8 : 16);
-    return k <= 8 ? 8 : 16;
+    const int def = o->mode == MRF_PROJ_FP32_EXACT ? 8 : (o->mode == MRF_PROJ_FP8 ? 32 : 16);
+    const int k = o->topk > 0 ? o->topk : def;
+    if (o->mode == MRF_PROJ_FP32_EXACT) return k <= 8 ? 8 : 16;   // FP32 scores: at most 16
+    return k <= 8 ? 8 : (k <= 16 ? 16 : 32);
 }
 
 mrf_status ensure_scratch(mrf_dict* D, int64_t n) {
@@ -133,7 +135,7 @@ mrf_status check_proj_opts(const mrf_dict* D, const mrf_proj_opts* o) {
     if (!o) return fail(MRF_EINVAL, "proj opts is NULL");
     if (o->cone != MRF_CONE_COMPLEX && o->cone != MRF_CONE_REAL_POS)
         return fail(MRF_EINVAL, "unknown cone");
-    if (o->topk < 0 || o->topk > 16) return fail(MRF_EINVAL, "topk must be in 0..16");
+    if (o->topk < 0 || o->topk > 32) return fail(MRF_EINVAL, "topk must be in 0..32");
     if (!(o->tie_tol >= 0.f && o->tie_tol < 0.5f)) return fail(MRF_EINVAL, "tie_tol out of range");
     switch (o->mode) {
         case MRF_PROJ_FP32_EXACT: return MRF_OK;
@@ -371,13 +373,14 @@ mrf_status project_impl(mrf_dict* D, const float2* Z, int64_t n, const mrf_proj_
             MRF_CUDA_TRY(cudaStreamSynchronize(st));
             if (cnt > 0) {
                 ProfScope ps5(5, 2, st);
+                const int K2 = K > 16 ? 16 : K;      // FP32 scores: 16 candidates suffice
                 const int S2 = fp32_choose_splits(cnt, D->d, D->num_sms);
-                MRF_TRY(ensure_part(D, cnt, S2, K));
+                MRF_TRY(ensure_part(D, cnt, S2, K2));
                 float* qs = static_cast<float*>(D->part);
-                int32_t* qi = reinterpret_cast<int32_t*>(qs + static_cast<size_t>(S2) * cnt * K);
-                MRF_TRY(launch_fp32_topk(Z, D->vlist, D->nlist, cnt, D, o->cone, K, S2, qs, qi,
+                int32_t* qi = reinterpret_cast<int32_t*>(qs + static_cast<size_t>(S2) * cnt * K2);
+                MRF_TRY(launch_fp32_topk(Z, D->vlist, D->nlist, cnt, D, o->cone, K2, S2, qs, qi,
                                          st));
-                MRF_TRY(launch_merge(Z, cnt, D, o->cone, K, S2, qs, qi, D->vlist, D->nlist,
+                MRF_TRY(launch_merge(Z, cnt, D, o->cone, K2, S2, qs, qi, D->vlist, D->nlist,
                                      o->tie_tol, 0, 0.f, idx_out, rho_out, X_out, nullptr,
                                      nullptr, D->err, D->counters, st));
             }

@@ -781,8 +781,8 @@ mrf_status launch_tc(bool f8, const void* zq, const float* qs, int64_t n, mrf_di
                          : "BF16 operand was not packed (mrf_index_opts.pack_bf16 = 0)");
         return MRF_EUNSUPPORTED;
     }
-    if (K != 8 && K != 16) {
-        mrf_set_error("tensor-core search: K must be 8 or 16");
+    if (K != 8 && K != 16 && K != 32) {
+        mrf_set_error("tensor-core search: K must be 8, 16 or 32");
         return MRF_EINVAL;
     }
     const bool pair = D->tune.bf16_pair > 0;
@@ -799,8 +799,9 @@ mrf_status launch_tc(bool f8, const void* zq, const float* qs, int64_t n, mrf_di
     sc.PG = (live + C - 1) / C;
     const int bps = static_cast<int>((D->nblk + S - 1) / S);
     const int64_t units = sc.NG * sc.S;
-    int nc = pair ? ((K == 8) ? max_pairs<8>(st) : max_pairs<16>(st))
-                  : ((K == 8) ? max_clusters_any<8>(C, st) : max_clusters_any<16>(C, st));
+    int nc = pair ? ((K == 8) ? max_pairs<8>(st) : (K == 16) ? max_pairs<16>(st) : max_pairs<32>(st))
+                  : ((K == 8) ? max_clusters_any<8>(C, st)
+                              : (K == 16) ? max_clusters_any<16>(C, st) : max_clusters_any<32>(C, st));
     if (nc <= 0) {
         mrf_set_error("tensor-core search: no cluster of the requested size fits on this device");
         return MRF_EUNSUPPORTED;
@@ -810,18 +811,20 @@ mrf_status launch_tc(bool f8, const void* zq, const float* qs, int64_t n, mrf_di
     D->tune.last_bf16_cluster = C;
     D->tune.last_bf16_splits = S;
     const float wts = f8 ? D->g8 : 1.f;
+#define MRF_TC_ARGS ta, tb, n, D, cone, sc, bps, nc, wts, qs, part_s, part_i, st
     if (pair) {
         if (f8)
-            return K == 8 ? launch_pair<8, true>(ta, tb, n, D, cone, sc, bps, nc, wts, qs, part_s, part_i, st)
-                          : launch_pair<16, true>(ta, tb, n, D, cone, sc, bps, nc, wts, qs, part_s, part_i, st);
-        return K == 8 ? launch_pair<8, false>(ta, tb, n, D, cone, sc, bps, nc, wts, qs, part_s, part_i, st)
-                      : launch_pair<16, false>(ta, tb, n, D, cone, sc, bps, nc, wts, qs, part_s, part_i, st);
+            return K == 8 ? launch_pair<8, true>(MRF_TC_ARGS)
+                 : K == 16 ? launch_pair<16, true>(MRF_TC_ARGS) : launch_pair<32, true>(MRF_TC_ARGS);
+        return K == 8 ? launch_pair<8, false>(MRF_TC_ARGS)
+             : K == 16 ? launch_pair<16, false>(MRF_TC_ARGS) : launch_pair<32, false>(MRF_TC_ARGS);
     }
     if (f8)
-        return K == 8 ? launch_c<8, true>(C, ta, tb, n, D, cone, sc, bps, nc, wts, qs, part_s, part_i, st)
-                      : launch_c<16, true>(C, ta, tb, n, D, cone, sc, bps, nc, wts, qs, part_s, part_i, st);
-    return K == 8 ? launch_c<8, false>(C, ta, tb, n, D, cone, sc, bps, nc, wts, qs, part_s, part_i, st)
-                  : launch_c<16, false>(C, ta, tb, n, D, cone, sc, bps, nc, wts, qs, part_s, part_i, st);
+        return K == 8 ? launch_c<8, true>(C, MRF_TC_ARGS)
+             : K == 16 ? launch_c<16, true>(C, MRF_TC_ARGS) : launch_c<32, true>(C, MRF_TC_ARGS);
+    return K == 8 ? launch_c<8, false>(C, MRF_TC_ARGS)
+         : K == 16 ? launch_c<16, false>(C, MRF_TC_ARGS) : launch_c<32, false>(C, MRF_TC_ARGS);
+#undef MRF_TC_ARGS
 }
 
 }  // namespace

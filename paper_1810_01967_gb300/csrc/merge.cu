@@ -67,7 +67,7 @@ __device__ __forceinline__ bool better(float sa, int32_t ja, float sb, int32_t j
 }
 
 template <int KT>
-__global__ void __launch_bounds__(WARPS * 32, 4)
+__global__ void __launch_bounds__(WARPS * 32, KT >= 32 ? 2 : 3)
 k_merge(const float2* __restrict__ Z, int64_t n_in, const int32_t* __restrict__ vlist,
         const int32_t* __restrict__ nlist, const float2* __restrict__ atoms,
         const float* __restrict__ inv_norm2, const double* __restrict__ norm2, int64_t d,
@@ -288,8 +288,14 @@ mrf_status launch_merge(const float2* Z, int64_t n, const mrf_dict* D, int cone,
                                                  tie_tol, certify, cert_margin, window,
                                                  idx_out, rho_out, X_out, fb_list, fb_n, err,
                                                  counters);
+    } else if (K == 32) {
+        k_merge<32><<<grid, WARPS * 32, 0, st>>>(Z, n, vlist, nlist, D->atoms, D->inv_norm2,
+                                                 D->norm2, D->d, D->L, cone, S, part_s, part_i,
+                                                 tie_tol, certify, cert_margin, window,
+                                                 idx_out, rho_out, X_out, fb_list, fb_n, err,
+                                                 counters);
     } else {
-        mrf_set_error("merge: K must be 8 or 16");
+        mrf_set_error("merge: K must be 8, 16 or 32");
         return MRF_EINVAL;
     }
     cudaError_t e = cudaGetLastError();

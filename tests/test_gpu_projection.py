@@ -119,8 +119,8 @@ def test_topk_and_uncertified_bf16(mrf, cfg1, topk):
     check_projection(Z, dic["atoms"], idx, r, g_X=X)
 
 
-@pytest.mark.parametrize("cone", ["complex", "real_pos"])
-def test_fp8_search_matches_e4m3_emulation(mrf, cfg1, cone):
+@pytest.mark.parametrize("cone,K", [("complex", 16), ("real_pos", 16), ("complex", 32)])
+def test_fp8_search_matches_e4m3_emulation(mrf, cfg1, cone, K):
     """The FP8 kernel ranks by the correlations of the E4M3-quantised operands (rows scaled by
     powers of two).  Uncertified, the answer is the exactly best atom among the 16 best by that
     ranking: compare with a float64 evaluation of the quantised products (fp8_emul), allowing
@@ -131,17 +131,17 @@ def test_fp8_search_matches_e4m3_emulation(mrf, cfg1, cone):
     A = dic["atoms"]
     Zs = Z[:600]
     D = mrf.build_dict_index(A, pack_fp8=True)
-    idx, r, X, st = run(mrf, D, Zs, "fp8", cone=cone, topk=16, certify=False)
+    idx, r, X, st = run(mrf, D, Zs, "fp8", cone=cone, topk=K, certify=False)
     S8 = fp8_scores(Zs, A, cone)
     Zc, Ac = Zs.astype(np.complex128), A.astype(np.complex128)
     C = Zc @ Ac.conj().T
     den = np.linalg.norm(Zc, axis=1)[:, None] * np.linalg.norm(Ac, axis=1)[None, :]
     ex = (np.abs(C) if cone == "complex" else C.real) / np.maximum(den, 1e-300)
     srt = -np.sort(-S8, axis=1)
-    kth = srt[:, 15]
+    kth = srt[:, K - 1]
     tol = 1e-4 * np.maximum(np.abs(srt[:, 0]), 1e-30)    # FP32 accumulation, generous
-    sure = S8 >= (kth + tol)[:, None]                     # in the top 16 for any rounding
-    maybe = S8 >= (kth - tol)[:, None]                    # possibly in the top 16
+    sure = S8 >= (kth + tol)[:, None]                     # in the top K for any rounding
+    maybe = S8 >= (kth - tol)[:, None]                    # possibly in the top K
     lo = np.max(np.where(sure, ex, -np.inf), axis=1)
     hi = np.max(np.where(maybe, ex, -np.inf), axis=1)
     got = ex[np.arange(len(idx)), idx]
@@ -149,7 +149,7 @@ def test_fp8_search_matches_e4m3_emulation(mrf, cfg1, cone):
     assert np.all(ok), np.flatnonzero(~ok)[:10]
     ref = mo.project(Zs, A, cone)
     agree = float(np.mean(idx == ref["idx"]))
-    print(f"fp8 uncertified ({cone}) agreement with the exact projection {agree:.4f}")
+    print(f"fp8 uncertified ({cone}, top-{K}) agreement with the exact projection {agree:.4f}")
     rr = mo.density(Zs, A, idx, cone)
     assert np.max(np.abs(r - rr) / np.maximum(np.abs(rr), 1e-30)) <= 1e-4
 
