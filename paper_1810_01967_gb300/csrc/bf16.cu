@@ -66,22 +66,24 @@ struct Sched {
     }
 };
 
+// Insert (s, j) into the descending list ts (ties keep the earlier entry first).  Every slot
+// decides on its own from one comparison with s -- stay, take s, or take its upper neighbour
+// -- so the KT steps carry no dependency chain: one warp per SM sub-partition runs this and
+// nothing else would hide the latency of a compare-exchange bubble.
 template <int KT>
 __device__ __forceinline__ void topk_insert(float (&ts)[KT], int32_t (&ti)[KT], float s,
                                             int32_t j) {
     if (s > ts[KT - 1]) {
-        ts[KT - 1] = s;
-        ti[KT - 1] = j;
+        bool ge[KT];
+#pragma unroll
+        for (int q = 0; q < KT; ++q) ge[q] = ts[q] >= s;
 #pragma unroll
         for (int q = KT - 1; q > 0; --q) {
-            bool up = ts[q] > ts[q - 1];
-            float a = ts[q], b = ts[q - 1];
-            int32_t ia = ti[q], ib = ti[q - 1];
-            ts[q - 1] = up ? a : b;
-            ts[q] = up ? b : a;
-            ti[q - 1] = up ? ia : ib;
-            ti[q] = up ? ib : ia;
+            ts[q] = ge[q] ? ts[q] : (ge[q - 1] ? s : ts[q - 1]);
+            ti[q] = ge[q] ? ti[q] : (ge[q - 1] ? j : ti[q - 1]);
         }
+        ts[0] = ge[0] ? ts[0] : s;
+        ti[0] = ge[0] ? ti[0] : j;
     }
 }
 

@@ -16,6 +16,7 @@
 namespace {
 
 constexpr int WARPS = 8;
+constexpr int MERGE_G = 8;      // candidates gathered per pass over the frames
 
 __device__ __forceinline__ float warp_sum(float x) {
     for (int o = 16; o; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
@@ -66,8 +67,18 @@ __device__ __forceinline__ bool better(float sa, int32_t ja, float sb, int32_t j
     return ja < jb;
 }
 
-template <int KT>
-__global__ void __launch_bounds__(WARPS * 32, KT >= 32 ? 2 : 3)
+// Order-preserving map of a float's bits to an unsigned key (larger float, larger key; a valid
+// score never maps to 0) and back.
+__device__ __forceinline__ uint32_t ord_key(float x) {
+    const uint32_t u = __float_as_uint(x);
+    return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+}
+__device__ __forceinline__ float key_score(uint32_t k) {
+    return __uint_as_float((k & 0x80000000u) ? (k & 0x7fffffffu) : ~k);
+}
+
+template <int KT, int NL>
+__global__ void __launch_bounds__(WARPS * 32, NL >= 32 ? 2 : 3)
 k_merge(const float2* __restrict__ Z, int64_t n_in, const int32_t* __restrict__ vlist,
         const int32_t* __restrict__ nlist, const float2* __restrict__ atoms,
         const float* __restrict__ inv_norm2, const double* __restrict__ norm2, int64_t d,
@@ -83,111 +94,155 @@ k_merge(const float2* __restrict__ Z, int64_t n_in, const int32_t* __restrict__ 
     const int64_t v = vlist ? static_cast<int64_t>(vlist[vl]) : vl;
     const float2* z = Z + v * L;
 
-    // 1. lane-local top-KT over a strided share of the S*KT candidates, then KT warp rounds
-    float ls[KT];
-    int32_t li[KT];
+    // 1. lane-local sorted lists of NL over a strided share of the S*KT candidates (NL covers
+    //    the lane's share), then KT warp rounds: the largest head by a warp max-reduction of
+    //    the order-preserving bit pattern of its score, ties to the smallest atom by a
+    //    min-reduction; its lane pops it
+    float ls[NL];
+    int32_t li[NL];
 #pragma unroll
-    for (int q = 0; q < KT; ++q) { ls[q] = -INFINITY; li[q] = -1; }
+    for (int q = 0; q < NL; ++q) { ls[q] = -INFINITY; li[q] = -1; }
     const int total = S * KT;
     for (int c = lane; c < total; c += 32) {
         const int s = c / KT, k = c - s * KT;
         const int64_t o = (static_cast<int64_t>(s) * n + vl) * KT + k;
         float sc = part_s[o];
         int32_t j = part_i[o];
-        if (j < 0 || j >= d) continue;
-        if (better(sc, j, ls[KT - 1], li[KT - 1])) {
-            ls[KT - 1] = sc;
-            li[KT - 1] = j;
+        if (j < 0 || j >= d || sc != sc) continue;
+        if (better(sc, j, ls[NL - 1], li[NL - 1])) {
+            // sorted insertion without a dependency chain: slot q keeps its entry, takes the
+            // new one, or takes its upper neighbour's
+            bool keep[NL];
 #pragma unroll
-            for (int q = KT - 1; q > 0; --q) {
-                bool up = better(ls[q], li[q], ls[q - 1], li[q - 1]);
-                float a = ls[q], b = ls[q - 1];
-                int32_t ia = li[q], ib = li[q - 1];
-                ls[q - 1] = up ? a : b; ls[q] = up ? b : a;
-                li[q - 1] = up ? ia : ib; li[q] = up ? ib : ia;
+            for (int q = 0; q < NL; ++q) keep[q] = !better(sc, j, ls[q], li[q]);
+#pragma unroll
+            for (int q = NL - 1; q > 0; --q) {
+                ls[q] = keep[q] ? ls[q] : (keep[q - 1] ? sc : ls[q - 1]);
+                li[q] = keep[q] ? li[q] : (keep[q - 1] ? j : li[q - 1]);
             }
+            ls[0] = keep[0] ? ls[0] : sc;
+            li[0] = keep[0] ? li[0] : j;
         }
     }
-    float cs[KT];       // kernel scores of the warp's top-KT (uniform across lanes)
-    int32_t cj[KT];
+    // kernel scores and atoms of the warp's top-KT, sorted (uniform across the warp; kept in
+    // shared memory to leave the registers to the gathers)
+    __shared__ float s_cs[WARPS][KT];
+    __shared__ int32_t s_cj[WARPS][KT];
+    float* cs = s_cs[threadIdx.x >> 5];
+    int32_t* cj = s_cj[threadIdx.x >> 5];
 #pragma unroll
     for (int q = 0; q < KT; ++q) {
-        float bs = ls[0];
-        int32_t bj = li[0];
-        int bl = lane;
-        for (int o = 16; o; o >>= 1) {
-            float os = __shfl_xor_sync(0xffffffffu, bs, o);
-            int32_t oj = __shfl_xor_sync(0xffffffffu, bj, o);
-            int ol = __shfl_xor_sync(0xffffffffu, bl, o);
-            if (better(os, oj, bs, bj) || (os == bs && oj == bj && ol < bl)) {
-                bs = os; bj = oj; bl = ol;
-            }
+        const uint32_t hk = li[0] >= 0 ? ord_key(ls[0]) : 0u;     // 0: empty
+        const uint32_t m = __reduce_max_sync(0xffffffffu, hk);
+        const uint32_t jc = (li[0] >= 0 && hk == m) ? static_cast<uint32_t>(li[0]) : 0xffffffffu;
+        const uint32_t jm = __reduce_min_sync(0xffffffffu, jc);
+        if (lane == 0) {
+            cs[q] = m ? key_score(m) : -INFINITY;
+            cj[q] = m ? static_cast<int32_t>(jm) : -1;
         }
-        cs[q] = bs;
-        cj[q] = bj;
-        if (lane == bl) {
+        if (m != 0 && jc == jm) {
 #pragma unroll
-            for (int p = 0; p < KT - 1; ++p) { ls[p] = ls[p + 1]; li[p] = li[p + 1]; }
-            ls[KT - 1] = -INFINITY;
-            li[KT - 1] = -1;
+            for (int p = 0; p < NL - 1; ++p) { ls[p] = ls[p + 1]; li[p] = li[p + 1]; }
+            ls[NL - 1] = -INFINITY;
+            li[NL - 1] = -1;
         }
     }
+    __syncwarp();
 
-    // 2. exact FP32 rescore of the candidates inside the window.  The candidates are sorted by
-    //    kernel score; one whose kernel correlation lies more than `window` below the first's
-    //    cannot be the exactly best (window = twice the kernel's error bound plus tie_tol), so
-    //    only a prefix of nw candidates is rescored.  All of them are gathered together (one
-    //    pass over the frames, up to KT independent loads in flight per lane).
+    // 2. exact FP32 rescore.  All KT candidates are gathered in passes of G over the frames
+    //    (G independent loads per lane and frame step, two frames per 16-byte load when the
+    //    rows allow it; rows of empty slots alias the first candidate's row), and ||z||^2
+    //    rides along with the first pass.  The candidates are sorted by kernel score; one
+    //    whose kernel correlation lies more than `window` below the first's cannot be the
+    //    exactly best (window = twice the kernel's error bound plus tie_tol), so only the
+    //    prefix of nw candidates inside the window competes for the best.
+    constexpr int G = KT < MERGE_G ? KT : MERGE_G;
     float zn2 = 0.f;
-    for (int t = lane; t < L; t += 32) { float2 a = z[t]; zn2 += a.x * a.x + a.y * a.y; }
-    zn2 = warp_sum(zn2);
     int nw = 0;
+    __shared__ float s_es[WARPS][KT];      // exact scores (-inf outside the window)
+    float* es = s_es[threadIdx.x >> 5];
+    if (lane < KT) es[lane] = -INFINITY;
+    __syncwarp();
+    float bsc = -INFINITY;      // best exact score and its atom
+    int32_t jstar = -1;
     {
-        float lower = -INFINITY;
-        if (window >= 0.f && cj[0] >= 0) {
-            const float zn0 = sqrtf(zn2);
-            if (cone == MRF_CONE_COMPLEX) {
-                const float c = sqrtf(fmaxf(cs[0], 0.f)) - window * zn0;
-                lower = c > 0.f ? c * c : -INFINITY;
-            } else {
-                lower = cs[0] - window * zn0;
+        const int64_t row0 = cj[0] >= 0 ? cj[0] : 0;
+        const bool vec2 = (L & 1) == 0 && (reinterpret_cast<uintptr_t>(Z) & 15) == 0 &&
+                          (reinterpret_cast<uintptr_t>(atoms) & 15) == 0;
+#pragma unroll
+        for (int g0 = 0; g0 < KT; g0 += G) {
+            const float2* ap[G];
+            float ar[G], ai[G];
+#pragma unroll
+            for (int q = 0; q < G; ++q) {
+                ar[q] = 0.f;
+                ai[q] = 0.f;
+                ap[q] = atoms + (cj[g0 + q] >= 0 ? static_cast<int64_t>(cj[g0 + q]) : row0) * L;
             }
-        }
+            float za = 0.f;
+            int t0 = 0;
+            if (vec2) {
+                // frames t, t + 1 in one load (t even; every row starts on 16 bytes)
+                for (int t = 2 * lane; t + 1 < L; t += 64) {
+                    const float4 zv = *reinterpret_cast<const float4*>(z + t);
+                    float4 dv[G];
 #pragma unroll
-        for (int q = 0; q < KT; ++q) nw += (cj[q] >= 0 && cs[q] >= lower) ? 1 : 0;
-    }
-    float er[KT], ei[KT];
-    const float2* ap[KT];
+                    for (int q = 0; q < G; ++q) dv[q] = *reinterpret_cast<const float4*>(ap[q] + t);
+                    if (g0 == 0)
+                        za = fmaf(zv.x, zv.x, fmaf(zv.y, zv.y, fmaf(zv.z, zv.z, fmaf(zv.w, zv.w, za))));
 #pragma unroll
-    for (int q = 0; q < KT; ++q) {
-        er[q] = 0.f;
-        ei[q] = 0.f;
-        ap[q] = atoms + static_cast<int64_t>(q < nw ? cj[q] : 0) * L;
-    }
-    for (int t = lane; t < L; t += 32) {
-        const float2 zv = z[t];
-#pragma unroll
-        for (int q = 0; q < KT; ++q) {
-            if (q < nw) {
-                const float2 dv = ap[q][t];
-                er[q] = fmaf(dv.x, zv.x, fmaf(dv.y, zv.y, er[q]));
-                ei[q] = fmaf(dv.x, zv.y, fmaf(-dv.y, zv.x, ei[q]));
+                    for (int q = 0; q < G; ++q) {
+                        ar[q] = fmaf(dv[q].x, zv.x, fmaf(dv[q].y, zv.y, ar[q]));
+                        ai[q] = fmaf(dv[q].x, zv.y, fmaf(-dv[q].y, zv.x, ai[q]));
+                        ar[q] = fmaf(dv[q].z, zv.z, fmaf(dv[q].w, zv.w, ar[q]));
+                        ai[q] = fmaf(dv[q].z, zv.w, fmaf(-dv[q].w, zv.z, ai[q]));
+                    }
+                }
+                t0 = L;
             }
+            for (int t = t0 + lane; t < L; t += 32) {
+                const float2 zv = z[t];
+                float2 dv[G];
+#pragma unroll
+                for (int q = 0; q < G; ++q) dv[q] = ap[q][t];
+                if (g0 == 0) za = fmaf(zv.x, zv.x, fmaf(zv.y, zv.y, za));
+#pragma unroll
+                for (int q = 0; q < G; ++q) {
+                    ar[q] = fmaf(dv[q].x, zv.x, fmaf(dv[q].y, zv.y, ar[q]));
+                    ai[q] = fmaf(dv[q].x, zv.y, fmaf(-dv[q].y, zv.x, ai[q]));
+                }
+            }
+            if (g0 == 0) {
+                zn2 = warp_sum(za);
+                float lower = -INFINITY;
+                if (window >= 0.f && cj[0] >= 0) {
+                    const float zn0 = sqrtf(zn2);
+                    if (cone == MRF_CONE_COMPLEX) {
+                        const float c = sqrtf(fmaxf(cs[0], 0.f)) - window * zn0;
+                        lower = c > 0.f ? c * c : -INFINITY;
+                    } else {
+                        lower = cs[0] - window * zn0;
+                    }
+                }
+#pragma unroll
+                for (int q = 0; q < KT; ++q) nw += (cj[q] >= 0 && cs[q] >= lower) ? 1 : 0;
+            }
+#pragma unroll
+            for (int q = 0; q < G; ++q) {
+                const int qq = g0 + q;
+                if (qq >= nw) continue;
+                const float re = warp_sum(ar[q]);
+                const float im = warp_sum(ai[q]);
+                const float w = inv_norm2[cj[qq]];
+                const float e = (cone == MRF_CONE_COMPLEX) ? (re * re + im * im) * w : re * sqrtf(w);
+                if (lane == 0) es[qq] = e;
+                if (jstar < 0 || better(e, cj[qq], bsc, jstar)) { bsc = e; jstar = cj[qq]; }
+            }
+            if (g0 + G >= nw) break;     // the remaining candidates lie outside the window
         }
     }
-    float es[KT];
-    int best = -1;
-#pragma unroll
-    for (int q = 0; q < KT; ++q) {
-        es[q] = -INFINITY;
-        if (q >= nw) continue;
-        const float re = warp_sum(er[q]);
-        const float im = warp_sum(ei[q]);
-        const float w = inv_norm2[cj[q]];
-        es[q] = (cone == MRF_CONE_COMPLEX) ? (re * re + im * im) * w : re * sqrtf(w);
-        if (best < 0 || better(es[q], cj[q], es[best], cj[best])) best = q;
-    }
-    if (best < 0) {          // no candidate at all (cannot happen with d >= 1)
+    __syncwarp();
+    if (jstar < 0) {         // no candidate at all (cannot happen with d >= 1)
         if (lane == 0) atomicOr(err, MRF_DERR_BOUNDS);
         return;
     }
@@ -195,7 +250,7 @@ k_merge(const float2* __restrict__ Z, int64_t n_in, const int32_t* __restrict__ 
     // 3. extended-precision rescore of the near-ties.  Windows are absolute in normalised correlation
     //    |c| / (||d|| ||z||): rounding errors of the FP32 (and BF16) sums scale with ||z||, not
     //    with the correlation itself.
-    const float eb = es[best];
+    const float eb = bsc;
     const float zn = sqrtf(zn2);
     auto floor_of = [&](float tol) -> float {     // lowest score still within `tol`
         if (cone == MRF_CONE_COMPLEX) {
@@ -208,7 +263,6 @@ k_merge(const float2* __restrict__ Z, int64_t n_in, const int32_t* __restrict__ 
     int ntie = 0;
 #pragma unroll
     for (int q = 0; q < KT; ++q) ntie += (cj[q] >= 0 && es[q] >= thr) ? 1 : 0;
-    int32_t jstar = cj[best];
     double cre = 0.0, cim = 0.0;
     bool have64 = false;
     if (ntie > 1) {
@@ -277,27 +331,31 @@ mrf_status launch_merge(const float2* Z, int64_t n, const mrf_dict* D, int cone,
                         cudaStream_t st, float window) {
     if (n == 0) return MRF_OK;
     dim3 grid(static_cast<unsigned>((n + WARPS - 1) / WARPS));
-    if (K == 8) {
-        k_merge<8><<<grid, WARPS * 32, 0, st>>>(Z, n, vlist, nlist, D->atoms, D->inv_norm2,
-                                                D->norm2, D->d, D->L, cone, S, part_s, part_i,
-                                                tie_tol, certify, cert_margin, window, idx_out,
-                                                rho_out, X_out, fb_list, fb_n, err, counters);
-    } else if (K == 16) {
-        k_merge<16><<<grid, WARPS * 32, 0, st>>>(Z, n, vlist, nlist, D->atoms, D->inv_norm2,
-                                                 D->norm2, D->d, D->L, cone, S, part_s, part_i,
-                                                 tie_tol, certify, cert_margin, window,
-                                                 idx_out, rho_out, X_out, fb_list, fb_n, err,
-                                                 counters);
-    } else if (K == 32) {
-        k_merge<32><<<grid, WARPS * 32, 0, st>>>(Z, n, vlist, nlist, D->atoms, D->inv_norm2,
-                                                 D->norm2, D->d, D->L, cone, S, part_s, part_i,
-                                                 tie_tol, certify, cert_margin, window,
-                                                 idx_out, rho_out, X_out, fb_list, fb_n, err,
-                                                 counters);
-    } else {
+    if (K != 8 && K != 16 && K != 32) {
         mrf_set_error("merge: K must be 8, 16 or 32");
         return MRF_EINVAL;
     }
+    // candidates per lane, rounded up to the lane-list length of an instantiation
+    const int64_t per = (static_cast<int64_t>(S) * K + 31) / 32;
+    const int NL = per <= 4 ? 4 : (per <= 8 ? 8 : (per <= 16 ? 16 : 32));
+    const int nl = NL < K ? NL : K;
+#define MRF_MERGE_ARGS Z, n, vlist, nlist, D->atoms, D->inv_norm2, D->norm2, D->d, D->L, cone, S, \
+        part_s, part_i, tie_tol, certify, cert_margin, window, idx_out, rho_out, X_out, fb_list,   \
+        fb_n, err, counters
+    if (K == 8) {
+        if (nl == 4) k_merge<8, 4><<<grid, WARPS * 32, 0, st>>>(MRF_MERGE_ARGS);
+        else k_merge<8, 8><<<grid, WARPS * 32, 0, st>>>(MRF_MERGE_ARGS);
+    } else if (K == 16) {
+        if (nl == 4) k_merge<16, 4><<<grid, WARPS * 32, 0, st>>>(MRF_MERGE_ARGS);
+        else if (nl == 8) k_merge<16, 8><<<grid, WARPS * 32, 0, st>>>(MRF_MERGE_ARGS);
+        else k_merge<16, 16><<<grid, WARPS * 32, 0, st>>>(MRF_MERGE_ARGS);
+    } else {
+        if (nl == 4) k_merge<32, 4><<<grid, WARPS * 32, 0, st>>>(MRF_MERGE_ARGS);
+        else if (nl == 8) k_merge<32, 8><<<grid, WARPS * 32, 0, st>>>(MRF_MERGE_ARGS);
+        else if (nl == 16) k_merge<32, 16><<<grid, WARPS * 32, 0, st>>>(MRF_MERGE_ARGS);
+        else k_merge<32, 32><<<grid, WARPS * 32, 0, st>>>(MRF_MERGE_ARGS);
+    }
+#undef MRF_MERGE_ARGS
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) {
         mrf_set_error(std::string("merge launch: ") + cudaGetErrorString(e));
