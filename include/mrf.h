@@ -105,7 +105,12 @@ typedef struct mrf_proj_opts {
                               its best distance to z/||z|| is above this goes to the exhaustive
                               search, where Algorithm 1 cannot prune (default 0.9; >= 2
                               disables routing) */
-    int32_t reserved[7];
+    int32_t learned_edge;  /* learned proposal: also send a voxel to the exhaustive search when
+                              the best atom of its neighbourhood lies on the neighbourhood's
+                              edge with grid cells beyond it (a better atom may lie outside);
+                              an accepted proposal is then a local maximum of the correlation
+                              over its grid neighbours (default 1) */
+    int32_t reserved[6];
 } mrf_proj_opts;
 
 /* Filled by calls given a non-NULL pointer; such calls synchronise `stream` before return. */
@@ -288,7 +293,8 @@ mrf_status mrf_project_fp32_static(const void* atoms, int64_t d, int32_t L, cons
  * maps the canonical fingerprint -- z/||z|| rotated by exp(-i angle(v1^H z)), v1 the
  * dictionary's dominant right singular vector -- to standardised (log T1, log T2, B0).  The
  * nearest grid cell's (2 radius + 1)^k neighbourhood of valid atoms is rescored exactly, and a
- * voxel whose best normalised correlation stays below mrf_proj_opts.fallback_thr is projected
+ * voxel whose best normalised correlation stays below mrf_proj_opts.fallback_thr, or (with
+ * mrf_proj_opts.learned_edge) whose best atom lies on the neighbourhood's edge, is projected
  * by the exhaustive search.  Training and inference run on this library's kernels.
  */
 typedef struct mrf_mlp mrf_mlp;

@@ -53,12 +53,14 @@ def _stream(stream) -> int | None:
 
 def proj_opts(mode: str = "fp32", cone: str = "complex", topk: int = 0, certify: bool = True,
               tie_tol: float = 1e-5, cert_margin: float = 0.0, eps: float = 0.0,
-              fallback_thr: float = 0.98, tree_route: float = 0.9) -> ProjOpts:
+              fallback_thr: float = 0.98, tree_route: float = 0.9,
+              learned_edge: bool = True) -> ProjOpts:
     o = ProjOpts()
     lib().mrf_default_proj_opts(C.byref(o))
     o.mode, o.cone, o.topk, o.certify = MODES[mode], CONES[cone], topk, int(certify)
     o.tie_tol, o.cert_margin, o.eps, o.fallback_thr = tie_tol, cert_margin, eps, fallback_thr
     o.tree_route = tree_route
+    o.learned_edge = int(learned_edge)
     return o
 
 

@@ -37,7 +37,7 @@ class ProjOpts(C.Structure):
     _fields_ = [("mode", C.c_int32), ("cone", C.c_int32), ("topk", C.c_int32),
                 ("certify", C.c_int32), ("tie_tol", C.c_float), ("cert_margin", C.c_float),
                 ("eps", C.c_float), ("fallback_thr", C.c_float), ("tree_route", C.c_float),
-                ("reserved", C.c_int32 * 7)]
+                ("learned_edge", C.c_int32), ("reserved", C.c_int32 * 6)]
 
 
 class Stats(C.Structure):

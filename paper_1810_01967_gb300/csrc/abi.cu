@@ -423,8 +423,8 @@ mrf_status project_impl(mrf_dict* D, const float2* Z, int64_t n, const mrf_proj_
             MRF_TRY(launch_merge(Z, n, D, o->cone, 8, 1, ps, pi, nullptr, nullptr, o->tie_tol, 0,
                                  0.f, idx_out, rho_out, X_out, nullptr, nullptr, D->err,
                                  D->counters, st));
-            MRF_TRY(learned_flag(D, Z, n, idx_out, o->fallback_thr, o->cone, D->vlist, D->nlist,
-                                 st));
+            MRF_TRY(learned_flag(D, Z, n, idx_out, o->fallback_thr, o->learned_edge != 0,
+                                 o->cone, D->vlist, D->nlist, st));
         }
         int32_t cnt = 0;
         MRF_CUDA_TRY(cudaMemcpyAsync(&cnt, D->nlist, sizeof(cnt), cudaMemcpyDeviceToHost, st));
@@ -536,6 +536,7 @@ void mrf_default_proj_opts(mrf_proj_opts* o) {
     o->eps = 0.f;
     o->fallback_thr = 0.98f;
     o->tree_route = 0.9f;
+    o->learned_edge = 1;
 }
 
 void mrf_default_recon_opts(mrf_recon_opts* o) {

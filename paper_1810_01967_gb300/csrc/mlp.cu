@@ -435,10 +435,13 @@ __device__ __forceinline__ int nearest_index(const float* ax, int n, float x, bo
 }
 
 // One warp per voxel: prediction -> nearest cell -> exact FP32 correlation of the valid atoms of
-// the neighbourhood; keeps the best 8 (score = |c|^2 / ||d||^2) for the merge.
+// the neighbourhood; keeps the best 8 (score = |c|^2 / ||d||^2) for the merge, and edge[v] = 1
+// when the best one lies on the neighbourhood's edge with grid cells beyond it (or the window
+// held no valid atom), i.e. when a better atom may lie outside the window.
 __global__ void k_nbhd(const float2* __restrict__ Z, int64_t n, int L, const float* __restrict__ Yp,
                        GridArgs G, const float2* __restrict__ atoms, const float* __restrict__ inv_norm2,
-                       int cone, float* __restrict__ part_s, int32_t* __restrict__ part_i) {
+                       int cone, float* __restrict__ part_s, int32_t* __restrict__ part_i,
+                       uint8_t* __restrict__ edge) {
     const int64_t v = (static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
     if (v >= n) return;
@@ -458,6 +461,12 @@ __global__ void k_nbhd(const float2* __restrict__ Z, int64_t n, int L, const flo
         ? (static_cast<int64_t>(c[0]) * G.shape[1] + c[1]) * G.shape[2] + c[2]
         : static_cast<int64_t>(c[0]) * G.shape[1] + c[1];
     bool any = false;
+    float best = -INFINITY;
+    bool best_edge = true;
+    // offset a of dimension k sits on the window's edge with a grid cell beyond it
+    auto on_edge = [&](int k, int a, int rk) {
+        return (a == -rk && c[k] + a - 1 >= 0) || (a == rk && c[k] + a + 1 < G.shape[k]);
+    };
     for (int a0 = -r; a0 <= r + 1; ++a0)
         for (int a1 = -r; a1 <= r; ++a1)
             for (int a2 = -r2; a2 <= r2; ++a2) {
@@ -489,6 +498,11 @@ __global__ void k_nbhd(const float2* __restrict__ Z, int64_t n, int L, const flo
                 }
                 const float w = inv_norm2[j];
                 const float s = (cone == MRF_CONE_COMPLEX) ? (re * re + im * im) * w : re * sqrtf(w);
+                if (s > best) {
+                    best = s;
+                    best_edge = a0 == r + 1 || on_edge(0, a0, r) || on_edge(1, a1, r) ||
+                                (G.ndim == 3 && on_edge(2, a2, r2));
+                }
                 if (s > bs[7]) {
                     bs[7] = s;
                     bi[7] = j;
@@ -513,12 +527,15 @@ __global__ void k_nbhd(const float2* __restrict__ Z, int64_t n, int L, const flo
         part_s[v * 8 + lane] = sv;
         part_i[v * 8 + lane] = iv;
     }
+    if (lane == 0) edge[v] = best_edge ? 1 : 0;
 }
 
-// voxels whose chosen atom's normalised correlation is below thr go to the fallback list
+// voxels whose chosen atom's normalised correlation is below thr, or (edge != NULL) whose
+// neighbourhood best lay on the window's edge, go to the fallback list
 __global__ void k_flag_low(const float2* __restrict__ Z, int64_t n, int L,
                            const int32_t* __restrict__ idx, const float2* __restrict__ atoms,
-                           const float* __restrict__ inv_norm2, float thr, int cone,
+                           const float* __restrict__ inv_norm2, float thr,
+                           const uint8_t* __restrict__ edge, int cone,
                            int32_t* __restrict__ list, int32_t* __restrict__ cnt_list,
                            unsigned long long* __restrict__ cnt) {
     const int64_t v = (static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
@@ -542,7 +559,7 @@ __global__ void k_flag_low(const float2* __restrict__ Z, int64_t n, int L,
     if (lane != 0 || s == 0.f) return;
     const float corr = ((cone == MRF_CONE_COMPLEX) ? sqrtf(re * re + im * im) : re) *
                        sqrtf(inv_norm2[j]) * rsqrtf(s);
-    if (corr < thr) {
+    if (corr < thr || (edge && edge[v])) {
         const int p = atomicAdd(cnt_list, 1);
         list[p] = static_cast<int32_t>(v);
         atomicAdd(cnt + CNT_FALLBACK, 1ULL);
@@ -576,6 +593,8 @@ struct mrf_mlp {
     int32_t* cell_atom = nullptr;
     int32_t* near_atom = nullptr;   // atom of the nearest valid cell (grid index distance)
     int radius = 2;
+    uint8_t* edge = nullptr;        // [edge_cap] per-voxel edge flags of the last neighbourhood pass
+    int64_t edge_cap = 0;
     // residues
     float2* pool = nullptr;
     int64_t pool_cap = 0;
@@ -899,7 +918,7 @@ void mrf_mlp_free(mrf_mlp* M) {
     if (M->blas) cublasDestroy(M->blas);
     void* ptrs[] = {M->par, M->grad, M->m, M->v, M->v1, M->axes, M->cell_atom, M->near_atom, M->pool,
                     M->pool_count, M->F, M->X, M->H1, M->A1, M->H2, M->A2, M->Y, M->T, M->dY,
-                    M->dA1, M->dA2, M->loss, M->w1b, M->w2b, M->xb, M->a1b};
+                    M->dA1, M->dA2, M->loss, M->w1b, M->w2b, M->xb, M->a1b, M->edge};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     delete M;
@@ -1060,21 +1079,26 @@ mrf_status learned_candidates(mrf_dict* D, const float2* Z, int64_t n, int cone,
     G.cell_atom = M->cell_atom;
     G.near_atom = M->near_atom;
     G.radius = M->radius;
+    if (n > M->edge_cap) {
+        MRF_TRY(alloc(&M->edge, static_cast<size_t>(n)));
+        M->edge_cap = n;
+    }
     for (int64_t s = 0; s < n; s += chunk) {
         const int64_t b = std::min(chunk, n - s);
         k_canon<<<gridw(b), kT, 0, st>>>(Z + s * M->L, nullptr, b, M->L, M->v1, M->X);
         MRF_TRY(forward_bf16(M, b, st));
         k_nbhd<<<gridw(b), kT, 0, st>>>(Z + s * M->L, b, M->L, M->Y, G, D->atoms, D->inv_norm2,
-                                       cone, part_s + s * 8, part_i + s * 8);
+                                       cone, part_s + s * 8, part_i + s * 8, M->edge + s);
     }
     MRF_CUDA_TRY(cudaGetLastError());
     return MRF_OK;
 }
 
 mrf_status learned_flag(mrf_dict* D, const float2* Z, int64_t n, const int32_t* idx, float thr,
-                        int cone, int32_t* list, int32_t* cnt_list, cudaStream_t st) {
-    k_flag_low<<<gridw(n), kT, 0, st>>>(Z, n, D->L, idx, D->atoms, D->inv_norm2, thr, cone, list,
-                                        cnt_list, D->counters);
+                        bool edge, int cone, int32_t* list, int32_t* cnt_list, cudaStream_t st) {
+    const uint8_t* ef = (edge && D->mlp && D->mlp->edge_cap >= n) ? D->mlp->edge : nullptr;
+    k_flag_low<<<gridw(n), kT, 0, st>>>(Z, n, D->L, idx, D->atoms, D->inv_norm2, thr, ef, cone,
+                                        list, cnt_list, D->counters);
     MRF_CUDA_TRY(cudaGetLastError());
     return MRF_OK;
 }

@@ -179,7 +179,7 @@ void mlp_detach(mrf_mlp* M);
 mrf_status learned_candidates(mrf_dict* D, const float2* Z, int64_t n, int cone, float* part_s,
                               int32_t* part_i, cudaStream_t st);
 mrf_status learned_flag(mrf_dict* D, const float2* Z, int64_t n, const int32_t* idx, float thr,
-                        int cone, int32_t* list, int32_t* cnt_list, cudaStream_t st);
+                        bool edge, int cone, int32_t* list, int32_t* cnt_list, cudaStream_t st);
 // merge.cu
 mrf_status launch_merge(const float2* Z, int64_t n, const mrf_dict* D, int cone, int K, int S,
                         const float* part_s, const int32_t* part_i, const int32_t* vlist,

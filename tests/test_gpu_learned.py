@@ -104,12 +104,41 @@ def test_projection_fallback_rules(mrf, cfg1):
     check_projection(Z, A, idx.cpu().numpy(), rho.cpu().numpy())
     assert st["n_fallback"] == n
     # no fallback: a valid atom of the neighbourhood with its exact density
-    st = mrf.project(D, to_dev(Z), idx, rho, opts=mrf.proj_opts(mode="learned", fallback_thr=0.0),
-                     stats=True)
+    st = mrf.project(D, to_dev(Z), idx, rho, stats=True,
+                     opts=mrf.proj_opts(mode="learned", fallback_thr=0.0, learned_edge=False))
     gi = idx.cpu().numpy()
     assert st["n_fallback"] == 0 and gi.min() >= 0 and gi.max() < A.shape[0]
     rr = mo.density(Z, A, gi)
     assert np.max(np.abs(rho.cpu().numpy() - rr) / np.abs(rr)) <= 1e-4
+    # edge rule alone (threshold 0): the untrained network's windows miss, so voxels fall back
+    st = mrf.project(D, to_dev(Z), idx, rho, stats=True,
+                     opts=mrf.proj_opts(mode="learned", fallback_thr=0.0, learned_edge=True))
+    assert st["n_fallback"] > 0
+    assert_local_max(Z, A, dic, idx.cpu().numpy())
+
+
+def assert_local_max(Z, A, dic, gi, tol=1e-5):
+    """Every voxel's atom is a local maximum of the normalised correlation over its valid grid
+    neighbours (all 3^k - 1 offsets): what the edge rule guarantees for accepted proposals, and
+    what the exhaustive answer satisfies anyway."""
+    n = Z.shape[0]
+    cell_atom = np.asarray(dic["cell_atom"])
+    cells = np.argwhere(cell_atom >= 0)          # row j = grid cell of atom j (C order)
+    assert np.array_equal(cell_atom[tuple(cells.T)], np.arange(A.shape[0]))
+    c0 = mo.correlation(Z, A, gi)
+    nz = np.linalg.norm(Z, axis=1) > 0
+    shape = np.array(cell_atom.shape)
+    for off in np.ndindex(*(3,) * cell_atom.ndim):
+        o = np.array(off) - 1
+        if not o.any():
+            continue
+        nc = cells[gi] + o
+        inside = np.all((nc >= 0) & (nc < shape), axis=1)
+        nj = np.full(n, -1)
+        nj[inside] = cell_atom[tuple(nc[inside].T)]
+        ok = nz & (nj >= 0)
+        cn = mo.correlation(Z[ok], A, nj[ok])
+        assert np.all(cn <= c0[ok] + tol), (off, float(np.max(cn - c0[ok])))
 
 
 def test_training_gain(mrf, cfg1):
@@ -160,3 +189,6 @@ def test_training_gain(mrf, cfg1):
     low = c < 0.98 - 1e-5
     near = c >= ref["s1"] - 1e-6
     assert np.all(near[low])
+    # the edge rule (on by default): accepted proposals are local maxima over the grid
+    assert out[True][1] < n
+    assert_local_max(Zh, A, dic, gi)
