@@ -1,7 +1,8 @@
 """GPU parity of the subspace-compressed BLIP (§3.3: eqs. CS1, gradupdate, gradcompression)
 against the float64 oracle (oracle/svd.py): the basis spans the dominant eigenvectors of the
 frame Gram matrix, compression and expansion, one compressed iteration from a common iterate,
-whole compressed reconstructions in FP32 and BF16, and the full basis reproducing BLIP."""
+whole compressed reconstructions in FP32 and BF16, the full basis reproducing BLIP, and the
+cover tree built on the compressed atoms (CoverBLIP in C^s)."""
 import numpy as np
 import pytest
 
@@ -140,3 +141,53 @@ def test_full_basis_reproduces_blip(mrf, cfg1):
     relX = np.linalg.norm(X.cpu().numpy() - ref["X"]) / np.linalg.norm(ref["X"])
     print(f"full basis: agreement with BLIP {agree:.5f} relX {relX:.2e}")
     assert agree >= 0.995 and relX < 1e-3
+
+
+@pytest.mark.parametrize("eps", [0.0, 0.5])
+def test_compressed_cover_tree(mrf, cfg1, eps):
+    """CoverBLIP in the compressed domain (the paper's temporal compression option for every
+    search, §4.3 and §6): the tree is built on the compressed atoms; eps = 0 reproduces the
+    compressed exhaustive projection, eps > 0 meets the (1+eps) bound of Definition eNN in C^s,
+    and whole compressed reconstructions match the oracle's compressed BLIP at eps = 0."""
+    from oracle import covertree as ct
+    dic, p = cfg1
+    Ny, Nx, L = p["Ny"], p["Nx"], p["L"]
+    n, s, iters = Ny * Nx, 20, p["iters"]
+    V64, so, _, Ac = _setup(mrf, dic, p, s)
+    Dc = mrf.build_dict_index(Ac, dic["params"], build_tree=True)
+    # one projection of the compressed first iterate
+    Zc = osvd.compress(mo.adjoint(p["Y"], p["masks"], Ny, Nx), V64).astype(np.complex64)
+    idx = torch.empty(n, dtype=torch.int32, device="cuda")
+    rho = torch.empty(n, dtype=torch.complex64, device="cuda")
+    st = mrf.project(Dc, to_dev(Zc), idx, rho, stats=True,
+                     opts=mrf.proj_opts(mode="covertree", eps=eps))
+    gi = idx.cpu().numpy()
+    if eps == 0.0:
+        check_projection(Zc, Ac, gi, rho.cpu().numpy())
+    else:
+        U = ct.unit_atoms(Ac.astype(np.complex128))
+        Zn = Zc.astype(np.complex128) / np.linalg.norm(Zc, axis=1)[:, None]
+        ref = mo.project(Zc, Ac)
+        dg = np.array([ct.pair_dist(Zn[v:v + 1], U[gi[v]:gi[v] + 1], "phase")[0, 0]
+                       for v in range(n)])
+        dn = np.array([ct.pair_dist(Zn[v:v + 1], U[ref["idx"][v]:ref["idx"][v] + 1], "phase")[0, 0]
+                       for v in range(n)])
+        assert np.all(dg <= (1 + eps) * dn + 1e-5), np.max(dg - (1 + eps) * dn)
+    assert 0 < st["n_dist_evals"] < n * Ac.shape[0] / 2
+    # whole compressed reconstruction
+    Xc = torch.empty((n, s), dtype=torch.complex64, device="cuda")
+    prm = torch.empty((n, dic["params"].shape[1]), dtype=torch.float32, device="cuda")
+    so.reconstruct(Dc, to_dev(p["Y"]), iters, Xc, idx, None, None, prm,
+                   opts=mrf.proj_opts(mode="covertree", eps=eps))
+    gi = idx.cpu().numpy()
+    ref = osvd.blip_svd(p["Y"], p["masks"], dic["atoms"], V64, Ny, Nx, iters=iters)
+    agree = float(np.mean(gi == ref["idx"]))
+    print(f"compressed CoverBLIP eps={eps}: agreement with the oracle's compressed BLIP {agree:.4f}")
+    fg = p["phantom"]["labels"] >= 0
+    acc = mo.accuracy(dic["params"][gi, 0], p["phantom"]["T1"], fg)
+    acc_ref = mo.accuracy(dic["params"][ref["idx"], 0], p["phantom"]["T1"], fg)
+    print(f"  T1 accuracy {acc:.4f} (oracle's compressed BLIP {acc_ref:.4f})")
+    if eps == 0.0:
+        assert agree >= 0.995
+    assert acc >= acc_ref - 0.02
+    assert np.array_equal(prm.cpu().numpy(), dic["params"][gi])
