@@ -462,7 +462,12 @@ typedef struct mrf_tune {
                                   each CTA staging half of every atom block) instead of clusters
                                   sharing atom blocks by multicast (bf16_cluster is then ignored);
                                   0 = the library's default */
-    int32_t reserved[6];
+    int32_t tree_order;        /* cover-tree queries of a warm-started search: 1 = processed in
+                                  the order of their warm-start atom's tree position, so that
+                                  queries of one subtree run side by side and share cached tree
+                                  nodes and atoms (results are the same either way); 2 = voxel
+                                  order; 0 = the library's default */
+    int32_t reserved[5];
 } mrf_tune;
 
 mrf_status mrf_get_tune(const mrf_dict* dict, mrf_tune* out);

@@ -810,6 +810,8 @@ mrf_status mrf_set_tune(mrf_dict* D, const mrf_tune* in) {
     D->tune.tree_list_cap = in->tree_list_cap;
     if (in->bf16_pair < 0 || in->bf16_pair > 1) return fail(MRF_EINVAL, "bf16_pair must be 0 or 1");
     D->tune.bf16_pair = in->bf16_pair;
+    if (in->tree_order < 0 || in->tree_order > 2) return fail(MRF_EINVAL, "tree_order must be 0, 1 or 2");
+    D->tune.tree_order = in->tree_order;
     D->tune.bf16_cluster = in->bf16_cluster;
     D->tune.bf16_live_tiles = in->bf16_live_tiles;
     D->tune.bf16_splits = in->bf16_splits;

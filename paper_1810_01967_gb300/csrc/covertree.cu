@@ -15,11 +15,19 @@
 // exhaustive search.  The 8 best atoms seen go to the merge
 // kernel, which rescores them exactly and computes the density.
 //
+// Query batching (the paper's closing remark on inter-voxel correlation in a query batch):
+// warm-started queries are taken in the order of their warm atom's position in the tree, so
+// the warps of a CTA and of neighbouring CTAs traverse the same subtrees and find the nodes'
+// atoms in L1/L2; each query still runs its own Algorithm 1, so results do not change.
+//
 // Distances: d(u, z) = min_phi ||z^ - e^{i phi} u|| for the complex cone (Euclidean for the real
 // cone), both unit vectors.  The first pass computes c = u^H z^ in FP32; when c is close to 1
 // (d < 0.2) a second pass evaluates ||z^ - w u|| with w = c / |c| directly, which keeps the
 // relative accuracy of small distances that 2 - 2|c| loses to cancellation.
 #include <chrono>
+#include <initializer_list>
+
+#include <cub/cub.cuh>
 
 #include "mrf_internal.cuh"
 #include "covertree_host.h"
@@ -37,6 +45,12 @@ struct CoverTreeDev {
     float* en_maxdist = nullptr;
     int64_t nt = 0, ne = 0;
     double build_ms = 0.0;
+    // query ordering scratch (grown on demand): sort keys and voxel indices, in and out
+    int32_t* okey = nullptr;
+    int32_t* oval = nullptr;
+    void* otmp = nullptr;
+    size_t otmp_bytes = 0;
+    int64_t ocap = 0;
 };
 
 namespace {
@@ -48,6 +62,7 @@ constexpr int WARPS = 4;          // warps (queries) per CTA
 constexpr int TOPC = 8;           // candidates handed to the merge
 constexpr int kRouteList = 64;    // list size from which far queries are routed away
 constexpr int kBatch = 8;         // candidate distances evaluated together
+constexpr int kDefaultOrder = 1;  // mrf_tune.tree_order when 0: warm-started queries in tree order
 
 struct TreeArgs {
     const float2* tatoms;
@@ -191,22 +206,36 @@ __device__ __forceinline__ void top_insert(float (&cs)[TOPC], int32_t (&ci)[TOPC
     }
 }
 
+// Sort keys of the query ordering: the tree position of each query's warm-start atom (queries
+// without a valid one last, key = `none`, one past the last position), and the identity
+// permutation to be sorted along.
+__global__ void k_order_keys(const int32_t* __restrict__ warm, int64_t n, TreeArgs T,
+                             int32_t none, int32_t* __restrict__ key, int32_t* __restrict__ val) {
+    const int64_t k = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    const int32_t a = warm[k];
+    key[k] = (a >= 0 && a < T.d) ? T.pos[T.rep[a]] : none;
+    val[k] = static_cast<int32_t>(k);
+}
+
+// One warp per query; warp k of the grid takes voxel order[k] (voxel k without an order).
 __global__ void __launch_bounds__(WARPS * 32)
 k_ct_search(const float2* __restrict__ Z, int64_t n, int L, TreeArgs T, int cap,
-            const int32_t* __restrict__ warm, float eps, float route,
-            float* __restrict__ part_s,
+            const int32_t* __restrict__ warm, const int32_t* __restrict__ order, float eps,
+            float route, float* __restrict__ part_s,
             int32_t* __restrict__ part_i, int32_t* __restrict__ fb_list,
             int32_t* __restrict__ fb_n, unsigned long long* cnt) {
     extern __shared__ __align__(16) unsigned char smem[];
     const int w = threadIdx.x >> 5;
     const int lane = threadIdx.x & 31;
-    const int64_t v = static_cast<int64_t>(blockIdx.x) * WARPS + w;
+    const int64_t kq = static_cast<int64_t>(blockIdx.x) * WARPS + w;
     const size_t per_warp = static_cast<size_t>(L) * sizeof(float2) + 2 * cap * sizeof(Entry);
     unsigned char* mine = smem + per_warp * w;
     float2* q = reinterpret_cast<float2*>(mine);
     Entry* QA = reinterpret_cast<Entry*>(mine + static_cast<size_t>(L) * sizeof(float2));
     Entry* QB = QA + cap;
-    if (v >= n) return;
+    if (kq >= n) return;
+    const int64_t v = order ? static_cast<int64_t>(order[kq]) : kq;
     // unit query
     const float2* z = Z + v * L;
     float s = 0.f;
@@ -374,7 +403,7 @@ mrf_status up(T** dst, const std::vector<T>& src) {
 void ct_free(CoverTreeDev* t) {
     if (!t) return;
     void* ptrs[] = {t->tatoms, t->rep, t->pos, t->order, t->node_first, t->en_level,
-                    t->en_cb, t->en_ce, t->en_maxdist};
+                    t->en_cb, t->en_ce, t->en_maxdist, t->okey, t->oval, t->otmp};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     delete t;
@@ -452,11 +481,54 @@ mrf_status launch_ct_search(const float2* Z, int64_t n, const mrf_dict* D, int c
     const int cap = D->tune.tree_list_cap > 0 ? D->tune.tree_list_cap : CAP;
     const size_t per_warp = static_cast<size_t>(D->L) * sizeof(float2) + 2 * cap * sizeof(Entry);
     const size_t sm = per_warp * WARPS;
+    // query order: warm-started queries sorted by their warm atom's tree position
+    const int32_t* order = nullptr;
+    const int tord = D->tune.tree_order ? D->tune.tree_order : kDefaultOrder;
+    if (warm && tord == 1 && n > 1) {
+        CoverTreeDev* tm = D->tree;
+        if (n > tm->ocap) {
+            size_t need = 0;
+            if (cub::DeviceRadixSort::SortPairs(nullptr, need, tm->okey, tm->okey, tm->oval,
+                                                tm->oval, static_cast<int>(n)) != cudaSuccess) {
+                mrf_set_error("query order: sort workspace query failed");
+                return MRF_ECUDA;
+            }
+            for (void** p : {reinterpret_cast<void**>(&tm->okey), reinterpret_cast<void**>(&tm->oval),
+                             &tm->otmp}) {
+                if (*p) cudaFree(*p);
+                *p = nullptr;
+            }
+            tm->ocap = 0;
+            MRF_CUDA_TRY(cudaMalloc(reinterpret_cast<void**>(&tm->okey), sizeof(int32_t) * 2 * n));
+            MRF_CUDA_TRY(cudaMalloc(reinterpret_cast<void**>(&tm->oval), sizeof(int32_t) * 2 * n));
+            MRF_CUDA_TRY(cudaMalloc(&tm->otmp, need));
+            tm->otmp_bytes = need;
+            tm->ocap = n;
+        }
+        int32_t* kin = tm->okey;
+        int32_t* kout = tm->okey + n;
+        int32_t* vin = tm->oval;
+        int32_t* vout = tm->oval + n;
+        const int32_t none = static_cast<int32_t>(tm->nt);
+        k_order_keys<<<static_cast<unsigned>((n + 255) / 256), 256, 0, st>>>(warm, n, T, none,
+                                                                            kin, vin);
+        MRF_CUDA_TRY(cudaGetLastError());
+        size_t bytes = tm->otmp_bytes;
+        int end_bit = 1;            // keys lie in [0, nt]
+        while (end_bit < 31 && (int64_t{1} << end_bit) <= tm->nt) ++end_bit;
+        if (cub::DeviceRadixSort::SortPairs(tm->otmp, bytes, kin, kout, vin, vout,
+                                            static_cast<int>(n), 0, end_bit, st) != cudaSuccess) {
+            mrf_set_error("query order: sort failed");
+            return MRF_ECUDA;
+        }
+        order = vout;
+    }
     cudaError_t e = cudaFuncSetAttribute(k_ct_search, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          static_cast<int>(sm));
     if (e == cudaSuccess) {
         k_ct_search<<<static_cast<unsigned>((n + WARPS - 1) / WARPS), WARPS * 32, sm, st>>>(
-            Z, n, D->L, T, cap, warm, eps, route, part_s, part_i, fb_list, fb_n, D->counters);
+            Z, n, D->L, T, cap, warm, order, eps, route, part_s, part_i, fb_list, fb_n,
+            D->counters);
         e = cudaGetLastError();
     }
     if (e != cudaSuccess) {

@@ -2,7 +2,8 @@
 exact rescore of the visited candidates) against the float64 oracle: the uploaded tree satisfies
 the invariants of §4.1, eps = 0 equals the exhaustive projection, eps > 0 meets the (1+eps)
 bound of Definition eNN, warm starts are non-expansive (§4.3), the search costs fewer distance
-evaluations than brute force, and CoverBLIP reconstructions match BLIP at eps = 0."""
+evaluations than brute force, the query order of warm-started searches does not change any
+result, and CoverBLIP reconstructions match BLIP at eps = 0."""
 import numpy as np
 import pytest
 
@@ -90,6 +91,29 @@ def test_eps_bound_and_warm_start(mrf, cfg1, eps):
         rr = mo.density(Z, A, idx)
         assert np.max(np.abs(rho - rr) / np.abs(rr)) <= 1e-4
         assert st["n_dist_evals"] < Z.shape[0] * A.shape[0] / 2
+
+
+@pytest.mark.parametrize("eps", [0.0, 0.5])
+def test_query_order_does_not_change_results(mrf, cfg1, eps):
+    """Warm-started queries run in the order of their warm atom's tree position (mrf_tune
+    tree_order = 1, the default) or in voxel order (2): each query runs its own Algorithm 1, so
+    indices, densities and the number of distance evaluations are identical."""
+    dic, p, Z = cfg1
+    A = dic["atoms"]
+    D = mrf.build_dict_index(A, build_tree=True)
+    g = np.random.Generator(np.random.PCG64(11))
+    warm = g.integers(-1, A.shape[0], Z.shape[0])      # includes invalid warm starts (-1)
+    out = {}
+    for order in (1, 2):
+        D.set_tune(tree_order=order)
+        out[order] = run(mrf, D, Z, eps, warm=warm)
+    assert D.get_tune()["tree_order"] == 2
+    assert np.array_equal(out[1][0], out[2][0])
+    assert np.array_equal(out[1][1], out[2][1])
+    assert out[1][3]["n_dist_evals"] == out[2][3]["n_dist_evals"]
+    assert out[1][3]["n_fallback"] == out[2][3]["n_fallback"]
+    if eps == 0.0:
+        check_projection(Z, A, out[1][0], out[1][1], g_X=out[1][2])
 
 
 def test_warm_start_at_the_answer_is_cheap(mrf, cfg1):
