@@ -103,8 +103,9 @@ typedef struct mrf_proj_opts {
     float   fallback_thr;  /* learned proposal: normalised correlation threshold (0.98) */
     float   tree_route;    /* cover tree: a voxel whose candidate list exceeds 64 entries while
                               its best distance to z/||z|| is above this goes to the exhaustive
-                              search, where Algorithm 1 cannot prune (default 0.9; >= 2
-                              disables routing) */
+                              search, where Algorithm 1 cannot prune; so does a warm-started
+                              voxel whose warm atom is already farther than this, before the
+                              traversal (default 0.9; >= 2 disables routing) */
     int32_t learned_edge;  /* learned proposal: also send a voxel to the exhaustive search when
                               the best atom of its neighbourhood lies on the neighbourhood's
                               edge with grid cells beyond it (a better atom may lie outside);

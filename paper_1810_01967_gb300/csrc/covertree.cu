@@ -12,7 +12,8 @@
 // update (q_c, dist_min), refine with dist <= dist_min + maxdist.  A voxel whose list has grown
 // past 64 entries while dist_min still exceeds `route` -- a far query, for which the refinement
 // keeps almost the whole net -- or whose list would exceed its capacity is handed to the
-// exhaustive search.  The 8 best atoms seen go to the merge
+// exhaustive search; so is, before any traversal, a warm-started voxel whose warm atom is
+// already farther than `route`.  The 8 best atoms seen go to the merge
 // kernel, which rescores them exactly and computes the density.
 //
 // Query batching (the paper's closing remark on inter-voxel correlation in a query batch):
@@ -275,9 +276,16 @@ k_ct_search(const float2* __restrict__ Z, int64_t n, int L, TreeArgs T, int cap,
         }
     }
     bool overflow = false;
+    // a warm-started query whose warm atom is already farther than `route` goes to the
+    // exhaustive search before the traversal (unless the stop rule would end the search at the
+    // first level): such a query would be routed after building its lists anyway
+    if (warm && dmin > route && (eps == 0.f || T.sigma * 2.f * (1.f + 1.f / eps) > dmin)) {
+        const int32_t a = warm[v];
+        if (a >= 0 && a < T.d) overflow = true;
+    }
     Entry* Q = QA;
     Entry* N = QB;
-    int nq = 1;
+    int nq = overflow ? 0 : 1;
     if (lane == 0) {
         const int32_t c0 = T.node_first[0];
         Q[0] = {0, droot, c0, (c0 < T.node_first[1]) ? T.en_maxdist[c0] : 0.f};
