@@ -1,0 +1,135 @@
+"""Parity at the benchmark's full size: one 256 x 256 slice, L = 1000 frames, the 100,011-atom
+IR-bSSFP dictionary (a ragged last block of 43 atoms), run in the launch configuration that
+bench.py times -- BF16 uncertified top-16 and FP8 uncertified top-32 with the default cluster
+geometry and atom splits -- and checked against the float64 oracle on seeded voxel samples it
+computes one by one: the adjoint A^H Y, the projection of that first iterate (exact rule when
+certified; the uncertified forms' error-bound rule otherwise), the density, and the gradient
+step of the next iteration."""
+import numpy as np
+import pytest
+
+import mrfgen
+from oracle import mrf_oracle as mo
+from gpu_util import to_dev, check_projection
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def mrf():
+    import paper_1810_01967_gb300 as m
+    from paper_1810_01967_gb300 import build as b
+    b.build()
+    return m
+
+
+@pytest.fixture(scope="module")
+def full(mrf):
+    dic = mrfgen.make_dictionary(2)
+    p = mrfgen.make_problem(2, i=0, dic=dic)
+    Ny, Nx, L = p["Ny"], p["Nx"], p["L"]
+    D = mrf.build_dict_index(dic["atoms"], dic["params"], pack_fp8=True)
+    op = mrf.make_op(Ny, Nx, L, to_dev(p["masks"]))
+    AHY = torch.empty((Ny * Nx, L), dtype=torch.complex64, device="cuda")
+    mrf.adjoint(op, to_dev(p["Y"]), AHY)
+    torch.cuda.synchronize()
+    g = np.random.Generator(np.random.PCG64(2024))
+    fg = np.flatnonzero(p["phantom"]["labels"] >= 0)
+    bg = np.flatnonzero(p["phantom"]["labels"] < 0)
+    sample = np.sort(np.concatenate([g.choice(fg, 256, replace=False),
+                                     g.choice(bg, 128, replace=False)]))
+    return {"dic": dic, "p": p, "D": D, "op": op, "AHY": AHY, "sample": sample}
+
+
+def _project(mrf, F, mode, certify):
+    n = F["AHY"].shape[0]
+    idx = torch.empty(n, dtype=torch.int32, device="cuda")
+    rho = torch.empty(n, dtype=torch.complex64, device="cuda")
+    st = mrf.project(F["D"], F["AHY"], idx, rho, opts=mrf.proj_opts(mode=mode, certify=certify),
+                     stats=True)
+    torch.cuda.synchronize()
+    return idx.cpu().numpy(), rho.cpu().numpy(), st
+
+
+def _fft_err(got, ref):
+    """Row errors relative to the sample's RMS row norm: the rounding error of an FP32 FFT is
+    bounded relative to the norm of the whole transform (a few units of log2(N) 2^-24 of it),
+    not to each output row, so a weak background row carries a larger relative error."""
+    scale = np.sqrt(np.mean(np.sum(np.abs(ref) ** 2, axis=1)))
+    return np.linalg.norm(got - ref, axis=1) / scale
+
+
+def _bound_rule(Zs, A, gi, ref, bound):
+    """Uncertified forms: the answer is the exact best of the kept candidates, so its
+    normalised correlation is within twice the kernel's error bound of the best."""
+    sg = mo.correlation(Zs, A, gi)
+    assert np.all(sg >= ref["s1"] - 2 * bound), float(np.min(sg - ref["s1"]))
+    return float(np.mean(gi == ref["idx"]))
+
+
+def test_adjoint_full_slice(mrf, full):
+    p, s = full["p"], full["sample"]
+    ref = mo.adjoint(p["Y"], p["masks"], p["Ny"], p["Nx"])[s]
+    got = full["AHY"].cpu().numpy()[s].astype(np.complex128)
+    assert np.max(_fft_err(got, ref)) < 1e-5
+
+
+def test_bf16_projection_full_slice(mrf, full):
+    A, s = full["dic"]["atoms"], full["sample"]
+    gi, gr, st = _project(mrf, full, "bf16", certify=False)
+    assert st["device_error"] == 0
+    assert gi.min() >= 0 and gi.max() < A.shape[0]
+    Zs = full["AHY"].cpu().numpy()[s]
+    ref = mo.project(Zs, A)
+    L = A.shape[1]
+    bound = 2.0 ** -7 + 2.0 ** -16 + 2 * L * 2.0 ** -24
+    agree = _bound_rule(Zs, A, gi[s], ref, bound)
+    print(f"full slice, BF16 top-16 uncertified: sampled agreement {agree:.4f}")
+    assert agree >= 0.98
+    same = gi[s] == ref["idx"]
+    rr = ref["rho"][same]
+    assert np.max(np.abs(gr[s][same] - rr) / np.maximum(np.abs(rr), 1e-30)) <= 1e-4
+
+
+def test_bf16_certified_full_slice(mrf, full):
+    A, s = full["dic"]["atoms"], full["sample"]
+    gi, gr, st = _project(mrf, full, "bf16", certify=True)
+    assert st["device_error"] == 0
+    Zs = full["AHY"].cpu().numpy()[s]
+    agree, ties = check_projection(Zs, A, gi[s], gr[s])
+    print(f"full slice, BF16 certified: sampled agreement {agree:.4f} ({ties} near-ties), "
+          f"{st['n_uncertified']} voxels re-searched in FP32")
+
+
+def test_fp8_projection_full_slice(mrf, full):
+    A, s = full["dic"]["atoms"], full["sample"]
+    gi, gr, st = _project(mrf, full, "fp8", certify=False)
+    assert st["device_error"] == 0
+    Zs = full["AHY"].cpu().numpy()[s]
+    ref = mo.project(Zs, A)
+    L = A.shape[1]
+    u8 = 2.0 ** -4 + np.sqrt(2 * L) * 2.0 ** -10 / 224
+    bound = 2 * u8 + u8 * u8 + 2 * L * 2.0 ** -13
+    agree = _bound_rule(Zs, A, gi[s], ref, bound)
+    print(f"full slice, FP8 top-32 uncertified: sampled agreement {agree:.4f}")
+    assert agree >= 0.85
+    rr = mo.density(Zs, A, gi[s])
+    assert np.max(np.abs(gr[s] - rr) / np.maximum(np.abs(rr), 1e-30)) <= 1e-4
+
+
+def test_gradient_step_full_slice(mrf, full):
+    """The next iteration's gradient step from the projected first iterate X = rho D_j (the
+    fused one-pass kernel for Ny = 256), on sampled rows."""
+    dic, p, s = full["dic"], full["p"], full["sample"]
+    A = dic["atoms"]
+    gi, gr, _ = _project(mrf, full, "bf16", certify=False)
+    X = (gr[:, None] * A[gi]).astype(np.complex64)
+    Xd = to_dev(X)
+    Z = torch.empty_like(Xd)
+    mrf.gradient(full["D"], full["op"], full["AHY"], Xd, 1.0, Z)
+    torch.cuda.synchronize()
+    ref = mo.gradient_step(X, p["Y"], p["masks"], p["Ny"], p["Nx"], 1.0)[s]
+    got = Z.cpu().numpy()[s].astype(np.complex128)
+    assert np.max(_fft_err(got, ref)) < 1e-5
