@@ -301,7 +301,7 @@ mrf_status mrf_project_fp32_static(const void* atoms, int64_t d, int32_t L, cons
 typedef struct mrf_mlp mrf_mlp;
 
 typedef struct mrf_mlp_opts {
-    int32_t  hidden;        /* hidden width (default 512) */
+    int32_t  hidden;        /* hidden width, a multiple of 16 in 16..4096 (default 512) */
     int32_t  radius;        /* neighbourhood radius per grid dimension (default 2: 5x5x5) */
     int64_t  residue_pool;  /* capacity of the aliasing-residue pool, fingerprints (262144) */
     uint64_t seed;          /* initialisation and sampling seed (default 5000) */
@@ -349,6 +349,13 @@ mrf_status mrf_mlp_params(mrf_mlp* mlp, float* host_params, int32_t set, int64_t
  * (grads_out, same layout as mrf_mlp_params, host or device).  Synchronises `stream`. */
 mrf_status mrf_mlp_grad(mrf_mlp* mlp, const float* X, const float* T, int64_t B, float* Y_out,
                         float* grads_out, double* loss_out, void* stream);
+
+/* Inference as the learned projection runs it: weights and activations rounded to BF16, the two
+ * hidden layers on the tensor cores with FP32 accumulation and bias + GELU in FP32, the output
+ * layer in FP32.  X device float32 [B][2L] (canonical inputs), Y_out device float32 [B][3]
+ * (standardised targets).  Asynchronous on `stream`; device errors are reported by the
+ * dictionary's next checked call (mrf_dict_check). */
+mrf_status mrf_mlp_infer(mrf_mlp* mlp, const float* X, int64_t B, float* Y_out, void* stream);
 
 /* Canonical network inputs of Z (device complex64 [n][L]) into X (device float32 [n][2L]); also
  * copies v1 (host complex64 [L]) and the target means and standard deviations (host float [6])

@@ -307,6 +307,14 @@ class MLP:
                                   C.byref(loss) if T is not None else None, _stream(stream)))
         return Y, (loss.value if T is not None else None), g
 
+    def infer(self, X, Y_out, stream=None) -> None:
+        """BF16 tensor-core inference (the learned projection's path): X [B][2L] float32,
+        Y_out [B][3] float32, both on the GPU."""
+        if X.shape[1] != 2 * self.L or Y_out.shape[0] != X.shape[0]:
+            raise ValueError("X must be [B][2L] and Y_out [B][3]")
+        _check(lib().mrf_mlp_infer(self.handle, _ptr(X), X.shape[0], _ptr(Y_out),
+                                   _stream(stream)))
+
     def canonical(self, Z, X_out, stream=None):
         import numpy as np
         v1 = np.empty(self.L, np.complex64)

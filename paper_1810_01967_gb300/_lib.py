@@ -135,6 +135,7 @@ SIGNATURES = {
                                C.c_void_p, C.c_void_p, C.c_void_p]),
     "mrf_mlp_canonical": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p,
                                     C.c_void_p, C.c_void_p]),
+    "mrf_mlp_infer": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p]),
     "mrf_dict_attach_mlp": (C.c_int, [C.c_void_p, C.c_void_p]),
     "mrf_batch_create": (C.c_int, [C.c_void_p, C.c_int32, C.c_void_p, C.POINTER(C.c_void_p)]),
     "mrf_batch_free": (None, [C.c_void_p]),

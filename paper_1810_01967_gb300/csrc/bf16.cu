@@ -25,6 +25,7 @@
 #include <cuda.h>
 #include "mrf_internal.cuh"
 #include "ptx.cuh"
+#include "tma_host.h"
 
 namespace {
 
@@ -573,10 +574,12 @@ EncodeFn get_encode() {
     return fn;
 }
 
+}  // namespace
+
 // Tensor map over a row-major [rows][Kp] operand of 2-byte (BF16) or 1-byte (E4M3) elements;
 // boxes of 128 bytes x box_rows rows with the 128-byte swizzle the UMMA descriptors expect.
-mrf_status make_map(CUtensorMap* m, const void* ptr, int64_t rows, int Kp, int box_rows,
-                    bool f8) {
+mrf_status tma_map_k128(CUtensorMap* m, const void* ptr, int64_t rows, int Kp, int box_rows,
+                        bool f8) {
     EncodeFn enc = get_encode();
     if (!enc) {
         mrf_set_error("cuTensorMapEncodeTiled is unavailable");
@@ -597,6 +600,8 @@ mrf_status make_map(CUtensorMap* m, const void* ptr, int64_t rows, int Kp, int b
     }
     return MRF_OK;
 }
+
+namespace {
 
 template <int KT, int C, bool F8>
 mrf_status launch_t(const CUtensorMap& ta, const CUtensorMap& tb, int64_t n, const mrf_dict* D,
@@ -791,8 +796,8 @@ mrf_status launch_tc(bool f8, const void* zq, const float* qs, int64_t n, mrf_di
     const int C = pair ? 2 : cluster_of(D);
     const int Kp = f8 ? D->Kp8 : D->Kp;
     CUtensorMap ta, tb;
-    MRF_TRY(make_map(&ta, zq, n, Kp, BM, f8));
-    MRF_TRY(make_map(&tb, op, D->nblk * 256, Kp, BN / C, f8));
+    MRF_TRY(tma_map_k128(&ta, zq, n, Kp, BM, f8));
+    MRF_TRY(tma_map_k128(&tb, op, D->nblk * 256, Kp, BN / C, f8));
     const int64_t Mt = (n + BM - 1) / BM;
     const int64_t live = D->tune.bf16_live_tiles > 0 ? D->tune.bf16_live_tiles : kDefaultLive;
     Sched sc;

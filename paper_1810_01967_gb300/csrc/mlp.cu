@@ -19,7 +19,6 @@
 // prediction to the nearest grid cell and rescores the valid atoms of the (2r+1)^k
 // neighbourhood in FP32; the merge kernel then rescores its best 8 exactly (extended-precision
 // near-ties) and forms the density.
-#include <cublas_v2.h>
 
 #include <cmath>
 #include <cstring>
@@ -114,22 +113,27 @@ k_gemm(int M, int N, int K, const float* __restrict__ A, int lda, const float* _
     }
 }
 
-__global__ void k_to_bf16(const float* __restrict__ a, int64_t n, __nv_bfloat16* __restrict__ b) {
+// b [rows][ldb] = BF16 of a [rows][cols] (FP32, row-major), zero in the padding columns
+__global__ void k_to_bf16_rows(const float* __restrict__ a, int64_t rows, int cols, int ldb,
+                               __nv_bfloat16* __restrict__ b) {
+    const int64_t n = rows * ldb;
     for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < n;
-         i += static_cast<int64_t>(gridDim.x) * blockDim.x)
-        b[i] = __float2bfloat16_rn(a[i]);
+         i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+        const int64_t r = i / ldb;
+        const int c = static_cast<int>(i - r * ldb);
+        b[i] = __float2bfloat16_rn(c < cols ? a[r * cols + c] : 0.f);
+    }
 }
 
-// A = gelu(H + bias) (FP32), and its BF16 copy when Ab is given
-__global__ void k_bias_gelu(const float* __restrict__ Hm, int64_t count, int N,
-                            const float* __restrict__ bias, float* __restrict__ A,
-                            __nv_bfloat16* __restrict__ Ab) {
-    for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < count;
+// bt [cols][ldb] = BF16 of the transpose of a [rows][cols] (FP32), zero beyond `rows`
+__global__ void k_to_bf16_t(const float* __restrict__ a, int rows, int cols, int ldb,
+                            __nv_bfloat16* __restrict__ bt) {
+    const int64_t n = static_cast<int64_t>(cols) * ldb;
+    for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < n;
          i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
-        const float v = Hm[i] + bias[i % N];
-        const float g = 0.5f * v * (1.f + erff(v * 0.70710678118654752f));
-        A[i] = g;
-        if (Ab) Ab[i] = __float2bfloat16_rn(g);
+        const int c = static_cast<int>(i / ldb);
+        const int r = static_cast<int>(i - static_cast<int64_t>(c) * ldb);
+        bt[i] = __float2bfloat16_rn(r < rows ? a[static_cast<int64_t>(r) * cols + c] : 0.f);
     }
 }
 
@@ -609,11 +613,12 @@ struct mrf_mlp {
     double* loss = nullptr;
     int64_t step = 0;
     uint64_t seed = 5000;
-    // inference in BF16 (weights rounded from the FP32 masters when they change)
-    cublasHandle_t blas = nullptr;
-    __nv_bfloat16* w1b = nullptr;   // [I][H]
-    __nv_bfloat16* w2b = nullptr;   // [H][H]
-    __nv_bfloat16* xb = nullptr;    // [cap_b][I]
+    // inference in BF16 on the tensor cores (weights rounded from the FP32 masters when they
+    // change), K-major operands with rows padded to Ip = I rounded up to 8 (16-byte pitch)
+    int Ip = 0;
+    __nv_bfloat16* w1b = nullptr;   // [H][Ip] = W1^T
+    __nv_bfloat16* w2b = nullptr;   // [H][H] = W2^T
+    __nv_bfloat16* xb = nullptr;    // [cap_b][Ip]
     __nv_bfloat16* a1b = nullptr;   // [cap_b][H]
     bool wb_valid = false;
 };
@@ -645,7 +650,7 @@ mrf_status ensure_batch(mrf_mlp* M, int64_t B) {
     MRF_TRY(alloc(&M->Y, B * 3));
     MRF_TRY(alloc(&M->T, B * 3));
     MRF_TRY(alloc(&M->dY, B * 3));
-    MRF_TRY(alloc(&M->xb, B * M->I));
+    MRF_TRY(alloc(&M->xb, B * M->Ip));
     MRF_TRY(alloc(&M->a1b, B * M->H));
     M->cap_b = B;
     return MRF_OK;
@@ -664,36 +669,23 @@ mrf_status forward(mrf_mlp* M, const float* X, int64_t B, cudaStream_t st) {
     return cudaGetLastError() == cudaSuccess ? MRF_OK : MRF_ECUDA;
 }
 
-// Inference with BF16 weights and activations, FP32 accumulation (cuBLAS GEMMs for the two
-// 512-wide layers; bias, GELU and the 3-wide output layer in FP32 here).
-mrf_status forward_bf16(mrf_mlp* M, int64_t B, cudaStream_t st) {
-    const int I = M->I, H = M->H;
-    if (cublasSetStream(M->blas, st) != CUBLAS_STATUS_SUCCESS) {
-        mrf_set_error("cublasSetStream failed");
-        return MRF_ECUDA;
-    }
+// Inference with BF16 weights and activations, FP32 accumulation: the two hidden layers on the
+// tensor cores with bias + GELU fused into their epilogues (tcgemm.cu), the 3-wide output
+// layer in FP32.  X [B][I] FP32 canonical inputs; the result lands in M->Y.
+mrf_status forward_bf16(mrf_mlp* M, const float* X, int64_t B, cudaStream_t st) {
+    const int I = M->I, H = M->H, Ip = M->Ip;
+    uint32_t* err = M->dict->err;
     if (!M->wb_valid) {
-        k_to_bf16<<<256, kT, 0, st>>>(P(M, 0), static_cast<int64_t>(I) * H, M->w1b);
-        k_to_bf16<<<256, kT, 0, st>>>(P(M, 2), static_cast<int64_t>(H) * H, M->w2b);
+        k_to_bf16_t<<<256, kT, 0, st>>>(P(M, 0), I, H, Ip, M->w1b);
+        k_to_bf16_t<<<256, kT, 0, st>>>(P(M, 2), H, H, H, M->w2b);
         M->wb_valid = true;
     }
-    k_to_bf16<<<1024, kT, 0, st>>>(M->X, B * I, M->xb);
-    const float one = 1.f, zero = 0.f;
-    // row-major H1 [B][H] = Xb [B][I] W1b [I][H]  <=>  column-major H1^T = W1b^T Xb^T
-    if (cublasGemmEx(M->blas, CUBLAS_OP_N, CUBLAS_OP_N, H, static_cast<int>(B), I, &one, M->w1b,
-                     CUDA_R_16BF, H, M->xb, CUDA_R_16BF, I, &zero, M->H1, CUDA_R_32F, H,
-                     CUBLAS_COMPUTE_32F, CUBLAS_GEMM_DEFAULT) != CUBLAS_STATUS_SUCCESS) {
-        mrf_set_error("cublasGemmEx (layer 1) failed");
-        return MRF_ECUDA;
-    }
-    k_bias_gelu<<<1024, kT, 0, st>>>(M->H1, B * H, H, P(M, 1), M->A1, M->a1b);
-    if (cublasGemmEx(M->blas, CUBLAS_OP_N, CUBLAS_OP_N, H, static_cast<int>(B), H, &one, M->w2b,
-                     CUDA_R_16BF, H, M->a1b, CUDA_R_16BF, H, &zero, M->H2, CUDA_R_32F, H,
-                     CUBLAS_COMPUTE_32F, CUBLAS_GEMM_DEFAULT) != CUBLAS_STATUS_SUCCESS) {
-        mrf_set_error("cublasGemmEx (layer 2) failed");
-        return MRF_ECUDA;
-    }
-    k_bias_gelu<<<1024, kT, 0, st>>>(M->H2, B * H, H, P(M, 3), M->A2, nullptr);
+    k_to_bf16_rows<<<1024, kT, 0, st>>>(X, B, I, Ip, M->xb);
+    MRF_CUDA_TRY(cudaGetLastError());
+    MRF_TRY(launch_dense_gelu(M->xb, static_cast<int>(B), Ip, M->w1b, H, P(M, 1), nullptr,
+                              M->a1b, err, st));
+    MRF_TRY(launch_dense_gelu(M->a1b, static_cast<int>(B), H, M->w2b, H, P(M, 3), M->A2,
+                              nullptr, err, st));
     k_out3<<<gridw(B), kT, 0, st>>>(M->A2, B, H, P(M, 4), P(M, 5), M->Y);
     return cudaGetLastError() == cudaSuccess ? MRF_OK : MRF_ECUDA;
 }
@@ -791,8 +783,9 @@ mrf_status mrf_mlp_create(mrf_dict* D, const float* grid_axes, const int32_t* ce
     if (!grid_axes || !cell_atom) { mrf_set_error("grid_axes and cell_atom are required"); return MRF_EINVAL; }
     mrf_mlp_opts o;
     if (opts) o = *opts; else mrf_default_mlp_opts(&o);
-    if (o.hidden < 8 || o.hidden > 4096 || o.radius < 0 || o.radius > 8 || o.residue_pool < 0) {
-        mrf_set_error("bad mlp options");
+    if (o.hidden < 16 || o.hidden > 4096 || o.hidden % 16 || o.radius < 0 || o.radius > 8 ||
+        o.residue_pool < 0) {
+        mrf_set_error("bad mlp options (hidden must be a multiple of 16 in 16..4096)");
         return MRF_EINVAL;
     }
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
@@ -800,6 +793,7 @@ mrf_status mrf_mlp_create(mrf_dict* D, const float* grid_axes, const int32_t* ce
     M->dict = D;
     M->L = D->L;
     M->I = 2 * D->L;
+    M->Ip = ((M->I + 7) / 8) * 8;
     M->H = o.hidden;
     M->radius = o.radius;
     M->seed = o.seed;
@@ -820,14 +814,9 @@ mrf_status mrf_mlp_create(mrf_dict* D, const float* grid_axes, const int32_t* ce
         (s = alloc(&M->cell_atom, static_cast<size_t>(cells))) ||
         (s = alloc(&M->near_atom, static_cast<size_t>(cells))) || (s = alloc(&M->loss, 1)) ||
         (s = alloc(&M->pool_count, 1)) ||
-        (s = alloc(&M->w1b, static_cast<size_t>(M->I) * M->H)) ||
+        (s = alloc(&M->w1b, static_cast<size_t>(M->Ip) * M->H)) ||
         (s = alloc(&M->w2b, static_cast<size_t>(M->H) * M->H)))
         return bail(s);
-    if (cublasCreate(&M->blas) != CUBLAS_STATUS_SUCCESS) {
-        M->blas = nullptr;
-        mrf_set_error("cublasCreate failed");
-        return bail(MRF_ECUDA);
-    }
     if (o.residue_pool > 0 && (s = alloc(&M->pool, static_cast<size_t>(o.residue_pool) * M->L)))
         return bail(s);
     M->pool_cap = o.residue_pool;
@@ -915,7 +904,6 @@ mrf_status mrf_mlp_create(mrf_dict* D, const float* grid_axes, const int32_t* ce
 void mrf_mlp_free(mrf_mlp* M) {
     if (!M) return;
     if (M->dict && M->dict->mlp == M) M->dict->mlp = nullptr;
-    if (M->blas) cublasDestroy(M->blas);
     void* ptrs[] = {M->par, M->grad, M->m, M->v, M->v1, M->axes, M->cell_atom, M->near_atom, M->pool,
                     M->pool_count, M->F, M->X, M->H1, M->A1, M->H2, M->A2, M->Y, M->T, M->dY,
                     M->dA1, M->dA2, M->loss, M->w1b, M->w2b, M->xb, M->a1b, M->edge};
@@ -1026,6 +1014,23 @@ mrf_status mrf_mlp_grad(mrf_mlp* M, const float* X, const float* T, int64_t B, f
     return MRF_OK;
 }
 
+mrf_status mrf_mlp_infer(mrf_mlp* M, const float* X, int64_t B, float* Y_out, void* stream) {
+    if (!M || !M->dict || B < 0 || (B > 0 && (!X || !Y_out))) {
+        mrf_set_error("bad arguments (or the model's dictionary was freed)");
+        return MRF_EINVAL;
+    }
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    const int64_t chunk = 16384;
+    MRF_TRY(ensure_batch(M, std::min<int64_t>(chunk, B)));
+    for (int64_t s = 0; s < B; s += chunk) {
+        const int64_t b = std::min(chunk, B - s);
+        MRF_TRY(forward_bf16(M, X + s * M->I, b, st));
+        MRF_CUDA_TRY(cudaMemcpyAsync(Y_out + s * 3, M->Y, b * 3 * sizeof(float),
+                                     cudaMemcpyDeviceToDevice, st));
+    }
+    return MRF_OK;
+}
+
 mrf_status mrf_mlp_canonical(mrf_mlp* M, const void* Z, int64_t n, float* X, float* v1_host,
                              float* tstats_host, void* stream) {
     if (!M || n < 0 || (n > 0 && (!Z || !X))) { mrf_set_error("bad arguments"); return MRF_EINVAL; }
@@ -1086,7 +1091,7 @@ mrf_status learned_candidates(mrf_dict* D, const float2* Z, int64_t n, int cone,
     for (int64_t s = 0; s < n; s += chunk) {
         const int64_t b = std::min(chunk, n - s);
         k_canon<<<gridw(b), kT, 0, st>>>(Z + s * M->L, nullptr, b, M->L, M->v1, M->X);
-        MRF_TRY(forward_bf16(M, b, st));
+        MRF_TRY(forward_bf16(M, M->X, b, st));
         k_nbhd<<<gridw(b), kT, 0, st>>>(Z + s * M->L, b, M->L, M->Y, G, D->atoms, D->inv_norm2,
                                        cone, part_s + s * 8, part_i + s * 8, M->edge + s);
     }

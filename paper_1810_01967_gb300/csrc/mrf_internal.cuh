@@ -174,6 +174,12 @@ mrf_status launch_align_queries(const mrf_dict* D, const float2* Z, int64_t n, f
                                 float2* eb, cudaStream_t st);
 mrf_status launch_align_post(const mrf_dict* D, int64_t n, const int32_t* idx, const float2* eb,
                              float2* rho, float2* X, cudaStream_t st);
+// tcgemm.cu: out/outb [M][N] = gelu(A [M][Kp] Wt^T + bias), BF16 operands (K-major, 16-byte row
+// pitch), FP32 accumulation on the tensor cores; N a multiple of 16; either output may be NULL
+mrf_status launch_dense_gelu(const __nv_bfloat16* A, int M, int Kp, const __nv_bfloat16* Wt,
+                             int N, const float* bias, float* out, __nv_bfloat16* outb,
+                             uint32_t* err, cudaStream_t st);
+int dense_tile_n(int N);
 // mlp.cu
 void mlp_detach(mrf_mlp* M);
 mrf_status learned_candidates(mrf_dict* D, const float2* Z, int64_t n, int cone, float* part_s,

@@ -1,0 +1,220 @@
+// Dense layers of the learned proposal's network on the 5th-generation tensor cores:
+//   out[m][n] = gelu(sum_k A[m][k] W[k][n] + bias[n]),  A [M][Kp] BF16, W given transposed as
+//   Wt [N][Kp] BF16 (both K-major), FP32 accumulation in tensor memory, bias and GELU in FP32.
+//
+// One CTA per 128-row x BN-column tile (BN <= 256, a multiple of 16 dividing N): warp 0 streams
+// 128-byte K slices of the A tile and of the BN weight rows with TMA into a 4-stage ring
+// (128-byte swizzle), warp 1 owns 256 TMEM columns and issues tcgen05.mma kind::f16
+// 128 x BN x 16 (four per stage), warps 2..5 wait for the last commit and drain the
+// accumulator row by row (TMEM lanes 32 (w mod 4) ...), fusing bias + GELU and writing the FP32
+// activations and/or their BF16 copy (the next layer's A operand).  Every mbarrier wait is
+// bounded; on expiry the CTA raises MRF_DERR_TIMEOUT, waits for the loads it issued and exits.
+#include <cuda.h>
+#include <string>
+
+#include "mrf_internal.cuh"
+#include "ptx.cuh"
+#include "tma_host.h"
+
+namespace {
+
+constexpr int TM = 128;                  // rows per tile
+constexpr int TK = 64;                   // BF16 elements per 128-byte stage row
+constexpr int TSTAGES = 4;
+constexpr int TBN_MAX = 256;
+constexpr int T_A_BYTES = TM * 128;      // 16 KB
+constexpr int T_B_BYTES = TBN_MAX * 128; // 32 KB (a BN-row tile uses BN x 128 bytes of it)
+constexpr int T_STAGE = T_A_BYTES + T_B_BYTES;
+constexpr int T_THREADS = 192;
+constexpr int T_TMEM_COLS = 256;
+
+struct DenseShared {
+    uint64_t full[TSTAGES];
+    uint64_t empty[TSTAGES];
+    uint64_t done;
+    uint32_t tmem_base;
+};
+
+constexpr size_t kDenseSmem = TSTAGES * T_STAGE + sizeof(DenseShared) + 1024;
+
+__device__ __forceinline__ float gelu(float v) {
+    return 0.5f * v * (1.f + erff(v * 0.70710678118654752f));
+}
+
+__global__ void __launch_bounds__(T_THREADS, 1)
+k_tc_dense_gelu(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+                int M, int N, int Kp, int BN, uint32_t idesc, const float* __restrict__ bias,
+                float* __restrict__ out, __nv_bfloat16* __restrict__ outb, uint32_t* err) {
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    unsigned char* base = reinterpret_cast<unsigned char*>(
+        (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
+    DenseShared* sh = reinterpret_cast<DenseShared*>(base + TSTAGES * T_STAGE);
+    const int warp = threadIdx.x >> 5;
+    const int lane = threadIdx.x & 31;
+    const int m0 = blockIdx.y * TM;
+    const int n0 = blockIdx.x * BN;
+    const int nk = (Kp + TK - 1) / TK;
+    const uint32_t b_bytes = static_cast<uint32_t>(BN) * 128u;
+
+    if (threadIdx.x == 0) {
+        for (int i = 0; i < TSTAGES; ++i) {
+            mrfk::mbar_init(&sh->full[i], 1);
+            mrfk::mbar_init(&sh->empty[i], 1);
+        }
+        mrfk::mbar_init(&sh->done, 1);
+        mrfk::fence_mbar_init();
+    }
+    if (warp == 1) {
+        mrfk::tmem_alloc(&sh->tmem_base, T_TMEM_COLS);
+        mrfk::tmem_relinquish();
+    }
+    if (warp == 0 && lane == 0) {
+        mrfk::tma_prefetch_desc(&tmA);
+        mrfk::tma_prefetch_desc(&tmB);
+    }
+    mrfk::tc_fence_before();
+    __syncthreads();
+    mrfk::tc_fence_after();
+    const uint32_t tmem = sh->tmem_base;
+
+    if (warp == 0) {
+        // ------------------------------------------------------------ TMA producer
+        if (lane == 0) {
+            int stage = 0;
+            uint32_t phase = 0;
+            bool used[TSTAGES] = {};
+            uint32_t last[TSTAGES] = {};
+            bool ok = true;
+            for (int kc = 0; kc < nk; ++kc) {
+                if (!mrfk::mbar_wait(&sh->empty[stage], phase ^ 1u)) {
+                    atomicOr(err, MRF_DERR_TIMEOUT);
+                    ok = false;
+                    break;
+                }
+                unsigned char* sa = base + stage * T_STAGE;
+                mrfk::mbar_arrive_expect_tx(&sh->full[stage], T_A_BYTES + b_bytes);
+                mrfk::tma_load_2d(sa, &tmA, &sh->full[stage], kc * TK, m0);
+                mrfk::tma_load_2d(sa + T_A_BYTES, &tmB, &sh->full[stage], kc * TK, n0);
+                used[stage] = true;
+                last[stage] = phase;
+                if (++stage == TSTAGES) { stage = 0; phase ^= 1u; }
+            }
+            // the CTA may not leave before every load it issued has landed
+            if (!ok)
+                for (int i = 0; i < TSTAGES; ++i)
+                    if (used[i]) mrfk::mbar_wait(&sh->full[i], last[i]);
+        }
+    } else if (warp == 1) {
+        // ------------------------------------------------------------ MMA issuer
+        if (lane == 0) {
+            int stage = 0;
+            uint32_t phase = 0;
+            for (int kc = 0; kc < nk; ++kc) {
+                if (!mrfk::mbar_wait(&sh->full[stage], phase)) {
+                    atomicOr(err, MRF_DERR_TIMEOUT);
+                    break;
+                }
+                mrfk::tc_fence_after();
+                const uint32_t sa = mrfk::smem_u32(base + stage * T_STAGE);
+                const uint32_t sb = sa + T_A_BYTES;
+#pragma unroll
+                for (int k = 0; k < TK / 16; ++k)
+                    mrfk::mma_bf16(tmem, mrfk::sdesc_k_sw128(sa + k * 32),
+                                   mrfk::sdesc_k_sw128(sb + k * 32), idesc,
+                                   (kc > 0 || k > 0) ? 1u : 0u);
+                mrfk::mma_commit(&sh->empty[stage]);
+                if (++stage == TSTAGES) { stage = 0; phase ^= 1u; }
+            }
+            mrfk::mma_commit(&sh->done);      // every MMA issued above has completed
+        }
+    } else {
+        // ------------------------------------------------------------ epilogue (4 warps)
+        const int quarter = warp & 3;
+        const int row = quarter * 32 + lane;
+        const int m = m0 + row;
+        const bool ok = mrfk::mbar_wait(&sh->done, 0);
+        if (!ok && lane == 0) atomicOr(err, MRF_DERR_TIMEOUT);
+        mrfk::tc_fence_after();
+        const uint32_t tb = tmem + (static_cast<uint32_t>(quarter * 32) << 16);
+        for (int c = 0; c * 32 < BN; ++c) {
+            uint32_t r[32];
+            __syncwarp();
+            mrfk::tmem_ld32(tb + c * 32, r);
+            mrfk::tmem_ld_wait();
+            if (!ok || m >= M) continue;
+            const int nb = n0 + c * 32;
+            const int cnt = BN - c * 32 < 32 ? BN - c * 32 : 32;
+            float g[32];
+#pragma unroll
+            for (int i = 0; i < 32; ++i)
+                g[i] = i < cnt ? gelu(__uint_as_float(r[i]) + bias[nb + i]) : 0.f;
+            const int64_t o = static_cast<int64_t>(m) * N + nb;
+            if (cnt == 32) {           // 16-byte stores (N and nb are multiples of 16)
+                if (out) {
+                    float4* d = reinterpret_cast<float4*>(out + o);
+#pragma unroll
+                    for (int i = 0; i < 8; ++i)
+                        d[i] = make_float4(g[4 * i], g[4 * i + 1], g[4 * i + 2], g[4 * i + 3]);
+                }
+                if (outb) {
+                    uint4* d = reinterpret_cast<uint4*>(outb + o);
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) {
+                        __nv_bfloat162 h[4];
+#pragma unroll
+                        for (int q = 0; q < 4; ++q)
+                            h[q] = __floats2bfloat162_rn(g[8 * i + 2 * q], g[8 * i + 2 * q + 1]);
+                        d[i] = *reinterpret_cast<uint4*>(h);
+                    }
+                }
+            } else {
+                for (int i = 0; i < cnt; ++i) {
+                    if (out) out[o + i] = g[i];
+                    if (outb) outb[o + i] = __float2bfloat16_rn(g[i]);
+                }
+            }
+        }
+    }
+    mrfk::tc_fence_before();
+    __syncthreads();
+    mrfk::tc_fence_after();
+    if (warp == 1) mrfk::tmem_dealloc(tmem, T_TMEM_COLS);
+}
+
+}  // namespace
+
+int dense_tile_n(int N) {
+    if (N <= 0 || N % 16) return 0;
+    int bn = N < TBN_MAX ? N : TBN_MAX;
+    while (bn > 16 && N % bn) bn -= 16;
+    return bn;
+}
+
+mrf_status launch_dense_gelu(const __nv_bfloat16* A, int M, int Kp, const __nv_bfloat16* Wt,
+                             int N, const float* bias, float* out, __nv_bfloat16* outb,
+                             uint32_t* err, cudaStream_t st) {
+    if (M == 0) return MRF_OK;
+    const int BN = dense_tile_n(N);
+    if (BN == 0 || Kp <= 0 || (Kp * 2) % 16) {
+        mrf_set_error("dense layer: N must be a multiple of 16 and the row pitch of 16 bytes");
+        return MRF_EINVAL;
+    }
+    CUtensorMap ta, tb;
+    MRF_TRY(tma_map_k128(&ta, A, M, Kp, TM, false));
+    MRF_TRY(tma_map_k128(&tb, Wt, N, Kp, BN, false));
+    const uint32_t idesc = mrfk::idesc_bf16(TM, static_cast<uint32_t>(BN));
+    cudaError_t e = cudaFuncSetAttribute(k_tc_dense_gelu,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         static_cast<int>(kDenseSmem));
+    if (e == cudaSuccess) {
+        dim3 grid(static_cast<unsigned>(N / BN), static_cast<unsigned>((M + TM - 1) / TM));
+        k_tc_dense_gelu<<<grid, T_THREADS, kDenseSmem, st>>>(ta, tb, M, N, Kp, BN, idesc, bias,
+                                                             out, outb, err);
+        e = cudaGetLastError();
+    }
+    if (e != cudaSuccess) {
+        mrf_set_error(std::string("dense layer launch: ") + cudaGetErrorString(e));
+        return MRF_ECUDA;
+    }
+    return MRF_OK;
+}

@@ -72,6 +72,50 @@ def test_gradients_match_oracle(mrf, cfg1):
         assert rel < 1e-4, (k, rel)
 
 
+@pytest.mark.parametrize("L,H,B", [(100, 512, 300), (37, 48, 16389), (100, 320, 129)])
+def test_bf16_inference_matches_emulation(mrf, cfg1, L, H, B):
+    """The learned projection's inference: BF16 weights and activations on the tensor cores
+    with FP32 accumulation, bias + GELU fused into the layer epilogues.  Against a float64
+    evaluation of the same network on the BF16-rounded weights, inputs and first-layer
+    activations; odd input widths (2L = 74, padded rows), hidden widths whose column tiles are not
+    multiples of 32 (48, 320 = 2 x 160), ragged row tiles and more rows than one chunk."""
+    dic = cfg1[0]
+    A = np.ascontiguousarray(dic["atoms"][:, :L])
+    D = mrf.build_dict_index(A, dic["params"], grid_shape=dic["grid_shape"])
+    M = mrf.MLP(D, dic["axes"], dic["cell_atom"], hidden=H)
+    I = 2 * L
+    g = np.random.Generator(np.random.PCG64(L + H))
+    p = omlp.init(I, n_hidden=H, n_out=3, seed=5)
+    for k in ("b1", "b2", "b3"):
+        p[k] = g.normal(0, 0.2, p[k].shape)
+    M.params(flat(p))
+    X = (g.normal(size=(B, I)) / np.sqrt(I) * 4).astype(np.float32)
+    Y = torch.empty((B, 3), dtype=torch.float32, device="cuda")
+    M.infer(to_dev(X), Y)
+    Yg = Y.cpu().numpy()
+
+    def bf(a):
+        return torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32)).to(
+            torch.bfloat16).to(torch.float64).numpy()
+
+    def gelu(v):
+        from scipy.special import erf
+        return 0.5 * v * (1 + erf(v / np.sqrt(2)))
+
+    f32 = {k: v.astype(np.float32).astype(np.float64) for k, v in p.items()}
+    a1 = gelu(bf(X) @ bf(p["W1"]) + f32["b1"])
+    a2 = gelu(bf(a1) @ bf(p["W2"]) + f32["b2"])
+    ref = a2 @ f32["W3"] + f32["b3"]
+    scale = np.abs(ref).max()
+    err = np.abs(Yg - ref).max() / scale
+    # the FP32 training path on the same weights differs by the BF16 rounding itself
+    Yf, _, _ = M.grad(to_dev(X[:256]), None)
+    errf = np.abs(Yg[:256] - Yf).max() / np.abs(Yf).max()
+    print(f"L={L} H={H} B={B}: BF16 inference vs emulation {err:.2e}, vs FP32 forward {errf:.2e}")
+    assert err < 2e-3
+    assert errf < 5e-2
+
+
 def test_v1_and_canonical_inputs(mrf, cfg1):
     dic, p, Z = cfg1
     D = dictionary(mrf, dic)
