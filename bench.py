@@ -444,9 +444,9 @@ def run_slices(args) -> None:
     """The batching form on the 64-slice workload: every slice's 20 BLIP iterations through
     mrf_batch.  Two schedules, all slices submitted at t = 0: one batch of all slices (one
     projection launch per iteration covers every slice; latency = the makespan), and groups of
-    `--group` slices, shortest first (per-slice latency = its group's completion).  Forms: BF16
-    and FP8 replayed as CUDA graphs, and the learned proposal with fallback (eager; its
-    fallback sizes the exhaustive search on the host).  Inputs: one seeded slice per matrix size
+    `--group` slices, shortest first (per-slice latency = its group's completion).  Forms: BF16,
+    FP8 and the learned proposal with exhaustive fallback, each iteration replayed as a CUDA
+    graph (the fallback reads its voxel count on the device).  Inputs: one seeded slice per matrix size
     is generated (k-space, masks), and the 64 slices of the seeded draw use the generated slice
     of their size.  Under torchrun the slices are dealt to ranks round-robin."""
     import torch
@@ -481,7 +481,7 @@ def run_slices(args) -> None:
     iters = args.iters
     forms = [("bf16", True), ("fp8", True)]
     if not args.no_forms:
-        forms.append(("learned", False))
+        forms.append(("learned", True))
 
     def sync():
         torch.cuda.synchronize()
@@ -491,7 +491,7 @@ def run_slices(args) -> None:
     out = {}
     mlp_s = None
     tuned = None
-    if args.autotune:
+    if not args.no_autotune:
         # search geometry from the autotuner, timed on the largest slice's A^H Y
         from paper_1810_01967_gb300 import autotune
         Nb = max(first)
@@ -967,7 +967,11 @@ def main():
     ap.add_argument("--mode", default="bf16", choices=["bf16", "fp8", "fp32", "covertree"],
                     help="projection of the timed step (covertree: --profile-case only)")
     ap.add_argument("--autotune", action="store_true",
-                    help="time the search geometries on the workload first and use the fastest")
+                    help="time the search geometries on the workload first and use the fastest "
+                         "(always on for the slices64 workload, whose batching form picks its "
+                         "geometry with the autotuner)")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="slices64: keep the library's default search geometry")
     ap.add_argument("--fp32-sample", type=int, default=0)
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--workload", default="slice", choices=["slice", "slices64", "tree1m"],

@@ -371,8 +371,10 @@ mrf_status mrf_dict_attach_mlp(mrf_dict* dict, mrf_mlp* mlp);
  * iterations).  The slices share the dictionary; all of them stay resident, stacked voxel-major,
  * and each iteration is every slice's gradient step followed by one projection of all stacked
  * voxels (one persistent launch of the search).  With use_graph the iteration is captured once
- * into a CUDA graph and replayed (projections without host synchronisation only: FP32 or BF16,
- * with certify = 0).  The masks of `ops` are read at every iteration and must stay alive.
+ * into a CUDA graph and replayed (projections without host synchronisation only, certify = 0:
+ * FP32, BF16, FP8, and -- when the dictionary has the BF16 operand -- the cover-tree and learned
+ * forms, whose exhaustive fallback then reads its voxel count on the device).  The masks of
+ * `ops` are read at every iteration and must stay alive.
  */
 typedef struct mrf_batch mrf_batch;
 

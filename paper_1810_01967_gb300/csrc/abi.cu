@@ -270,6 +270,22 @@ mrf_status check_proj_public(const mrf_dict* D, const mrf_proj_opts* o) {
 mrf_status exhaustive_on_list(mrf_dict* D, const float2* Z, int32_t cnt, const mrf_proj_opts* o,
                               int32_t* idx_out, float2* rho_out, float2* X_out, cudaStream_t st) {
     ProfScope ps5(5, 0, st);
+    if (D->bop && D->sync_free && !o->certify) {
+        // the list's length stays on the device: cnt is its capacity, the kernels read the
+        // count and skip what lies past it
+        const int K = 16;
+        MRF_TRY(launch_pack_gather(Z, D->vlist, cnt, D->L, D->Kp, D->zq, st, D->nlist));
+        const int S = bf16_choose_splits(D, cnt);
+        MRF_TRY(ensure_part(D, cnt, S, K));
+        float* qs = static_cast<float*>(D->part);
+        int32_t* qi = reinterpret_cast<int32_t*>(qs + static_cast<size_t>(S) * cnt * K);
+        MRF_TRY(launch_bf16_topk(D->zq, cnt, D, o->cone, K, S, qs, qi, st, D->nlist));
+        float bound;
+        bf16_margin(D, &kRigorous, &bound);
+        return launch_merge(Z, cnt, D, o->cone, K, S, qs, qi, D->vlist, D->nlist, o->tie_tol, 0,
+                            0.f, idx_out, rho_out, X_out, nullptr, nullptr, D->err, D->counters,
+                            st, 2.f * bound + o->tie_tol);
+    }
     if (D->bop) {
         const int K = 16;
         MRF_TRY(launch_pack_gather(Z, D->vlist, cnt, D->L, D->Kp, D->zq, st));
@@ -403,6 +419,8 @@ mrf_status project_impl(mrf_dict* D, const float2* Z, int64_t n, const mrf_proj_
                                  0.f, idx_out, rho_out, X_out, nullptr, nullptr, D->err,
                                  D->counters, st));
         }
+        if (D->sync_free && D->bop && !o->certify)
+            return exhaustive_on_list(D, Z, static_cast<int32_t>(n), o, idx_out, rho_out, X_out, st);
         int32_t cnt = 0;
         MRF_CUDA_TRY(cudaMemcpyAsync(&cnt, D->nlist, sizeof(cnt), cudaMemcpyDeviceToHost, st));
         MRF_CUDA_TRY(cudaStreamSynchronize(st));
@@ -426,6 +444,8 @@ mrf_status project_impl(mrf_dict* D, const float2* Z, int64_t n, const mrf_proj_
             MRF_TRY(learned_flag(D, Z, n, idx_out, o->fallback_thr, o->learned_edge != 0,
                                  o->cone, D->vlist, D->nlist, st));
         }
+        if (D->sync_free && D->bop && !o->certify)
+            return exhaustive_on_list(D, Z, static_cast<int32_t>(n), o, idx_out, rho_out, X_out, st);
         int32_t cnt = 0;
         MRF_CUDA_TRY(cudaMemcpyAsync(&cnt, D->nlist, sizeof(cnt), cudaMemcpyDeviceToHost, st));
         MRF_CUDA_TRY(cudaStreamSynchronize(st));

@@ -7,8 +7,10 @@
 // launch of the search kernel against the shared dictionary, however uneven the slices.  With
 // `use_graph` the iteration is captured once into a CUDA graph on an internal stream and
 // replayed; the first iteration runs eagerly so that cuFFT plans and scratch are created
-// outside the capture.  Only projections without host synchronisation can be captured (FP32,
-// BF16 or FP8, without certification).
+// outside the capture.  Only projections without host synchronisation can be captured: FP32,
+// BF16 or FP8 without certification, and -- with the dictionary's BF16 operand -- the cover-tree
+// and learned forms, whose exhaustive fallback then takes its voxel count from the device
+// (mrf_dict::sync_free) instead of reading it back.
 #include <cstring>
 #include <vector>
 
@@ -38,10 +40,20 @@ mrf_status bfail(mrf_status s, const std::string& m) {
     return s;
 }
 
-bool capturable(const mrf_proj_opts& o) {
-    return !o.certify && (o.mode == MRF_PROJ_FP32_EXACT || o.mode == MRF_PROJ_BF16 ||
-                           o.mode == MRF_PROJ_FP8);
+bool capturable(const mrf_dict* D, const mrf_proj_opts& o) {
+    if (o.certify) return false;
+    if (o.mode == MRF_PROJ_FP32_EXACT || o.mode == MRF_PROJ_BF16 || o.mode == MRF_PROJ_FP8)
+        return true;
+    return (o.mode == MRF_PROJ_COVERTREE || o.mode == MRF_PROJ_LEARNED) && D->bop != nullptr;
 }
+
+// Sets the dictionary's sync-free mode for the lifetime of a graph run.
+struct SyncFree {
+    mrf_dict* D;
+    bool prev;
+    SyncFree(mrf_dict* d, bool on) : D(d), prev(d->sync_free) { if (on) D->sync_free = true; }
+    ~SyncFree() { D->sync_free = prev; }
+};
 
 mrf_status iterate(mrf_batch* B, float mu, const mrf_proj_opts* o, cudaStream_t st) {
     mrf_dict* D = B->D;
@@ -135,10 +147,12 @@ mrf_status mrf_batch_run(mrf_batch* B, int32_t iters, float mu, const mrf_proj_o
     mrf_proj_opts o;
     if (opts) o = *opts; else mrf_default_proj_opts(&o);
     MRF_TRY(check_proj_public(B->D, &o));
-    if (use_graph && !capturable(o))
+    if (use_graph && !capturable(B->D, o))
         return bfail(MRF_EUNSUPPORTED, "graph replay needs a projection without host "
-                                       "synchronisation (FP32, BF16 or FP8 with certify = 0)");
+                                       "synchronisation (certify = 0; the cover-tree and learned "
+                                       "forms also need the BF16 operand)");
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    SyncFree guard(B->D, use_graph != 0);
     for (int32_t it = 0; it < iters; ++it) {
         if (!use_graph || it == 0) {
             MRF_TRY(iterate(B, mu, &o, st));

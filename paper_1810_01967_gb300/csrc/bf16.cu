@@ -138,7 +138,7 @@ template <int KT, int C, bool F8>
 __global__ void __launch_bounds__(NTHREADS, 1)
 k_tc_topk(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
           int64_t n, int64_t d, int64_t nblk, int Kp, int cone, Sched sc, int blocks_per_split,
-          float gsc, const float* __restrict__ qs,
+          float gsc, const float* __restrict__ qs, const int32_t* __restrict__ count,
           float* __restrict__ part_s, int32_t* __restrict__ part_i, uint32_t* err) {
     constexpr int EK = F8 ? 128 : 64;     // elements per stage row
     constexpr int KPER = F8 ? 32 : 16;    // elements per MMA instruction (32 bytes either way)
@@ -153,6 +153,8 @@ k_tc_topk(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
     const int64_t cluster = blockIdx.x / C;
     const int64_t nclusters = gridDim.x / C;
     const int64_t units = sc.NG * sc.S;
+    // with a device-side voxel count (lists built on the device) the tiles past it are skipped
+    const int64_t nact = count ? min(static_cast<int64_t>(*count), n) : n;
     const int nk = (Kp + EK - 1) / EK;
     constexpr uint16_t kMask = static_cast<uint16_t>((1u << C) - 1u);
     constexpr int SLICE_ROWS = BN / C;
@@ -200,6 +202,7 @@ k_tc_topk(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
             for (int64_t uc = cluster; uc < units && !sh->abort; uc += nclusters) {
                 int64_t s, g;
                 sc.map(uc, s, g);
+                if (g * C * BM >= nact) continue;     // the cluster's tiles are all past the count
                 const int64_t m = g * C + rank;
                 const int64_t b0 = s * blocks_per_split;
                 const int64_t b1 = min(b0 + blocks_per_split, nblk);
@@ -243,6 +246,7 @@ k_tc_topk(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
             for (int64_t uc = cluster; uc < units && !sh->abort; uc += nclusters) {
                 int64_t s, g;
                 sc.map(uc, s, g);
+                if (g * C * BM >= nact) continue;     // the cluster's tiles are all past the count
                 const int64_t b0 = s * blocks_per_split;
                 const int64_t b1 = min(b0 + blocks_per_split, nblk);
                 for (int64_t b = b0; b < b1 && !sh->abort; ++b) {
@@ -296,6 +300,7 @@ k_tc_topk(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
         for (int64_t uc = cluster; uc < units && !sh->abort; uc += nclusters) {
             int64_t s, g;
             sc.map(uc, s, g);
+            if (g * C * BM >= nact) continue;     // the cluster's tiles are all past the count
             const int64_t m = g * C + rank;
             const int64_t b0 = s * blocks_per_split;
             const int64_t b1 = min(b0 + blocks_per_split, nblk);
@@ -365,7 +370,8 @@ __global__ void __launch_bounds__(NTHREADS, 1)
 k_tc_topk_pair(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                int64_t n, int64_t d, int64_t nblk, int Kp, int cone, Sched sc,
                int blocks_per_split, float gsc, const float* __restrict__ qs,
-               float* __restrict__ part_s, int32_t* __restrict__ part_i, uint32_t* err) {
+               const int32_t* __restrict__ count, float* __restrict__ part_s,
+               int32_t* __restrict__ part_i, uint32_t* err) {
     constexpr int EK = F8 ? 128 : 64;
     constexpr int KPER = F8 ? 32 : 16;
     extern __shared__ __align__(1024) unsigned char smem_raw[];
@@ -379,6 +385,7 @@ k_tc_topk_pair(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
     const int64_t cluster = blockIdx.x / 2;
     const int64_t nclusters = gridDim.x / 2;
     const int64_t units = sc.NG * sc.S;
+    const int64_t nact = count ? min(static_cast<int64_t>(*count), n) : n;
     const int nk = (Kp + EK - 1) / EK;
 
     if (threadIdx.x == 0) {
@@ -424,6 +431,7 @@ k_tc_topk_pair(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
             for (int64_t uc = cluster; uc < units && !sh->abort; uc += nclusters) {
                 int64_t s, g;
                 sc.map(uc, s, g);
+                if (g * 2 * BM >= nact) continue;     // the cluster's tiles are all past the count
                 const int64_t m = g * 2 + rank;
                 const int64_t b0 = s * blocks_per_split;
                 const int64_t b1 = min(b0 + blocks_per_split, nblk);
@@ -461,6 +469,7 @@ k_tc_topk_pair(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
             for (int64_t uc = cluster; uc < units && !sh->abort; uc += nclusters) {
                 int64_t s, g;
                 sc.map(uc, s, g);
+                if (g * 2 * BM >= nact) continue;     // the cluster's tiles are all past the count
                 const int64_t b0 = s * blocks_per_split;
                 const int64_t b1 = min(b0 + blocks_per_split, nblk);
                 for (int64_t b = b0; b < b1 && !sh->abort; ++b) {
@@ -509,6 +518,7 @@ k_tc_topk_pair(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
         for (int64_t uc = cluster; uc < units && !sh->abort; uc += nclusters) {
             int64_t s, g;
             sc.map(uc, s, g);
+            if (g * 2 * BM >= nact) continue;     // the cluster's tiles are all past the count
             const int64_t m = g * 2 + rank;
             const int64_t b0 = s * blocks_per_split;
             const int64_t b1 = min(b0 + blocks_per_split, nblk);
@@ -606,7 +616,7 @@ namespace {
 template <int KT, int C, bool F8>
 mrf_status launch_t(const CUtensorMap& ta, const CUtensorMap& tb, int64_t n, const mrf_dict* D,
                     int cone, Sched sc, int bps, int nclusters, float gsc, const float* qs,
-                    float* part_s, int32_t* part_i, cudaStream_t st) {
+                    const int32_t* count, float* part_s, int32_t* part_i, cudaStream_t st) {
     auto kern = k_tc_topk<KT, C, F8>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          static_cast<int>(kSmem));
@@ -624,7 +634,7 @@ mrf_status launch_t(const CUtensorMap& ta, const CUtensorMap& tb, int64_t n, con
         cfg.attrs = attr;
         cfg.numAttrs = 1;
         e = cudaLaunchKernelEx(&cfg, kern, ta, tb, n, D->d, D->nblk, F8 ? D->Kp8 : D->Kp, cone,
-                               sc, bps, gsc, qs, part_s, part_i, D->err);
+                               sc, bps, gsc, qs, count, part_s, part_i, D->err);
     }
     if (e != cudaSuccess) {
         mrf_set_error(std::string("tensor-core search launch: ") + cudaGetErrorString(e));
@@ -636,7 +646,7 @@ mrf_status launch_t(const CUtensorMap& ta, const CUtensorMap& tb, int64_t n, con
 template <int KT, bool F8>
 mrf_status launch_pair(const CUtensorMap& ta, const CUtensorMap& tb, int64_t n, const mrf_dict* D,
                        int cone, Sched sc, int bps, int nclusters, float gsc, const float* qs,
-                       float* part_s, int32_t* part_i, cudaStream_t st) {
+                       const int32_t* count, float* part_s, int32_t* part_i, cudaStream_t st) {
     auto kern = k_tc_topk_pair<KT, F8>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          static_cast<int>(kSmemP));
@@ -654,7 +664,7 @@ mrf_status launch_pair(const CUtensorMap& ta, const CUtensorMap& tb, int64_t n, 
         cfg.attrs = attr;
         cfg.numAttrs = 1;
         e = cudaLaunchKernelEx(&cfg, kern, ta, tb, n, D->d, D->nblk, F8 ? D->Kp8 : D->Kp, cone,
-                               sc, bps, gsc, qs, part_s, part_i, D->err);
+                               sc, bps, gsc, qs, count, part_s, part_i, D->err);
     }
     if (e != cudaSuccess) {
         mrf_set_error(std::string("tensor-core search (CTA pairs) launch: ") + cudaGetErrorString(e));
@@ -770,17 +780,19 @@ namespace {
 template <int KT, bool F8>
 mrf_status launch_c(int C, const CUtensorMap& ta, const CUtensorMap& tb, int64_t n,
                     const mrf_dict* D, int cone, Sched sc, int bps, int nc, float wts,
-                    const float* qs, float* part_s, int32_t* part_i, cudaStream_t st) {
+                    const float* qs, const int32_t* count, float* part_s, int32_t* part_i,
+                    cudaStream_t st) {
     switch (C) {
-        case 1: return launch_t<KT, 1, F8>(ta, tb, n, D, cone, sc, bps, nc, wts, qs, part_s, part_i, st);
-        case 2: return launch_t<KT, 2, F8>(ta, tb, n, D, cone, sc, bps, nc, wts, qs, part_s, part_i, st);
-        default: return launch_t<KT, 4, F8>(ta, tb, n, D, cone, sc, bps, nc, wts, qs, part_s, part_i, st);
+        case 1: return launch_t<KT, 1, F8>(ta, tb, n, D, cone, sc, bps, nc, wts, qs, count, part_s, part_i, st);
+        case 2: return launch_t<KT, 2, F8>(ta, tb, n, D, cone, sc, bps, nc, wts, qs, count, part_s, part_i, st);
+        default: return launch_t<KT, 4, F8>(ta, tb, n, D, cone, sc, bps, nc, wts, qs, count, part_s, part_i, st);
     }
 }
 
 // Shared launch path of both element types: operand maps, schedule, persistent grid.
 mrf_status launch_tc(bool f8, const void* zq, const float* qs, int64_t n, mrf_dict* D, int cone,
-                     int K, int S, float* part_s, int32_t* part_i, cudaStream_t st) {
+                     int K, int S, float* part_s, int32_t* part_i, const int32_t* count,
+                     cudaStream_t st) {
     if (n == 0) return MRF_OK;
     const void* op = f8 ? static_cast<const void*>(D->fop) : static_cast<const void*>(D->bop);
     if (!op) {
@@ -818,7 +830,7 @@ mrf_status launch_tc(bool f8, const void* zq, const float* qs, int64_t n, mrf_di
     D->tune.last_bf16_cluster = C;
     D->tune.last_bf16_splits = S;
     const float wts = f8 ? D->g8 : 1.f;
-#define MRF_TC_ARGS ta, tb, n, D, cone, sc, bps, nc, wts, qs, part_s, part_i, st
+#define MRF_TC_ARGS ta, tb, n, D, cone, sc, bps, nc, wts, qs, count, part_s, part_i, st
     if (pair) {
         if (f8)
             return K == 8 ? launch_pair<8, true>(MRF_TC_ARGS)
@@ -837,11 +849,12 @@ mrf_status launch_tc(bool f8, const void* zq, const float* qs, int64_t n, mrf_di
 }  // namespace
 
 mrf_status launch_bf16_topk(const __nv_bfloat16* zq, int64_t n, mrf_dict* D, int cone, int K,
-                            int S, float* part_s, int32_t* part_i, cudaStream_t st) {
-    return launch_tc(false, zq, nullptr, n, D, cone, K, S, part_s, part_i, st);
+                            int S, float* part_s, int32_t* part_i, cudaStream_t st,
+                            const int32_t* count) {
+    return launch_tc(false, zq, nullptr, n, D, cone, K, S, part_s, part_i, count, st);
 }
 
 mrf_status launch_fp8_topk(const uint8_t* zq8, const float* qs, int64_t n, mrf_dict* D, int cone,
                            int K, int S, float* part_s, int32_t* part_i, cudaStream_t st) {
-    return launch_tc(true, zq8, qs, n, D, cone, K, S, part_s, part_i, st);
+    return launch_tc(true, zq8, qs, n, D, cone, K, S, part_s, part_i, nullptr, st);
 }

@@ -88,7 +88,9 @@ k_merge(const float2* __restrict__ Z, int64_t n_in, const int32_t* __restrict__ 
         float2* __restrict__ X_out, int32_t* __restrict__ fb_list, int32_t* __restrict__ fb_n,
         uint32_t* err, unsigned long long* cnt) {
     const int lane = threadIdx.x & 31;
-    const int64_t n = vlist ? static_cast<int64_t>(*nlist) : n_in;
+    // with a list, *nlist voxels are present; the candidate lists keep the stride n_in (the
+    // capacity the search was launched for)
+    const int64_t n = vlist ? min(static_cast<int64_t>(*nlist), n_in) : n_in;
     const int64_t vl = static_cast<int64_t>(blockIdx.x) * WARPS + (threadIdx.x >> 5);
     if (vl >= n) return;
     const int64_t v = vlist ? static_cast<int64_t>(vlist[vl]) : vl;
@@ -105,7 +107,7 @@ k_merge(const float2* __restrict__ Z, int64_t n_in, const int32_t* __restrict__ 
     const int total = S * KT;
     for (int c = lane; c < total; c += 32) {
         const int s = c / KT, k = c - s * KT;
-        const int64_t o = (static_cast<int64_t>(s) * n + vl) * KT + k;
+        const int64_t o = (static_cast<int64_t>(s) * n_in + vl) * KT + k;
         float sc = part_s[o];
         int32_t j = part_i[o];
         if (j < 0 || j >= d || sc != sc) continue;

@@ -74,6 +74,9 @@ struct mrf_dict {
     float2* ealign = nullptr;        // [d] e^{i alpha_j}
     float2* qph = nullptr;           // [cap_n] e^{i beta_v} of the last aligned queries
     int num_sms = 148;
+    // no host synchronisation inside a projection (set while a batch iteration is captured into
+    // a graph): the cover-tree and learned fallbacks take their voxel count from the device
+    bool sync_free = false;
     mrf_tune tune = {};              // requested geometry (0 = default) and last launches
 };
 
@@ -130,7 +133,8 @@ mrf_status launch_pack_fop(mrf_dict* D, float s, cudaStream_t st);
 mrf_status launch_pack_queries_fp8(const float2* Z, const int32_t* vlist, int64_t n, int L,
                                    int Kp8, uint8_t* zq8, float* qs, cudaStream_t st);
 mrf_status launch_pack_gather(const float2* Z, const int32_t* vlist, int64_t n, int L, int Kp,
-                              __nv_bfloat16* zq, cudaStream_t st);
+                              __nv_bfloat16* zq, cudaStream_t st,
+                              const int32_t* count = nullptr);
 mrf_status launch_mask_ky(float2* W, const uint8_t* mask, int Ny, int Nx, int L,
                           cudaStream_t st);
 mrf_status launch_grad_combine(const float2* X, const float2* G, const float2* AHY, float2* Z,
@@ -150,8 +154,11 @@ mrf_status launch_fp32_topk(const float2* Z, const int32_t* vlist, const int32_t
                             float* part_s, int32_t* part_i, cudaStream_t st);
 int fp32_choose_splits(int64_t n, int64_t d, int num_sms);
 // bf16.cu
+// count (device, may be NULL): voxels actually present when the rows were listed on the device;
+// n is then the capacity the launch is sized for
 mrf_status launch_bf16_topk(const __nv_bfloat16* zq, int64_t n, mrf_dict* D, int cone, int K,
-                            int S, float* part_s, int32_t* part_i, cudaStream_t st);
+                            int S, float* part_s, int32_t* part_i, cudaStream_t st,
+                            const int32_t* count = nullptr);
 int bf16_choose_splits(const mrf_dict* D, int64_t n);
 mrf_status launch_fp8_topk(const uint8_t* zq8, const float* qs, int64_t n, mrf_dict* D, int cone,
                            int K, int S, float* part_s, int32_t* part_i, cudaStream_t st);

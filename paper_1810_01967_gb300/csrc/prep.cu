@@ -68,12 +68,16 @@ __global__ void k_pack_queries(const float2* __restrict__ Z, int64_t n, int L, i
     zq[i] = __floats2bfloat162_rn(z.x, z.y);
 }
 
+// Rows of the listed voxels; with `count` (device) only the first *count entries of the list
+// are present and n is the list's capacity.
 __global__ void k_pack_gather(const float2* __restrict__ Z, const int32_t* __restrict__ vlist,
-                              int64_t n, int L, int Kp, __nv_bfloat162* __restrict__ zq) {
+                              const int32_t* __restrict__ count, int64_t n, int L, int Kp,
+                              __nv_bfloat162* __restrict__ zq) {
     int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
     int64_t half = Kp / 2;
     if (i >= n * half) return;
     int64_t k = i / half;
+    if (count && k >= *count) return;
     int t = static_cast<int>(i - k * half);
     const int64_t v = vlist[k];
     float2 z = (t < L) ? Z[v * L + t] : make_float2(0.f, 0.f);
@@ -337,10 +341,10 @@ mrf_status launch_pack_queries(const float2* Z, int64_t n, int L, int Kp, __nv_b
 }
 
 mrf_status launch_pack_gather(const float2* Z, const int32_t* vlist, int64_t n, int L, int Kp,
-                              __nv_bfloat16* zq, cudaStream_t st) {
+                              __nv_bfloat16* zq, cudaStream_t st, const int32_t* count) {
     if (n == 0) return MRF_OK;
     k_pack_gather<<<grid_for(n * (Kp / 2)), kThreads, 0, st>>>(
-        Z, vlist, n, L, Kp, reinterpret_cast<__nv_bfloat162*>(zq));
+        Z, vlist, count, n, L, Kp, reinterpret_cast<__nv_bfloat162*>(zq));
     LAUNCH_CHECK();
     return MRF_OK;
 }

@@ -104,6 +104,42 @@ def test_batch_follows_the_oracle(mrf, setup):
         assert np.array_equal(prm[a:a + v["n"]], dic["params"][idx])
 
 
+@pytest.mark.parametrize("mode", ["covertree", "learned"])
+def test_graph_replay_with_device_side_fallback(mrf, setup, mode):
+    """The cover-tree and learned forms under graph replay: their exhaustive fallback takes the
+    listed voxel count from the device (no read-back inside the captured iteration).  Graph and
+    eager runs give the same answers up to BF16 near-ties (the fallback's atom split is sized
+    for the list's capacity instead of its length), and both follow the float64 oracle."""
+    dic, probs = setup
+    D = mrf.build_dict_index(dic["atoms"], dic["params"], grid_shape=dic["grid_shape"],
+                             pack_bf16=True, build_tree=(mode == "covertree"))
+    if mode == "learned":
+        M = mrf.MLP(D, dic["axes"], dic["cell_atom"], hidden=32)
+        mrf.attach_mlp(D, M)
+    opts = mrf.proj_opts(mode=mode, certify=False, eps=0.0)
+    iters = 3
+    res = {}
+    for g in (False, True):
+        B, ops = make_batch(mrf, D, probs)
+        B.run(iters, 1.0, opts, use_graph=g)
+        torch.cuda.synchronize()
+        res[g] = [slice_arrays(B, s) for s in range(len(probs))]
+        B.close()
+    D.check()
+    for s, p in enumerate(probs):
+        Xg, ig, _ = res[True][s]
+        Xe, ie, _ = res[False][s]
+        same = ig == ie
+        assert same.mean() >= 0.99, (s, same.mean())
+        np.testing.assert_allclose(Xg[same], Xe[same], rtol=0, atol=1e-5 * np.abs(Xe).max())
+        ref = mo.blip(p["Y"], p["masks"], dic["atoms"], p["Ny"], p["Nx"], iters=iters)
+        agree = float(np.mean(ig == ref["idx"]))
+        rel = float(np.linalg.norm(Xg - ref["X"]) / np.linalg.norm(ref["X"]))
+        print(f"{mode} slice {s}: graph vs eager {same.mean():.4f}, vs oracle {agree:.4f}, "
+              f"image rel err {rel:.2e}")
+        assert agree >= 0.98 and rel <= 2e-2, (s, agree, rel)
+
+
 def test_capture_rules_and_errors(mrf, setup):
     from paper_1810_01967_gb300 import MRFError
     dic, probs = setup
