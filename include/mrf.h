@@ -141,7 +141,12 @@ typedef struct mrf_recon_opts {
     int32_t kappa;         /* rescale the first iterate by ||Y|| / ||A X^1|| (default 0) */
     float   tol;           /* stop when the objective's relative progress < tol (0 = off) */
     int32_t max_shrink;    /* bound on step-rule shrinks per iteration (default 30) */
-    int32_t reserved[5];
+    int32_t resume;        /* 1: continue from the iterate in X_out and the warm-start atoms in
+                              idx_out (a saved checkpoint: the iterate is fully described by X,
+                              or by idx and rho) instead of X^0 = 0; the kappa rescale of the
+                              first iterate is skipped and the step rule restarts from mu
+                              (default 0) */
+    int32_t reserved[4];
     mrf_proj_opts proj;
 } mrf_recon_opts;
 
@@ -254,8 +259,9 @@ mrf_status mrf_ipg_step(mrf_dict* dict, const mrf_op* op, const void* AHY, void*
                         mrf_stats* stats, void* stream);
 
 /*
- * Whole reconstruction (Algorithm 2): A^H Y once, X^0 = 0, `iters` iterations with the
- * options' step rule and kappa rescale, then the look-up table.  Synchronises `stream`.
+ * Whole reconstruction (Algorithm 2): A^H Y once, X^0 = 0 (or the iterate in X_out with
+ * mrf_recon_opts.resume), `iters` iterations with the options' step rule and kappa rescale,
+ * then the look-up table.  Synchronises `stream`.
  *   Y          device complex64 [Ny][Nx][L]
  *   X_out      device complex64 [n][L]
  *   idx_out    device int32 [n]
@@ -498,6 +504,19 @@ mrf_status mrf_set_tune(mrf_dict* dict, const mrf_tune* in);
 #define MRF_PROFILE_STAGES 8
 mrf_status mrf_profile_enable(int32_t on);
 mrf_status mrf_profile_read(double* ms, int64_t* launches, int32_t n_stages);
+
+/*
+ * Failure injection, for tests of the error paths (no GPU fault is ever provoked).
+ * mrf_debug_fail_alloc(k): the library's device allocations (dictionary index, scratch, the
+ * reconstruction's buffers) succeed k more times, then one is refused with MRF_ENOMEM and
+ * injection turns itself off; k < 0 turns it off.  Process-wide.
+ * mrf_selftest_wait_timeout: one thread waits on an mbarrier that nothing arrives on, with the
+ * library's bounded wait cut to timeout_ns (1 ns .. 1 s); the wait gives up, the kernel raises
+ * the device error word and the call returns MRF_ETIMEOUT -- the path every persistent kernel of
+ * the library takes when a bound expires.  Synchronises `stream`.
+ */
+void mrf_debug_fail_alloc(int32_t k);
+mrf_status mrf_selftest_wait_timeout(int64_t timeout_ns, void* stream);
 
 const char* mrf_status_str(mrf_status s);
 const char* mrf_last_error(void);   /* thread-local message of the last failure */

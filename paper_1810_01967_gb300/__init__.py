@@ -65,11 +65,12 @@ def proj_opts(mode: str = "fp32", cone: str = "complex", topk: int = 0, certify:
 
 
 def recon_opts(iters: int = 10, mu: float = 1.0, adaptive: bool = False, zeta: float = 2.0,
-               kappa: bool = False, tol: float = 0.0, max_shrink: int = 30, **proj) -> ReconOpts:
+               kappa: bool = False, tol: float = 0.0, max_shrink: int = 30,
+               resume: bool = False, **proj) -> ReconOpts:
     r = ReconOpts()
     lib().mrf_default_recon_opts(C.byref(r))
     r.iters, r.mu, r.adaptive, r.zeta = iters, mu, int(adaptive), zeta
-    r.kappa, r.tol, r.max_shrink = int(kappa), tol, max_shrink
+    r.kappa, r.tol, r.max_shrink, r.resume = int(kappa), tol, max_shrink, int(resume)
     r.proj = proj_opts(**proj)
     return r
 
@@ -456,3 +457,14 @@ def profile_read() -> dict:
     ln = (C.c_int64 * n)()
     _check(lib().mrf_profile_read(ms, ln, n))
     return {name: (ms[i], ln[i]) for i, name in enumerate(PROFILE_STAGES)}
+
+
+def debug_fail_alloc(k: int) -> None:
+    """Fault injection: the library's device allocations succeed k more times, then one fails
+    with MRF_ENOMEM (k < 0: off)."""
+    lib().mrf_debug_fail_alloc(k)
+
+
+def selftest_wait_timeout(timeout_ns: int = 1_000_000, stream=None) -> None:
+    """Runs the bounded-wait self-test; raises MRFError (status MRF_ETIMEOUT) as it should."""
+    _check(lib().mrf_selftest_wait_timeout(timeout_ns, _stream(stream)))

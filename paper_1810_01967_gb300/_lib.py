@@ -57,7 +57,8 @@ class Op(C.Structure):
 class ReconOpts(C.Structure):
     _fields_ = [("iters", C.c_int32), ("mu", C.c_float), ("adaptive", C.c_int32),
                 ("zeta", C.c_float), ("kappa", C.c_int32), ("tol", C.c_float),
-                ("max_shrink", C.c_int32), ("reserved", C.c_int32 * 5), ("proj", ProjOpts)]
+                ("max_shrink", C.c_int32), ("resume", C.c_int32), ("reserved", C.c_int32 * 4),
+                ("proj", ProjOpts)]
 
 
 class Tune(C.Structure):
@@ -157,6 +158,8 @@ SIGNATURES = {
     "mrf_svd_reconstruct": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32, C.c_float,
                                       C.POINTER(ProjOpts), C.c_void_p, C.c_void_p, C.c_void_p,
                                       C.c_void_p, C.c_void_p, C.c_void_p]),
+    "mrf_debug_fail_alloc": (None, [C.c_int32]),
+    "mrf_selftest_wait_timeout": (C.c_int, [C.c_int64, C.c_void_p]),
     "mrf_status_str": (C.c_char_p, [C.c_int]),
     "mrf_last_error": (C.c_char_p, []),
 }

@@ -2,10 +2,12 @@
 // management, cuFFT plans of the sampling operator and the BLIP / CoverBLIP driver loop
 // (§3.2 eq. blip, Algorithm 2 with the step rule eq. steprule and the kappa rescale).
 #include <cufft.h>
+#include <nvtx3/nvToolsExt.h>
 #include <cmath>
 #include <cstring>
 #include <map>
 #include <mutex>
+#include <atomic>
 #include <tuple>
 
 #include "mrf_internal.cuh"
@@ -23,10 +25,17 @@ mrf_status fail(mrf_status s, const std::string& msg) {
     return s;
 }
 
+// Fault injection (mrf_debug_fail_alloc): the number of allocations still to succeed before one
+// is refused, or -1.
+std::atomic<int64_t> g_fail_alloc_after{-1};
+
 template <typename T>
 mrf_status dalloc(T** p, size_t count) {
     if (*p) { cudaFree(*p); *p = nullptr; }
     if (count == 0) return MRF_OK;
+    int64_t left = g_fail_alloc_after.load();
+    while (left >= 0 && !g_fail_alloc_after.compare_exchange_weak(left, left - 1)) {}
+    if (left == 0) return fail(MRF_ENOMEM, "injected allocation failure (mrf_debug_fail_alloc)");
     cudaError_t e = cudaMalloc(reinterpret_cast<void**>(p), count * sizeof(T));
     if (e != cudaSuccess) {
         *p = nullptr;
@@ -101,6 +110,8 @@ int topk_slots(const mrf_proj_opts* o) {
 mrf_status ensure_scratch(mrf_dict* D, int64_t n) {
     if (n <= D->cap_n) return MRF_OK;
     const int64_t L = D->L;
+    // a growth that fails part way leaves no scratch (the next call reallocates all of it)
+    D->cap_n = 0;
     MRF_TRY(dalloc(&D->zbuf, static_cast<size_t>(n * L)));
     MRF_TRY(dalloc(&D->wbuf, static_cast<size_t>(n * L)));
     MRF_TRY(dalloc(&D->vlist, static_cast<size_t>(n)));
@@ -200,7 +211,14 @@ void prof_clear() {
 
 }  // namespace
 
+// Stage names of the NVTX ranges (tools such as ncu and Nsight Systems show them; without a tool
+// attached the calls return at once).
+const char* const kStageName[MRF_PROFILE_STAGES] = {
+    "mrf:gradient", "mrf:pack_queries", "mrf:search_tc", "mrf:search_fp32",
+    "mrf:merge", "mrf:fallback", "mrf:lut", "mrf:search_proposal"};
+
 ProfScope::ProfScope(int stage, int launches, cudaStream_t s) : on(g_prof_on), st(s) {
+    nvtxRangePushA(stage >= 0 && stage < MRF_PROFILE_STAGES ? kStageName[stage] : "mrf:stage");
     if (!on) return;
     stage_ = stage;
     launches_ = launches;
@@ -210,6 +228,7 @@ ProfScope::ProfScope(int stage, int launches, cudaStream_t s) : on(g_prof_on), s
 }
 
 ProfScope::~ProfScope() {
+    nvtxRangePop();
     if (!on) return;
     cudaEventRecord(b_, st);
     g_prof_pending.push_back(ProfEntry{stage_, launches_, a_, b_});
@@ -876,7 +895,8 @@ mrf_status mrf_reconstruct(mrf_dict* D, const mrf_op* op, const void* Y,
     if (!Y || !X_out || !idx_out) return fail(MRF_EINVAL, "Y, X_out and idx_out are required");
     mrf_recon_opts r;
     if (ropts) r = *ropts; else mrf_default_recon_opts(&r);
-    if (r.iters < 0 || !(r.mu > 0.f) || (r.adaptive && !(r.zeta > 1.f)) || r.max_shrink < 0)
+    if (r.iters < 0 || !(r.mu > 0.f) || (r.adaptive && !(r.zeta > 1.f)) || r.max_shrink < 0 ||
+        r.resume < 0 || r.resume > 1)
         return fail(MRF_EINVAL, "bad reconstruction options");
     MRF_TRY(check_proj_opts(D, &r.proj));
     if (params_out && D->P == 0) return fail(MRF_EINVAL, "dictionary has no parameter table");
@@ -902,8 +922,10 @@ mrf_status mrf_reconstruct(mrf_dict* D, const mrf_op* op, const void* Y,
     auto body = [&]() -> mrf_status {
         MRF_CUDA_TRY(cudaMemsetAsync(D->counters, 0, sizeof(unsigned long long) * CNT_N, st));
         MRF_TRY(mrf_adjoint(op, Y, AHY, stream));
-        MRF_CUDA_TRY(cudaMemsetAsync(X, 0, sizeof(float2) * cnt, st));
-        MRF_CUDA_TRY(cudaMemsetAsync(idx_out, 0, sizeof(int32_t) * n, st));
+        if (!r.resume) {
+            MRF_CUDA_TRY(cudaMemsetAsync(X, 0, sizeof(float2) * cnt, st));
+            MRF_CUDA_TRY(cudaMemsetAsync(idx_out, 0, sizeof(int32_t) * n, st));
+        }
         double ynorm2 = -1.0, prev_obj = -1.0;
         float mu0 = r.mu;
         for (int k = 0; k < r.iters; ++k) {
@@ -930,7 +952,7 @@ mrf_status mrf_reconstruct(mrf_dict* D, const mrf_op* op, const void* Y,
                     break;
                 mu_k /= r.zeta;
             }
-            if (r.kappa && k == 0) {
+            if (r.kappa && k == 0 && !r.resume) {
                 if (ynorm2 < 0.0) {
                     MRF_CUDA_TRY(cudaMemsetAsync(D->red + 2, 0, sizeof(double), st));
                     MRF_TRY(launch_sqnorm(static_cast<const float2*>(Y), cnt, D->red + 2, st));
@@ -972,5 +994,7 @@ mrf_status mrf_reconstruct(mrf_dict* D, const mrf_op* op, const void* Y,
     if (s != MRF_OK) return s;
     return s2;
 }
+
+void mrf_debug_fail_alloc(int32_t k) { g_fail_alloc_after.store(k < 0 ? -1 : k); }
 
 }  // extern "C"

@@ -58,6 +58,7 @@ struct SyncFree {
 mrf_status iterate(mrf_batch* B, float mu, const mrf_proj_opts* o, cudaStream_t st) {
     mrf_dict* D = B->D;
     const int L = D->L;
+    MRF_TRY(dict_ensure_scratch(D, B->n_total));     // a no-op unless another call shrank it
     const bool zq = (o->mode == MRF_PROJ_BF16);
     for (size_t s = 0; s < B->ops.size(); ++s) {
         const int64_t a = B->off[s];

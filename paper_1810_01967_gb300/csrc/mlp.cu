@@ -639,6 +639,7 @@ mrf_status alloc(T** p, size_t count) {
 
 mrf_status ensure_batch(mrf_mlp* M, int64_t B) {
     if (B <= M->cap_b) return MRF_OK;
+    M->cap_b = 0;        // a growth that fails part way leaves no workspace
     MRF_TRY(alloc(&M->F, B * M->L));
     MRF_TRY(alloc(&M->X, B * M->I));
     MRF_TRY(alloc(&M->H1, B * M->H));
@@ -1085,6 +1086,7 @@ mrf_status learned_candidates(mrf_dict* D, const float2* Z, int64_t n, int cone,
     G.near_atom = M->near_atom;
     G.radius = M->radius;
     if (n > M->edge_cap) {
+        M->edge_cap = 0;
         MRF_TRY(alloc(&M->edge, static_cast<size_t>(n)));
         M->edge_cap = n;
     }
