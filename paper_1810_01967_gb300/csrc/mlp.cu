@@ -15,10 +15,12 @@
 //     dominant right singular vector (power iteration, phase fixed so its largest entry is real
 //     positive).
 // Inference (MRF_PROJ_LEARNED) runs the forward pass on the queries with BF16 weights and
-// activations and FP32 accumulation (the two 512-wide layers as cuBLAS GEMMs), maps the
-// prediction to the nearest grid cell and rescores the valid atoms of the (2r+1)^k
-// neighbourhood in FP32; the merge kernel then rescores its best 8 exactly (extended-precision
-// near-ties) and forms the density.
+// activations and FP32 accumulation (the two 512-wide layers on the tensor cores with bias and
+// GELU fused into the epilogue, tcgemm.cu), maps the prediction to the nearest grid cell and
+// rescores the valid atoms of the (2r+1)^k neighbourhood in FP32; the merge kernel then rescores
+// its best 8 exactly (extended-precision near-ties) and forms the density.  A voxel falls back
+// to the exhaustive search when that best correlation is below the threshold or, with the edge
+// rule, when the window's best atom lies on its edge.
 
 #include <cmath>
 #include <cstring>
