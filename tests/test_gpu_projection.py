@@ -154,6 +154,38 @@ def test_fp8_search_matches_e4m3_emulation(mrf, cfg1, cone, K):
     assert np.max(np.abs(r - rr) / np.maximum(np.abs(rr), 1e-30)) <= 1e-4
 
 
+@pytest.mark.parametrize("mode,K", [("bf16", 16), ("fp8", 32)])
+@pytest.mark.parametrize("S", [1, 3, 8, 32, 64])
+def test_atom_splits_and_merge_lane_lists(mrf, cfg1, mode, K, S):
+    """The search split into S atom ranges (more splits than the 16 atom blocks leave empty
+    ranges) and the merge's lane lists sized for S x K candidates per voxel (4 up to 32 per
+    lane): the same projection for every split."""
+    dic, p, Z = cfg1
+    A = dic["atoms"]
+    D = mrf.build_dict_index(A, pack_fp8=(mode == "fp8"))
+    D.set_tune(bf16_splits=S)
+    Zs = Z[:777]
+    L = A.shape[1]
+    # uncertified: the exact best of the kept candidates, within twice the kernel's bound
+    idx, rho, X, st = run(mrf, D, Zs, mode, topk=K, certify=False)
+    assert D.get_tune()["last_bf16_splits"] == S
+    assert st["device_error"] == 0
+    if mode == "bf16":
+        bound = 2.0 ** -7 + 2.0 ** -16 + 2 * L * 2.0 ** -24
+    else:
+        u8 = 2.0 ** -4 + np.sqrt(2 * L) * 2.0 ** -10 / 224
+        bound = 2 * u8 + u8 * u8 + 2 * L * 2.0 ** -13
+    ref = mo.project(Zs, A)
+    sg = mo.correlation(Zs, A, idx)
+    assert np.all(sg >= ref["s1"] - 2 * bound)
+    assert np.mean(idx == ref["idx"]) >= (0.97 if mode == "bf16" else 0.6)
+    rr = mo.density(Zs, A, idx)
+    assert np.max(np.abs(rho - rr) / np.maximum(np.abs(rr), 1e-30)) <= 1e-4
+    # certified: the exact projection
+    idx, rho, X, st = run(mrf, D, Zs, mode, topk=K, certify=True)
+    check_projection(Zs, A, idx, rho, g_X=X, ref=ref)
+
+
 def test_empty_projection_is_a_no_op(mrf, cfg1):
     dic = cfg1[0]
     D = mrf.build_dict_index(dic["atoms"])
