@@ -742,7 +742,9 @@ def run_reference(args) -> None:
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1e3 * dt / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "sample_voxels": int(sample.shape[0])},
+            "config": {"workload": WORKLOAD, "n_voxels": int(Z.shape[0]), "L": int(atoms.shape[1]),
+                       "d": int(d), "step": "exhaustive float64 projection of a voxel sample",
+                       "projection": "oracle", "sample_voxels": int(sample.shape[0])},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores(), "kind": "oracle",
                              "sample": f"{sample.shape[0]} voxels x {d} atoms per step"},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,

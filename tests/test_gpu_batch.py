@@ -104,8 +104,8 @@ def test_batch_follows_the_oracle(mrf, setup):
         assert np.array_equal(prm[a:a + v["n"]], dic["params"][idx])
 
 
-@pytest.mark.parametrize("mode", ["covertree", "learned"])
-def test_graph_replay_with_device_side_fallback(mrf, setup, mode):
+@pytest.mark.parametrize("mode,pair", [("covertree", 0), ("learned", 0), ("learned", 1)])
+def test_graph_replay_with_device_side_fallback(mrf, setup, mode, pair):
     """The cover-tree and learned forms under graph replay: their exhaustive fallback takes the
     listed voxel count from the device (no read-back inside the captured iteration).  Graph and
     eager runs give the same answers up to BF16 near-ties (the fallback's atom split is sized
@@ -116,6 +116,7 @@ def test_graph_replay_with_device_side_fallback(mrf, setup, mode):
     if mode == "learned":
         M = mrf.MLP(D, dic["axes"], dic["cell_atom"], hidden=32)
         mrf.attach_mlp(D, M)
+    D.set_tune(bf16_pair=pair)           # the fallback's search on clusters or on CTA pairs
     opts = mrf.proj_opts(mode=mode, certify=False, eps=0.0)
     iters = 3
     res = {}
