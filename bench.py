@@ -490,17 +490,23 @@ def run_slices(args) -> None:
 
     out = {}
     mlp_s = None
-    tuned = None
+    tuned = {}
+    Zt = None
     if not args.no_autotune:
-        # search geometry from the autotuner, timed on the largest slice's A^H Y
+        # the largest slice's A^H Y: the autotuner times the search geometries on it, once per
+        # element type (the learned form's fallback searches in BF16)
         from paper_1810_01967_gb300 import autotune
         Nb = max(first)
         opb = mrf.make_op(Nb, Nb, L, masks[Nb])
         Zt = torch.empty((Nb * Nb, L), dtype=torch.complex64, device=dev)
         mrf.adjoint(opb, Ys[Nb], Zt)
-        tuned = autotune.tune(D, Zt, "bf16", reps=2)
-        del Zt
     for mode, graph in forms:
+        if Zt is not None:
+            tmode = "fp8" if mode == "fp8" else "bf16"
+            if tmode not in tuned:
+                tuned[tmode] = autotune.tune(D, Zt, tmode, reps=2)
+            else:
+                D.set_tune(**tuned[tmode]["tune"])
         kw = {}
         if mode == "learned":
             M, mlp_s, _ = train_learned(mrf, D, dic, dev)
@@ -574,7 +580,7 @@ def run_slices(args) -> None:
             "config": {"workload": SLICES_WORKLOAD, "voxels": int(sum(geo[i][0] ** 2 for i in range(64))),
                        "inputs": "one generated slice per matrix size, reused by the slices of that size"},
             "forms": out, "learned_train_gpu_s": mlp_s,
-            "autotune": None if tuned is None else {"tune": tuned["tune"], "ms": tuned["ms"]}}
+            "autotune": {m: {"tune": t["tune"], "ms": t["ms"]} for m, t in tuned.items()} or None}
     print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
