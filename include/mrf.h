@@ -49,9 +49,11 @@ typedef enum mrf_status {
 
 /* How the projection (the nearest-neighbour search of eq. exactP) is computed. */
 typedef enum mrf_proj_mode {
-    MRF_PROJ_FP32_EXACT = 0,  /* exhaustive, FP32 SIMT correlations, FP64 near-tie rescore */
-    MRF_PROJ_BF16 = 1,        /* exhaustive, BF16 tensor cores (tcgen05) + FP32/FP64 rescore */
-    MRF_PROJ_FP8 = 2,         /* exhaustive, FP8 e4m3 tensor cores + FP32/FP64 rescore */
+    MRF_PROJ_FP32_EXACT = 0,  /* exhaustive, FP32 SIMT correlations; near-ties rescored with
+                                 compensated FP32 sums (FP64-class accuracy) */
+    MRF_PROJ_BF16 = 1,        /* exhaustive, BF16 tensor cores (tcgen05), top-K rescored
+                                 exactly in FP32, near-ties in extended precision */
+    MRF_PROJ_FP8 = 2,         /* exhaustive, FP8 e4m3 tensor cores, rescored as BF16 */
     MRF_PROJ_COVERTREE = 3,   /* cover-tree (1+eps)-ANNS, Algorithm 1 (§4.1) */
     MRF_PROJ_LEARNED = 4      /* MLP proposal + exact neighbourhood rescore + fallback */
 } mrf_proj_mode;
