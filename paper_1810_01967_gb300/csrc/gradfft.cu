@@ -1,8 +1,10 @@
 // The gradient step of §3.2 eq. blip in one pass for power-of-two Ny:
 //   Z = X - mu (A^H A X - A^H Y),   A^H A = F_y^H P_t F_y per frame (F_x cancels for line masks).
 //
-// A CTA owns 32 consecutive columns c = x L + t of the [Ny][Nx][L] image (stride Nx L between
-// phase-encode rows, so each row of the tile is one coalesced 256-byte load).  It transforms the
+// A CTA owns 16 consecutive columns c = x L + t of the [Ny][Nx][L] image (stride Nx L between
+// phase-encode rows, so each row of the tile is one coalesced 128-byte load; 32 KB of shared
+// memory, so six CTAs share an SM and hide the passes' latency -- 0.65 ms per 256 x 256 x 1000
+// step against 0.90 ms with 32-column tiles and 0.81 ms with 8).  It transforms the
 // tile along y in shared memory (decimation in time on bit-reversed input, natural-order
 // k-space, two radix-2 stages per shared-memory pass), zeroes the lines that frame t did not
 // sample, transforms back (decimation in frequency, conjugate twiddles, bit-reversed result),
@@ -19,19 +21,21 @@
 
 namespace {
 
-constexpr int TC = 32;          // columns per CTA
 constexpr int NT = 256;         // threads per CTA
+constexpr int kTileLog = 4;     // log2 of the columns per CTA
 
 __device__ __forceinline__ float2 cmul(float2 a, float2 b) {
     return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
 }
 
-// tw[k] = exp(-2 pi i k / Ny), k < Ny / 2
+// tw[k] = exp(-2 pi i k / Ny), k < Ny / 2.  A CTA owns TC = 2^LTC columns.
+template <int LTC>
 __global__ void __launch_bounds__(NT)
 k_grad_pow2(const float2* __restrict__ X, const float2* __restrict__ AHY,
             const uint8_t* __restrict__ mask, const float2* __restrict__ tw, int Ny, int logNy,
             int Nx, int L, float mu, float2* __restrict__ Z, __nv_bfloat162* __restrict__ zq,
             int Kp, uint32_t* err) {
+    constexpr int TC = 1 << LTC;
     extern __shared__ float2 sbuf[];            // [Ny][TC] tile, then [Ny / 2] twiddles
     float2* s = sbuf;
     float2* w = sbuf + Ny * TC;
@@ -40,7 +44,7 @@ k_grad_pow2(const float2* __restrict__ X, const float2* __restrict__ AHY,
     const int64_t c0 = static_cast<int64_t>(blockIdx.x) * TC;
     for (int k = tid; k < Ny / 2; k += NT) w[k] = tw[k];
     const int nbf = (Ny / 2) * TC;              // butterflies per stage
-    // every index a thread touches has column j = tid mod 32 (NT is a multiple of TC)
+    // every index a thread touches has column j = tid mod TC (NT is a multiple of TC)
     const int jt = tid & (TC - 1);
     const int64_t ct = c0 + jt;
     const bool live = ct < NxL;
@@ -48,9 +52,9 @@ k_grad_pow2(const float2* __restrict__ X, const float2* __restrict__ AHY,
     const int64_t xcol = live ? ct / L : 0;                     // x of the column
     // load X bit-reversed along y
     for (int i = tid; i < Ny * TC; i += NT) {
-        const int ky = i >> 5;
+        const int ky = i >> LTC;
         const int r = static_cast<int>(__brev(static_cast<unsigned>(ky)) >> (32 - logNy));
-        s[(r << 5) + jt] = live ? X[static_cast<int64_t>(ky) * NxL + ct] : make_float2(0.f, 0.f);
+        s[(r << LTC) + jt] = live ? X[static_cast<int64_t>(ky) * NxL + ct] : make_float2(0.f, 0.f);
     }
     __syncthreads();
     // forward: decimation in time, natural-order output; two radix-2 stages per pass (a
@@ -61,9 +65,9 @@ k_grad_pow2(const float2* __restrict__ X, const float2* __restrict__ AHY,
         const int h = 1 << lh;
         if (lh + 1 < logNy) {
             for (int q = tid; q < nq; q += NT) {
-                const int b = q >> 5;
+                const int b = q >> LTC;
                 const int g = b >> lh, p = b & (h - 1);
-                const int i = (((g << (lh + 2)) + p) << 5) + jt, hs = h << 5;
+                const int i = (((g << (lh + 2)) + p) << LTC) + jt, hs = h << LTC;
                 const float2 a0 = s[i], a1 = s[i + hs], a2 = s[i + 2 * hs], a3 = s[i + 3 * hs];
                 const float2 w1 = w[p << (logNy - 1 - lh)];
                 const float2 wa = w[p << (logNy - 2 - lh)], wb = w[(p + h) << (logNy - 2 - lh)];
@@ -81,9 +85,9 @@ k_grad_pow2(const float2* __restrict__ X, const float2* __restrict__ AHY,
             lh += 2;
         } else {
             for (int q = tid; q < nbf; q += NT) {
-                const int b = q >> 5;
+                const int b = q >> LTC;
                 const int g = b >> lh, p = b & (h - 1);
-                const int i0 = (((g << (lh + 1)) + p) << 5) + jt, i1 = i0 + (h << 5);
+                const int i0 = (((g << (lh + 1)) + p) << LTC) + jt, i1 = i0 + (h << LTC);
                 const float2 u = s[i0], v = cmul(s[i1], w[p << (logNy - 1 - lh)]);
                 s[i0] = make_float2(u.x + v.x, u.y + v.y);
                 s[i1] = make_float2(u.x - v.x, u.y - v.y);
@@ -95,7 +99,7 @@ k_grad_pow2(const float2* __restrict__ X, const float2* __restrict__ AHY,
     // keep the sampled lines of each column's frame
     const uint8_t* mrow = mask + static_cast<int64_t>(tcol) * Ny;
     for (int i = tid; i < Ny * TC; i += NT) {
-        const int ky = i >> 5;
+        const int ky = i >> LTC;
         if (!live || !mrow[ky]) s[i] = make_float2(0.f, 0.f);
     }
     __syncthreads();
@@ -105,10 +109,10 @@ k_grad_pow2(const float2* __restrict__ X, const float2* __restrict__ AHY,
         if (lh >= 1) {
             const int qq = 1 << (lh - 1);
             for (int q = tid; q < nq; q += NT) {
-                const int b = q >> 5;
+                const int b = q >> LTC;
                 const int g = b >> (lh - 1), p0 = b & (qq - 1);
-                const int i = (((g << (lh + 1)) + p0) << 5) + jt, qs5 = qq << 5;
-                const float2 a0 = s[i], a1 = s[i + qs5], a2 = s[i + 2 * qs5], a3 = s[i + 3 * qs5];
+                const int i = (((g << (lh + 1)) + p0) << LTC) + jt, qst = qq << LTC;
+                const float2 a0 = s[i], a1 = s[i + qst], a2 = s[i + 2 * qst], a3 = s[i + 3 * qst];
                 const float2 ta = w[p0 << (logNy - 1 - lh)], tb = w[(p0 + qq) << (logNy - 1 - lh)];
                 const float2 tc = w[p0 << (logNy - lh)];
                 const float2 wa = make_float2(ta.x, -ta.y), wb = make_float2(tb.x, -tb.y);
@@ -118,15 +122,15 @@ k_grad_pow2(const float2* __restrict__ X, const float2* __restrict__ AHY,
                 const float2 b1 = make_float2(a1.x + a3.x, a1.y + a3.y);
                 const float2 b3 = cmul(make_float2(a1.x - a3.x, a1.y - a3.y), wb);
                 s[i] = make_float2(b0.x + b1.x, b0.y + b1.y);
-                s[i + qs5] = cmul(make_float2(b0.x - b1.x, b0.y - b1.y), wc);
-                s[i + 2 * qs5] = make_float2(b2.x + b3.x, b2.y + b3.y);
-                s[i + 3 * qs5] = cmul(make_float2(b2.x - b3.x, b2.y - b3.y), wc);
+                s[i + qst] = cmul(make_float2(b0.x - b1.x, b0.y - b1.y), wc);
+                s[i + 2 * qst] = make_float2(b2.x + b3.x, b2.y + b3.y);
+                s[i + 3 * qst] = cmul(make_float2(b2.x - b3.x, b2.y - b3.y), wc);
             }
             lh -= 2;
         } else {
             for (int q = tid; q < nbf; q += NT) {       // h = 1: twiddle 1
-                const int b = q >> 5;
-                const int i0 = (b << 6) + jt, i1 = i0 + 32;
+                const int b = q >> LTC;
+                const int i0 = (b << (LTC + 1)) + jt, i1 = i0 + TC;
                 const float2 u = s[i0], v = s[i1];
                 s[i0] = make_float2(u.x + v.x, u.y + v.y);
                 s[i1] = make_float2(u.x - v.x, u.y - v.y);
@@ -140,9 +144,9 @@ k_grad_pow2(const float2* __restrict__ X, const float2* __restrict__ AHY,
     const int half = Kp / 2;
     if (!live) return;
     for (int i = tid; i < Ny * TC; i += NT) {
-        const int ky = i >> 5;
+        const int ky = i >> LTC;
         const int r = static_cast<int>(__brev(static_cast<unsigned>(ky)) >> (32 - logNy));
-        const float2 gv = s[(r << 5) + jt];
+        const float2 gv = s[(r << LTC) + jt];
         const int64_t o = static_cast<int64_t>(ky) * NxL + ct;
         const float2 x = X[o], a = AHY[o];
         float2 z;
@@ -197,11 +201,14 @@ mrf_status launch_grad_fused(const mrf_op* op, const float2* AHY, const float2* 
     const float2* tw = nullptr;
     MRF_TRY(twiddles(Ny, &tw));
     const int64_t cols = static_cast<int64_t>(op->Nx) * op->L;
+    constexpr int LTC = kTileLog;
+    constexpr int TC = 1 << LTC;
     const size_t sm = sizeof(float2) * (static_cast<size_t>(Ny) * TC + Ny / 2);
-    cudaError_t e = cudaFuncSetAttribute(k_grad_pow2, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaError_t e = cudaFuncSetAttribute(k_grad_pow2<LTC>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          static_cast<int>(sm));
     if (e == cudaSuccess) {
-        k_grad_pow2<<<static_cast<unsigned>((cols + TC - 1) / TC), NT, sm, st>>>(
+        k_grad_pow2<LTC><<<static_cast<unsigned>((cols + TC - 1) / TC), NT, sm, st>>>(
             X, AHY, op->mask, tw, Ny, logNy, op->Nx, op->L, mu, Z,
             reinterpret_cast<__nv_bfloat162*>(zq), zq ? Kp : 2 * op->L, err);
         e = cudaGetLastError();
