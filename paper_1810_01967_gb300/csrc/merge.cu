@@ -16,7 +16,11 @@
 namespace {
 
 constexpr int WARPS = 8;
-constexpr int MERGE_G = 8;      // candidates gathered per pass over the frames
+// Candidates gathered per pass over the frames and resident blocks per SM: for K <= 16 four per
+// pass at 64 registers (four blocks of 8 warps per SM, more gathers in flight), for K = 32 eight
+// per pass at 80 (three blocks; 64 registers would spill its lists).
+template <int KT> constexpr int merge_g() { return KT >= 32 ? 8 : 4; }
+template <int KT, int NL> constexpr int merge_min_blocks() { return NL >= 32 ? 2 : (KT >= 32 ? 3 : 4); }
 
 __device__ __forceinline__ float warp_sum(float x) {
     for (int o = 16; o; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
@@ -78,7 +82,7 @@ __device__ __forceinline__ float key_score(uint32_t k) {
 }
 
 template <int KT, int NL>
-__global__ void __launch_bounds__(WARPS * 32, NL >= 32 ? 2 : 3)
+__global__ void __launch_bounds__(WARPS * 32, (merge_min_blocks<KT, NL>()))
 k_merge(const float2* __restrict__ Z, int64_t n_in, const int32_t* __restrict__ vlist,
         const int32_t* __restrict__ nlist, const float2* __restrict__ atoms,
         const float* __restrict__ inv_norm2, const double* __restrict__ norm2, int64_t d,
@@ -158,7 +162,7 @@ k_merge(const float2* __restrict__ Z, int64_t n_in, const int32_t* __restrict__ 
     //    whose kernel correlation lies more than `window` below the first's cannot be the
     //    exactly best (window = twice the kernel's error bound plus tie_tol), so only the
     //    prefix of nw candidates inside the window competes for the best.
-    constexpr int G = KT < MERGE_G ? KT : MERGE_G;
+    constexpr int G = KT < merge_g<KT>() ? KT : merge_g<KT>();
     float zn2 = 0.f;
     int nw = 0;
     __shared__ float s_es[WARPS][KT];      // exact scores (-inf outside the window)
