@@ -132,8 +132,9 @@ __device__ __forceinline__ float tree_dist(const TreeArgs& T, const float2* q, i
 }
 
 // The same distances for up to B candidates at once: one pass over the frames with B
-// independent accumulations per lane (B loads in flight instead of one), then the accurate
-// second pass for the few close ones.  nb (<= B) is uniform across the warp.
+// independent accumulations per lane (B unconditional loads in flight; slots past nb alias the
+// first candidate's row), then one accurate second pass shared by the close candidates.  nb
+// (<= B) is uniform across the warp.
 template <int B>
 __device__ __forceinline__ void tree_dist_batch(const TreeArgs& T, const float2* q, int L,
                                                 const int32_t (&pos)[B], int nb, int lane,
@@ -149,44 +150,61 @@ __device__ __forceinline__ void tree_dist_batch(const TreeArgs& T, const float2*
 #pragma unroll 2
     for (int t = lane; t < L; t += 32) {
         const float2 z = q[t];
+        float2 a[B];
+#pragma unroll
+        for (int b = 0; b < B; ++b) a[b] = u[b][t];
 #pragma unroll
         for (int b = 0; b < B; ++b) {
-            if (b < nb) {
-                const float2 a = u[b][t];
-                re[b] = fmaf(a.x, z.x, fmaf(a.y, z.y, re[b]));
-                im[b] = fmaf(a.x, z.y, fmaf(-a.y, z.x, im[b]));
+            re[b] = fmaf(a[b].x, z.x, fmaf(a[b].y, z.y, re[b]));
+            im[b] = fmaf(a[b].x, z.y, fmaf(-a[b].y, z.x, im[b]));
+        }
+    }
+    float wr[B], wi[B];
+    unsigned close = 0;          // candidates that need the accurate distance (warp-uniform)
+#pragma unroll
+    for (int b = 0; b < B; ++b) {
+        const float r = warp_sum(re[b]);
+        const float m = warp_sum(im[b]);
+        float c;
+        if (T.metric == 0) {
+            c = sqrtf(r * r + m * m);
+            wr[b] = c > 0.f ? r / c : 1.f;
+            wi[b] = c > 0.f ? m / c : 0.f;
+        } else {
+            c = r;
+            wr[b] = 1.f;
+            wi[b] = 0.f;
+        }
+        corr[b] = c;
+        const float d2 = fmaxf(0.f, 2.f - 2.f * c);
+        dist[b] = d2;
+        if (b < nb && d2 < 0.04f) close |= 1u << b;
+    }
+    if (close) {                 // accurate small distances: ||z^ - w u||^2
+        float sacc[B];
+#pragma unroll
+        for (int b = 0; b < B; ++b) sacc[b] = 0.f;
+#pragma unroll 2
+        for (int t = lane; t < L; t += 32) {
+            const float2 z = q[t];
+            float2 a[B];
+#pragma unroll
+            for (int b = 0; b < B; ++b) a[b] = u[b][t];
+#pragma unroll
+            for (int b = 0; b < B; ++b) {
+                const float xr = z.x - (wr[b] * a[b].x - wi[b] * a[b].y);
+                const float xi = z.y - (wr[b] * a[b].y + wi[b] * a[b].x);
+                sacc[b] = fmaf(xr, xr, fmaf(xi, xi, sacc[b]));
             }
+        }
+#pragma unroll
+        for (int b = 0; b < B; ++b) {
+            const float s2 = warp_sum(sacc[b]);
+            if (close & (1u << b)) dist[b] = s2;
         }
     }
 #pragma unroll
-    for (int b = 0; b < B; ++b) {
-        if (b >= nb) continue;
-        const float r = warp_sum(re[b]);
-        const float m = warp_sum(im[b]);
-        float c, wr, wi;
-        if (T.metric == 0) {
-            c = sqrtf(r * r + m * m);
-            wr = c > 0.f ? r / c : 1.f;
-            wi = c > 0.f ? m / c : 0.f;
-        } else {
-            c = r;
-            wr = 1.f;
-            wi = 0.f;
-        }
-        corr[b] = c;
-        float d2 = fmaxf(0.f, 2.f - 2.f * c);
-        if (d2 < 0.04f) {   // accurate small distances: ||z^ - w u||^2
-            float sacc = 0.f;
-            for (int t = lane; t < L; t += 32) {
-                const float2 a = u[b][t], z = q[t];
-                const float xr = z.x - (wr * a.x - wi * a.y);
-                const float xi = z.y - (wr * a.y + wi * a.x);
-                sacc = fmaf(xr, xr, fmaf(xi, xi, sacc));
-            }
-            d2 = warp_sum(sacc);
-        }
-        dist[b] = sqrtf(d2);
-    }
+    for (int b = 0; b < B; ++b) dist[b] = sqrtf(dist[b]);
 }
 
 __device__ __forceinline__ void top_insert(float (&cs)[TOPC], int32_t (&ci)[TOPC], float c,
