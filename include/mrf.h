@@ -473,9 +473,11 @@ typedef struct mrf_tune {
     int32_t last_bf16_cluster; /* out: its cluster size */
     int32_t last_bf16_splits;  /* out: its atom splits */
     int32_t last_fp32_splits;  /* out: atom splits of the last FP32 search launch */
-    int32_t tree_list_cap;     /* cover-tree candidate list capacity per voxel, 64..512 (0 = 256);
-                                  smaller lists fit more warps per SM, longer lists route fewer
-                                  voxels to the exhaustive search */
+    int32_t tree_list_cap;     /* cover-tree candidate list capacity per voxel, 64..512; 0 = the
+                                  longest list with which four CTAs of four queries stay
+                                  resident per SM (256 for L <= 768, 192 at L = 1000, 64 from
+                                  L = 1480): shorter lists fit more warps per SM, longer lists
+                                  route fewer voxels to the exhaustive search */
     int32_t bf16_pair;         /* 1: the tensor-core search on CTA pairs (2-SM MMA, M = 256,
                                   each CTA staging half of every atom block) instead of clusters
                                   sharing atom blocks by multicast (bf16_cluster is then ignored);
