@@ -133,3 +133,34 @@ def test_gradient_step_full_slice(mrf, full):
     ref = mo.gradient_step(X, p["Y"], p["masks"], p["Ny"], p["Nx"], 1.0)[s]
     got = Z.cpu().numpy()[s].astype(np.complex128)
     assert np.max(_fft_err(got, ref)) < 1e-5
+
+
+@pytest.mark.parametrize("eps", [0.0, 0.4])
+def test_cover_tree_long_fingerprints(mrf, full, eps):
+    """The cover tree at L = 1000, where the default candidate list (192 entries) is sized for
+    four resident CTAs: a tree over 3,000 of the workload's atoms, the first iterate's sampled
+    voxels; eps = 0 is the exact projection of that dictionary, eps > 0 meets the (1+eps)
+    bound of Definition eNN."""
+    from oracle import covertree as ct
+    A = np.ascontiguousarray(full["dic"]["atoms"][:3000])
+    s = full["sample"]
+    Zs = full["AHY"].cpu().numpy()[s]
+    D = mrf.build_dict_index(A, build_tree=True)
+    n = Zs.shape[0]
+    idx = torch.empty(n, dtype=torch.int32, device="cuda")
+    rho = torch.empty(n, dtype=torch.complex64, device="cuda")
+    st = mrf.project(D, to_dev(Zs), idx, rho, stats=True,
+                     opts=mrf.proj_opts(mode="covertree", eps=eps))
+    assert st["device_error"] == 0
+    gi = idx.cpu().numpy()
+    if eps == 0.0:
+        check_projection(Zs, A, gi, rho.cpu().numpy())
+    else:
+        ref = mo.project(Zs, A)
+        U = ct.unit_atoms(A.astype(np.complex128))
+        Zn = Zs.astype(np.complex128) / np.linalg.norm(Zs, axis=1)[:, None]
+        dg = np.array([ct.pair_dist(Zn[v:v + 1], U[gi[v]:gi[v] + 1], "phase")[0, 0]
+                       for v in range(n)])
+        dn = np.array([ct.pair_dist(Zn[v:v + 1], U[ref["idx"][v]:ref["idx"][v] + 1], "phase")[0, 0]
+                       for v in range(n)])
+        assert np.all(dg <= (1 + eps) * dn + 1e-5), np.max(dg - (1 + eps) * dn)
