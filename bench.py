@@ -133,10 +133,11 @@ def kernel_digest() -> str:
     return hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
 
 
-def traffic_per_launch(n: int, d: int) -> float | None:
-    """DRAM bytes per launch of the search kernel from the committed ncu summary, scaled to
-    this workload by the number of voxel-atom pairs; None if the kernel changed since."""
-    p = os.path.join(ROOT, "profiles", "bf16_search_traffic.json")
+def traffic_per_launch(n: int, d: int, mode: str = "bf16") -> float | None:
+    """DRAM bytes per launch of the search kernel (BF16 or FP8 operands) from the committed ncu
+    summary, scaled to this workload by the number of voxel-atom pairs; None if the kernel
+    changed since."""
+    p = os.path.join(ROOT, "profiles", f"{mode}_search_traffic.json")
     if not os.path.exists(p):
         return None
     t = json.load(open(p))
@@ -916,7 +917,7 @@ def run_ours(args) -> None:
             peak, src = 2.0 * peak, src + " x 2 (nominal fp8 / bf16 dense ratio, 4.5 / 2.25)"
         roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                 "frac": achieved / peak,
-                "traffic": traffic_per_launch(n, d) if args.mode == "bf16" else None,
+                "traffic": traffic_per_launch(n, d, args.mode),
                 "kernel": "k_tc_topk", "peak_source": src, "flops_per_launch": flops_per_launch}
     else:
         # FP32 SIMT: 152 SMs x 128 FP32 lanes x 2 flop (FFMA) x 2070 MHz maximum SM clock
