@@ -399,7 +399,11 @@ def run_profile_case(args) -> None:
     kernel-level ncu captures (about 2 GB on the device).  Exhaustive modes project the first
     N rows of A^H Y; the cover tree (eps 0.4) projects the phantom's object fingerprints with
     the slice's noise level, i.e. queries near the dictionary, where the tree search does its
-    work instead of routing far queries to the exhaustive search."""
+    work instead of routing far queries to the exhaustive search.  Two more cases time single
+    stages: `gradient` runs whole IPG steps (mrf_ipg_step, fixed mu = 1) of the full N x N x L
+    slice against the first 4,096 atoms, so the fused gradient kernel runs at full size with a
+    small dictionary (N voxels ignored), and `mlp` runs the learned proposal's BF16 tensor-core
+    inference of N fingerprints (random network: the timing does not depend on the weights)."""
     import torch
     import paper_1810_01967_gb300 as mrf
     from paper_1810_01967_gb300 import build as b
@@ -407,6 +411,9 @@ def run_profile_case(args) -> None:
     dic, p = make_workload(0)
     Ny, Nx, L = p["Ny"], p["Nx"], p["L"]
     n = args.profile_case
+    if args.mode in ("gradient", "mlp"):
+        run_stage_case(args, mrf, dic, p)
+        return
     tree = args.mode == "covertree"
     D = mrf.build_dict_index(dic["atoms"], dic["params"], pack_fp8=(args.mode == "fp8"),
                              build_tree=tree)
@@ -433,6 +440,48 @@ def run_profile_case(args) -> None:
     prof = mrf.profile_read()
     torch.cuda.synchronize()
     print(json.dumps({"profile_case": n, "d": int(dic["atoms"].shape[0]), "L": L,
+                      "stage_ms": {k: v[0] for k, v in prof.items()},
+                      "stage_launches": {k: v[1] for k, v in prof.items()}}))
+
+
+def run_stage_case(args, mrf, dic, p) -> None:
+    import torch
+    Ny, Nx, L = p["Ny"], p["Nx"], p["L"]
+    mrf.profile_enable(True)
+    if args.mode == "gradient":
+        D = mrf.build_dict_index(np.ascontiguousarray(dic["atoms"][:4096]), None)
+        op = mrf.make_op(Ny, Nx, L, torch.from_numpy(p["masks"]).cuda())
+        AHY = torch.empty((Ny * Nx, L), dtype=torch.complex64, device="cuda")
+        mrf.adjoint(op, torch.from_numpy(p["Y"]).cuda(), AHY)
+        X = AHY.clone()
+        idx = torch.zeros(Ny * Nx, dtype=torch.int32, device="cuda")
+        o = mrf.proj_opts(mode="bf16", certify=False)
+
+        def call():
+            mrf.ipg_step(D, op, AHY, X, 1.0, idx, opts=o)
+        n = Ny * Nx
+    else:
+        D = mrf.build_dict_index(dic["atoms"], dic["params"], grid_shape=dic["grid_shape"],
+                                 pack_bf16=False)
+        M = mrf.MLP(D, dic["axes"], dic["cell_atom"], hidden=512, residue_pool=4096)
+        n = args.profile_case
+        g = torch.Generator(device="cuda").manual_seed(7)
+        Xin = torch.randn((n, 2 * L), generator=g, device="cuda", dtype=torch.float32)
+        Y = torch.empty((n, 3), dtype=torch.float32, device="cuda")
+
+        def call():
+            M.infer(Xin, Y)
+    call()                                   # first call: plans and scratch
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.steps):
+        call()
+    e1.record()
+    torch.cuda.synchronize()
+    prof = mrf.profile_read()
+    print(json.dumps({"profile_case": n, "mode": args.mode, "L": L,
+                      "ms_per_call": e0.elapsed_time(e1) / args.steps,
                       "stage_ms": {k: v[0] for k, v in prof.items()},
                       "stage_launches": {k: v[1] for k, v in prof.items()}}))
 
@@ -973,8 +1022,10 @@ def main():
     ap.add_argument("--no-forms", action="store_true", help="skip the cover tree and learned forms")
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--mode", default="bf16", choices=["bf16", "fp8", "fp32", "covertree"],
-                    help="projection of the timed step (covertree: --profile-case only)")
+    ap.add_argument("--mode", default="bf16",
+                    choices=["bf16", "fp8", "fp32", "covertree", "gradient", "mlp"],
+                    help="projection of the timed step (covertree, gradient, mlp: "
+                         "--profile-case only)")
     ap.add_argument("--autotune", action="store_true",
                     help="time the search geometries on the workload first and use the fastest "
                          "(always on for the slices64 workload, whose batching form picks its "
@@ -992,6 +1043,8 @@ def main():
     ap.add_argument("--profile-case", type=int, default=0,
                     help="projection-only small case with N voxels (for ncu captures)")
     args = ap.parse_args()
+    if args.mode in ("covertree", "gradient", "mlp") and args.profile_case <= 0:
+        ap.error(f"--mode {args.mode} needs --profile-case")
     if args.profile_case > 0:
         run_profile_case(args)
     elif args.workload == "slices64" and args.impl == "ours":
