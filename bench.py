@@ -402,8 +402,10 @@ def run_profile_case(args) -> None:
     work instead of routing far queries to the exhaustive search.  Two more cases time single
     stages: `gradient` runs whole IPG steps (mrf_ipg_step, fixed mu = 1) of the full N x N x L
     slice against the first 4,096 atoms, so the fused gradient kernel runs at full size with a
-    small dictionary (N voxels ignored), and `mlp` runs the learned proposal's BF16 tensor-core
-    inference of N fingerprints (random network: the timing does not depend on the weights)."""
+    small dictionary (N voxels ignored), `mlp` runs the learned proposal's BF16 tensor-core
+    inference of N fingerprints (random network: the timing does not depend on the weights),
+    and `learned` the whole learned projection of the first N rows of A^H Y with that network
+    (inference, neighbourhood rescore, exhaustive fallback)."""
     import torch
     import paper_1810_01967_gb300 as mrf
     from paper_1810_01967_gb300 import build as b
@@ -411,7 +413,7 @@ def run_profile_case(args) -> None:
     dic, p = make_workload(0)
     Ny, Nx, L = p["Ny"], p["Nx"], p["L"]
     n = args.profile_case
-    if args.mode in ("gradient", "mlp"):
+    if args.mode in ("gradient", "mlp", "learned"):
         run_stage_case(args, mrf, dic, p)
         return
     tree = args.mode == "covertree"
@@ -460,6 +462,22 @@ def run_stage_case(args, mrf, dic, p) -> None:
         def call():
             mrf.ipg_step(D, op, AHY, X, 1.0, idx, opts=o)
         n = Ny * Nx
+    elif args.mode == "learned":
+        D = mrf.build_dict_index(dic["atoms"], dic["params"], grid_shape=dic["grid_shape"])
+        M = mrf.MLP(D, dic["axes"], dic["cell_atom"], hidden=512, residue_pool=4096)
+        mrf.attach_mlp(D, M)
+        n = args.profile_case
+        op = mrf.make_op(Ny, Nx, L, torch.from_numpy(p["masks"]).cuda())
+        AHY = torch.empty((Ny * Nx, L), dtype=torch.complex64, device="cuda")
+        mrf.adjoint(op, torch.from_numpy(p["Y"]).cuda(), AHY)
+        Z = AHY[:n].contiguous()
+        del AHY
+        idx = torch.empty(n, dtype=torch.int32, device="cuda")
+        rho = torch.empty(n, dtype=torch.complex64, device="cuda")
+        o = mrf.proj_opts(mode="learned", certify=False, fallback_thr=0.98)
+
+        def call():
+            mrf.project(D, Z, idx, rho, opts=o)
     else:
         D = mrf.build_dict_index(dic["atoms"], dic["params"], grid_shape=dic["grid_shape"],
                                  pack_bf16=False)
@@ -1023,8 +1041,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--mode", default="bf16",
-                    choices=["bf16", "fp8", "fp32", "covertree", "gradient", "mlp"],
-                    help="projection of the timed step (covertree, gradient, mlp: "
+                    choices=["bf16", "fp8", "fp32", "covertree", "gradient", "mlp", "learned"],
+                    help="projection of the timed step (covertree, gradient, mlp, learned: "
                          "--profile-case only)")
     ap.add_argument("--autotune", action="store_true",
                     help="time the search geometries on the workload first and use the fastest "
@@ -1043,7 +1061,7 @@ def main():
     ap.add_argument("--profile-case", type=int, default=0,
                     help="projection-only small case with N voxels (for ncu captures)")
     args = ap.parse_args()
-    if args.mode in ("covertree", "gradient", "mlp") and args.profile_case <= 0:
+    if args.mode in ("covertree", "gradient", "mlp", "learned") and args.profile_case <= 0:
         ap.error(f"--mode {args.mode} needs --profile-case")
     if args.profile_case > 0:
         run_profile_case(args)
