@@ -100,3 +100,61 @@ def test_iterations_improve_on_tm(dic1):
         accs.append(mo.accuracy(est[:, 0], p["phantom"]["T1"], fg))
     assert accs[1] > accs[0]
     assert accs[1] > 0.85
+
+
+def _objective(X, Y, masks, Ny, Nx):
+    """f(X) = 1/2 ||A(X) - Y||^2, the data-fidelity term whose gradient step eq. blip takes."""
+    R = mo.forward(X, masks, Ny, Nx) - Y
+    return 0.5 * float(np.sum(np.abs(R) ** 2))
+
+
+def test_gradient_step_is_the_fidelity_gradient():
+    """(X - Z) / mu is the gradient of f at X, checked by central differences along random
+    complex directions (partial line masks): 2 eps Re<grad, E> = f(X + eps E) - f(X - eps E)
+    exactly for a quadratic."""
+    g = np.random.Generator(np.random.PCG64(31))
+    Ny, Nx, L, mu = 8, 6, 5, 0.7
+    masks = (g.random((L, Ny)) < 0.5).astype(np.uint8)
+    X, X0 = _rand(g, Ny * Nx, L), _rand(g, Ny * Nx, L)
+    Y = mo.forward(X0, masks, Ny, Nx) + 0.1 * _rand(g, Ny, Nx, L) * masks.T[:, None, :]
+    grad = (X - mo.gradient_step(X, Y, masks, Ny, Nx, mu)) / mu
+    eps = 1e-3
+    for _ in range(4):
+        E = _rand(g, Ny * Nx, L)
+        fd = (_objective(X + eps * E, Y, masks, Ny, Nx)
+              - _objective(X - eps * E, Y, masks, Ny, Nx)) / (2 * eps)
+        assert abs(fd - float(np.real(np.vdot(grad, E)))) <= 1e-9 * max(1.0, abs(fd))
+
+
+def test_gradient_step_special_cases():
+    """Full sampling (A^H A = I): Z = (1 - mu) X + mu X0 for Y = A X0.  No sampled line
+    (A = 0, Y = 0): Z = X."""
+    g = np.random.Generator(np.random.PCG64(32))
+    Ny, Nx, L, mu = 8, 4, 3, 0.3
+    X, X0 = _rand(g, Ny * Nx, L), _rand(g, Ny * Nx, L)
+    full = np.ones((L, Ny), np.uint8)
+    Z = mo.gradient_step(X, mo.forward(X0, full, Ny, Nx), full, Ny, Nx, mu)
+    np.testing.assert_allclose(Z, (1 - mu) * X + mu * X0, atol=1e-12)
+    none = np.zeros((L, Ny), np.uint8)
+    Z = mo.gradient_step(X, np.zeros((Ny, Nx, L), complex), none, Ny, Nx, mu)
+    np.testing.assert_allclose(Z, X, atol=0)
+
+
+def test_rescale_reproduces_complex_multiples_of_atoms():
+    """Projection then rescale (eq. exactPs) maps rho D_k back to itself for any complex rho."""
+    g = np.random.Generator(np.random.PCG64(33))
+    D = _rand(g, 40, 12)
+    k = g.integers(0, 40, 9)
+    rho = _rand(g, 9)
+    Z = rho[:, None] * D[k]
+    r = mo.project(Z, D)
+    np.testing.assert_array_equal(r["idx"], k)
+    np.testing.assert_allclose(mo.rescale(r["idx"], r["rho"], D), Z, atol=1e-12)
+
+
+def test_nmse_values():
+    g = np.random.Generator(np.random.PCG64(34))
+    X0 = _rand(g, 10, 4)
+    assert mo.nmse(X0, X0) == 0.0
+    assert mo.nmse(2 * X0, X0) == pytest.approx(1.0)
+    assert mo.nmse(np.zeros_like(X0), X0) == pytest.approx(1.0)

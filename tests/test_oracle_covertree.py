@@ -101,3 +101,15 @@ def test_search_cost_below_brute_force(small_dic):
     Q = _queries(small_dic, g, noise=0.05)
     evals = [tree.search(p, 0.5)[1] for p in Q]
     assert np.mean(evals) < 0.5 * small_dic.shape[0]
+
+
+def test_unit_atoms_keep_direction_and_phase():
+    """u_j = D_j / ||D_j||: unit rows, and D_j is a positive multiple of u_j."""
+    g = np.random.Generator(np.random.PCG64(51))
+    D = (g.standard_normal((6, 9)) + 1j * g.standard_normal((6, 9))) * g.uniform(0.1, 5, (6, 1))
+    U = ct.unit_atoms(D)
+    np.testing.assert_allclose(np.linalg.norm(U, axis=1), 1.0, atol=1e-14)
+    ratio = D / U
+    np.testing.assert_allclose(ratio.imag, 0.0, atol=1e-12)
+    assert np.all(ratio.real > 0)
+    np.testing.assert_allclose(ratio.real, np.linalg.norm(D, axis=1)[:, None] * np.ones((1, 9)))

@@ -43,3 +43,11 @@ def test_aligned_score_is_bounded_by_the_complex_score():
     r = phase.project_phase_aligned(Z, A)
     c = mo.project(Z, A, "complex")
     assert np.all(r["s1"] <= c["s1"] + 1e-12)
+
+
+def test_unit_phase_values():
+    """e^{i theta} of r e^{i theta} for r > 0, and 1 for a zero value (no phase to remove)."""
+    th = np.array([0.0, 0.5, -2.0, np.pi])
+    r = np.array([3.0, 1e-20, 7.0, 0.25])
+    np.testing.assert_allclose(phase.unit_phase(r * np.exp(1j * th)), np.exp(1j * th), atol=1e-15)
+    assert phase.unit_phase(np.array([0j]))[0] == 1.0

@@ -63,3 +63,42 @@ def test_exactly_low_rank_dictionary():
     ref = mo.blip(Y, masks, A, Ny, Nx, iters=4)
     assert np.array_equal(r["idx"], ref["idx"])
     np.testing.assert_allclose(r["X"], ref["X"], atol=1e-9 * np.abs(ref["X"]).max())
+
+
+def _rand(g, *shape):
+    return g.standard_normal(shape) + 1j * g.standard_normal(shape)
+
+
+def test_expand_inverts_compress():
+    """With orthonormal columns (V^H V = I) compress(expand(Xc)) = Xc for any s; with the full
+    basis (V unitary) expand(compress(X)) = X as well."""
+    g = np.random.Generator(np.random.PCG64(41))
+    L = 9
+    Q, _ = np.linalg.qr(_rand(g, L, L))
+    Xc = _rand(g, 7, 4)
+    np.testing.assert_allclose(svd.compress(svd.expand(Xc, Q[:, :4]), Q[:, :4]), Xc, atol=1e-12)
+    X = _rand(g, 7, L)
+    np.testing.assert_allclose(svd.expand(svd.compress(X, Q), Q), X, atol=1e-12)
+
+
+def test_compressed_step_is_the_compressed_fidelity_gradient():
+    """eq. gradupdate: (Xc - Zc) / mu is the gradient of f_c(Xc) = 1/2 ||A(V_s Xc) - Y||^2,
+    checked by central differences along random complex directions (partial masks)."""
+    g = np.random.Generator(np.random.PCG64(42))
+    Ny, Nx, L, s, mu = 8, 4, 6, 3, 0.9
+    Q, _ = np.linalg.qr(_rand(g, L, L))
+    V = Q[:, :s]
+    masks = (g.random((L, Ny)) < 0.5).astype(np.uint8)
+    Y = mo.forward(_rand(g, Ny * Nx, L), masks, Ny, Nx)
+    Xc = _rand(g, Ny * Nx, s)
+
+    def f(Xc_):
+        R = mo.forward(svd.expand(Xc_, V), masks, Ny, Nx) - Y
+        return 0.5 * float(np.sum(np.abs(R) ** 2))
+
+    grad = (Xc - svd.gradient_step_c(Xc, Y, masks, Ny, Nx, mu, V)) / mu
+    eps = 1e-3
+    for _ in range(4):
+        E = _rand(g, Ny * Nx, s)
+        fd = (f(Xc + eps * E) - f(Xc - eps * E)) / (2 * eps)
+        assert abs(fd - float(np.real(np.vdot(grad, E)))) <= 1e-9 * max(1.0, abs(fd))
