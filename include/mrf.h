@@ -94,7 +94,8 @@ typedef struct mrf_proj_opts {
                               cert_margin of the best with the FP32 exact kernel (default 1) */
     float   tie_tol;       /* candidates whose normalised correlation |D_j^H Z_v| /
                               (||D_j|| ||Z_v||) is within this absolute distance of the best
-                              are rescored in FP64 (default 1e-5) */
+                              are rescored with FP64-class accuracy: compensated FP32
+                              sums reduced in FP64 (default 1e-5) */
     float   cert_margin;   /* margin of `certify`, same units; <= 0 selects the rigorous
                               bound of the BF16 correlation error, 2^-7 + 2^-16 (operand
                               rounding) + 2L 2^-24 (FP32 accumulation), or for FP8
@@ -120,7 +121,8 @@ typedef struct mrf_proj_opts {
 typedef struct mrf_stats {
     int64_t n_voxels;         /* voxels projected */
     int64_t n_zero;           /* zero queries (idx 0, rho 0) */
-    int64_t n_tie_rescored;   /* voxels whose leading candidates were rescored in FP64 */
+    int64_t n_tie_rescored;   /* voxels whose leading candidates were rescored with
+                                 FP64-class accuracy (compensated FP32, FP64 reduction) */
     int64_t n_tie_overflow;   /* voxels whose k-th candidate was still within tie_tol */
     int64_t n_uncertified;    /* BF16/FP8 voxels sent to the FP32 exact kernel */
     int64_t n_fallback;       /* learned proposal voxels sent to the exhaustive search */
@@ -221,14 +223,16 @@ mrf_status mrf_dict_check(mrf_dict* dict, void* stream);
  * Matched-filtering projection of n fingerprints (§3.2, eqs. exactP / exactPs; with
  * MRF_PROJ_COVERTREE, the (1+eps)-ANNS of Algorithm 1 on Z_v / ||Z_v|| warm-started at
  * warm_idx (§4.3, eq. ANN1), then the exact rescore of the 8 best atoms it visited; voxels
- * routed away by `tree_route` or whose candidate list would exceed 512 entries are projected by
- * the exhaustive search instead: BF16 tensor cores (certified as `certify` says) when the
+ * routed away by `tree_route` (a warm atom, or a long candidate list, still farther than it) or
+ * whose candidate list would exceed its capacity (mrf_tune.tree_list_cap) are projected by the
+ * exhaustive search instead: BF16 tensor cores (certified as `certify` says) when the
  * dictionary has the BF16 operand, else FP32).
  *   Z         device complex64 [n][L]
  *   warm_idx  device int32 [n] or NULL: previous atoms, the warm start of the tree search
  *   idx_out   device int32 [n]: j*_v
  *   rho_out   device complex64 [n]: rho_v = D_j*^H Z_v / ||D_j*||^2 (complex cone) or
- *             gamma_v (real cone, imaginary part 0); FP64 accumulation
+ *             gamma_v (real cone, imaginary part 0); compensated FP32 sums (exact products,
+ *             two-sum accumulation) reduced in FP64, an error of a few units of 2^-46
  *   X_out     device complex64 [n][L] or NULL: X_v = rho_v D_j*
  * A zero fingerprint gives j* = 0, rho = 0.  Exact ties go to the smallest index.
  */
@@ -285,8 +289,8 @@ mrf_status mrf_reconstruct(mrf_dict* dict, const mrf_op* op, const void* Y,
  *   Z        device complex64 [n][L], 0 <= n <= 4096 voxels per call
  *   cone     mrf_cone
  *   idx_out  device int32 [n]; rho_out device complex64 [n] or NULL; X_out device [n][L] or NULL
- * Results equal mrf_project's FP32 mode (top-8 candidates, FP64 near-tie rescore, FP64
- * density).  Larger sizes return MRF_EINVAL with a message, before any launch.  The first call
+ * Results equal mrf_project's FP32 mode (top-8 candidates, near-tie rescore and density in
+ * compensated FP32 reduced in FP64).  Larger sizes return MRF_EINVAL with a message, before any launch.  The first call
  * on a device looks up the array's device address (cudaGetSymbolAddress) with that device
  * current; make that first call before any stream capture.  All calls share the one array, so
  * calls that overlap on the GPU (other streams, other threads) race; serialise them.  The call
