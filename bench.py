@@ -291,9 +291,11 @@ def reconstruction_quality(mrf, D, op, p, dic, dev, stream, iters: int, fp32: bo
     runs = [("bf16", {}), ("fp8", {})]
     if fp32:
         runs.append(("fp32", {}))
+    D2 = None
     if forms:
+        # a second dictionary with the cover tree and the learned model; the caller's D stays
+        # open (its owner closes it)
         t0 = time.perf_counter()
-        D.close()
         D2 = mrf.build_dict_index(dic["atoms"], dic["params"], grid_shape=dic["grid_shape"],
                                   build_tree=True, pack_fp8=True)
         out["tree_build_s"] = time.perf_counter() - t0
@@ -381,6 +383,8 @@ def reconstruction_quality(mrf, D, op, p, dic, dev, stream, iters: int, fp32: bo
                                     "T2_acc": t_accuracy(pr[:, 1], ph["T2"], fg),
                                     "B0_mae_hz": float(np.mean(np.abs(pr[fg, 2] - ph["B0"][fg])))}
         Da.close()
+    if D2 is not None:
+        D2.close()
     for mode in idxs:
         if "fp32" in idxs:
             out[mode]["atom_agreement_vs_fp32"] = float(np.mean(idxs[mode] == idxs["fp32"]))
@@ -875,9 +879,9 @@ def run_ours(args) -> None:
         step(X, AHY, idx, rho, prm)
     barrier()
     # ------------------------------------------------------------- timed region (device)
+    # No instrumentation inside: the stage profiler runs in a separate pass below.
     clk = ClockSampler(local)
     clk.start()
-    mrf.profile_enable(True)
     barrier()
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
@@ -887,56 +891,42 @@ def run_ours(args) -> None:
     e1.record(stream)
     barrier()
     ms = e0.elapsed_time(e1)
-    prof = mrf.profile_read()
-    mrf.profile_enable(False)
     clocks = clk.stop()
     ms_max = max_over_ranks(ms, world, dev)
     D.check()
+    # ------------------------------------------------------------- stage split (profiled pass)
+    # The same K steps again with the library's stage profiler on: CUDA events on the stream
+    # every stage is launched on give each stage's time and launch count (the search kernel's
+    # average duration for the roofline).
+    mrf.profile_enable(True)
+    for _ in range(args.steps):
+        step(X, AHY, idx, rho, prm)
+    barrier()
+    prof = mrf.profile_read()
+    mrf.profile_enable(False)
     # ------------------------------------------------------------- end to end (host buffers)
-    # Every step copies its inputs (X, A^H Y) from pinned host memory and reads its results
-    # (indices, densities, parameter maps) back.  The inputs are double-buffered on the device
-    # and step k + 1's copy runs on a second stream while step k computes, as a serving loop
-    # would; every copy lies inside the timed region.
-    Xh = X.cpu().pin_memory()
-    AHYh = AHY.cpu().pin_memory()
+    # One call of the public API, mrf_reconstruct, from host k-space to host outputs: the
+    # library copies Y in, computes A^H Y, runs K iterations of the timed step's form and the
+    # look-up table, and copies X, the atoms, the densities and the parameter maps back, all
+    # inside the call (pinned host buffers).
+    Yh = torch.from_numpy(p["Y"]).pin_memory()
+    Xh = torch.empty((n, L), dtype=torch.complex64).pin_memory()
     idx_h = torch.empty(n, dtype=torch.int32).pin_memory()
     rho_h = torch.empty(n, dtype=torch.complex64).pin_memory()
     prm_h = torch.empty((n, params.shape[1]), dtype=torch.float32).pin_memory()
     e2e_steps = max(1, args.steps)
-    Xb = [X, torch.empty_like(X)]
-    Ab = [AHY, torch.empty_like(AHY)]
-    copy_stream = torch.cuda.Stream(device=dev)
-    ev_in = [torch.cuda.Event() for _ in range(2)]
-    ev_free = [torch.cuda.Event() for _ in range(2)]
-
-    def issue_copy(k):
-        b = k % 2
-        with torch.cuda.stream(copy_stream):
-            copy_stream.wait_event(ev_free[b])      # the step that last read buffer b is done
-            Xb[b].copy_(Xh, non_blocking=True)
-            Ab[b].copy_(AHYh, non_blocking=True)
-            ev_in[b].record(copy_stream)
-
+    ro_warm = mrf.recon_opts(iters=1, mode=args.mode, certify=opts.certify != 0)
+    ro = mrf.recon_opts(iters=e2e_steps, mode=args.mode, certify=opts.certify != 0)
+    mrf.reconstruct(D, op, Yh, Xh, idx_h, rho_h, prm_h, opts=ro_warm)
     barrier()
     t0 = time.perf_counter()
-    for b in range(2):
-        ev_free[b].record(stream)
-    issue_copy(0)
-    for k in range(e2e_steps):
-        b = k % 2
-        if k + 1 < e2e_steps:
-            issue_copy(k + 1)
-        stream.wait_event(ev_in[b])
-        step(Xb[b], Ab[b], idx, rho, prm)
-        ev_free[b].record(stream)
-        idx_h.copy_(idx, non_blocking=True)
-        rho_h.copy_(rho, non_blocking=True)
-        prm_h.copy_(prm, non_blocking=True)
+    mrf.reconstruct(D, op, Yh, Xh, idx_h, rho_h, prm_h, opts=ro)
     barrier()
     e2e_s = time.perf_counter() - t0
     e2e_s = max_over_ranks(e2e_s, world, dev)
-    h2d = Xh.numel() * 8 + AHYh.numel() * 8
-    d2h = n * 4 + n * 8 + n * params.shape[1] * 4
+    h2d = Yh.numel() * 8
+    d2h = n * L * 8 + n * 4 + n * 8 + n * params.shape[1] * 4
+    del Yh, Xh
     # ------------------------------------------------------------- FP32 exact comparator
     fp32_rate = None
     if args.fp32_sample > 0 and rank == 0:
@@ -1016,7 +1006,11 @@ def run_ours(args) -> None:
                        "l2": "inputs larger than L2 (BF16 dictionary operand 800 MB)"},
             "roofline": roof, "cpu_baseline": cpu,
             "e2e": {"value": world * n * d * e2e_steps / e2e_s, "unit": UNIT,
-                    "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+                    "h2d_bytes_per_step": h2d / e2e_steps, "d2h_bytes_per_step": d2h / e2e_steps,
+                    "call": f"mrf_reconstruct from pinned host buffers, {e2e_steps} iterations "
+                            f"per call (Y in, X / atoms / densities / parameter maps out)",
+                    "h2d_bytes_per_call": h2d, "d2h_bytes_per_call": d2h,
+                    "s_per_call": e2e_s},
             "gpu_launches": launches, "clocks": clocks,
             "extra": {"recon_s_per_slice_20_iters": 20 * ms_max / args.steps / 1e3,
                       "quality": quality,

@@ -268,11 +268,16 @@ mrf_status mrf_ipg_step(mrf_dict* dict, const mrf_op* op, const void* AHY, void*
  * Whole reconstruction (Algorithm 2): A^H Y once, X^0 = 0 (or the iterate in X_out with
  * mrf_recon_opts.resume), `iters` iterations with the options' step rule and kappa rescale,
  * then the look-up table.  Synchronises `stream`.
- *   Y          device complex64 [Ny][Nx][L]
- *   X_out      device complex64 [n][L]
- *   idx_out    device int32 [n]
- *   rho_out    device complex64 [n] or NULL
- *   params_out device float32 [n][P] or NULL
+ *   Y          complex64 [Ny][Nx][L]
+ *   X_out      complex64 [n][L]
+ *   idx_out    int32 [n]
+ *   rho_out    complex64 [n] or NULL
+ *   params_out float32 [n][P] or NULL
+ * Each of these may be device memory or host memory (pinned or pageable; detected).  Host
+ * buffers are staged through device buffers that the call allocates and frees: Y (and, with
+ * `resume`, X_out and idx_out) is copied in at the start and the outputs are copied back
+ * before the call returns, so every transfer lies inside the call.  op->mask stays device
+ * memory.
  */
 mrf_status mrf_reconstruct(mrf_dict* dict, const mrf_op* op, const void* Y,
                            const mrf_recon_opts* opts, void* X_out, int32_t* idx_out,
@@ -289,8 +294,11 @@ mrf_status mrf_reconstruct(mrf_dict* dict, const mrf_op* op, const void* Y,
  *   Z        device complex64 [n][L], 0 <= n <= 4096 voxels per call
  *   cone     mrf_cone
  *   idx_out  device int32 [n]; rho_out device complex64 [n] or NULL; X_out device [n][L] or NULL
- * Results equal mrf_project's FP32 mode (top-8 candidates, near-tie rescore and density in
- * compensated FP32 reduced in FP64).  Larger sizes return MRF_EINVAL with a message, before any launch.  The first call
+ * The atoms are used as given: no phase alignment is applied (with MRF_CONE_REAL_POS the real
+ * positive rule runs on the atoms and queries as they are).  Results equal mrf_project's FP32
+ * mode on a dictionary built from the same atoms without phase_align (top-8 candidates,
+ * near-tie rescore and density in compensated FP32 reduced in FP64).  Larger sizes return
+ * MRF_EINVAL with a message, before any launch.  The first call
  * on a device looks up the array's device address (cudaGetSymbolAddress) with that device
  * current; make that first call before any stream capture.  All calls share the one array, so
  * calls that overlap on the GPU (other streams, other threads) race; serialise them.  The call
@@ -469,7 +477,8 @@ mrf_status mrf_lut(const mrf_dict* dict, const int32_t* idx, int64_t n, float* p
  * recent launch on this dictionary.
  */
 typedef struct mrf_tune {
-    int32_t bf16_cluster;      /* CTAs per cluster sharing atom blocks by multicast: 1, 2, 4 */
+    int32_t bf16_cluster;      /* CTAs per cluster co-scheduled on the same atom blocks, each
+                                  loading its own copy (no multicast): 1, 2, 4; default 1 */
     int32_t bf16_live_tiles;   /* voxel tiles (128 rows) kept live per super-group, >= 1 */
     int32_t bf16_splits;       /* atom splits of the BF16 search, >= 1 */
     int32_t fp32_splits;       /* atom splits of the FP32 search, >= 1 */
@@ -483,8 +492,8 @@ typedef struct mrf_tune {
                                   L = 1480): shorter lists fit more warps per SM, longer lists
                                   route fewer voxels to the exhaustive search */
     int32_t bf16_pair;         /* 1: the tensor-core search on CTA pairs (2-SM MMA, M = 256,
-                                  each CTA staging half of every atom block) instead of clusters
-                                  sharing atom blocks by multicast (bf16_cluster is then ignored);
+                                  each CTA staging half of every atom block) instead of single
+                                  CTAs or clusters (bf16_cluster is then ignored);
                                   0 = the library's default */
     int32_t tree_order;        /* cover-tree queries of a warm-started search: 1 = processed in
                                   the order of their warm-start atom's tree position, so that

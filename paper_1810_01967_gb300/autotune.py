@@ -1,8 +1,9 @@
 """Launch-geometry autotuner for the tensor-core search (mrf_get_tune / mrf_set_tune).
 
-The search kernel's geometry has three knobs: the cluster size C (CTAs sharing every atom block
-by TMA multicast), the number of voxel tiles kept live per super-group (how many query tiles
-the persistent clusters sweep together, i.e. the L2 working set), and the atom split S (work
+The search kernel's geometry has three knobs: the cluster size C (CTAs co-scheduled on the
+same atom blocks, each loading its own copy with plain TMA tile loads), the number of voxel
+tiles kept live per super-group (how many query tiles the persistent clusters sweep together,
+i.e. the L2 working set), and the atom split S (work
 units per voxel tile; 0 lets the library pick it from its makespan model).  `tune` times
 mrf_project on the caller's queries for each combination with CUDA events on the current
 stream, keeps the fastest, applies it to the dictionary and records it in a JSON cache keyed by

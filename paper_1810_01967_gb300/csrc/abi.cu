@@ -886,7 +886,8 @@ mrf_status mrf_profile_read(double* ms, int64_t* launches, int32_t n_stages) {
     return MRF_OK;
 }
 
-mrf_status mrf_reconstruct(mrf_dict* D, const mrf_op* op, const void* Y,
+namespace {
+mrf_status reconstruct_dev(mrf_dict* D, const mrf_op* op, const void* Y,
                            const mrf_recon_opts* ropts, void* X_out, int32_t* idx_out,
                            void* rho_out, float* params_out, mrf_stats* stats, void* stream) {
     if (!D) return fail(MRF_EINVAL, "dict is NULL");
@@ -993,6 +994,72 @@ mrf_status mrf_reconstruct(mrf_dict* D, const mrf_op* op, const void* Y,
     if (rho_tmp) cudaFree(rho_tmp);
     if (s != MRF_OK) return s;
     return s2;
+}
+
+// Host memory (pinned or pageable) as opposed to memory a kernel of this device can address.
+bool is_host_ptr(const void* p) {
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return true;
+    }
+    return a.type == cudaMemoryTypeHost || a.type == cudaMemoryTypeUnregistered;
+}
+}  // namespace
+
+// Whole reconstruction; host buffers (pinned or pageable) among Y and the outputs are staged
+// through device buffers allocated for the call, with every copy inside the call.
+mrf_status mrf_reconstruct(mrf_dict* D, const mrf_op* op, const void* Y,
+                           const mrf_recon_opts* ropts, void* X_out, int32_t* idx_out,
+                           void* rho_out, float* params_out, mrf_stats* stats, void* stream) {
+    if (!D) return fail(MRF_EINVAL, "dict is NULL");
+    MRF_TRY(check_op(op));
+    if (!Y || !X_out || !idx_out) return fail(MRF_EINVAL, "Y, X_out and idx_out are required");
+    const bool hY = is_host_ptr(Y), hX = is_host_ptr(X_out), hI = is_host_ptr(idx_out);
+    const bool hR = rho_out && is_host_ptr(rho_out);
+    const bool hP = params_out && is_host_ptr(params_out);
+    if (!hY && !hX && !hI && !hR && !hP)
+        return reconstruct_dev(D, op, Y, ropts, X_out, idx_out, rho_out, params_out, stats, stream);
+    cudaStream_t st = S_(stream);
+    const int64_t n = static_cast<int64_t>(op->Ny) * op->Nx;
+    const size_t cnt = static_cast<size_t>(n) * op->L;
+    const bool resume = ropts && ropts->resume;
+    float2 *dY = nullptr, *dX = nullptr, *dR = nullptr;
+    int32_t* dI = nullptr;
+    float* dP = nullptr;
+    auto release = [&]() {
+        void* ptrs[] = {dY, dX, dR, dI, dP};
+        for (void* q : ptrs)
+            if (q) cudaFree(q);
+    };
+    mrf_status s = MRF_OK;
+    auto run = [&]() -> mrf_status {
+        if (hY) MRF_TRY(dalloc(&dY, cnt));
+        if (hX) MRF_TRY(dalloc(&dX, cnt));
+        if (hI) MRF_TRY(dalloc(&dI, static_cast<size_t>(n)));
+        if (hR) MRF_TRY(dalloc(&dR, static_cast<size_t>(n)));
+        if (hP) MRF_TRY(dalloc(&dP, static_cast<size_t>(n) * (D->P > 0 ? D->P : 1)));
+        if (hY) MRF_CUDA_TRY(cudaMemcpyAsync(dY, Y, sizeof(float2) * cnt, cudaMemcpyHostToDevice, st));
+        if (hX && resume)
+            MRF_CUDA_TRY(cudaMemcpyAsync(dX, X_out, sizeof(float2) * cnt, cudaMemcpyHostToDevice, st));
+        if (hI && resume)
+            MRF_CUDA_TRY(cudaMemcpyAsync(dI, idx_out, sizeof(int32_t) * n, cudaMemcpyHostToDevice, st));
+        MRF_TRY(reconstruct_dev(D, op, hY ? dY : Y, ropts, hX ? dX : X_out, hI ? dI : idx_out,
+                                hR ? static_cast<void*>(dR) : rho_out, hP ? dP : params_out,
+                                stats, stream));
+        if (hX) MRF_CUDA_TRY(cudaMemcpyAsync(X_out, dX, sizeof(float2) * cnt, cudaMemcpyDeviceToHost, st));
+        if (hI) MRF_CUDA_TRY(cudaMemcpyAsync(idx_out, dI, sizeof(int32_t) * n, cudaMemcpyDeviceToHost, st));
+        if (hR) MRF_CUDA_TRY(cudaMemcpyAsync(rho_out, dR, sizeof(float2) * n, cudaMemcpyDeviceToHost, st));
+        if (hP)
+            MRF_CUDA_TRY(cudaMemcpyAsync(params_out, dP, sizeof(float) * n * D->P,
+                                         cudaMemcpyDeviceToHost, st));
+        MRF_CUDA_TRY(cudaStreamSynchronize(st));
+        return MRF_OK;
+    };
+    s = run();
+    cudaStreamSynchronize(st);
+    release();
+    return s;
 }
 
 void mrf_debug_fail_alloc(int32_t k) { g_fail_alloc_after.store(k < 0 ? -1 : k); }

@@ -9,11 +9,12 @@
 // same TMEM lane, so the epilogue thread that owns the row forms |c|^2 / ||D_j||^2 without any
 // data exchange and keeps a sorted top-K in registers.  Scores never reach global memory.
 //
-// Clusters of C CTAs work on C consecutive voxel tiles against the same atom blocks: each CTA
-// loads 1/C of every atom block and multicasts it to the whole cluster, so a block crosses L2
-// once per cluster.  Persistent clusters walk work units (atom split s, voxel-tile group g); the
-// unit order keeps a few dozen voxel tiles live at a time (super-groups of PG groups, all splits)
-// so the query tiles being re-read stay resident in L2 while the atom blocks stream.
+// Clusters of C CTAs (default C = 1) work on C consecutive voxel tiles against the same atom
+// blocks at the same time; every CTA loads its own copy of each atom block with a plain TMA
+// tile load (no multicast), so the second and later reads of a block are L2 hits.  Persistent
+// clusters walk work units (atom split s, voxel-tile group g); the unit order keeps a few dozen
+// voxel tiles live at a time (super-groups of PG groups, all splits) so the query tiles being
+// re-read stay resident in L2 while the atom blocks stream.
 // Warp roles: warp 0 = TMA producer, warp 1 = TMEM owner and MMA issuer, warps 2..5 = epilogue
 // (TMEM lanes 32 (w mod 4) ...).  4-stage shared-memory ring (48 KB per stage: A 128 rows and
 // B 256 rows of 128 bytes = 64 BF16 or 128 E4M3 elements, 128-byte swizzle), double-buffered
@@ -156,14 +157,11 @@ k_tc_topk(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
     // with a device-side voxel count (lists built on the device) the tiles past it are skipped
     const int64_t nact = count ? min(static_cast<int64_t>(*count), n) : n;
     const int nk = (Kp + EK - 1) / EK;
-    constexpr uint16_t kMask = static_cast<uint16_t>((1u << C) - 1u);
-    constexpr int SLICE_ROWS = BN / C;
-    constexpr int SLICE_BYTES = B_BYTES / C;
 
     if (threadIdx.x == 0) {
         for (int i = 0; i < STAGES; ++i) {
             mrfk::mbar_init(&sh->full[i], 1);
-            mrfk::mbar_init(&sh->empty[i], C);
+            mrfk::mbar_init(&sh->empty[i], 1);
         }
         for (int i = 0; i < 2; ++i) {
             mrfk::mbar_init(&sh->tfull[i], 1);
@@ -213,22 +211,16 @@ k_tc_topk(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
                         mrfk::mbar_arrive_expect_tx(&sh->full[stage], STAGE_BYTES);
                         mrfk::tma_load_2d(sa, &tmA, &sh->full[stage], kc * EK,
                                           static_cast<int32_t>(m * BM));
-                        if (C > 1)
-                            mrfk::tma_load_2d_mc(sa + A_BYTES + rank * SLICE_BYTES, &tmB,
-                                                 &sh->full[stage], kc * EK,
-                                                 static_cast<int32_t>(b * BN + rank * SLICE_ROWS),
-                                                 kMask);
-                        else
-                            mrfk::tma_load_2d(sa + A_BYTES, &tmB, &sh->full[stage], kc * EK,
-                                              static_cast<int32_t>(b * BN));
+                        mrfk::tma_load_2d(sa + A_BYTES, &tmB, &sh->full[stage], kc * EK,
+                                          static_cast<int32_t>(b * BN));
                         slot_used[stage] = true;
                         slot_phase[stage] = phase;
                         if (++stage == STAGES) { stage = 0; phase ^= 1u; }
                     }
                 }
             }
-            // Before the CTA may leave: every fill of its slots has landed, and every consumer
-            // of the cluster has released them (their commit arrivals target this CTA).
+            // Before the CTA may leave: every fill of its slots has landed, and its MMAs have
+            // released them.
             for (int i = 0; i < STAGES; ++i) {
                 if (!slot_used[i]) continue;
                 if (sh->abort) mrfk::mbar_wait(&sh->full[i], slot_phase[i]);
@@ -269,8 +261,7 @@ k_tc_topk(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
                             else
                                 mrfk::mma_bf16(dt, da, db, IDESC, (kc > 0 || k > 0) ? 1u : 0u);
                         }
-                        if (C > 1) mrfk::mma_commit_mc(&sh->empty[stage], kMask);
-                        else mrfk::mma_commit(&sh->empty[stage]);
+                        mrfk::mma_commit(&sh->empty[stage]);
                         any = true;
                         if (++stage == STAGES) { stage = 0; phase ^= 1u; }
                     }
@@ -748,7 +739,7 @@ int choose_splits(int64_t NG, int64_t nblk, int64_t G) {
     return best;
 }
 
-constexpr int kDefaultCluster = 2;     // CTAs sharing each atom block by multicast
+constexpr int kDefaultCluster = 1;     // CTAs co-scheduled on the same atom blocks
 constexpr int64_t kDefaultLive = 32;   // voxel tiles kept live per super-group (~16 MB, L=1000)
 
 int cluster_of(const mrf_dict* D) {
@@ -809,7 +800,7 @@ mrf_status launch_tc(bool f8, const void* zq, const float* qs, int64_t n, mrf_di
     const int Kp = f8 ? D->Kp8 : D->Kp;
     CUtensorMap ta, tb;
     MRF_TRY(tma_map_k128(&ta, zq, n, Kp, BM, f8));
-    MRF_TRY(tma_map_k128(&tb, op, D->nblk * 256, Kp, BN / C, f8));
+    MRF_TRY(tma_map_k128(&tb, op, D->nblk * 256, Kp, pair ? BN / 2 : BN, f8));
     const int64_t Mt = (n + BM - 1) / BM;
     const int64_t live = D->tune.bf16_live_tiles > 0 ? D->tune.bf16_live_tiles : kDefaultLive;
     Sched sc;

@@ -68,18 +68,6 @@ __device__ __forceinline__ void tma_load_2d(void* smem_dst, const void* desc, ui
         : "memory");
 }
 
-// Multicast variant: the box lands at the same shared-memory offset, and its transaction bytes
-// on the same mbarrier offset, in every CTA of the cluster whose bit is set in `mask`.
-__device__ __forceinline__ void tma_load_2d_mc(void* smem_dst, const void* desc, uint64_t* bar,
-                                               int32_t x, int32_t y, uint16_t mask) {
-    asm volatile(
-        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
-        ".multicast::cluster [%0], [%1, {%2, %3}], [%4], %5;"
-        ::"r"(smem_u32(smem_dst)), "l"(reinterpret_cast<uint64_t>(desc)), "r"(x), "r"(y),
-          "r"(smem_u32(bar)), "h"(mask)
-        : "memory");
-}
-
 // CTA-pair variant: the box lands in this CTA's shared memory and its transaction bytes are
 // reported to the mbarrier at shared::cluster address `bar_cluster`, which may belong to the
 // peer CTA of the pair (cta_group::2).
@@ -218,13 +206,6 @@ __device__ __forceinline__ void mma_commit(uint64_t* bar) {
     asm volatile(
         "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
         ::"r"(smem_u32(bar)) : "memory");
-}
-// As mma_commit, arriving on the mbarrier at the same offset in every CTA set in `mask`.
-__device__ __forceinline__ void mma_commit_mc(uint64_t* bar, uint16_t mask) {
-    asm volatile(
-        "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64"
-        " [%0], %1;"
-        ::"r"(smem_u32(bar)), "h"(mask) : "memory");
 }
 // 32 lanes x 32 consecutive 32-bit columns: thread i of the warp gets row (lane base + i).
 __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
