@@ -391,6 +391,58 @@ def reconstruction_quality(mrf, D, op, p, dic, dev, stream, iters: int, fp32: bo
     return out
 
 
+def peaks_sustained() -> tuple[float, str]:
+    pk = measured_peaks()
+    return (float(pk.get("bf16_tflops_sustained", pk.get("bf16_tflops"))),
+            pk["_source"] + " sustained bf16")
+
+
+def exact_tc_leg(mrf, D, op, AHY, n, d, L, stream, peak, steps: int = 5) -> dict:
+    """The exact tensor-core form (split-BF16, certified) on the same slice: `steps` BLIP
+    iterations from X = 0 timed with CUDA events, then the same steps with the stage profiler
+    for the search kernel's duration and the voxels certification sent to the FP32 search.
+    Roofline: 8 L flop per pair against a third of the sustained BF16 peak (three products)."""
+    import torch
+    X = torch.zeros((n, L), dtype=torch.complex64, device=AHY.device)
+    idx = torch.zeros(n, dtype=torch.int32, device=AHY.device)
+    rho = torch.empty(n, dtype=torch.complex64, device=AHY.device)
+    o = mrf.proj_opts(mode="bf16x3", certify=True)
+    mrf.ipg_step(D, op, AHY, X, 1.0, idx, rho, opts=o)          # warm-up (scratch, maps)
+    X.zero_()
+    idx.zero_()
+    torch.cuda.synchronize()
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    for _ in range(steps):
+        mrf.ipg_step(D, op, AHY, X, 1.0, idx, rho, opts=o)
+    b.record(stream)
+    torch.cuda.synchronize()
+    ms = a.elapsed_time(b) / steps
+    X.zero_()
+    idx.zero_()
+    mrf.profile_enable(True)
+    unc = []
+    for _ in range(steps):
+        st = mrf.ipg_step(D, op, AHY, X, 1.0, idx, rho, opts=o, stats=True)
+        unc.append(int(st["n_uncertified"]))
+    torch.cuda.synchronize()
+    prof = mrf.profile_read()
+    mrf.profile_enable(False)
+    sm, sl = prof["search_tc"]
+    fl = 8.0 * L * n * d
+    ach = fl * sl / (sm / 1e3) / 1e12 if sm else 0.0
+    pk, src = peak
+    return {"matches_per_s": n * d / (ms / 1e3), "ms_per_iteration": ms, "iterations": steps,
+            "uncertified_voxels_per_iteration": unc,
+            "uncertified_fraction_max": max(unc) / n if unc else None,
+            "stage_ms_per_iteration": {k: v[0] / steps for k, v in prof.items()},
+            "roofline": {"bound": "tensor", "achieved": ach, "peak": pk / 3.0,
+                         "unit": "TFLOP/s", "frac": ach / (pk / 3.0), "kernel": "k_tc_topk (split)",
+                         "peak_source": src + " / 3 (three BF16 products per pair)",
+                         "flops_per_launch": fl}}
+
+
 def run_profile_case(args) -> None:
     """Projection only (mrf_project) on N voxels of the workload's slice: the small case for
     kernel-level ncu captures (about 2 GB on the device).  Exhaustive modes project the first
@@ -851,7 +903,7 @@ def run_ours(args) -> None:
     n = Ny * Nx
     dev = torch.device("cuda", local)
     stream = torch.cuda.current_stream()
-    D = mrf.build_dict_index(atoms, params, pack_fp8=True)
+    D = mrf.build_dict_index(atoms, params, pack_fp8=True, pack_bf16x3=True)
     D.reserve(n)
     mask = torch.from_numpy(p["masks"]).to(dev)
     op = mrf.make_op(Ny, Nx, L, mask)
@@ -863,7 +915,8 @@ def run_ours(args) -> None:
     idx = torch.zeros(n, dtype=torch.int32, device=dev)
     rho = torch.empty(n, dtype=torch.complex64, device=dev)
     prm = torch.empty((n, params.shape[1]), dtype=torch.float32, device=dev)
-    opts = mrf.proj_opts(mode=args.mode, certify=False)
+    exact = args.mode == "bf16x3"        # the exact tensor-core form runs certified
+    opts = mrf.proj_opts(mode=args.mode, certify=exact)
     tuned = None
     if args.autotune and args.mode in ("bf16", "fp8"):
         from paper_1810_01967_gb300 import autotune
@@ -927,6 +980,11 @@ def run_ours(args) -> None:
     h2d = Yh.numel() * 8
     d2h = n * L * 8 + n * 4 + n * 8 + n * params.shape[1] * 4
     del Yh, Xh
+    # ------------------------------------------------------------- exact tensor-core leg
+    exact_leg = None
+    if rank == 0 and not exact and not args.no_exact:
+        exact_leg = exact_tc_leg(mrf, D, op, AHY, n, d, L, stream, peaks_sustained(),
+                                 steps=min(args.steps, 5))
     # ------------------------------------------------------------- FP32 exact comparator
     fp32_rate = None
     if args.fp32_sample > 0 and rank == 0:
@@ -956,14 +1014,17 @@ def run_ours(args) -> None:
     # ------------------------------------------------------------- report
     peaks = measured_peaks()
     value = world * n * d * args.steps / (ms_max / 1e3)
-    search_ms, search_launches = prof["search_tc"] if args.mode in ("bf16", "fp8") else prof["search_fp32"]
+    tc = args.mode in ("bf16", "fp8", "bf16x3")
+    search_ms, search_launches = prof["search_tc"] if tc else prof["search_fp32"]
     flops_per_launch = 8.0 * L * n * d
     achieved = flops_per_launch * search_launches / (search_ms / 1e3) / 1e12 if search_ms else 0.0
-    if args.mode in ("bf16", "fp8"):
+    if tc:
         peak = float(peaks.get("bf16_tflops_sustained", peaks.get("bf16_tflops")))
         src = peaks["_source"] + " sustained bf16"
         if args.mode == "fp8":
             peak, src = 2.0 * peak, src + " x 2 (nominal fp8 / bf16 dense ratio, 4.5 / 2.25)"
+        if args.mode == "bf16x3":
+            peak, src = peak / 3.0, src + " / 3 (three BF16 products per voxel-atom pair)"
         roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                 "frac": achieved / peak,
                 "traffic": traffic_per_launch(n, d, args.mode),
@@ -997,12 +1058,14 @@ def run_ours(args) -> None:
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": {"bf16": "bf16", "fp8": "fp8_e4m3", "fp32": "f32"}[args.mode],
+            "dtype": {"bf16": "bf16", "fp8": "fp8_e4m3", "fp32": "f32",
+                      "bf16x3": "bf16x3 (split bf16, f32 accumulate)"}[args.mode],
             "data": "synthetic",
             "config": {"workload": WORKLOAD, "n_voxels": n, "L": L, "d": d,
                        "step": "one BLIP iteration (ipg_step) + look-up table",
                        "projection": args.mode,
-                       "topk": {"fp32": 8, "bf16": 16, "fp8": 32}[args.mode], "certify": False,
+                       "topk": {"fp32": 8, "bf16": 16, "fp8": 32, "bf16x3": 32}[args.mode],
+                       "certify": exact,
                        "l2": "inputs larger than L2 (BF16 dictionary operand 800 MB)"},
             "roofline": roof, "cpu_baseline": cpu,
             "e2e": {"value": world * n * d * e2e_steps / e2e_s, "unit": UNIT,
@@ -1019,6 +1082,7 @@ def run_ours(args) -> None:
                       "cpu_baseline_1thread": cpu1,
                       "autotune": tuned,
                       "fp32_exact_matches_per_s": fp32_rate,
+                      "exact_tc": exact_leg,
                       "fp32_sample_voxels": args.fp32_sample}}
     print(json.dumps(line), flush=True)
     if world > 1:
@@ -1036,7 +1100,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--mode", default="bf16",
-                    choices=["bf16", "fp8", "fp32", "covertree", "gradient", "mlp", "learned"],
+                    choices=["bf16", "fp8", "fp32", "bf16x3", "covertree", "gradient", "mlp",
+                             "learned"],
                     help="projection of the timed step (covertree, gradient, mlp, learned: "
                          "--profile-case only)")
     ap.add_argument("--autotune", action="store_true",
@@ -1047,6 +1112,8 @@ def main():
                     help="slices64: keep the library's default search geometry")
     ap.add_argument("--fp32-sample", type=int, default=0)
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-exact", action="store_true",
+                    help="skip the exact tensor-core (split-BF16) leg of the default run")
     ap.add_argument("--workload", default="slice", choices=["slice", "slices64", "tree1m"],
                     help="slice: the BLIP-iteration bench; slices64: the batching form; "
                          "tree1m: the cover tree on the million-atom dictionary")

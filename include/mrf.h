@@ -55,7 +55,13 @@ typedef enum mrf_proj_mode {
                                  exactly in FP32, near-ties in extended precision */
     MRF_PROJ_FP8 = 2,         /* exhaustive, FP8 e4m3 tensor cores, rescored as BF16 */
     MRF_PROJ_COVERTREE = 3,   /* cover-tree (1+eps)-ANNS, Algorithm 1 (§4.1) */
-    MRF_PROJ_LEARNED = 4      /* MLP proposal + exact neighbourhood rescore + fallback */
+    MRF_PROJ_LEARNED = 4,     /* MLP proposal + exact neighbourhood rescore + fallback */
+    MRF_PROJ_BF16X3 = 5       /* exact exhaustive projection on the tensor cores: split-BF16
+                                 operands (x = hi + lo, three products per pair in one FP32
+                                 accumulation), top-K (default 32) rescored exactly, every voxel
+                                 certified against its own error bound (see cert_margin) and
+                                 the uncertified ones searched in FP32; needs
+                                 mrf_index_opts.pack_bf16x3 */
 } mrf_proj_mode;
 
 /* The cone of eq. model/conedef.  COMPLEX: X_v = rho D_j, rho complex, j maximises
@@ -80,7 +86,9 @@ typedef struct mrf_index_opts {
                               query the same way, project with the real positive density and
                               restore the query's phase, so rho = gamma e^{i(beta_v - alpha_j)}.
                               Densities are always reported relative to the atoms as given. */
-    int32_t reserved[2];
+    int32_t pack_bf16x3;   /* build the split-BF16 operand of MRF_PROJ_BF16X3 (default 0):
+                              3 x the BF16 operand's memory (2.4 GB for 100k atoms at L = 1000) */
+    int32_t reserved[1];
 } mrf_index_opts;
 
 typedef struct mrf_proj_opts {
@@ -89,8 +97,9 @@ typedef struct mrf_proj_opts {
     int32_t topk;          /* candidates kept per voxel by the exhaustive kernels, 1..32
                               (rounded up to 8, 16 or 32; FP32 at most 16); 0 = mode default
                               (8 for FP32, 16 for BF16, 32 for FP8, whose coarser scores need
-                              the longer list to hold the best atom) */
-    int32_t certify;       /* BF16/FP8: recompute voxels whose k-th candidate is within
+                              the longer list to hold the best atom, and 32 for BF16X3, whose
+                              flat background voxels have many atoms inside their bound) */
+    int32_t certify;       /* BF16/FP8/BF16X3: recompute voxels whose k-th candidate is within
                               cert_margin of the best with the FP32 exact kernel (default 1) */
     float   tie_tol;       /* candidates whose normalised correlation |D_j^H Z_v| /
                               (||D_j|| ||Z_v||) is within this absolute distance of the best
@@ -101,7 +110,13 @@ typedef struct mrf_proj_opts {
                               rounding) + 2L 2^-24 (FP32 accumulation), or for FP8
                               2 u8 + u8^2 + 2L 2^-13 with u8 = 2^-4 + sqrt(2L) 2^-10 / 224
                               (E4M3 rounding of rows scaled into (224, 448]; 13-bit partial
-                              sums assumed) (default 0) */
+                              sums assumed); for MRF_PROJ_BF16X3 each voxel's own bound
+                              (operand part rigorous from the stored split residuals:
+                              ||z_lo|| A_l + ||z_hi + z_lo|| A_e + ||e_z||, with A_l, A_e the
+                              largest residual norms of the atoms; accumulation part from a
+                              model of one FP32 rounding per MMA instruction, the small
+                              products summed first) plus the FP32 rescore's bound
+                              (default 0) */
     float   eps;           /* cover tree (1+eps) approximation (default 0) */
     float   fallback_thr;  /* learned proposal: normalised correlation threshold (0.98) */
     float   tree_route;    /* cover tree: a voxel whose candidate list exceeds 64 entries while
@@ -239,6 +254,23 @@ mrf_status mrf_dict_check(mrf_dict* dict, void* stream);
 mrf_status mrf_project(mrf_dict* dict, const void* Z, int64_t n, const mrf_proj_opts* opts,
                        const int32_t* warm_idx, int32_t* idx_out, void* rho_out, void* X_out,
                        mrf_stats* stats, void* stream);
+
+/*
+ * Candidate lists of the tensor-core matched filter, before any rescore (diagnostics and the
+ * error-bound tests): for modes MRF_PROJ_BF16, MRF_PROJ_FP8 and MRF_PROJ_BF16X3 the kernel's K
+ * best atoms of each voxel (K = the mode's topk) with one atom split, in descending kernel
+ * score, ties to the smallest index.  Queries are used as given (no phase alignment).
+ *   Z          device complex64 [n][L]
+ *   score_out  device float32 [n][K]: |c~|^2 (complex cone) or Re c~ (real cone), c~ the
+ *              kernel's correlation of the voxel with the normalised atom D_j / ||D_j||
+ *   idx_out    device int32 [n][K]: the atoms (-1 for slots past d)
+ *   bound_out  device float32 [n] or NULL: the bound of |c~ - c| / ||Z_v|| the library uses
+ *              for that mode (the voxel's own bound for MRF_PROJ_BF16X3)
+ * Errors: MRF_EINVAL (other modes, null outputs), MRF_EUNSUPPORTED (operand not packed).
+ */
+mrf_status mrf_search_candidates(mrf_dict* dict, const void* Z, int64_t n,
+                                 const mrf_proj_opts* opts, float* score_out, int32_t* idx_out,
+                                 float* bound_out, void* stream);
 
 /* A(X) = P_Omega F X: X device complex64 [n][L] -> Y device complex64 [Ny][Nx][L] (lines
  * outside Omega_t are written as zero). */

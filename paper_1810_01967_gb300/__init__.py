@@ -88,7 +88,7 @@ class Dictionary:
     def __init__(self, atoms, params=None, grid_shape=None, pack_bf16: bool = True,
                  build_tree: bool = False, tree_cone: str = "complex",
                  tree_dup_tol: float = 1e-5, stream=None, pack_fp8: bool = False,
-                 phase_align: bool = False):
+                 phase_align: bool = False, pack_bf16x3: bool = False):
         import numpy as np
         d, L = atoms.shape
         o = IndexOpts()
@@ -96,6 +96,7 @@ class Dictionary:
         o.pack_bf16 = int(pack_bf16)
         o.pack_fp8 = int(pack_fp8)
         o.phase_align = int(phase_align)
+        o.pack_bf16x3 = int(pack_bf16x3)
         o.build_tree = int(build_tree)
         o.tree_cone = CONES[tree_cone]
         o.tree_dup_tol = tree_dup_tol
@@ -163,9 +164,9 @@ class Dictionary:
 
 def build_dict_index(atoms, params=None, grid_shape=None, pack_bf16=True, build_tree=False,
                      tree_cone="complex", tree_dup_tol=1e-5, stream=None, pack_fp8=False,
-                     phase_align=False):
+                     phase_align=False, pack_bf16x3=False):
     return Dictionary(atoms, params, grid_shape, pack_bf16, build_tree, tree_cone, tree_dup_tol,
-                      stream, pack_fp8, phase_align)
+                      stream, pack_fp8, phase_align, pack_bf16x3)
 
 
 def tree_build_host(atoms, cone: str = "complex", dup_tol: float = 1e-5) -> dict:
@@ -197,6 +198,16 @@ def project(D: Dictionary, Z, idx_out, rho_out=None, X_out=None, warm_idx=None, 
                              _ptr(rho_out), _ptr(X_out), C.byref(st) if st else None,
                              _stream(stream)))
     return st.as_dict() if st else None
+
+
+def search_candidates(D: Dictionary, Z, score_out, idx_out, bound_out=None, opts=None,
+                      stream=None) -> None:
+    """The tensor-core kernel's K best atoms per voxel before any rescore
+    (mrf_search_candidates): score_out float32 [n][K], idx_out int32 [n][K], bound_out float32
+    [n] or None."""
+    o = opts or proj_opts(mode="bf16")
+    _check(lib().mrf_search_candidates(D.handle, _ptr(Z), Z.shape[0], C.byref(o), _ptr(score_out),
+                                       _ptr(idx_out), _ptr(bound_out), _stream(stream)))
 
 
 def forward(op: Op, X, Y, stream=None) -> None:

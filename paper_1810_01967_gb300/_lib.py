@@ -14,14 +14,15 @@ LIB_PATH = os.path.join(HERE, "_build", "libmrf.so")
 
 MRF_OK, MRF_EINVAL, MRF_ENOMEM, MRF_ECUDA, MRF_ENONFINITE, MRF_ETIMEOUT, \
     MRF_EUNSUPPORTED, MRF_EINTERNAL = range(8)
-MODES = {"fp32": 0, "bf16": 1, "fp8": 2, "covertree": 3, "learned": 4}
+MODES = {"fp32": 0, "bf16": 1, "fp8": 2, "covertree": 3, "learned": 4, "bf16x3": 5}
 CONES = {"complex": 0, "real_pos": 1}
 
 
 class IndexOpts(C.Structure):
     _fields_ = [("pack_bf16", C.c_int32), ("pack_fp8", C.c_int32), ("build_tree", C.c_int32),
                 ("tree_cone", C.c_int32), ("tree_dup_tol", C.c_float),
-                ("phase_align", C.c_int32), ("reserved", C.c_int32 * 2)]
+                ("phase_align", C.c_int32), ("pack_bf16x3", C.c_int32),
+                ("reserved", C.c_int32 * 1)]
 
 
 class TreeInfo(C.Structure):
@@ -106,6 +107,8 @@ SIGNATURES = {
     "mrf_project": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.POINTER(ProjOpts),
                               C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
                               C.POINTER(Stats), C.c_void_p]),
+    "mrf_search_candidates": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.POINTER(ProjOpts),
+                                        C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "mrf_forward": (C.c_int, [C.POINTER(Op), C.c_void_p, C.c_void_p, C.c_void_p]),
     "mrf_adjoint": (C.c_int, [C.POINTER(Op), C.c_void_p, C.c_void_p, C.c_void_p]),
     "mrf_gradient": (C.c_int, [C.c_void_p, C.POINTER(Op), C.c_void_p, C.c_void_p, C.c_float,

@@ -101,7 +101,9 @@ mrf_status check_op(const mrf_op* op) {
 
 // ------------------------------------------------------------------------------ scratch
 int topk_slots(const mrf_proj_opts* o) {
-    const int def = o->mode == MRF_PROJ_FP32_EXACT ? 8 : (o->mode == MRF_PROJ_FP8 ? 32 : 16);
+    const int def = o->mode == MRF_PROJ_FP32_EXACT
+                        ? 8
+                        : ((o->mode == MRF_PROJ_FP8 || o->mode == MRF_PROJ_BF16X3) ? 32 : 16);
     const int k = o->topk > 0 ? o->topk : def;
     if (o->mode == MRF_PROJ_FP32_EXACT) return k <= 8 ? 8 : 16;   // FP32 scores: at most 16
     return k <= 8 ? 8 : (k <= 16 ? 16 : 32);
@@ -120,6 +122,10 @@ mrf_status ensure_scratch(mrf_dict* D, int64_t n) {
     if (D->fop) {
         MRF_TRY(dalloc(&D->zq8, static_cast<size_t>(n * D->Kp8)));
         MRF_TRY(dalloc(&D->qs8, static_cast<size_t>(n)));
+    }
+    if (D->bop3) {
+        MRF_TRY(dalloc(&D->zq3, static_cast<size_t>(n * D->Kp3)));
+        MRF_TRY(dalloc(&D->zmarg, static_cast<size_t>(n)));
     }
     if (D->xprev) MRF_TRY(dalloc(&D->xprev, static_cast<size_t>(n * L)));
     if (D->aligned) MRF_TRY(dalloc(&D->qph, static_cast<size_t>(n)));
@@ -162,6 +168,10 @@ mrf_status check_proj_opts(const mrf_dict* D, const mrf_proj_opts* o) {
             return MRF_OK;
         case MRF_PROJ_FP8:
             if (!D->fop) return fail(MRF_EUNSUPPORTED, "dictionary built without the FP8 operand");
+            return MRF_OK;
+        case MRF_PROJ_BF16X3:
+            if (!D->bop3)
+                return fail(MRF_EUNSUPPORTED, "dictionary built without the split-BF16 operand");
             return MRF_OK;
         default: return fail(MRF_EINVAL, "unknown projection mode");
     }
@@ -267,6 +277,26 @@ mrf_status fp8_margin(const mrf_dict* D, const mrf_proj_opts* o, float* m) {
     return MRF_OK;
 }
 
+// Bound of the merge's FP32 rescore of one candidate, in normalised-correlation units: each lane
+// accumulates 2 ceil(L/32) fused multiply-adds, five butterfly additions join the lanes, and a
+// few roundings form the score (unit roundoff 2^-24 each, relative to sum |terms| <= ||z||).
+float rescore_bound(int L) {
+    return static_cast<float>((2.0 * ((L + 31) / 32) + 9.0) * std::ldexp(1.0, -24));
+}
+
+// Largest per-voxel bound of the split-BF16 form (the split.cu formula at the worst query
+// split, ||z_lo|| = u (1 + u), ||e_z|| = u^2, ||z_hi|| = 1 + u, u = 2^-8): the rescore window.
+float x3_bound_worst(const mrf_dict* D) {
+    const double u = std::ldexp(1.0, -8), Al = D->x3_al, Ae = D->x3_ae;
+    const double zl = u * (1 + u), ze = u * u, zh = 1 + u, dh = 1 + Al + Ae;
+    const double Kp = D->Kp3 / 3;
+    const double e_op = zl * Al + (1 + ze) * Ae + ze;
+    const double m_lo = zl * dh + zh * Al, m_hi = m_lo + zh * dh;
+    const double eps = std::ldexp(1.0, -23);
+    const double e_acc = eps * (2.0 * Kp / 16.0 * m_lo + Kp / 16.0 * m_hi);
+    return static_cast<float>((e_op + std::sqrt(2.0) * e_acc + eps) * (1.0 + 1e-6));
+}
+
 }  // namespace
 
 mrf_status dict_ensure_scratch(mrf_dict* D, int64_t n) { return ensure_scratch(D, n); }
@@ -345,6 +375,26 @@ mrf_status exhaustive_on_list(mrf_dict* D, const float2* Z, int32_t cnt, const m
 }
 
 namespace {
+// FP32 exhaustive search of the voxels the merge listed as uncertified (D->vlist, length in
+// D->nlist[0]), then their merge: the exact answer for those voxels.
+mrf_status research_uncertified(mrf_dict* D, const float2* Z, int K, const mrf_proj_opts* o,
+                                int32_t* idx_out, float2* rho_out, float2* X_out,
+                                cudaStream_t st) {
+    int32_t cnt = 0;
+    MRF_CUDA_TRY(cudaMemcpyAsync(&cnt, D->nlist, sizeof(cnt), cudaMemcpyDeviceToHost, st));
+    MRF_CUDA_TRY(cudaStreamSynchronize(st));
+    if (cnt == 0) return MRF_OK;
+    ProfScope ps5(5, 2, st);
+    const int K2 = K > 16 ? 16 : K;      // FP32 scores: 16 candidates suffice
+    const int S2 = fp32_choose_splits(cnt, D->d, D->num_sms);
+    MRF_TRY(ensure_part(D, cnt, S2, K2));
+    float* qs = static_cast<float*>(D->part);
+    int32_t* qi = reinterpret_cast<int32_t*>(qs + static_cast<size_t>(S2) * cnt * K2);
+    MRF_TRY(launch_fp32_topk(Z, D->vlist, D->nlist, cnt, D, o->cone, K2, S2, qs, qi, st));
+    return launch_merge(Z, cnt, D, o->cone, K2, S2, qs, qi, D->vlist, D->nlist, o->tie_tol, 0,
+                        0.f, idx_out, rho_out, X_out, nullptr, nullptr, D->err, D->counters, st);
+}
+
 // The projection proper.  `zq_ready` says the BF16 operand of Z is already in D->zq.
 mrf_status project_impl(mrf_dict* D, const float2* Z, int64_t n, const mrf_proj_opts* o,
                         const int32_t* warm, int32_t* idx_out, float2* rho_out, float2* X_out,
@@ -402,24 +452,37 @@ mrf_status project_impl(mrf_dict* D, const float2* Z, int64_t n, const mrf_proj_
                                  o->certify, margin, idx_out, rho_out, X_out, D->vlist,
                                  D->nlist, D->err, D->counters, st, 2.f * bound + o->tie_tol));
         }
-        if (o->certify) {
-            int32_t cnt = 0;
-            MRF_CUDA_TRY(cudaMemcpyAsync(&cnt, D->nlist, sizeof(cnt), cudaMemcpyDeviceToHost, st));
-            MRF_CUDA_TRY(cudaStreamSynchronize(st));
-            if (cnt > 0) {
-                ProfScope ps5(5, 2, st);
-                const int K2 = K > 16 ? 16 : K;      // FP32 scores: 16 candidates suffice
-                const int S2 = fp32_choose_splits(cnt, D->d, D->num_sms);
-                MRF_TRY(ensure_part(D, cnt, S2, K2));
-                float* qs = static_cast<float*>(D->part);
-                int32_t* qi = reinterpret_cast<int32_t*>(qs + static_cast<size_t>(S2) * cnt * K2);
-                MRF_TRY(launch_fp32_topk(Z, D->vlist, D->nlist, cnt, D, o->cone, K2, S2, qs, qi,
-                                         st));
-                MRF_TRY(launch_merge(Z, cnt, D, o->cone, K2, S2, qs, qi, D->vlist, D->nlist,
-                                     o->tie_tol, 0, 0.f, idx_out, rho_out, X_out, nullptr,
-                                     nullptr, D->err, D->counters, st));
-            }
+        if (o->certify) MRF_TRY(research_uncertified(D, Z, K, o, idx_out, rho_out, X_out, st));
+        return MRF_OK;
+    }
+    if (o->mode == MRF_PROJ_BF16X3) {
+        // exact form: split-BF16 correlations on the tensor cores, the top K rescored exactly,
+        // each voxel certified against its own rigorous bound, the rest searched in FP32
+        const float brs = rescore_bound(D->L);
+        {
+            ProfScope ps1(1, 1, st);
+            MRF_TRY(launch_pack_queries_x3(Z, n, D, brs, D->zq3, D->zmarg, st));
         }
+        const int S = bf16_choose_splits(D, n);
+        MRF_TRY(ensure_part(D, n, S, K));
+        float* ps = static_cast<float*>(D->part);
+        int32_t* pi = reinterpret_cast<int32_t*>(ps + static_cast<size_t>(S) * n * K);
+        {
+            ProfScope ps2(2, 1, st);
+            MRF_TRY(launch_x3_topk(D->zq3, n, D, o->cone, K, S, ps, pi, st));
+        }
+        if (o->certify) MRF_CUDA_TRY(cudaMemsetAsync(D->nlist, 0, sizeof(int32_t), st));
+        {
+            ProfScope ps4(4, 1, st);
+            // rescore window: twice the largest kernel bound, plus tie_tol
+            const float window = 2.f * x3_bound_worst(D) + o->tie_tol;
+            const bool own = !(o->cert_margin > 0.f);
+            MRF_TRY(launch_merge(Z, n, D, o->cone, K, S, ps, pi, nullptr, nullptr, o->tie_tol,
+                                 o->certify, o->cert_margin, idx_out, rho_out, X_out, D->vlist,
+                                 D->nlist, D->err, D->counters, st, window,
+                                 own ? D->zmarg : nullptr));
+        }
+        if (o->certify) MRF_TRY(research_uncertified(D, Z, K, o, idx_out, rho_out, X_out, st));
         return MRF_OK;
     }
     if (o->mode == MRF_PROJ_COVERTREE) {
@@ -593,7 +656,7 @@ void mrf_dict_free(mrf_dict* D) {
     if (D->tree) ct_free(D->tree);
     if (D->mlp) mlp_detach(D->mlp);
     void* ptrs[] = {D->atoms, D->inv_norm2, D->inv_norm, D->norm2, D->params, D->bop, D->zq, D->fop,
-                    D->zq8, D->qs8, D->v1, D->ealign, D->qph, D->zbuf,
+                    D->zq8, D->qs8, D->bop3, D->zq3, D->zmarg, D->v1, D->ealign, D->qph, D->zbuf,
                     D->wbuf, D->xprev, D->vlist, D->vlist2, D->nlist, D->part, D->err,
                     D->counters, D->red};
     for (void* p : ptrs)
@@ -652,11 +715,17 @@ mrf_status mrf_build_dict_index(const void* atoms, int64_t d, int32_t L, const f
     if ((s = launch_atom_norms(D, st)) != MRF_OK) return bail(s);
     if (o.phase_align && (s = phase_align_dictionary(D, st)) != MRF_OK) return bail(s);
     D->nblk = (d + 127) / 128;
+    D->Kp = ((2 * L + 15) / 16) * 16;
     if (o.pack_bf16) {
-        D->Kp = ((2 * L + 15) / 16) * 16;
         if ((s = dalloc(&D->bop, static_cast<size_t>(D->nblk * 256 * D->Kp))) != MRF_OK)
             return bail(s);
         if ((s = launch_pack_bop(D, st)) != MRF_OK) return bail(s);
+    }
+    if (o.pack_bf16x3) {
+        D->Kp3 = 3 * D->Kp;
+        if ((s = dalloc(&D->bop3, static_cast<size_t>(D->nblk * 256 * D->Kp3))) != MRF_OK)
+            return bail(s);
+        if ((s = launch_pack_bop3(D, st)) != MRF_OK) return bail(s);
     }
     if (o.pack_fp8) {
         D->Kp8 = ((2 * L + 31) / 32) * 32;
@@ -747,6 +816,46 @@ mrf_status mrf_project(mrf_dict* D, const void* Z, int64_t n, const mrf_proj_opt
     MRF_TRY(project_core(D, static_cast<const float2*>(Z), n, &o, warm_idx, idx_out,
                          static_cast<float2*>(rho_out), static_cast<float2*>(X_out), false, st));
     if (stats) return read_stats(D, n, stats, st);
+    return MRF_OK;
+}
+
+mrf_status mrf_search_candidates(mrf_dict* D, const void* Z, int64_t n,
+                                 const mrf_proj_opts* opts, float* score_out, int32_t* idx_out,
+                                 float* bound_out, void* stream) {
+    if (!D) return fail(MRF_EINVAL, "dict is NULL");
+    if (n < 0 || n > INT32_MAX) return fail(MRF_EINVAL, "n out of range");
+    mrf_proj_opts o;
+    if (opts) o = *opts; else mrf_default_proj_opts(&o);
+    MRF_TRY(check_proj_opts(D, &o));
+    if (o.mode != MRF_PROJ_BF16 && o.mode != MRF_PROJ_FP8 && o.mode != MRF_PROJ_BF16X3)
+        return fail(MRF_EINVAL, "candidate lists exist for the tensor-core modes only");
+    if (n == 0) return MRF_OK;
+    if (!Z || !score_out || !idx_out) return fail(MRF_EINVAL, "Z, score_out and idx_out are required");
+    cudaStream_t st = S_(stream);
+    const int K = topk_slots(&o);
+    MRF_TRY(ensure_scratch(D, n));
+    MRF_TRY(ensure_part(D, n, 1, K));
+    float* ps = static_cast<float*>(D->part);
+    int32_t* pi = reinterpret_cast<int32_t*>(ps + static_cast<size_t>(n) * K);
+    const float2* z = static_cast<const float2*>(Z);
+    if (o.mode == MRF_PROJ_BF16X3) {
+        MRF_TRY(launch_pack_queries_x3(z, n, D, 0.f, D->zq3, bound_out ? bound_out : D->zmarg, st));
+        MRF_TRY(launch_x3_topk(D->zq3, n, D, o.cone, K, 1, ps, pi, st));
+    } else if (o.mode == MRF_PROJ_FP8) {
+        MRF_TRY(launch_pack_queries_fp8(z, nullptr, n, D->L, D->Kp8, D->zq8, D->qs8, st));
+        MRF_TRY(launch_fp8_topk(D->zq8, D->qs8, n, D, o.cone, K, 1, ps, pi, st));
+        float b;
+        fp8_margin(D, &kRigorous, &b);
+        if (bound_out) MRF_TRY(launch_fill(bound_out, n, b, st));
+    } else {
+        MRF_TRY(launch_pack_queries(z, n, D->L, D->Kp, D->zq, st));
+        MRF_TRY(launch_bf16_topk(D->zq, n, D, o.cone, K, 1, ps, pi, st));
+        float b;
+        bf16_margin(D, &kRigorous, &b);
+        if (bound_out) MRF_TRY(launch_fill(bound_out, n, b, st));
+    }
+    MRF_CUDA_TRY(cudaMemcpyAsync(score_out, ps, sizeof(float) * n * K, cudaMemcpyDeviceToDevice, st));
+    MRF_CUDA_TRY(cudaMemcpyAsync(idx_out, pi, sizeof(int32_t) * n * K, cudaMemcpyDeviceToDevice, st));
     return MRF_OK;
 }
 

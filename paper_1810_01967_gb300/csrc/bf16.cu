@@ -606,7 +606,7 @@ namespace {
 
 template <int KT, int C, bool F8>
 mrf_status launch_t(const CUtensorMap& ta, const CUtensorMap& tb, int64_t n, const mrf_dict* D,
-                    int cone, Sched sc, int bps, int nclusters, float gsc, const float* qs,
+                    int Kp, int cone, Sched sc, int bps, int nclusters, float gsc, const float* qs,
                     const int32_t* count, float* part_s, int32_t* part_i, cudaStream_t st) {
     auto kern = k_tc_topk<KT, C, F8>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -624,7 +624,7 @@ mrf_status launch_t(const CUtensorMap& ta, const CUtensorMap& tb, int64_t n, con
         attr[0].val.clusterDim.z = 1;
         cfg.attrs = attr;
         cfg.numAttrs = 1;
-        e = cudaLaunchKernelEx(&cfg, kern, ta, tb, n, D->d, D->nblk, F8 ? D->Kp8 : D->Kp, cone,
+        e = cudaLaunchKernelEx(&cfg, kern, ta, tb, n, D->d, D->nblk, Kp, cone,
                                sc, bps, gsc, qs, count, part_s, part_i, D->err);
     }
     if (e != cudaSuccess) {
@@ -636,8 +636,9 @@ mrf_status launch_t(const CUtensorMap& ta, const CUtensorMap& tb, int64_t n, con
 
 template <int KT, bool F8>
 mrf_status launch_pair(const CUtensorMap& ta, const CUtensorMap& tb, int64_t n, const mrf_dict* D,
-                       int cone, Sched sc, int bps, int nclusters, float gsc, const float* qs,
-                       const int32_t* count, float* part_s, int32_t* part_i, cudaStream_t st) {
+                       int Kp, int cone, Sched sc, int bps, int nclusters, float gsc,
+                       const float* qs, const int32_t* count, float* part_s, int32_t* part_i,
+                       cudaStream_t st) {
     auto kern = k_tc_topk_pair<KT, F8>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          static_cast<int>(kSmemP));
@@ -654,7 +655,7 @@ mrf_status launch_pair(const CUtensorMap& ta, const CUtensorMap& tb, int64_t n, 
         attr[0].val.clusterDim.z = 1;
         cfg.attrs = attr;
         cfg.numAttrs = 1;
-        e = cudaLaunchKernelEx(&cfg, kern, ta, tb, n, D->d, D->nblk, F8 ? D->Kp8 : D->Kp, cone,
+        e = cudaLaunchKernelEx(&cfg, kern, ta, tb, n, D->d, D->nblk, Kp, cone,
                                sc, bps, gsc, qs, count, part_s, part_i, D->err);
     }
     if (e != cudaSuccess) {
@@ -770,25 +771,34 @@ namespace {
 
 template <int KT, bool F8>
 mrf_status launch_c(int C, const CUtensorMap& ta, const CUtensorMap& tb, int64_t n,
-                    const mrf_dict* D, int cone, Sched sc, int bps, int nc, float wts,
+                    const mrf_dict* D, int Kp, int cone, Sched sc, int bps, int nc, float wts,
                     const float* qs, const int32_t* count, float* part_s, int32_t* part_i,
                     cudaStream_t st) {
     switch (C) {
-        case 1: return launch_t<KT, 1, F8>(ta, tb, n, D, cone, sc, bps, nc, wts, qs, count, part_s, part_i, st);
-        case 2: return launch_t<KT, 2, F8>(ta, tb, n, D, cone, sc, bps, nc, wts, qs, count, part_s, part_i, st);
-        default: return launch_t<KT, 4, F8>(ta, tb, n, D, cone, sc, bps, nc, wts, qs, count, part_s, part_i, st);
+        case 1: return launch_t<KT, 1, F8>(ta, tb, n, D, Kp, cone, sc, bps, nc, wts, qs, count, part_s, part_i, st);
+        case 2: return launch_t<KT, 2, F8>(ta, tb, n, D, Kp, cone, sc, bps, nc, wts, qs, count, part_s, part_i, st);
+        default: return launch_t<KT, 4, F8>(ta, tb, n, D, Kp, cone, sc, bps, nc, wts, qs, count, part_s, part_i, st);
     }
 }
 
-// Shared launch path of both element types: operand maps, schedule, persistent grid.
-mrf_status launch_tc(bool f8, const void* zq, const float* qs, int64_t n, mrf_dict* D, int cone,
+// Operand forms of the tensor-core search.
+enum Form { FORM_BF16 = 0, FORM_FP8 = 1, FORM_X3 = 2 };
+
+// Shared launch path of every operand form: operand maps, schedule, persistent grid.  The split
+// form runs the BF16 kernel over its three-segment rows (Kp3 = 3 Kp).
+mrf_status launch_tc(int form, const void* zq, const float* qs, int64_t n, mrf_dict* D, int cone,
                      int K, int S, float* part_s, int32_t* part_i, const int32_t* count,
                      cudaStream_t st) {
     if (n == 0) return MRF_OK;
-    const void* op = f8 ? static_cast<const void*>(D->fop) : static_cast<const void*>(D->bop);
+    const bool f8 = (form == FORM_FP8);
+    const void* op = f8 ? static_cast<const void*>(D->fop)
+                        : (form == FORM_X3 ? static_cast<const void*>(D->bop3)
+                                           : static_cast<const void*>(D->bop));
     if (!op) {
         mrf_set_error(f8 ? "FP8 operand was not packed (mrf_index_opts.pack_fp8 = 0)"
-                         : "BF16 operand was not packed (mrf_index_opts.pack_bf16 = 0)");
+                         : (form == FORM_X3
+                                ? "split-BF16 operand was not packed (mrf_index_opts.pack_bf16x3 = 0)"
+                                : "BF16 operand was not packed (mrf_index_opts.pack_bf16 = 0)"));
         return MRF_EUNSUPPORTED;
     }
     if (K != 8 && K != 16 && K != 32) {
@@ -797,7 +807,7 @@ mrf_status launch_tc(bool f8, const void* zq, const float* qs, int64_t n, mrf_di
     }
     const bool pair = D->tune.bf16_pair > 0;
     const int C = pair ? 2 : cluster_of(D);
-    const int Kp = f8 ? D->Kp8 : D->Kp;
+    const int Kp = f8 ? D->Kp8 : (form == FORM_X3 ? D->Kp3 : D->Kp);
     CUtensorMap ta, tb;
     MRF_TRY(tma_map_k128(&ta, zq, n, Kp, BM, f8));
     MRF_TRY(tma_map_k128(&tb, op, D->nblk * 256, Kp, pair ? BN / 2 : BN, f8));
@@ -821,7 +831,7 @@ mrf_status launch_tc(bool f8, const void* zq, const float* qs, int64_t n, mrf_di
     D->tune.last_bf16_cluster = C;
     D->tune.last_bf16_splits = S;
     const float wts = f8 ? D->g8 : 1.f;
-#define MRF_TC_ARGS ta, tb, n, D, cone, sc, bps, nc, wts, qs, count, part_s, part_i, st
+#define MRF_TC_ARGS ta, tb, n, D, Kp, cone, sc, bps, nc, wts, qs, count, part_s, part_i, st
     if (pair) {
         if (f8)
             return K == 8 ? launch_pair<8, true>(MRF_TC_ARGS)
@@ -842,10 +852,15 @@ mrf_status launch_tc(bool f8, const void* zq, const float* qs, int64_t n, mrf_di
 mrf_status launch_bf16_topk(const __nv_bfloat16* zq, int64_t n, mrf_dict* D, int cone, int K,
                             int S, float* part_s, int32_t* part_i, cudaStream_t st,
                             const int32_t* count) {
-    return launch_tc(false, zq, nullptr, n, D, cone, K, S, part_s, part_i, count, st);
+    return launch_tc(FORM_BF16, zq, nullptr, n, D, cone, K, S, part_s, part_i, count, st);
 }
 
 mrf_status launch_fp8_topk(const uint8_t* zq8, const float* qs, int64_t n, mrf_dict* D, int cone,
                            int K, int S, float* part_s, int32_t* part_i, cudaStream_t st) {
-    return launch_tc(true, zq8, qs, n, D, cone, K, S, part_s, part_i, nullptr, st);
+    return launch_tc(FORM_FP8, zq8, qs, n, D, cone, K, S, part_s, part_i, nullptr, st);
+}
+
+mrf_status launch_x3_topk(const __nv_bfloat16* zq3, int64_t n, mrf_dict* D, int cone, int K,
+                          int S, float* part_s, int32_t* part_i, cudaStream_t st) {
+    return launch_tc(FORM_X3, zq3, nullptr, n, D, cone, K, S, part_s, part_i, nullptr, st);
 }

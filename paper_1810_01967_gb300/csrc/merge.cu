@@ -88,7 +88,8 @@ k_merge(const float2* __restrict__ Z, int64_t n_in, const int32_t* __restrict__ 
         const float* __restrict__ inv_norm2, const double* __restrict__ norm2, int64_t d,
         int L, int cone, int S, const float* __restrict__ part_s,
         const int32_t* __restrict__ part_i, float tie_tol, int certify, float cert_margin,
-        float window, int32_t* __restrict__ idx_out, float2* __restrict__ rho_out,
+        float window, const float* __restrict__ vmargin, int32_t* __restrict__ idx_out,
+        float2* __restrict__ rho_out,
         float2* __restrict__ X_out, int32_t* __restrict__ fb_list, int32_t* __restrict__ fb_n,
         uint32_t* err, unsigned long long* cnt) {
     const int lane = threadIdx.x & 31;
@@ -293,8 +294,10 @@ k_merge(const float2* __restrict__ Z, int64_t n_in, const int32_t* __restrict__ 
             atomicAdd(cnt + CNT_TIE_OVERFLOW, 1ULL);
     }
     // 4. certification of the low-precision ranking: the K-th kernel score must lie more than
-    //    cert_margin (normalised correlation) below the best exact score
-    if (certify && cj[KT - 1] >= 0 && zn2 > 0.f && cs[KT - 1] >= floor_of(cert_margin)) {
+    //    cert_margin (normalised correlation; the voxel's own margin when vmargin is given)
+    //    below the best exact score
+    if (certify && cj[KT - 1] >= 0 && zn2 > 0.f &&
+        cs[KT - 1] >= floor_of(vmargin ? vmargin[v] : cert_margin)) {
         if (lane == 0) {
             int pos = atomicAdd(fb_n, 1);
             fb_list[pos] = static_cast<int32_t>(v);
@@ -334,7 +337,7 @@ mrf_status launch_merge(const float2* Z, int64_t n, const mrf_dict* D, int cone,
                         const int32_t* nlist, float tie_tol, int certify, float cert_margin,
                         int32_t* idx_out, float2* rho_out, float2* X_out, int32_t* fb_list,
                         int32_t* fb_n, uint32_t* err, unsigned long long* counters,
-                        cudaStream_t st, float window) {
+                        cudaStream_t st, float window, const float* vmargin) {
     if (n == 0) return MRF_OK;
     dim3 grid(static_cast<unsigned>((n + WARPS - 1) / WARPS));
     if (K != 8 && K != 16 && K != 32) {
@@ -346,7 +349,8 @@ mrf_status launch_merge(const float2* Z, int64_t n, const mrf_dict* D, int cone,
     const int NL = per <= 4 ? 4 : (per <= 8 ? 8 : (per <= 16 ? 16 : 32));
     const int nl = NL < K ? NL : K;
 #define MRF_MERGE_ARGS Z, n, vlist, nlist, D->atoms, D->inv_norm2, D->norm2, D->d, D->L, cone, S, \
-        part_s, part_i, tie_tol, certify, cert_margin, window, idx_out, rho_out, X_out, fb_list,   \
+        part_s, part_i, tie_tol, certify, cert_margin, window, vmargin, idx_out, rho_out, X_out,   \
+        fb_list,                                                                                    \
         fb_n, err, counters
     if (K == 8) {
         if (nl == 4) k_merge<8, 4><<<grid, WARPS * 32, 0, st>>>(MRF_MERGE_ARGS);

@@ -50,10 +50,20 @@ struct mrf_dict {
     uint8_t* fop = nullptr;
     float g8 = 1.f;
     int32_t Kp8 = 0;
+    // Split-BF16 operand of the exact tensor-core form: the same blocks and rows, each row three
+    // segments of Kp elements, [hi | lo | hi] of the normalised atom (hi = bf16(d), lo =
+    // bf16(d - hi)), against query rows [lo | hi | hi], so one MMA chain over Kp3 = 3 Kp sums
+    // z_lo d_hi + z_hi d_lo (the small products first) + z_hi d_hi.  x3_al / x3_ae: the largest
+    // ||lo|| and ||D_j/||D_j|| - hi - lo|| over the atoms (FP64, rounded up).
+    __nv_bfloat16* bop3 = nullptr;
+    int32_t Kp3 = 0;
+    float x3_al = 0.f, x3_ae = 0.f;
     // scratch (grown on demand, or reserved up front)
     int64_t cap_n = 0;
     __nv_bfloat16* zq = nullptr;    // [cap_n][Kp]
     uint8_t* zq8 = nullptr;         // [cap_n][Kp8] FP8 queries (with the FP8 operand)
+    __nv_bfloat16* zq3 = nullptr;   // [cap_n][Kp3] split-BF16 queries (with the split operand)
+    float* zmarg = nullptr;         // [cap_n] per-voxel certification margin of the split form
     float* qs8 = nullptr;           // [cap_n] 1 / s of each FP8 query row
     float2* zbuf = nullptr;         // [cap_n][L] gradient-step output Z
     float2* wbuf = nullptr;         // [cap_n][L] FFT workspace
@@ -137,6 +147,14 @@ mrf_status launch_pack_gather(const float2* Z, const int32_t* vlist, int64_t n, 
                               const int32_t* count = nullptr);
 mrf_status launch_mask_ky(float2* W, const uint8_t* mask, int Ny, int Nx, int L,
                           cudaStream_t st);
+// split-BF16 operand of the atoms (D->bop3) and the split statistics D->x3_al / D->x3_ae
+// (synchronises `st` to read them)
+mrf_status launch_pack_bop3(mrf_dict* D, cudaStream_t st);
+// split-BF16 query rows [lo | hi | hi] and, per voxel, the rigorous error bound of the split
+// form's correlations (normalised-correlation units) plus `extra` (the rescore's bound)
+mrf_status launch_pack_queries_x3(const float2* Z, int64_t n, const mrf_dict* D, float extra,
+                                  __nv_bfloat16* zq3, float* margin, cudaStream_t st);
+mrf_status launch_fill(float* out, int64_t n, float v, cudaStream_t st);
 mrf_status launch_grad_combine(const float2* X, const float2* G, const float2* AHY, float2* Z,
                                int64_t n, int L, float mu, float g_scale, __nv_bfloat16* zq,
                                int Kp, uint32_t* err, cudaStream_t st);
@@ -162,6 +180,8 @@ mrf_status launch_bf16_topk(const __nv_bfloat16* zq, int64_t n, mrf_dict* D, int
 int bf16_choose_splits(const mrf_dict* D, int64_t n);
 mrf_status launch_fp8_topk(const uint8_t* zq8, const float* qs, int64_t n, mrf_dict* D, int cone,
                            int K, int S, float* part_s, int32_t* part_i, cudaStream_t st);
+mrf_status launch_x3_topk(const __nv_bfloat16* zq3, int64_t n, mrf_dict* D, int cone, int K,
+                          int S, float* part_s, int32_t* part_i, cudaStream_t st);
 // covertree.cu
 mrf_status ct_build_upload(mrf_dict* D, int metric, double dup_tol);
 void ct_free(CoverTreeDev* t);
@@ -199,4 +219,5 @@ mrf_status launch_merge(const float2* Z, int64_t n, const mrf_dict* D, int cone,
                         const int32_t* nlist, float tie_tol, int certify, float cert_margin,
                         int32_t* idx_out, float2* rho_out, float2* X_out, int32_t* fb_list,
                         int32_t* fb_n, uint32_t* err, unsigned long long* counters,
-                        cudaStream_t st, float window = -1.f);   // window < 0: rescore all K
+                        cudaStream_t st, float window = -1.f,    // window < 0: rescore all K
+                        const float* vmargin = nullptr);  // per-voxel cert_margin when given
