@@ -467,7 +467,7 @@ def run_profile_case(args) -> None:
         return
     tree = args.mode == "covertree"
     D = mrf.build_dict_index(dic["atoms"], dic["params"], pack_fp8=(args.mode == "fp8"),
-                             build_tree=tree)
+                             build_tree=tree, pack_bf16x3=(args.mode == "bf16x3"))
     if tree:
         fg = np.flatnonzero(p["phantom"]["labels"] >= 0)
         g = np.random.Generator(np.random.PCG64(123))
@@ -484,7 +484,8 @@ def run_profile_case(args) -> None:
         del AHY
     idx = torch.empty(n, dtype=torch.int32, device="cuda")
     rho = torch.empty(n, dtype=torch.complex64, device="cuda")
-    o = mrf.proj_opts(mode=args.mode, certify=False, eps=0.4 if tree else 0.0)
+    o = mrf.proj_opts(mode=args.mode, certify=(args.mode == "bf16x3"),
+                      eps=0.4 if tree else 0.0)
     mrf.profile_enable(True)
     for _ in range(args.steps):
         mrf.project(D, Z, idx, rho, opts=o)

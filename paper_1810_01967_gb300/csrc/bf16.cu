@@ -742,6 +742,7 @@ int choose_splits(int64_t NG, int64_t nblk, int64_t G) {
 
 constexpr int kDefaultCluster = 1;     // CTAs co-scheduled on the same atom blocks
 constexpr int64_t kDefaultLive = 32;   // voxel tiles kept live per super-group (~16 MB, L=1000)
+constexpr int64_t kDefaultLiveX3 = 8;  // the same for the split-BF16 form
 
 int cluster_of(const mrf_dict* D) {
     int c = D->tune.bf16_cluster;
@@ -812,7 +813,11 @@ mrf_status launch_tc(int form, const void* zq, const float* qs, int64_t n, mrf_d
     MRF_TRY(tma_map_k128(&ta, zq, n, Kp, BM, f8));
     MRF_TRY(tma_map_k128(&tb, op, D->nblk * 256, Kp, pair ? BN / 2 : BN, f8));
     const int64_t Mt = (n + BM - 1) / BM;
-    const int64_t live = D->tune.bf16_live_tiles > 0 ? D->tune.bf16_live_tiles : kDefaultLive;
+    // the split form's 128-atom blocks are three times longer (3 MB at L = 1000): fewer live
+    // voxel tiles keep the CTAs that stream the same atoms close enough for L2 to serve them
+    const int64_t live = D->tune.bf16_live_tiles > 0
+                             ? D->tune.bf16_live_tiles
+                             : (form == FORM_X3 ? kDefaultLiveX3 : kDefaultLive);
     Sched sc;
     sc.NG = (Mt + C - 1) / C;
     sc.S = S;

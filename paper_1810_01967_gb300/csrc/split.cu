@@ -23,8 +23,9 @@
 //     most 2^-23 (2 Kp / 16 m_lo + Kp / 16 m_hi) in each of Re c and Im c (sqrt 2 of it in |c|);
 //   epilogue: the score re^2 + im^2 with two FP32 roundings, at most 2^-23 in |c|.
 // The margin written per voxel is that bound plus `extra` (the caller adds the bound of the
-// FP32 rescore it compares against).  Rows with ||z|| below 2^-60 (where subnormal BF16 parts
-// could be flushed) are not covered by the bound; a zero row gets margin 0.
+// FP32 rescore it compares against).  Rows with ||z|| below 2^-40 (where subnormal parts and
+// the squares of the split residuals underflow) are not covered by the bound; a zero row gets
+// margin 0.
 #include <cstring>
 
 #include "mrf_internal.cuh"
@@ -115,7 +116,9 @@ __global__ void k_pack_queries_x3(const float2* __restrict__ Z, int64_t n, int L
     const int half = Kp / 2;
     const float2* z = Z + v * L;
     __nv_bfloat162* row = zq3 + v * (3 * half);
-    double zz = 0.0, ll = 0.0, ee = 0.0, hh = 0.0;
+    // squared norms in FP32 (each a sum of non-negative terms: relative error below
+    // (L / 32 + 5) 2^-24, covered by the final (1 + 2^-10) inflation of the ratios below)
+    float zz = 0.f, ll = 0.f, ee = 0.f, hh = 0.f;
     for (int t = lane; t < half; t += 32) {
         const float2 a = (t < L) ? z[t] : make_float2(0.f, 0.f);
         __nv_bfloat16 hx, lx, hy, ly;
@@ -125,20 +128,25 @@ __global__ void k_pack_queries_x3(const float2* __restrict__ Z, int64_t n, int L
         row[t] = __halves2bfloat162(lx, ly);
         row[half + t] = __halves2bfloat162(hx, hy);
         row[2 * half + t] = __halves2bfloat162(hx, hy);
-        zz += static_cast<double>(a.x) * a.x + static_cast<double>(a.y) * a.y;
-        ll += static_cast<double>(lxf) * lxf + static_cast<double>(lyf) * lyf;
-        ee += static_cast<double>(ex) * ex + static_cast<double>(ey) * ey;
-        hh += static_cast<double>(hxf) * hxf + static_cast<double>(hyf) * hyf;
+        zz = fmaf(a.x, a.x, fmaf(a.y, a.y, zz));
+        ll = fmaf(lxf, lxf, fmaf(lyf, lyf, ll));
+        ee = fmaf(ex, ex, fmaf(ey, ey, ee));
+        hh = fmaf(hxf, hxf, fmaf(hyf, hyf, hh));
     }
-    zz = warp_sumd(zz);
-    ll = warp_sumd(ll);
-    ee = warp_sumd(ee);
-    hh = warp_sumd(hh);
+    for (int o = 16; o; o >>= 1) {
+        zz += __shfl_xor_sync(0xffffffffu, zz, o);
+        ll += __shfl_xor_sync(0xffffffffu, ll, o);
+        ee += __shfl_xor_sync(0xffffffffu, ee, o);
+        hh += __shfl_xor_sync(0xffffffffu, hh, o);
+    }
     if (lane == 0 && margin) {
         float m = 0.f;
-        if (zz > 0.0) {
-            const double zn = sqrt(zz);
-            const double zl = sqrt(ll) / zn, ze = sqrt(ee) / zn, zh = sqrt(hh) / zn;
+        if (zz > 0.f) {
+            const double zn = sqrt(static_cast<double>(zz)) * (1.0 - 0x1p-10);
+            const double up = 1.0 + 0x1p-10;
+            const double zl = sqrt(static_cast<double>(ll)) * up / zn;
+            const double ze = sqrt(static_cast<double>(ee)) * up / zn;
+            const double zh = sqrt(static_cast<double>(hh)) * up / zn;
             const double dh = 1.0 + bc.Al + bc.Ae;            // bound on ||d_hi||
             const double e_op = zl * bc.Al + (1.0 + ze) * bc.Ae + ze;
             const double m_lo = zl * dh + zh * bc.Al;
