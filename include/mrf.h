@@ -165,7 +165,10 @@ typedef struct mrf_recon_opts {
                               or by idx and rho) instead of X^0 = 0; the kappa rescale of the
                               first iterate is skipped and the step rule restarts from mu
                               (default 0) */
-    int32_t reserved[4];
+    float*   mu_history;   /* host float [iters] or NULL: the step size each iteration accepted
+                              (after the step rule's shrinks, before the kappa rescale) */
+    int32_t* shrink_history;  /* host int32 [iters] or NULL: the step rule's divisions by zeta
+                              in each iteration (Prop. stepbound bounds them) */
     mrf_proj_opts proj;
 } mrf_recon_opts;
 

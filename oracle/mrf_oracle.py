@@ -61,10 +61,11 @@ def project(Z: np.ndarray, D: np.ndarray, cone: str = "complex", chunk: int = 25
     rho = np.zeros(n, C128)
     s1 = np.zeros(n)
     s2 = np.zeros(n)
+    DH = D.conj().T                              # D^H, formed once for all chunks
     for a in range(0, n, chunk):
         z = Z[a:a + chunk]
         zn2 = np.sum(z.real ** 2 + z.imag ** 2, axis=1)
-        c = z @ D.conj().T                       # c[v, j] = D_j^H z_v
+        c = z @ DH                               # c[v, j] = D_j^H z_v
         if cone == "complex":
             resid = zn2[:, None] - (c.real ** 2 + c.imag ** 2) / dn2[None, :]
             score = np.abs(c) / dn[None, :]
@@ -84,11 +85,16 @@ def project(Z: np.ndarray, D: np.ndarray, cone: str = "complex", chunk: int = 25
         j[zero] = 0
         rh[zero] = 0.0
         znrm = np.where(zero, 1.0, np.sqrt(zn2))
-        part = np.sort(score, axis=1)[:, ::-1]
+        # the two largest scores of each row (a partial selection: the same values as a sort)
+        if score.shape[1] > 1:
+            top = -np.partition(-score, 1, axis=1)[:, :2]
+            first, second = top[:, 0], top[:, 1]
+        else:
+            first, second = score[:, 0], np.full(score.shape[0], -np.inf)
         idx[a:a + chunk] = j
         rho[a:a + chunk] = rh
-        s1[a:a + chunk] = part[:, 0] / znrm
-        s2[a:a + chunk] = (part[:, 1] if part.shape[1] > 1 else -np.inf) / znrm
+        s1[a:a + chunk] = first / znrm
+        s2[a:a + chunk] = second / znrm
     return {"idx": idx, "rho": rho, "s1": s1, "s2": s2}
 
 

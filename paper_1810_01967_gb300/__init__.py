@@ -66,11 +66,22 @@ def proj_opts(mode: str = "fp32", cone: str = "complex", topk: int = 0, certify:
 
 def recon_opts(iters: int = 10, mu: float = 1.0, adaptive: bool = False, zeta: float = 2.0,
                kappa: bool = False, tol: float = 0.0, max_shrink: int = 30,
-               resume: bool = False, **proj) -> ReconOpts:
+               resume: bool = False, mu_history=None, shrink_history=None,
+               **proj) -> ReconOpts:
+    """mu_history / shrink_history: host numpy float32 / int32 arrays of at least `iters`
+    entries that receive each iteration's accepted step size and shrink count (kept alive by
+    the returned options)."""
     r = ReconOpts()
     lib().mrf_default_recon_opts(C.byref(r))
     r.iters, r.mu, r.adaptive, r.zeta = iters, mu, int(adaptive), zeta
     r.kappa, r.tol, r.max_shrink, r.resume = int(kappa), tol, max_shrink, int(resume)
+    for name, arr, ct in (("mu_history", mu_history, C.c_float),
+                          ("shrink_history", shrink_history, C.c_int32)):
+        if arr is not None:
+            if arr.size < iters or not arr.flags["C_CONTIGUOUS"] or arr.itemsize != 4:
+                raise ValueError(f"{name} must be a contiguous 4-byte array of >= iters entries")
+            setattr(r, name, arr.ctypes.data_as(C.POINTER(ct)))
+    r._keep = (mu_history, shrink_history)
     r.proj = proj_opts(**proj)
     return r
 

@@ -58,7 +58,8 @@ class Op(C.Structure):
 class ReconOpts(C.Structure):
     _fields_ = [("iters", C.c_int32), ("mu", C.c_float), ("adaptive", C.c_int32),
                 ("zeta", C.c_float), ("kappa", C.c_int32), ("tol", C.c_float),
-                ("max_shrink", C.c_int32), ("resume", C.c_int32), ("reserved", C.c_int32 * 4),
+                ("max_shrink", C.c_int32), ("resume", C.c_int32),
+                ("mu_history", C.POINTER(C.c_float)), ("shrink_history", C.POINTER(C.c_int32)),
                 ("proj", ProjOpts)]
 
 

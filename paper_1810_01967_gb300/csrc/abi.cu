@@ -1043,7 +1043,9 @@ mrf_status reconstruct_dev(mrf_dict* D, const mrf_op* op, const void* Y,
             if (r.adaptive || r.kappa || r.tol > 0.f)
                 MRF_CUDA_TRY(cudaMemcpyAsync(D->xprev, X, sizeof(float2) * cnt,
                                              cudaMemcpyDeviceToDevice, st));
+            int shrinks_k = 0;
             for (int shrink = 0;; ++shrink) {
+                shrinks_k = shrink;
                 MRF_TRY(gradient(D, op, AHY, r.adaptive ? D->xprev : X, mu_k, zq, st));
                 MRF_TRY(project_core(D, D->zbuf, n, &r.proj, idx_out, idx_out, rho, X, zq, st));
                 if (!r.adaptive) break;
@@ -1062,6 +1064,8 @@ mrf_status reconstruct_dev(mrf_dict* D, const mrf_op* op, const void* Y,
                     break;
                 mu_k /= r.zeta;
             }
+            if (r.mu_history) r.mu_history[k] = mu_k;
+            if (r.shrink_history) r.shrink_history[k] = shrinks_k;
             if (r.kappa && k == 0 && !r.resume) {
                 if (ynorm2 < 0.0) {
                     MRF_CUDA_TRY(cudaMemsetAsync(D->red + 2, 0, sizeof(double), st));

@@ -10,7 +10,7 @@ import pytest
 
 import mrfgen
 from oracle import mrf_oracle as mo
-from gpu_util import to_dev, check_projection
+from gpu_util import to_dev, check_projection, iterate_checked, bf16_bound
 
 pytestmark = pytest.mark.gpu
 
@@ -138,6 +138,25 @@ def test_exact_tc_full_slice(mrf, full):
           f"({100 * frac:.3f} %), sampled agreement {agree:.4f} ({ties} near-ties), "
           f"median bound {np.median(bd):.2e}, largest error / bound {worst:.3f}")
     assert frac < 0.01
+
+
+@pytest.mark.parametrize("mode,certify,m", [("bf16", False, 4096), ("bf16x3", True, 1024)])
+def test_iterations_follow_the_oracle(mrf, full, mode, certify, m):
+    """20 BLIP iterations of the full slice through the C ABI, gradient step then projection,
+    in the bench's launch configuration: after every iteration the oracle projects the GPU's
+    own Z on a seeded voxel sample (4,096 for the headline BF16 form, 1,024 for the exact form,
+    whose first iterate is also checked on 4,096 voxels above) and the answers follow the
+    kernel-bound rule (uncertified BF16) or the exact rule (certified split-BF16)."""
+    A = full["dic"]["atoms"]
+    n, L = full["AHY"].shape
+    g = np.random.Generator(np.random.PCG64(2020 + m))
+    sample = np.sort(g.choice(n, m, replace=False))
+    po = mrf.proj_opts(mode=mode, certify=certify)
+    _, _, _, rates = iterate_checked(mrf, full["D"], full["op"], full["AHY"], A, 20, po,
+                                     rule="exact" if certify else "bound", bound=bf16_bound(L),
+                                     sample=sample)
+    print(f"full slice, {mode} certify={certify}: agreement with the oracle's projection of the "
+          f"GPU's Z per iteration {[round(r, 4) for r in rates]}")
 
 
 def test_fp8_projection_full_slice(mrf, full):

@@ -7,7 +7,7 @@ import pytest
 import mrfgen
 from oracle import mrf_oracle as mo
 from oracle import phase as oph
-from gpu_util import to_dev, check_projection
+from gpu_util import to_dev, check_projection, iterate_checked
 
 pytestmark = pytest.mark.gpu
 
@@ -48,25 +48,33 @@ def run(mrf, D, Z, mode, cone):
     return idx.cpu().numpy(), rho.cpu().numpy(), X.cpu().numpy()
 
 
-@pytest.mark.parametrize("mode", ["fp32", "bf16"])
-def test_aligned_projection_matches_oracle(mrf, cfg1, mode):
-    dic, p, Z = cfg1
-    A = dic["atoms"]
-    D = mrf.build_dict_index(A, phase_align=True)
-    gi, gr, gX = run(mrf, D, Z, mode, "real_pos")
-    ref = oph.project_phase_aligned(Z, A)
+def check_aligned(Z, A, gi, gr, gX, v1=None, tie=2e-6):
+    """The phase-aligned real positive projection against the oracle's: the atom (exact except
+    aligned near-ties), the density gamma e^{i(beta - alpha)} relative to the atom as given and
+    X = rho D_j, within 1e-4.  Returns the exact agreement rate."""
+    ref = oph.project_phase_aligned(Z, A, v1)
     sg = aligned_scores(Z, A, gi, ref)
-    ok = (gi == ref["idx"]) | (sg >= ref["s1"] - 2e-6 * np.abs(ref["s1"]))
+    ok = (gi == ref["idx"]) | (sg >= ref["s1"] - tie * np.abs(ref["s1"]))
     assert np.all(ok), np.flatnonzero(~ok)[:10]
-    # density relative to the atom as given: gamma e^{i(beta - alpha)}
     Ad = A.astype(np.complex128)[gi]
     gam = np.maximum(sg * np.linalg.norm(Z, axis=1) / np.linalg.norm(Ad, axis=1), 0.0)
     rr = gam * ref["eb"] * ref["ea"][gi].conj()
     err = np.abs(gr - rr) / np.maximum(np.abs(rr), 1e-30)
     assert np.max(np.where(np.abs(rr) > 0, err, np.abs(gr))) < 1e-4
     Xr = rr[:, None] * Ad
-    assert np.max(np.linalg.norm(gX - Xr, axis=1) / np.maximum(np.linalg.norm(Xr, axis=1), 1e-30)) < 1e-4
-    print(f"{mode}: aligned agreement {np.mean(gi == ref['idx']):.5f}")
+    assert np.max(np.linalg.norm(gX - Xr, axis=1) /
+                  np.maximum(np.linalg.norm(Xr, axis=1), 1e-30)) < 1e-4
+    return float(np.mean(gi == ref["idx"]))
+
+
+@pytest.mark.parametrize("mode", ["fp32", "bf16"])
+def test_aligned_projection_matches_oracle(mrf, cfg1, mode):
+    dic, p, Z = cfg1
+    A = dic["atoms"]
+    D = mrf.build_dict_index(A, phase_align=True)
+    gi, gr, gX = run(mrf, D, Z, mode, "real_pos")
+    agree = check_aligned(Z, A, gi, gr, gX)
+    print(f"{mode}: aligned agreement {agree:.5f}")
 
 
 def test_complex_cone_unchanged_by_alignment(mrf, cfg1):
@@ -77,28 +85,38 @@ def test_complex_cone_unchanged_by_alignment(mrf, cfg1):
     check_projection(Z, A, gi, gr, g_X=gX)
 
 
-def test_aligned_reconstruction(mrf, cfg1):
+@pytest.mark.parametrize("mode", ["fp32", "bf16"])
+def test_aligned_reconstruction(mrf, cfg1, mode):
+    """Whole aligned reconstructions: every iteration's projection of the GPU's own Z follows
+    the oracle's phase-aligned projection (the certified forms), and the single-call
+    mrf_reconstruct reproduces the iteration-by-iteration run bit for bit.  The agreement with
+    the oracle's own aligned BLIP is printed as a report."""
     dic, p, _ = cfg1
     Ny, Nx, L = p["Ny"], p["Nx"], p["L"]
     n, iters = Ny * Nx, p["iters"]
     A = dic["atoms"]
     V1 = oph.project_phase_aligned(np.zeros((1, L)), A)["v1"]
+    D = mrf.build_dict_index(A, dic["params"], phase_align=True)
+    op = mrf.make_op(Ny, Nx, L, to_dev(p["masks"]))
+    AHY = torch.empty((n, L), dtype=torch.complex64, device="cuda")
+    mrf.adjoint(op, to_dev(p["Y"]), AHY)
+    po = mrf.proj_opts(mode=mode, cone="real_pos")
+    Xi, ii, _, rates = iterate_checked(
+        mrf, D, op, AHY, A, iters, po, cone="real_pos",
+        check=lambda Z, gi, gr, gx: check_aligned(Z, A, gi, gr, gx, V1))
+    X = torch.empty((n, L), dtype=torch.complex64, device="cuda")
+    idx = torch.empty(n, dtype=torch.int32, device="cuda")
+    mrf.reconstruct(D, op, to_dev(p["Y"]), X, idx,
+                    opts=mrf.recon_opts(iters=iters, mode=mode, cone="real_pos"))
+    torch.cuda.synchronize()
+    assert torch.equal(idx, ii) and torch.equal(X, Xi)
 
     def pf(Zv, warm):
         r = oph.project_phase_aligned(Zv, A, V1)
         return r["idx"], r["rho"]
 
     ref = mo.blip(p["Y"], p["masks"], A, Ny, Nx, iters=iters, project_fn=pf)
-    D = mrf.build_dict_index(A, dic["params"], phase_align=True)
-    op = mrf.make_op(Ny, Nx, L, to_dev(p["masks"]))
-    X = torch.empty((n, L), dtype=torch.complex64, device="cuda")
-    idx = torch.empty(n, dtype=torch.int32, device="cuda")
-    mrf.reconstruct(D, op, to_dev(p["Y"]), X, idx,
-                    opts=mrf.recon_opts(iters=iters, mode="fp32", cone="real_pos"))
     agree = float(np.mean(idx.cpu().numpy() == ref["idx"]))
     relX = np.linalg.norm(X.cpu().numpy() - ref["X"]) / np.linalg.norm(ref["X"])
-    fg = p["phantom"]["labels"] >= 0
-    t1 = {k: mo.accuracy(dic["params"][v][:, 0], p["phantom"]["T1"], fg)
-          for k, v in (("gpu", idx.cpu().numpy()), ("oracle", ref["idx"]))}
-    print(f"aligned recon: agreement {agree:.5f} relX {relX:.2e} T1 acc {t1}")
-    assert agree >= 0.99 and relX < 1e-2
+    print(f"aligned recon {mode}: per-iteration agreement {min(rates):.5f}..{max(rates):.5f}; "
+          f"end state vs the oracle's aligned BLIP {agree:.5f}, relX {relX:.2e}")
