@@ -215,11 +215,13 @@ def test_kappa_rescale_matches_oracle(mrf, cfg1):
     gi, gx = idx.cpu().numpy(), X.cpu().numpy()
     same = gi == ref["idx"]
     assert same.mean() >= 0.999, same.mean()
+    # row errors relative to the image's RMS row norm: the FP32 transforms' rounding is bounded
+    # relative to the whole transform, so weak background rows carry larger relative errors
     num = np.linalg.norm(gx[same] - ref["X"][same], axis=1)
-    den = np.maximum(np.linalg.norm(ref["X"][same], axis=1), 1e-30)
-    assert np.max(num / den) < 1e-4, np.max(num / den)
+    rms = np.sqrt(np.mean(np.sum(np.abs(ref["X"]) ** 2, axis=1)))
+    assert np.max(num / rms) < 1e-5, np.max(num / rms)
     print(f"kappa {kap:.6f}: atoms equal to the oracle's {same.mean():.5f}, "
-          f"largest per-voxel image error {np.max(num / den):.2e}")
+          f"largest row error / RMS row norm {np.max(num / rms):.2e}")
 
 
 @pytest.mark.parametrize("N", [16, 24, 32, 64, 40])
