@@ -439,6 +439,7 @@ def exact_tc_leg(mrf, D, op, AHY, n, d, L, stream, peak, steps: int = 5) -> dict
             "stage_ms_per_iteration": {k: v[0] / steps for k, v in prof.items()},
             "roofline": {"bound": "tensor", "achieved": ach, "peak": pk / 3.0,
                          "unit": "TFLOP/s", "frac": ach / (pk / 3.0), "kernel": "k_tc_topk (split)",
+                         "traffic": traffic_per_launch(n, d, "bf16x3"),
                          "peak_source": src + " / 3 (three BF16 products per pair)",
                          "flops_per_launch": fl}}
 
