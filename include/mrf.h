@@ -486,6 +486,13 @@ mrf_status mrf_svd_compress(const mrf_svd_op* so, const void* X, int64_t n, void
 mrf_status mrf_svd_expand(const mrf_svd_op* so, const void* Xc, int64_t n, void* X,
                           void* stream);
 
+/* The compressed gradient step alone (eq. gradupdate / gradcompression):
+ * Zc = Xc - mu (compress(A^H A expand(Xc)) - AHYc), all device complex64 [n][s]; the same
+ * kernels as mrf_svd_ipg_step's gradient (for power-of-two Ny the two halves of the fused
+ * y-transform kernel around the per-line s x s product, else cuFFT). */
+mrf_status mrf_svd_gradient(mrf_dict* dict_c, mrf_svd_op* so, const void* AHYc, const void* Xc,
+                            float mu, void* Zc, void* stream);
+
 /* One compressed iteration (eq. gradupdate + projection onto cone(D conj(V_s))): dict_c is the
  * index of the compressed atoms (its L must be s), AHYc = compress(A^H Y), Xc [n][s] in/out,
  * idx_io the warm start / result.  Same projection options as mrf_project. */
@@ -493,11 +500,16 @@ mrf_status mrf_svd_ipg_step(mrf_dict* dict_c, mrf_svd_op* so, const void* AHYc, 
                             float mu, const mrf_proj_opts* opts, int32_t* idx_io,
                             void* rho_out, void* stream);
 
-/* Whole compressed BLIP from Xc = 0 with a fixed step: A^H Y, compression, `iters` iterations,
- * optionally the expanded image X_out [n][L] and the look-up table params_out [n][P].
+/* Whole compressed BLIP from Xc = 0 (Algorithm 2 in C^s): A^H Y, compression, opts->iters
+ * iterations with opts->mu and, when opts->adaptive, the step rule of eq. steprule in the
+ * compressed form of §4.3, mu_k < ||Xc^{k+1} - Xc^k||^2 / ||A((Xc^{k+1} - Xc^k) V_s^T)||^2
+ * (shrinks by opts->zeta, at most opts->max_shrink), the kappa rescale of the first iterate
+ * (opts->kappa), the histories of opts->mu_history / shrink_history, then optionally the
+ * expanded image X_out [n][L] and the look-up table params_out [n][P].  opts->tol and
+ * opts->resume are not available here (MRF_EUNSUPPORTED).  Y device [Ny][Nx][L].
  * Synchronous; reports device errors. */
-mrf_status mrf_svd_reconstruct(mrf_dict* dict_c, mrf_svd_op* so, const void* Y, int32_t iters,
-                               float mu, const mrf_proj_opts* opts, void* Xc_out, void* X_out,
+mrf_status mrf_svd_reconstruct(mrf_dict* dict_c, mrf_svd_op* so, const void* Y,
+                               const mrf_recon_opts* opts, void* Xc_out, void* X_out,
                                int32_t* idx_out, void* rho_out, float* params_out,
                                void* stream);
 

@@ -50,17 +50,49 @@ def gradient_step_c(Xc, Y, masks, Ny, Nx, mu, V) -> np.ndarray:
     return np.asarray(Xc, C128) - mu * compress(mo.adjoint(R, masks, Ny, Nx), V)
 
 
-def blip_svd(Y, masks, D, V, Ny, Nx, iters, mu=1.0, cone="complex") -> dict:
+def blip_svd(Y, masks, D, V, Ny, Nx, iters, mu=1.0, cone="complex", adaptive=False, zeta=2.0,
+             kappa=False, max_shrink=60, history=False) -> dict:
     """BLIP in the compressed domain from Xc = 0: returns the compressed image Xc [n, s], the
-    atoms idx, the densities rho and the expanded image X = expand(Xc)."""
+    atoms idx, the densities rho and the expanded image X = expand(Xc).
+
+    With ``adaptive`` each iteration starts from ``mu`` and divides it by ``zeta`` while
+    mu_k >= ||Xc^{k+1} - Xc^k||^2 / ||A(expand(Xc^{k+1} - Xc^k))||^2 (the compressed form of
+    eq. steprule, §4.3), recomputing the iteration each time.  With ``kappa`` the first iterate
+    is rescaled by kappa = ||Y|| / ||A(expand(Xc^1))|| and mu by kappa (§4.3)."""
     Dc = compress(D, V)
     n, s = Ny * Nx, V.shape[1]
     Xc = np.zeros((n, s), C128)
     idx = np.zeros(n, np.int64)
     rho = np.zeros(n, C128)
-    for _ in range(iters):
-        Zc = gradient_step_c(Xc, Y, masks, Ny, Nx, mu, V)
-        r = mo.project(Zc, Dc, cone)
+    mu0 = float(mu)
+    hist = {"mu": [], "shrinks": []}
+    for k in range(iters):
+        mu_k = mu0
+        shrinks = 0
+        while True:
+            Zc = gradient_step_c(Xc, Y, masks, Ny, Nx, mu_k, V)
+            r = mo.project(Zc, Dc, cone)
+            Xn = r["rho"][:, None] * Dc[r["idx"]]
+            if not adaptive:
+                break
+            dXc = Xn - Xc
+            num = np.sum(np.abs(dXc) ** 2)
+            den = np.sum(np.abs(mo.forward(expand(dXc, V), masks, Ny, Nx)) ** 2)
+            if den == 0.0 or mu_k < num / den or shrinks >= max_shrink:
+                break
+            mu_k /= zeta
+            shrinks += 1
         idx, rho = r["idx"], r["rho"]
-        Xc = rho[:, None] * Dc[idx]
-    return {"Xc": Xc, "idx": idx, "rho": rho, "X": expand(Xc, V)}
+        if kappa and k == 0:
+            kap = np.linalg.norm(Y) / max(np.linalg.norm(mo.forward(expand(Xn, V), masks, Ny, Nx)),
+                                         1e-300)
+            Xn = kap * Xn
+            rho = kap * rho
+            mu0 *= kap
+        Xc = Xn
+        hist["mu"].append(mu_k)
+        hist["shrinks"].append(shrinks)
+    out = {"Xc": Xc, "idx": idx, "rho": rho, "X": expand(Xc, V)}
+    if history:
+        out["history"] = hist
+    return out

@@ -451,10 +451,21 @@ class SvdOp:
         _check(lib().mrf_svd_ipg_step(Dc.handle, self.handle, _ptr(AHYc), _ptr(Xc), mu, C.byref(o),
                                       _ptr(idx_io), _ptr(rho_out), _stream(stream)))
 
+    def gradient(self, Dc: Dictionary, AHYc, Xc, mu: float, Zc_out, stream=None):
+        _check(lib().mrf_svd_gradient(Dc.handle, self.handle, _ptr(AHYc), _ptr(Xc), mu,
+                                      _ptr(Zc_out), _stream(stream)))
+
     def reconstruct(self, Dc: Dictionary, Y, iters: int, Xc_out, idx_out, X_out=None,
-                    rho_out=None, params_out=None, mu: float = 1.0, opts=None, stream=None):
-        o = opts or proj_opts()
-        _check(lib().mrf_svd_reconstruct(Dc.handle, self.handle, _ptr(Y), iters, mu, C.byref(o),
+                    rho_out=None, params_out=None, mu: float = 1.0, opts=None, stream=None,
+                    adaptive: bool = False, zeta: float = 2.0, kappa: bool = False,
+                    max_shrink: int = 30, mu_history=None, shrink_history=None):
+        """Compressed BLIP (mrf_svd_reconstruct); `opts` are the projection options."""
+        r = recon_opts(iters=iters, mu=mu, adaptive=adaptive, zeta=zeta, kappa=kappa,
+                       max_shrink=max_shrink, mu_history=mu_history,
+                       shrink_history=shrink_history)
+        if opts is not None:
+            r.proj = opts
+        _check(lib().mrf_svd_reconstruct(Dc.handle, self.handle, _ptr(Y), C.byref(r),
                                          _ptr(Xc_out), _ptr(X_out), _ptr(idx_out), _ptr(rho_out),
                                          _ptr(params_out), _stream(stream)))
 

@@ -159,9 +159,11 @@ SIGNATURES = {
     "mrf_svd_expand": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p]),
     "mrf_svd_ipg_step": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_float,
                                    C.POINTER(ProjOpts), C.c_void_p, C.c_void_p, C.c_void_p]),
-    "mrf_svd_reconstruct": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32, C.c_float,
-                                      C.POINTER(ProjOpts), C.c_void_p, C.c_void_p, C.c_void_p,
-                                      C.c_void_p, C.c_void_p, C.c_void_p]),
+    "mrf_svd_reconstruct": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(ReconOpts),
+                                      C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
+                                      C.c_void_p, C.c_void_p]),
+    "mrf_svd_gradient": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_float,
+                                   C.c_void_p, C.c_void_p]),
     "mrf_debug_fail_alloc": (None, [C.c_int32]),
     "mrf_selftest_wait_timeout": (C.c_int, [C.c_int64, C.c_void_p]),
     "mrf_status_str": (C.c_char_p, [C.c_int]),

@@ -28,38 +28,15 @@ __device__ __forceinline__ float2 cmul(float2 a, float2 b) {
     return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
 }
 
-// tw[k] = exp(-2 pi i k / Ny), k < Ny / 2.  A CTA owns TC = 2^LTC columns.
+// Forward transform along y of the TC columns of the tile s ([Ny][TC], bit-reversed rows on
+// entry, natural-order k-space on exit): decimation in time, two radix-2 stages per pass (a
+// quadruple {i, i + h, i + 2h, i + 3h} closes under the stages h and 2h), a last single stage
+// when log2 Ny is odd.  Ends with a barrier.
 template <int LTC>
-__global__ void __launch_bounds__(NT)
-k_grad_pow2(const float2* __restrict__ X, const float2* __restrict__ AHY,
-            const uint8_t* __restrict__ mask, const float2* __restrict__ tw, int Ny, int logNy,
-            int Nx, int L, float mu, float2* __restrict__ Z, __nv_bfloat162* __restrict__ zq,
-            int Kp, uint32_t* err) {
+__device__ __forceinline__ void tile_fft_fwd(float2* s, const float2* w, int Ny, int logNy,
+                                             int tid, int jt) {
     constexpr int TC = 1 << LTC;
-    extern __shared__ float2 sbuf[];            // [Ny][TC] tile, then [Ny / 2] twiddles
-    float2* s = sbuf;
-    float2* w = sbuf + Ny * TC;
-    const int tid = threadIdx.x;
-    const int64_t NxL = static_cast<int64_t>(Nx) * L;
-    const int64_t c0 = static_cast<int64_t>(blockIdx.x) * TC;
-    for (int k = tid; k < Ny / 2; k += NT) w[k] = tw[k];
-    const int nbf = (Ny / 2) * TC;              // butterflies per stage
-    // every index a thread touches has column j = tid mod TC (NT is a multiple of TC)
-    const int jt = tid & (TC - 1);
-    const int64_t ct = c0 + jt;
-    const bool live = ct < NxL;
-    const int tcol = live ? static_cast<int>(ct % L) : 0;      // frame of the column
-    const int64_t xcol = live ? ct / L : 0;                     // x of the column
-    // load X bit-reversed along y
-    for (int i = tid; i < Ny * TC; i += NT) {
-        const int ky = i >> LTC;
-        const int r = static_cast<int>(__brev(static_cast<unsigned>(ky)) >> (32 - logNy));
-        s[(r << LTC) + jt] = live ? X[static_cast<int64_t>(ky) * NxL + ct] : make_float2(0.f, 0.f);
-    }
-    __syncthreads();
-    // forward: decimation in time, natural-order output; two radix-2 stages per pass (a
-    // quadruple {i, i + h, i + 2h, i + 3h} closes under the stages h and 2h), a last single
-    // stage when log2 Ny is odd
+    const int nbf = (Ny / 2) * TC;
     const int nq = (Ny / 4) * TC;
     for (int lh = 0; lh < logNy;) {
         const int h = 1 << lh;
@@ -96,15 +73,17 @@ k_grad_pow2(const float2* __restrict__ X, const float2* __restrict__ AHY,
         }
         __syncthreads();
     }
-    // keep the sampled lines of each column's frame
-    const uint8_t* mrow = mask + static_cast<int64_t>(tcol) * Ny;
-    for (int i = tid; i < Ny * TC; i += NT) {
-        const int ky = i >> LTC;
-        if (!live || !mrow[ky]) s[i] = make_float2(0.f, 0.f);
-    }
-    __syncthreads();
-    // inverse: decimation in frequency with conjugate twiddles, bit-reversed output; stages
-    // 2q and q in one pass on the quadruple {i, i + q, i + 2q, i + 3q}
+}
+
+// Inverse transform along y (natural-order rows on entry, bit-reversed rows on exit, no 1/Ny):
+// decimation in frequency with conjugate twiddles, stages 2q and q in one pass on the quadruple
+// {i, i + q, i + 2q, i + 3q}.  Ends with a barrier.
+template <int LTC>
+__device__ __forceinline__ void tile_fft_inv(float2* s, const float2* w, int Ny, int logNy,
+                                             int tid, int jt) {
+    constexpr int TC = 1 << LTC;
+    const int nbf = (Ny / 2) * TC;
+    const int nq = (Ny / 4) * TC;
     for (int lh = logNy - 1; lh >= 0;) {
         if (lh >= 1) {
             const int qq = 1 << (lh - 1);
@@ -139,10 +118,24 @@ k_grad_pow2(const float2* __restrict__ X, const float2* __restrict__ AHY,
         }
         __syncthreads();
     }
-    // combine: Z = X - mu (G / Ny - AHY), G = the tile read back in natural order
+}
+
+// Z = X - mu (G / Ny - AHY) for the tile's columns, G = the tile (bit-reversed rows) read back
+// in natural order; also the BF16 query operand of Z when zq is given.
+template <int LTC>
+__device__ __forceinline__ void tile_combine(const float2* s, const float2* __restrict__ X,
+                                             const float2* __restrict__ AHY, int Ny, int logNy,
+                                             int Nx, int L, float mu, float2* __restrict__ Z,
+                                             __nv_bfloat162* __restrict__ zq, int Kp,
+                                             uint32_t* err, int tid, int jt, int64_t ct,
+                                             bool live) {
+    constexpr int TC = 1 << LTC;
+    const int64_t NxL = static_cast<int64_t>(Nx) * L;
     const float gs = 1.0f / static_cast<float>(Ny);
     const int half = Kp / 2;
     if (!live) return;
+    const int tcol = static_cast<int>(ct % L);
+    const int64_t xcol = ct / L;
     for (int i = tid; i < Ny * TC; i += NT) {
         const int ky = i >> LTC;
         const int r = static_cast<int>(__brev(static_cast<unsigned>(ky)) >> (32 - logNy));
@@ -161,6 +154,105 @@ k_grad_pow2(const float2* __restrict__ X, const float2* __restrict__ AHY,
                 for (int tt = L; tt < half; ++tt) zq[v * half + tt] = __floats2bfloat162_rn(0.f, 0.f);
         }
     }
+}
+
+// tw[k] = exp(-2 pi i k / Ny), k < Ny / 2.  A CTA owns TC = 2^LTC columns.
+template <int LTC>
+__global__ void __launch_bounds__(NT)
+k_grad_pow2(const float2* __restrict__ X, const float2* __restrict__ AHY,
+            const uint8_t* __restrict__ mask, const float2* __restrict__ tw, int Ny, int logNy,
+            int Nx, int L, float mu, float2* __restrict__ Z, __nv_bfloat162* __restrict__ zq,
+            int Kp, uint32_t* err) {
+    constexpr int TC = 1 << LTC;
+    extern __shared__ float2 sbuf[];            // [Ny][TC] tile, then [Ny / 2] twiddles
+    float2* s = sbuf;
+    float2* w = sbuf + Ny * TC;
+    const int tid = threadIdx.x;
+    const int64_t NxL = static_cast<int64_t>(Nx) * L;
+    const int64_t c0 = static_cast<int64_t>(blockIdx.x) * TC;
+    for (int k = tid; k < Ny / 2; k += NT) w[k] = tw[k];
+    // every index a thread touches has column j = tid mod TC (NT is a multiple of TC)
+    const int jt = tid & (TC - 1);
+    const int64_t ct = c0 + jt;
+    const bool live = ct < NxL;
+    const int tcol = live ? static_cast<int>(ct % L) : 0;      // frame of the column
+    const int64_t xcol = live ? ct / L : 0;                     // x of the column
+    // load X bit-reversed along y
+    for (int i = tid; i < Ny * TC; i += NT) {
+        const int ky = i >> LTC;
+        const int r = static_cast<int>(__brev(static_cast<unsigned>(ky)) >> (32 - logNy));
+        s[(r << LTC) + jt] = live ? X[static_cast<int64_t>(ky) * NxL + ct] : make_float2(0.f, 0.f);
+    }
+    __syncthreads();
+    tile_fft_fwd<LTC>(s, w, Ny, logNy, tid, jt);
+    // keep the sampled lines of each column's frame
+    const uint8_t* mrow = mask + static_cast<int64_t>(tcol) * Ny;
+    for (int i = tid; i < Ny * TC; i += NT) {
+        const int ky = i >> LTC;
+        if (!live || !mrow[ky]) s[i] = make_float2(0.f, 0.f);
+    }
+    __syncthreads();
+    tile_fft_inv<LTC>(s, w, Ny, logNy, tid, jt);
+    tile_combine<LTC>(s, X, AHY, Ny, logNy, Nx, L, mu, Z, zq, Kp, err, tid, jt, ct, live);
+}
+
+// The two halves of the one-pass kernel around an operator that mixes the columns of one
+// phase-encode line (the compressed gradient of §3.3, eq. gradcompression, where the per-frame
+// masks become an s x s product per line): the forward y-transform of every column into W
+// (natural-order k-space, no scaling), and the inverse y-transform of W2 followed by the same
+// combine as above.
+template <int LTC>
+__global__ void __launch_bounds__(NT)
+k_yfft_fwd(const float2* __restrict__ X, const float2* __restrict__ tw, int Ny, int logNy,
+           int64_t NxL, float2* __restrict__ W) {
+    constexpr int TC = 1 << LTC;
+    extern __shared__ float2 sbuf[];
+    float2* s = sbuf;
+    float2* w = sbuf + Ny * TC;
+    const int tid = threadIdx.x;
+    const int64_t c0 = static_cast<int64_t>(blockIdx.x) * TC;
+    for (int k = tid; k < Ny / 2; k += NT) w[k] = tw[k];
+    const int jt = tid & (TC - 1);
+    const int64_t ct = c0 + jt;
+    const bool live = ct < NxL;
+    for (int i = tid; i < Ny * TC; i += NT) {
+        const int ky = i >> LTC;
+        const int r = static_cast<int>(__brev(static_cast<unsigned>(ky)) >> (32 - logNy));
+        s[(r << LTC) + jt] = live ? X[static_cast<int64_t>(ky) * NxL + ct] : make_float2(0.f, 0.f);
+    }
+    __syncthreads();
+    tile_fft_fwd<LTC>(s, w, Ny, logNy, tid, jt);
+    if (!live) return;
+    for (int i = tid; i < Ny * TC; i += NT) {
+        const int ky = i >> LTC;
+        W[static_cast<int64_t>(ky) * NxL + ct] = s[i];
+    }
+}
+
+template <int LTC>
+__global__ void __launch_bounds__(NT)
+k_yfft_inv_combine(const float2* __restrict__ W2, const float2* __restrict__ X,
+                   const float2* __restrict__ AHY, const float2* __restrict__ tw, int Ny,
+                   int logNy, int Nx, int L, float mu, float2* __restrict__ Z,
+                   __nv_bfloat162* __restrict__ zq, int Kp, uint32_t* err) {
+    constexpr int TC = 1 << LTC;
+    extern __shared__ float2 sbuf[];
+    float2* s = sbuf;
+    float2* w = sbuf + Ny * TC;
+    const int tid = threadIdx.x;
+    const int64_t NxL = static_cast<int64_t>(Nx) * L;
+    const int64_t c0 = static_cast<int64_t>(blockIdx.x) * TC;
+    for (int k = tid; k < Ny / 2; k += NT) w[k] = tw[k];
+    const int jt = tid & (TC - 1);
+    const int64_t ct = c0 + jt;
+    const bool live = ct < NxL;
+    for (int i = tid; i < Ny * TC; i += NT) {
+        const int ky = i >> LTC;
+        s[i] = live ? W2[static_cast<int64_t>(ky) * NxL + ct] : make_float2(0.f, 0.f);
+    }
+    __syncthreads();
+    tile_fft_inv<LTC>(s, w, Ny, logNy, tid, jt);
+    tile_combine<LTC>(s, X, AHY, Ny, logNy, Nx, L, mu, Z, zq, Kp, err, tid, jt, ct, live);
 }
 
 std::mutex g_tw_mu;
@@ -215,6 +307,62 @@ mrf_status launch_grad_fused(const mrf_op* op, const float2* AHY, const float2* 
     }
     if (e != cudaSuccess) {
         mrf_set_error(std::string("fused gradient launch: ") + cudaGetErrorString(e));
+        return MRF_ECUDA;
+    }
+    return MRF_OK;
+}
+
+namespace {
+int log2_of(int Ny) {
+    int l = 0;
+    while ((1 << l) < Ny) ++l;
+    return l;
+}
+}  // namespace
+
+mrf_status launch_yfft_fwd(const float2* X, int Ny, int Nx, int C, float2* W, cudaStream_t st) {
+    const int logNy = log2_of(Ny);
+    const float2* tw = nullptr;
+    MRF_TRY(twiddles(Ny, &tw));
+    const int64_t cols = static_cast<int64_t>(Nx) * C;
+    constexpr int LTC = kTileLog;
+    constexpr int TC = 1 << LTC;
+    const size_t sm = sizeof(float2) * (static_cast<size_t>(Ny) * TC + Ny / 2);
+    cudaError_t e = cudaFuncSetAttribute(k_yfft_fwd<LTC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         static_cast<int>(sm));
+    if (e == cudaSuccess) {
+        k_yfft_fwd<LTC><<<static_cast<unsigned>((cols + TC - 1) / TC), NT, sm, st>>>(
+            X, tw, Ny, logNy, cols, W);
+        e = cudaGetLastError();
+    }
+    if (e != cudaSuccess) {
+        mrf_set_error(std::string("forward y-transform launch: ") + cudaGetErrorString(e));
+        return MRF_ECUDA;
+    }
+    return MRF_OK;
+}
+
+mrf_status launch_yfft_inv_combine(const float2* W2, const float2* X, const float2* AHY, int Ny,
+                                   int Nx, int C, float mu, float2* Z, __nv_bfloat16* zq, int Kp,
+                                   uint32_t* err, cudaStream_t st) {
+    const int logNy = log2_of(Ny);
+    const float2* tw = nullptr;
+    MRF_TRY(twiddles(Ny, &tw));
+    const int64_t cols = static_cast<int64_t>(Nx) * C;
+    constexpr int LTC = kTileLog;
+    constexpr int TC = 1 << LTC;
+    const size_t sm = sizeof(float2) * (static_cast<size_t>(Ny) * TC + Ny / 2);
+    cudaError_t e = cudaFuncSetAttribute(k_yfft_inv_combine<LTC>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         static_cast<int>(sm));
+    if (e == cudaSuccess) {
+        k_yfft_inv_combine<LTC><<<static_cast<unsigned>((cols + TC - 1) / TC), NT, sm, st>>>(
+            W2, X, AHY, tw, Ny, logNy, Nx, C, mu, Z, reinterpret_cast<__nv_bfloat162*>(zq),
+            zq ? Kp : 2 * C, err);
+        e = cudaGetLastError();
+    }
+    if (e != cudaSuccess) {
+        mrf_set_error(std::string("inverse y-transform launch: ") + cudaGetErrorString(e));
         return MRF_ECUDA;
     }
     return MRF_OK;

@@ -195,6 +195,22 @@ mrf_status ct_export(const mrf_dict* D, int32_t* first_level, int32_t* parent, i
 bool grad_fused_supported(int Ny);
 mrf_status launch_grad_fused(const mrf_op* op, const float2* AHY, const float2* X, float mu,
                              float2* Z, __nv_bfloat16* zq, int Kp, uint32_t* err, cudaStream_t st);
+// the halves of the fused kernel for an image of C columns per x (power-of-two Ny): W = the
+// unscaled y-DFT of X; Z = X - mu (F_y^-1 W2 (unscaled, then / Ny) - AHY) (+ BF16 operand)
+mrf_status launch_yfft_fwd(const float2* X, int Ny, int Nx, int C, float2* W, cudaStream_t st);
+mrf_status launch_yfft_inv_combine(const float2* W2, const float2* X, const float2* AHY, int Ny,
+                                   int Nx, int C, float mu, float2* Z, __nv_bfloat16* zq, int Kp,
+                                   uint32_t* err, cudaStream_t st);
+// cgemm.cu: batched complex FP32 product Out[b][r][j] = sum_k In[b][r][k] m_b(k) op(M[b][k][j])
+// (row-major; op = conj when conj_m; m_b(k) = kmask[b * kmask_bs + k * kmask_ld] != 0 when a
+// mask is given, else 1)
+mrf_status launch_cgemm(const float2* In, int64_t in_ld, int64_t in_bs, const float2* M,
+                        int64_t m_ld, int64_t m_bs, bool conj_m, float2* Out, int64_t out_ld,
+                        int64_t out_bs, int R, int K, int J, int batches, const uint8_t* kmask,
+                        int64_t kmask_ld, int64_t kmask_bs, cudaStream_t st);
+// Re sum_i conj(a_i) b_i accumulated in FP64 into *out (added)
+mrf_status launch_cdot_re(const float2* a, const float2* b, int64_t count, double* out,
+                          cudaStream_t st);
 // phase.cu
 mrf_status phase_align_dictionary(mrf_dict* D, cudaStream_t st);
 mrf_status launch_align_queries(const mrf_dict* D, const float2* Z, int64_t n, float2* Zout,

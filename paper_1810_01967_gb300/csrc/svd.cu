@@ -3,16 +3,22 @@
 //
 // V_s (L x s) spans the s dominant eigenvectors of the frame Gram matrix
 // M = sum_j D_j D_j^H.  Fingerprints are rows, so compression is X -> X conj(V_s) and expansion
-// Xc -> Xc V_s^T (cuBLAS GEMMs: plain library products).  The compressed gradient of
+// Xc -> Xc V_s^T (the library's batched complex product, cgemm.cu).  The compressed gradient of
 // eq. gradcompression runs the y-transforms on s compressed frames; the per-frame line masks do
 // not commute with V_s, so between the transforms each k-space row is multiplied by the s x s
 // matrix H_ky = V_s^H diag(mask[., ky]) V_s of its phase-encode line (decompress, mask,
-// compress in one step; one batched GEMM over the Ny lines).  The projection is the ordinary
-// one on a dictionary index built from the compressed atoms D conj(V_s).
+// compress in one step; one batched product over the Ny lines).  For power-of-two Ny the
+// transforms are the two halves of the fused gradient kernel (forward transform; inverse
+// transform with the combine and the BF16 packing), otherwise cuFFT with the combine kernel.
+// The step rule of eq. steprule in the compressed domain (§4.3) needs ||A(dXc V_s^T)||^2, which
+// is sum over k-space rows of Re(K^H H_ky K) / Ny with K the unscaled y-transform of dXc.  The
+// projection is the ordinary one on a dictionary index built from the compressed atoms
+// D conj(V_s).
 //
 // The basis comes from subspace iteration on M in FP64 (M from Hermitian rank-k updates of
-// the atoms converted to FP64, shifted CholeskyQR3 orthonormalisation) followed by Rayleigh-Ritz with a cyclic Jacobi
-// eigensolver on the host.  Any orthonormal basis of the same subspace gives identical
+// the atoms converted to FP64 with cuBLAS, shifted CholeskyQR3 orthonormalisation) followed by
+// Rayleigh-Ritz with a cyclic Jacobi eigensolver on the host: a one-time set-up, outside the
+// iterations.  Any orthonormal basis of the same subspace gives identical
 // reconstructions (only V_s V_s^H enters), so the Ritz step only selects the dominant s
 // directions among the iterated ones.
 #include <cublas_v2.h>
@@ -34,9 +40,8 @@ struct mrf_svd_op {
     int32_t L = 0, s = 0;
     bool has_op = false;
     mrf_op op = {};
-    cublasHandle_t blas = nullptr;
     float2* V = nullptr;    // [L][s]
-    float2* Vc = nullptr;   // conj(V) [L][s]
+    float2* VT = nullptr;   // V transposed, [s][L]
     float2* H = nullptr;    // [Ny] blocks of s x s; block ky holds H_ky[b][a] at b + a s
     float2* w2 = nullptr;   // [cap][s] workspace of the gradient
     int64_t cap = 0;
@@ -65,21 +70,22 @@ inline unsigned blocks(int64_t work) {
     return static_cast<unsigned>(std::min<int64_t>((work + kT - 1) / kT, 1 << 20));
 }
 
-__global__ void k_conj(const float2* __restrict__ a, int64_t n, float2* __restrict__ b) {
-    for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < n;
-         i += static_cast<int64_t>(gridDim.x) * blockDim.x)
-        b[i] = make_float2(a[i].x, -a[i].y);
-}
-
-// Vm[t][a] = mask[t][ky] V[t][a]
-__global__ void k_mask_rows(const float2* __restrict__ V, const uint8_t* __restrict__ mask,
-                            int L, int s, int Ny, int ky, float2* __restrict__ Vm) {
+// VT[a][t] = V[t][a]
+__global__ void k_transpose(const float2* __restrict__ V, int L, int s, float2* __restrict__ VT) {
     const int64_t n = static_cast<int64_t>(L) * s;
     for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < n;
          i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
-        const int t = static_cast<int>(i / s);
-        Vm[i] = mask[static_cast<int64_t>(t) * Ny + ky] ? V[i] : make_float2(0.f, 0.f);
+        const int a = static_cast<int>(i / L), t = static_cast<int>(i - static_cast<int64_t>(a) * L);
+        VT[i] = V[static_cast<int64_t>(t) * s + a];
     }
+}
+
+// D = A - B
+__global__ void k_sub(const float2* __restrict__ A, const float2* __restrict__ B, int64_t n,
+                      float2* __restrict__ D) {
+    for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < n;
+         i += static_cast<int64_t>(gridDim.x) * blockDim.x)
+        D[i] = make_float2(A[i].x - B[i].x, A[i].y - B[i].y);
 }
 
 __global__ void k_f2d(const float2* __restrict__ a, int64_t n, double2* __restrict__ b) {
@@ -199,30 +205,36 @@ mrf_status ensure_w2(mrf_svd_op* so, int64_t n) {
     return MRF_OK;
 }
 
-// Xc = X conj(V) for rows of length L -> s (column-major view: Xc^T = V^H X^T).
+// Xc = X conj(V) for rows of length L -> s.
 mrf_status compress_rows(const mrf_svd_op* so, const float2* X, int64_t n, float2* Xc,
                          cudaStream_t st) {
-    if (n == 0) return MRF_OK;
-    BLAS_TRY(cublasSetStream(so->blas, st));
-    const cuComplex one = make_cuComplex(1.f, 0.f), zero = make_cuComplex(0.f, 0.f);
-    BLAS_TRY(cublasCgemm(so->blas, CUBLAS_OP_N, CUBLAS_OP_N, so->s, static_cast<int>(n), so->L,
-                         &one, reinterpret_cast<const cuComplex*>(so->Vc), so->s,
-                         reinterpret_cast<const cuComplex*>(X), so->L, &zero,
-                         reinterpret_cast<cuComplex*>(Xc), so->s));
-    return MRF_OK;
+    return launch_cgemm(X, so->L, 0, so->V, so->s, 0, true, Xc, so->s, 0, static_cast<int>(n),
+                        so->L, so->s, 1, nullptr, 0, 0, st);
 }
 
-// X = Xc V^T (column-major view: X^T = V Xc^T, V = transpose of the stored [L][s] array).
+// X = Xc V^T for rows of length s -> L.
 mrf_status expand_rows(const mrf_svd_op* so, const float2* Xc, int64_t n, float2* X,
                        cudaStream_t st) {
-    if (n == 0) return MRF_OK;
-    BLAS_TRY(cublasSetStream(so->blas, st));
-    const cuComplex one = make_cuComplex(1.f, 0.f), zero = make_cuComplex(0.f, 0.f);
-    BLAS_TRY(cublasCgemm(so->blas, CUBLAS_OP_T, CUBLAS_OP_N, so->L, static_cast<int>(n), so->s,
-                         &one, reinterpret_cast<const cuComplex*>(so->V), so->s,
-                         reinterpret_cast<const cuComplex*>(Xc), so->s, &zero,
-                         reinterpret_cast<cuComplex*>(X), so->L));
-    return MRF_OK;
+    return launch_cgemm(Xc, so->s, 0, so->VT, so->L, 0, false, X, so->L, 0, static_cast<int>(n),
+                        so->s, so->L, 1, nullptr, 0, 0, st);
+}
+
+// K (unscaled y-transform, natural order) of the compressed image Xc [Ny][Nx][s].
+mrf_status yfft_c(mrf_svd_op* so, const float2* Xc, float2* K, cudaStream_t st) {
+    const mrf_op& op = so->op;
+    if (grad_fused_supported(op.Ny)) return launch_yfft_fwd(Xc, op.Ny, op.Nx, so->s, K, st);
+    cufftHandle hy;
+    MRF_TRY(get_plan(0, op.Ny, op.Nx, so->s, st, &hy));
+    return fft_exec(hy, Xc, K, CUFFT_FORWARD);
+}
+
+// W2 = H_ky applied to every k-space row of line ky: W2[ky][kx][b] = sum_a H_ky[b][a] W[ky][kx][a].
+mrf_status apply_h(mrf_svd_op* so, const float2* W, float2* W2, cudaStream_t st) {
+    const mrf_op& op = so->op;
+    const int s = so->s;
+    return launch_cgemm(W, s, static_cast<int64_t>(op.Nx) * s, so->H, s,
+                        static_cast<int64_t>(s) * s, false, W2, s,
+                        static_cast<int64_t>(op.Nx) * s, op.Nx, s, s, op.Ny, nullptr, 0, 0, st);
 }
 
 // Zc = Xc - mu (compress(A^H A expand(Xc)) - AHYc) into D->zbuf (and the BF16 operand).
@@ -232,24 +244,37 @@ mrf_status gradient_c(mrf_dict* D, mrf_svd_op* so, const float2* AHYc, const flo
     const int s = so->s;
     const int64_t n = static_cast<int64_t>(op.Ny) * op.Nx;
     MRF_TRY(ensure_w2(so, n));
+    ProfScope ps0(0, 3, st);
+    MRF_TRY(yfft_c(so, Xc, D->wbuf, st));
+    MRF_TRY(apply_h(so, D->wbuf, so->w2, st));
+    __nv_bfloat16* zq = want_zq ? D->zq : nullptr;
+    if (grad_fused_supported(op.Ny))
+        return launch_yfft_inv_combine(so->w2, Xc, AHYc, op.Ny, op.Nx, s, mu, D->zbuf, zq, D->Kp,
+                                       D->err, st);
     cufftHandle hy;
     MRF_TRY(get_plan(0, op.Ny, op.Nx, s, st, &hy));
-    ProfScope ps0(0, 1, st);
-    MRF_TRY(fft_exec(hy, Xc, D->wbuf, CUFFT_FORWARD));
-    BLAS_TRY(cublasSetStream(so->blas, st));
-    const cuComplex one = make_cuComplex(1.f, 0.f), zero = make_cuComplex(0.f, 0.f);
-    // row r = (ky, kx): out[r][b] = sum_a H_ky[b][a] in[r][a]; column-major per ky:
-    // out_ky (s x Nx) = H_ky (s x s) in_ky (s x Nx)
-    BLAS_TRY(cublasCgemmStridedBatched(
-        so->blas, CUBLAS_OP_N, CUBLAS_OP_N, s, op.Nx, s, &one,
-        reinterpret_cast<const cuComplex*>(so->H), s, static_cast<long long>(s) * s,
-        reinterpret_cast<const cuComplex*>(D->wbuf), s, static_cast<long long>(op.Nx) * s, &zero,
-        reinterpret_cast<cuComplex*>(so->w2), s, static_cast<long long>(op.Nx) * s, op.Ny));
     MRF_TRY(fft_exec(hy, so->w2, so->w2, CUFFT_INVERSE));
-    MRF_TRY(launch_grad_combine(Xc, so->w2, AHYc, D->zbuf, n, s, mu,
-                                1.0f / static_cast<float>(op.Ny), want_zq ? D->zq : nullptr,
-                                D->Kp, D->err, st));
-    return MRF_OK;
+    return launch_grad_combine(Xc, so->w2, AHYc, D->zbuf, n, s, mu,
+                               1.0f / static_cast<float>(op.Ny), zq, D->Kp, D->err, st);
+}
+
+// *out += ||A(expand(Dc))||^2 = sum of Re(K^H H_ky K) / Ny over the k-space rows, K the
+// unscaled y-transform of Dc; uses D->zbuf and so->w2 as workspace (Dc may be D->wbuf).
+mrf_status normal_quad(mrf_dict* D, mrf_svd_op* so, const float2* Dc, double* out,
+                       cudaStream_t st) {
+    const int64_t cnt = static_cast<int64_t>(so->op.Ny) * so->op.Nx * so->s;
+    MRF_TRY(ensure_w2(so, static_cast<int64_t>(so->op.Ny) * so->op.Nx));
+    MRF_TRY(yfft_c(so, Dc, D->zbuf, st));
+    MRF_TRY(apply_h(so, D->zbuf, so->w2, st));
+    return launch_cdot_re(D->zbuf, so->w2, cnt, out, st);
+}
+
+double read_dev(const double* p, cudaStream_t st, mrf_status* s) {
+    double v = 0.0;
+    if (cudaMemcpyAsync(&v, p, sizeof(v), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess)
+        *s = sfail(MRF_ECUDA, "reading a device reduction failed");
+    return v;
 }
 
 }  // namespace
@@ -382,8 +407,7 @@ mrf_status mrf_svd_basis(const mrf_dict* D, int32_t s, void* V_out, double* eig_
 
 void mrf_svd_op_free(mrf_svd_op* so) {
     if (!so) return;
-    if (so->blas) cublasDestroy(so->blas);
-    void* ptrs[] = {so->V, so->Vc, so->H, so->w2};
+    void* ptrs[] = {so->V, so->VT, so->H, so->w2};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     delete so;
@@ -396,6 +420,7 @@ mrf_status mrf_svd_op_create(const mrf_op* op, const void* V, int32_t L, int32_t
     if (op) {
         MRF_TRY(check_op_public(op));
         if (op->L != L) return sfail(MRF_EINVAL, "op->L differs from L");
+        if (op->Ny > 65535) return sfail(MRF_EINVAL, "Ny above 65535 phase-encode lines");
     }
     if (L < 1 || s < 1 || s > L) return sfail(MRF_EINVAL, "need 1 <= s <= L");
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
@@ -406,55 +431,35 @@ mrf_status mrf_svd_op_create(const mrf_op* op, const void* V, int32_t L, int32_t
         mrf_svd_op_free(so);
         return sfail(e, m);
     };
-    if (cublasCreate(&so->blas) != CUBLAS_STATUS_SUCCESS) {
-        so->blas = nullptr;
-        return bail(MRF_ECUDA, "cublasCreate failed");
-    }
     const size_t Ls = static_cast<size_t>(L) * s;
     if (cudaMalloc(&so->V, Ls * sizeof(float2)) != cudaSuccess ||
-        cudaMalloc(&so->Vc, Ls * sizeof(float2)) != cudaSuccess) {
+        cudaMalloc(&so->VT, Ls * sizeof(float2)) != cudaSuccess) {
         cudaGetLastError();
         return bail(MRF_ENOMEM, "svd op allocation failed");
     }
     cudaError_t e = cudaMemcpyAsync(so->V, V, Ls * sizeof(float2), cudaMemcpyDefault, st);
     if (e != cudaSuccess) return bail(MRF_ECUDA, std::string("copy V: ") + cudaGetErrorString(e));
-    k_conj<<<blocks(static_cast<int64_t>(Ls)), kT, 0, st>>>(so->V, static_cast<int64_t>(Ls), so->Vc);
+    k_transpose<<<blocks(static_cast<int64_t>(Ls)), kT, 0, st>>>(so->V, L, s, so->VT);
     if (op) {
         so->has_op = true;
         so->op = *op;
         const int Ny = op->Ny;
-        float2* Vm = nullptr;
-        if (cudaMalloc(&so->H, sizeof(float2) * Ny * s * s) != cudaSuccess ||
-            cudaMalloc(&Vm, Ls * sizeof(float2)) != cudaSuccess) {
+        if (cudaMalloc(&so->H, sizeof(float2) * Ny * s * s) != cudaSuccess) {
             cudaGetLastError();
-            if (Vm) cudaFree(Vm);
             return bail(MRF_ENOMEM, "svd op allocation failed");
         }
-        if (cublasSetStream(so->blas, st) != CUBLAS_STATUS_SUCCESS) {
-            cudaFree(Vm);
-            return bail(MRF_ECUDA, "cublasSetStream failed");
+        // block ky, element (a, b) at a s + b: sum_t V[t][a] mask[t][ky] conj(V[t][b]) =
+        // H_ky[b][a] (row b of H_ky is what line ky's compressed row a contributes to)
+        mrf_status r = launch_cgemm(so->VT, L, 0, so->V, s, 0, true, so->H, s,
+                                    static_cast<int64_t>(s) * s, s, L, s, Ny, op->mask, Ny, 1, st);
+        if (r != MRF_OK) {
+            mrf_svd_op_free(so);
+            return r;
         }
-        const cuComplex one = make_cuComplex(1.f, 0.f), zero = make_cuComplex(0.f, 0.f);
-        for (int ky = 0; ky < Ny; ++ky) {
-            k_mask_rows<<<blocks(static_cast<int64_t>(Ls)), kT, 0, st>>>(so->V, op->mask, L, s, Ny, ky, Vm);
-            // P (column-major s x s) = V_cm Vm_cm^H, (a, b) = sum_t V[t][a] m conj(V[t][b]) =
-            // H_ky[b][a] at a + b s; the stored block is conj(P): H_ky[b][a] at b + a s
-            float2* Hk = so->H + static_cast<size_t>(ky) * s * s;
-            if (cublasCgemm(so->blas, CUBLAS_OP_N, CUBLAS_OP_C, s, s, L, &one,
-                            reinterpret_cast<const cuComplex*>(so->V), s,
-                            reinterpret_cast<const cuComplex*>(Vm), s, &zero,
-                            reinterpret_cast<cuComplex*>(Hk), s) != CUBLAS_STATUS_SUCCESS) {
-                cudaFree(Vm);
-                return bail(MRF_ECUDA, "cublasCgemm (line Gram matrices) failed");
-            }
-            k_conj<<<blocks(static_cast<int64_t>(s) * s), kT, 0, st>>>(Hk, static_cast<int64_t>(s) * s, Hk);
-        }
-        e = cudaStreamSynchronize(st);
-        cudaFree(Vm);
-        if (e != cudaSuccess) return bail(MRF_ECUDA, std::string("svd op: ") + cudaGetErrorString(e));
     }
-    if ((e = cudaGetLastError()) != cudaSuccess)
-        return bail(MRF_ECUDA, std::string("svd op: ") + cudaGetErrorString(e));
+    e = cudaStreamSynchronize(st);
+    if (e == cudaSuccess) e = cudaGetLastError();
+    if (e != cudaSuccess) return bail(MRF_ECUDA, std::string("svd op: ") + cudaGetErrorString(e));
     *out = so;
     return MRF_OK;
 }
@@ -473,6 +478,22 @@ mrf_status mrf_svd_expand(const mrf_svd_op* so, const void* Xc, int64_t n, void*
     if (n > INT32_MAX) return sfail(MRF_EINVAL, "too many rows");
     return expand_rows(so, static_cast<const float2*>(Xc), n, static_cast<float2*>(X),
                        reinterpret_cast<cudaStream_t>(stream));
+}
+
+mrf_status mrf_svd_gradient(mrf_dict* Dc, mrf_svd_op* so, const void* AHYc, const void* Xc,
+                            float mu, void* Zc, void* stream) {
+    if (!Dc || !so || !AHYc || !Xc || !Zc) return sfail(MRF_EINVAL, "missing argument");
+    if (!so->has_op) return sfail(MRF_EINVAL, "the svd op was created without a sampling op");
+    if (Dc->L != so->s) return sfail(MRF_EINVAL, "dictionary length differs from s");
+    if (!std::isfinite(mu)) return sfail(MRF_EINVAL, "mu must be finite");
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    const int64_t n = static_cast<int64_t>(so->op.Ny) * so->op.Nx;
+    MRF_TRY(dict_ensure_scratch(Dc, n));
+    MRF_TRY(gradient_c(Dc, so, static_cast<const float2*>(AHYc), static_cast<const float2*>(Xc),
+                       mu, false, st));
+    MRF_CUDA_TRY(cudaMemcpyAsync(Zc, Dc->zbuf, sizeof(float2) * n * so->s,
+                                 cudaMemcpyDeviceToDevice, st));
+    return MRF_OK;
 }
 
 mrf_status mrf_svd_ipg_step(mrf_dict* Dc, mrf_svd_op* so, const void* AHYc, void* Xc, float mu,
@@ -495,40 +516,99 @@ mrf_status mrf_svd_ipg_step(mrf_dict* Dc, mrf_svd_op* so, const void* AHYc, void
                         static_cast<float2*>(Xc), zq, st);
 }
 
-mrf_status mrf_svd_reconstruct(mrf_dict* Dc, mrf_svd_op* so, const void* Y, int32_t iters,
-                               float mu, const mrf_proj_opts* opts, void* Xc_out, void* X_out,
+mrf_status mrf_svd_reconstruct(mrf_dict* Dc, mrf_svd_op* so, const void* Y,
+                               const mrf_recon_opts* ropts, void* Xc_out, void* X_out,
                                int32_t* idx_out, void* rho_out, float* params_out,
                                void* stream) {
-    if (!Dc || !so || !Y || !Xc_out || !idx_out || iters < 0)
-        return sfail(MRF_EINVAL, "missing argument");
+    if (!Dc || !so || !Y || !Xc_out || !idx_out) return sfail(MRF_EINVAL, "missing argument");
     if (!so->has_op) return sfail(MRF_EINVAL, "the svd op was created without a sampling op");
+    if (Dc->L != so->s) return sfail(MRF_EINVAL, "dictionary length differs from s");
+    mrf_recon_opts r;
+    if (ropts) r = *ropts; else mrf_default_recon_opts(&r);
+    if (r.iters < 0 || !(r.mu > 0.f) || (r.adaptive && !(r.zeta > 1.f)) || r.max_shrink < 0)
+        return sfail(MRF_EINVAL, "bad reconstruction options");
+    if (r.tol > 0.f || r.resume)
+        return sfail(MRF_EUNSUPPORTED, "tol and resume are not available for compressed iterations");
+    MRF_TRY(check_proj_public(Dc, &r.proj));
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     const int64_t n = static_cast<int64_t>(so->op.Ny) * so->op.Nx;
+    const int64_t cnt = n * so->s;
+    MRF_TRY(dict_ensure_scratch(Dc, n));
     float2* AHY = nullptr;
     float2* AHYc = nullptr;
-    if (cudaMalloc(&AHY, sizeof(float2) * n * so->L) != cudaSuccess ||
-        cudaMalloc(&AHYc, sizeof(float2) * n * so->s) != cudaSuccess) {
-        cudaGetLastError();
-        if (AHY) cudaFree(AHY);
-        return sfail(MRF_ENOMEM, "svd reconstruction allocation failed");
-    }
+    float2* Xp = nullptr;
+    float2* rho_tmp = nullptr;
+    double* red = nullptr;
     auto run = [&]() -> mrf_status {
+        if (cudaMalloc(&AHY, sizeof(float2) * n * so->L) != cudaSuccess ||
+            cudaMalloc(&AHYc, sizeof(float2) * cnt) != cudaSuccess ||
+            cudaMalloc(&red, sizeof(double) * 4) != cudaSuccess ||
+            ((r.adaptive || r.kappa) && cudaMalloc(&Xp, sizeof(float2) * cnt) != cudaSuccess) ||
+            (!rho_out && cudaMalloc(&rho_tmp, sizeof(float2) * n) != cudaSuccess)) {
+            cudaGetLastError();
+            return sfail(MRF_ENOMEM, "svd reconstruction allocation failed");
+        }
+        float2* Xc = static_cast<float2*>(Xc_out);
+        float2* rho = rho_out ? static_cast<float2*>(rho_out) : rho_tmp;
         MRF_TRY(mrf_adjoint(&so->op, Y, AHY, stream));
         MRF_TRY(compress_rows(so, AHY, n, AHYc, st));
-        MRF_CUDA_TRY(cudaMemsetAsync(Xc_out, 0, sizeof(float2) * n * so->s, st));
+        MRF_CUDA_TRY(cudaMemsetAsync(Xc, 0, sizeof(float2) * cnt, st));
         MRF_CUDA_TRY(cudaMemsetAsync(idx_out, 0, sizeof(int32_t) * n, st));
-        for (int32_t it = 0; it < iters; ++it)
-            MRF_TRY(mrf_svd_ipg_step(Dc, so, AHYc, Xc_out, mu, opts, idx_out, rho_out, stream));
-        if (X_out) MRF_TRY(expand_rows(so, static_cast<const float2*>(Xc_out), n,
-                                       static_cast<float2*>(X_out), st));
+        const bool zq = (r.proj.mode == MRF_PROJ_BF16);
+        float mu0 = r.mu;
+        mrf_status rs = MRF_OK;
+        for (int32_t k = 0; k < r.iters; ++k) {
+            float mu_k = mu0;
+            int shrinks_k = 0;
+            if (r.adaptive || r.kappa)
+                MRF_CUDA_TRY(cudaMemcpyAsync(Xp, Xc, sizeof(float2) * cnt,
+                                             cudaMemcpyDeviceToDevice, st));
+            for (int shrink = 0;; ++shrink) {
+                shrinks_k = shrink;
+                MRF_TRY(gradient_c(Dc, so, AHYc, r.adaptive ? Xp : Xc, mu_k, zq, st));
+                MRF_TRY(project_core(Dc, Dc->zbuf, n, &r.proj, idx_out, idx_out, rho, Xc, zq, st));
+                if (!r.adaptive) break;
+                // compressed step rule (§4.3): mu_k < ||dXc||^2 / ||A(expand(dXc))||^2
+                MRF_CUDA_TRY(cudaMemsetAsync(red, 0, sizeof(double) * 2, st));
+                k_sub<<<blocks(cnt), kT, 0, st>>>(Xc, Xp, cnt, Dc->wbuf);
+                MRF_CUDA_TRY(cudaGetLastError());
+                MRF_TRY(launch_sqnorm(Dc->wbuf, cnt, red, st));
+                MRF_TRY(normal_quad(Dc, so, Dc->wbuf, red + 1, st));
+                const double num = read_dev(red, st, &rs);
+                const double den = read_dev(red + 1, st, &rs) / so->op.Ny;
+                if (rs != MRF_OK) return rs;
+                if (den <= 0.0 || static_cast<double>(mu_k) < num / den || shrink >= r.max_shrink)
+                    break;
+                mu_k /= r.zeta;
+            }
+            if (r.mu_history) r.mu_history[k] = mu_k;
+            if (r.shrink_history) r.shrink_history[k] = shrinks_k;
+            if (r.kappa && k == 0) {
+                // kappa = ||Y|| / ||A(X^1)||, X^1 and rho scaled, mu scaled alike
+                MRF_CUDA_TRY(cudaMemsetAsync(red + 2, 0, sizeof(double) * 2, st));
+                MRF_TRY(launch_sqnorm(static_cast<const float2*>(Y), n * so->L, red + 2, st));
+                MRF_TRY(normal_quad(Dc, so, Xc, red + 3, st));
+                const double yy = read_dev(red + 2, st, &rs);
+                const double ax = read_dev(red + 3, st, &rs) / so->op.Ny;
+                if (rs != MRF_OK) return rs;
+                if (ax > 0.0) {
+                    const float kap = static_cast<float>(std::sqrt(yy / ax));
+                    MRF_TRY(launch_scale(Xc, cnt, kap, st));
+                    MRF_TRY(launch_scale(rho, n, kap, st));
+                    mu0 *= kap;
+                }
+            }
+        }
+        if (X_out) MRF_TRY(expand_rows(so, Xc, n, static_cast<float2*>(X_out), st));
         if (params_out && Dc->P > 0) MRF_TRY(mrf_lut(Dc, idx_out, n, params_out, stream));
         MRF_CUDA_TRY(cudaStreamSynchronize(st));
         return MRF_OK;
     };
-    const mrf_status r = run();
-    cudaFree(AHY);
-    cudaFree(AHYc);
-    if (r != MRF_OK) return r;
+    const mrf_status rr = run();
+    void* ptrs[] = {AHY, AHYc, Xp, rho_tmp, red};
+    for (void* q : ptrs)
+        if (q) cudaFree(q);
+    if (rr != MRF_OK) return rr;
     return mrf_dict_check(Dc, stream);
 }
 

@@ -102,3 +102,44 @@ def test_compressed_step_is_the_compressed_fidelity_gradient():
         E = _rand(g, Ny * Nx, s)
         fd = (f(Xc + eps * E) - f(Xc - eps * E)) / (2 * eps)
         assert abs(fd - float(np.real(np.vdot(grad, E)))) <= 1e-9 * max(1.0, abs(fd))
+
+
+def test_full_basis_step_rule_and_kappa_reproduce_blip():
+    """With the full basis the compressed step rule of §4.3 is eq. steprule itself (expansion is
+    unitary, so ||dXc|| = ||dX|| and A(expand(dXc)) = A(dX)): adaptive compressed BLIP takes
+    the same steps, shrinks and iterates as the oracle's adaptive BLIP, and its kappa rescale
+    the same factor."""
+    dic, p = small_problem()
+    Ny, Nx, L = p["Ny"], p["Nx"], p["L"]
+    V, _ = svd.svd_basis(dic["atoms"], L)
+    mu = float(Ny / p["masks"].sum(1).mean())
+    r = svd.blip_svd(p["Y"], p["masks"], dic["atoms"], V, Ny, Nx, iters=4, mu=mu, adaptive=True,
+                     history=True)
+    ref = mo.blip(p["Y"], p["masks"], dic["atoms"], Ny, Nx, iters=4, mu=mu, adaptive=True,
+                  history=True)
+    assert r["history"]["shrinks"] == ref["history"]["shrinks"]
+    np.testing.assert_allclose(r["history"]["mu"], ref["history"]["mu"], rtol=1e-12)
+    assert max(r["history"]["shrinks"]) > 0          # the rule did shrink
+    assert np.array_equal(r["idx"], ref["idx"])
+    np.testing.assert_allclose(r["X"], ref["X"], rtol=0, atol=1e-9 * np.abs(ref["X"]).max())
+    rk = svd.blip_svd(p["Y"], p["masks"], dic["atoms"], V, Ny, Nx, iters=3, kappa=True)
+    refk = mo.blip(p["Y"], p["masks"], dic["atoms"], Ny, Nx, iters=3, kappa=True)
+    assert np.array_equal(rk["idx"], refk["idx"])
+    np.testing.assert_allclose(rk["X"], refk["X"], rtol=0, atol=1e-9 * np.abs(refk["X"]).max())
+
+
+def test_compressed_step_rule_monotone_fidelity():
+    """With s < L the accepted steps meet the compressed rule and the fidelity
+    ||Y - A(expand(Xc^k))|| does not increase (Thm. inexactmonotone with the compressed
+    projection, which is a projection onto a cone inside the compressed subspace)."""
+    dic, p = small_problem()
+    Ny, Nx = p["Ny"], p["Nx"]
+    V, _ = svd.svd_basis(dic["atoms"], 12)
+    mu = float(Ny / p["masks"].sum(1).mean())
+    fid = []
+    for k in range(1, 6):
+        r = svd.blip_svd(p["Y"], p["masks"], dic["atoms"], V, Ny, Nx, iters=k, mu=mu,
+                         adaptive=True, history=True)
+        fid.append(np.linalg.norm(p["Y"] - mo.forward(r["X"], p["masks"], Ny, Nx)))
+    assert all(b <= a * (1 + 1e-12) for a, b in zip(fid, fid[1:])), fid
+    assert all(1.0 / 2.0 <= m <= mu for m in r["history"]["mu"])
