@@ -275,12 +275,14 @@ def train_learned(mrf, D, dic, dev, phantoms: int = 64, steps: int = 2000):
 
 
 def reconstruction_quality(mrf, D, op, p, dic, dev, stream, iters: int, fp32: bool = True,
-                           forms: bool = True) -> dict:
+                           forms: bool = True, keep: bool = False):
     """Whole reconstructions (iters BLIP / CoverBLIP iterations) of the slice with every form of
     the projection -- BF16 exhaustive, FP32 exhaustive (the plain comparator), cover tree
     (eps = 0.4, CoverBLIP) and the learned proposal (threshold 0.98) -- reporting time per slice,
     matches/s, T1/T2 accuracy against the phantom (mask rho != 0), B0 error, atom agreement with
-    FP32 and the search work."""
+    FP32 and the search work.  With `keep` the second dictionary (cover tree, FP8 operand,
+    trained learned model attached) is returned open with the results, for the caller to reuse
+    and close."""
     import torch
     Ny, Nx, L = p["Ny"], p["Nx"], p["L"]
     n, d = Ny * Nx, dic["atoms"].shape[0]
@@ -383,12 +385,13 @@ def reconstruction_quality(mrf, D, op, p, dic, dev, stream, iters: int, fp32: bo
                                     "T2_acc": t_accuracy(pr[:, 1], ph["T2"], fg),
                                     "B0_mae_hz": float(np.mean(np.abs(pr[fg, 2] - ph["B0"][fg])))}
         Da.close()
-    if D2 is not None:
+    if D2 is not None and not keep:
         D2.close()
+        D2 = None
     for mode in idxs:
         if "fp32" in idxs:
             out[mode]["atom_agreement_vs_fp32"] = float(np.mean(idxs[mode] == idxs["fp32"]))
-    return out
+    return (out, D2) if keep else out
 
 
 def peaks_sustained() -> tuple[float, str]:
@@ -559,6 +562,131 @@ SLICES_WORKLOAD = ("64 slices of {128,192,256,320}^2 (seeded draw), L=1000, d=10
                    "(T1,T2,B0) IR-bSSFP, R in [8,24], 20 BLIP iterations")
 
 
+def slices_inputs(dic, dev, rank: int = 0, world: int = 1):
+    """The 64-slice workload's seeded geometry (matrix size and acceleration per slice), this
+    rank's slices, and one generated slice per matrix size (masks and k-space on the device),
+    reused by every slice of that size."""
+    import torch
+    import mrfgen
+    geo = [mrfgen.slice_geometry(5, i) for i in range(64)]
+    mine = rank_slices(64, rank, world)
+    first = {}
+    for i in mine:
+        first.setdefault(geo[i][0], i)
+    probs = {N: mrfgen.make_problem(5, i, dic=dic) for N, i in first.items()}
+    masks = {N: torch.from_numpy(p["masks"]).to(dev) for N, p in probs.items()}
+    Ys = {N: torch.from_numpy(p["Y"]).to(dev) for N, p in probs.items()}
+    return geo, mine, masks, Ys
+
+
+def slices_leg(mrf, D, dic, dev, stream, masks, Ys, geo, mine, forms, group, iters, world,
+               autotune_on, both=True, model=None):
+    """The batching form's measurement on the 64-slice workload (all slices submitted at t = 0):
+    per form, one batch of all slices (latency = the makespan, when `both`) and groups of
+    `group` slices, shortest first (latency = its group's completion).  `model` (an MLP already
+    attached to D) skips the learned form's training.  Returns (per-form results, training
+    seconds, autotuned geometries)."""
+    import torch
+    import torch.distributed as dist
+
+    def sync():
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+
+    L = dic["atoms"].shape[1]
+    first = {}
+    for i in mine:
+        first.setdefault(geo[i][0], i)
+    out = {}
+    mlp_s = None
+    tuned = {}
+    Zt = None
+    if autotune_on:
+        # the largest slice's A^H Y: the autotuner times the search geometries on it, once per
+        # element type (the learned form's fallback searches in BF16)
+        from paper_1810_01967_gb300 import autotune
+        Nb = max(first)
+        opb = mrf.make_op(Nb, Nb, L, masks[Nb])
+        Zt = torch.empty((Nb * Nb, L), dtype=torch.complex64, device=dev)
+        mrf.adjoint(opb, Ys[Nb], Zt)
+    for mode, graph in forms:
+        if Zt is not None:
+            tmode = "fp8" if mode == "fp8" else "bf16"
+            if tmode not in tuned:
+                tuned[tmode] = autotune.tune(D, Zt, tmode, reps=2)
+            else:
+                D.set_tune(**tuned[tmode]["tune"])
+        kw = {}
+        if mode == "learned":
+            if model is None:
+                M, mlp_s, _ = train_learned(mrf, D, dic, dev)
+                mrf.attach_mlp(D, M)
+            kw = {"fallback_thr": 0.98}
+        o = mrf.proj_opts(mode=mode, certify=False, **kw)
+        # --- all slices in one batch
+        t_all = None
+        if both:
+            ops = [mrf.make_op(geo[i][0], geo[i][0], L, masks[geo[i][0]]) for i in mine]
+            B = mrf.Batch(D, ops)
+            B.load([Ys[geo[i][0]] for i in mine])
+            B.run(2, 1.0, o, use_graph=graph)        # warm-up: plans, scratch, graph capture
+            sync()
+            a = torch.cuda.Event(enable_timing=True)
+            e = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            B.load([Ys[geo[i][0]] for i in mine])
+            B.run(iters, 1.0, o, use_graph=graph)
+            e.record(stream)
+            sync()
+            t_all = max_over_ranks(a.elapsed_time(e) / 1e3, world, dev)
+            B.close()
+            del B
+        # --- groups of `group` slices, shortest first
+        order = sorted(mine, key=lambda i: (geo[i][0], i))
+        groups = [order[k:k + group] for k in range(0, len(order), group)]
+        # warm up the largest group first: it sizes the dictionary's scratch, so no later
+        # warm-up reallocates buffers that an earlier group's captured graph references
+        Bs = [None] * len(groups)
+        for k in reversed(range(len(groups))):
+            gi = groups[k]
+            og = [mrf.make_op(geo[i][0], geo[i][0], L, masks[geo[i][0]]) for i in gi]
+            Bg = mrf.Batch(D, og)
+            Bg.load([Ys[geo[i][0]] for i in gi])
+            Bg.run(2, 1.0, o, use_graph=graph)
+            Bs[k] = Bg
+        sync()
+        a = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        ends = []
+        for gi, Bg in zip(groups, Bs):
+            Bg.load([Ys[geo[i][0]] for i in gi])
+            Bg.run(iters, 1.0, o, use_graph=graph)
+            ev = torch.cuda.Event(enable_timing=True)
+            ev.record(stream)
+            ends.append(ev)
+        sync()
+        lat = []
+        for gi, ev in zip(groups, ends):
+            lat += [a.elapsed_time(ev) / 1e3] * len(gi)
+        t_grp = max_over_ranks(max(lat), world, dev)
+        for Bg in Bs:
+            Bg.close()
+        del Bs
+        lat_all = lat
+        if world > 1:
+            g = [None] * world
+            dist.all_gather_object(g, lat)
+            lat_all = [x for part in g for x in part]
+        one = None if t_all is None else {"s": t_all, "slices_per_s": 64 / t_all,
+                                          "p50_s": t_all, "p99_s": t_all}
+        out[mode] = {"graph": graph, "one_batch": one,
+                     "groups": {"group": group, "s": t_grp, "slices_per_s": 64 / t_grp,
+                                "p50_s": float(np.percentile(lat_all, 50)),
+                                "p99_s": float(np.percentile(lat_all, 99))}, **kw}
+    return out, mlp_s, tuned
+
+
 def run_slices(args) -> None:
     """The batching form on the 64-slice workload: every slice's 20 BLIP iterations through
     mrf_batch.  Two schedules, all slices submitted at t = 0: one batch of all slices (one
@@ -588,15 +716,8 @@ def run_slices(args) -> None:
     dic = mrfgen.make_dictionary(5)
     atoms, params = dic["atoms"], dic["params"]
     d, L = atoms.shape
-    geo = [mrfgen.slice_geometry(5, i) for i in range(64)]
-    mine = rank_slices(64, rank, world)
-    first = {}
-    for i in mine:
-        first.setdefault(geo[i][0], i)
-    probs = {N: mrfgen.make_problem(5, i, dic=dic) for N, i in first.items()}
+    geo, mine, masks, Ys = slices_inputs(dic, dev, rank, world)
     D = mrf.build_dict_index(atoms, params, grid_shape=dic["grid_shape"], pack_fp8=True)
-    masks = {N: torch.from_numpy(p["masks"]).to(dev) for N, p in probs.items()}
-    Ys = {N: torch.from_numpy(p["Y"]).to(dev) for N, p in probs.items()}
     iters = args.iters
     forms = [("bf16", True), ("fp8", True)]
     if not args.no_forms:
@@ -607,85 +728,8 @@ def run_slices(args) -> None:
         if world > 1:
             dist.barrier()
 
-    out = {}
-    mlp_s = None
-    tuned = {}
-    Zt = None
-    if not args.no_autotune:
-        # the largest slice's A^H Y: the autotuner times the search geometries on it, once per
-        # element type (the learned form's fallback searches in BF16)
-        from paper_1810_01967_gb300 import autotune
-        Nb = max(first)
-        opb = mrf.make_op(Nb, Nb, L, masks[Nb])
-        Zt = torch.empty((Nb * Nb, L), dtype=torch.complex64, device=dev)
-        mrf.adjoint(opb, Ys[Nb], Zt)
-    for mode, graph in forms:
-        if Zt is not None:
-            tmode = "fp8" if mode == "fp8" else "bf16"
-            if tmode not in tuned:
-                tuned[tmode] = autotune.tune(D, Zt, tmode, reps=2)
-            else:
-                D.set_tune(**tuned[tmode]["tune"])
-        kw = {}
-        if mode == "learned":
-            M, mlp_s, _ = train_learned(mrf, D, dic, dev)
-            mrf.attach_mlp(D, M)
-            kw = {"fallback_thr": 0.98}
-        o = mrf.proj_opts(mode=mode, certify=False, **kw)
-        # --- all slices in one batch
-        ops = [mrf.make_op(geo[i][0], geo[i][0], L, masks[geo[i][0]]) for i in mine]
-        B = mrf.Batch(D, ops)
-        B.load([Ys[geo[i][0]] for i in mine])
-        B.run(2, 1.0, o, use_graph=graph)            # warm-up: plans, scratch, graph capture
-        sync()
-        a = torch.cuda.Event(enable_timing=True)
-        e = torch.cuda.Event(enable_timing=True)
-        a.record(stream)
-        B.load([Ys[geo[i][0]] for i in mine])
-        B.run(iters, 1.0, o, use_graph=graph)
-        e.record(stream)
-        sync()
-        t_all = max_over_ranks(a.elapsed_time(e) / 1e3, world, dev)
-        B.close()
-        del B
-        # --- groups of `group` slices, shortest first
-        order = sorted(mine, key=lambda i: (geo[i][0], i))
-        groups = [order[k:k + args.group] for k in range(0, len(order), args.group)]
-        Bs = []
-        for gi in groups:
-            og = [mrf.make_op(geo[i][0], geo[i][0], L, masks[geo[i][0]]) for i in gi]
-            Bg = mrf.Batch(D, og)
-            Bg.load([Ys[geo[i][0]] for i in gi])
-            Bg.run(2, 1.0, o, use_graph=graph)
-            Bs.append(Bg)
-        sync()
-        a = torch.cuda.Event(enable_timing=True)
-        a.record(stream)
-        ends = []
-        for gi, Bg in zip(groups, Bs):
-            Bg.load([Ys[geo[i][0]] for i in gi])
-            Bg.run(iters, 1.0, o, use_graph=graph)
-            ev = torch.cuda.Event(enable_timing=True)
-            ev.record(stream)
-            ends.append(ev)
-        sync()
-        lat = []
-        for gi, ev in zip(groups, ends):
-            lat += [a.elapsed_time(ev) / 1e3] * len(gi)
-        t_grp = max_over_ranks(max(lat), world, dev)
-        for Bg in Bs:
-            Bg.close()
-        del Bs
-        lat_all = lat
-        if world > 1:
-            g = [None] * world
-            dist.all_gather_object(g, lat)
-            lat_all = [x for part in g for x in part]
-        out[mode] = {"graph": graph, "one_batch": {"s": t_all, "slices_per_s": 64 / t_all,
-                                                   "p50_s": t_all, "p99_s": t_all},
-                     "groups": {"group": args.group, "s": t_grp, "slices_per_s": 64 / t_grp,
-                                "p50_s": float(np.percentile(lat_all, 50)),
-                                "p99_s": float(np.percentile(lat_all, 99))}, **kw}
+    out, mlp_s, tuned = slices_leg(mrf, D, dic, dev, stream, masks, Ys, geo, mine, forms,
+                                   args.group, iters, world, not args.no_autotune, both=True)
     if world > 1:
         dist.barrier()
     if rank != 0:
@@ -710,18 +754,20 @@ TREE_WORKLOAD = ("256x256, L=500, d=999,702 (T1,T2,B1,B0) IR-bSSFP, smooth B0/B1
                  "and both searches on temporally compressed fingerprints")
 
 
-def run_tree(args) -> None:
+def tree_leg(mrf, dev, stream, iters: int, tree_svd=()) -> dict:
     """The cover-tree workload: the million-atom dictionary, the tree built on the host, then
     whole reconstructions of one slice with the BF16 tensor-core brute force and with CoverBLIP
-    (Algorithm 2, warm-started searches) at several eps, plus one cold tree projection of
-    A^H Y per eps for the search kernel's own rate (distance evaluations, unique bytes)."""
+    (Algorithm 2, warm-started searches) at eps in {0, 0.2, 0.5, 1.0}, plus one cold tree
+    projection of A^H Y per eps for the search kernel's own rate (distance evaluations, unique
+    bytes), and for each s of `tree_svd` both searches on temporally compressed fingerprints."""
     import torch
     import mrfgen
-    import paper_1810_01967_gb300 as mrf
-    from paper_1810_01967_gb300 import build as b
-    b.build()
-    dev = torch.device("cuda", 0)
-    stream = torch.cuda.current_stream()
+
+    class _A:
+        pass
+
+    args = _A()
+    args.iters, args.tree_svd = iters, list(tree_svd)
     t0 = time.perf_counter()
     dic = mrfgen.make_dictionary(3)
     p = mrfgen.make_problem(3, dic=dic)
@@ -834,13 +880,27 @@ def run_tree(args) -> None:
             Dc.close()
             del Ac, AHYc, Xc
         del A_dev
+    D.close()
+    return {"n_voxels": n, "L": L, "d": d, "tree": {"build_s_host": build_s, **info},
+            "generate_s": gen_s, "forms": out}
+
+
+def run_tree(args) -> None:
+    import torch
+    import paper_1810_01967_gb300 as mrf
+    from paper_1810_01967_gb300 import build as b
+    b.build()
+    r = tree_leg(mrf, torch.device("cuda", 0), torch.cuda.current_stream(), args.iters,
+                 args.tree_svd)
+    out = r["forms"]
     line = {"metric": "recon s/slice at fixed T1/T2 error (cover tree vs brute force)",
             "value": out["covertree_eps0.5"]["s_per_slice"], "unit": "s/slice", "n_gpus": 1,
             "steps": 1, "warmup": 0, "ms_per_step": 1e3 * out["covertree_eps0.5"]["s_per_slice"],
             "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic",
-            "config": {"workload": TREE_WORKLOAD, "n_voxels": n, "L": L, "d": d},
-            "tree": {"build_s_host": build_s, **info}, "generate_s": gen_s, "forms": out}
+            "config": {"workload": TREE_WORKLOAD, "n_voxels": r["n_voxels"], "L": r["L"],
+                       "d": r["d"]},
+            "tree": r["tree"], "generate_s": r["generate_s"], "forms": out}
     print(json.dumps(line), flush=True)
 
 
@@ -1005,9 +1065,31 @@ def run_ours(args) -> None:
         fp32_rate = m * d / (f0.elapsed_time(f1) / 1e3)
     # ------------------------------------------------------------- quality (rank 0)
     quality = None
+    D2 = None
     if rank == 0 and not args.no_quality:
-        quality = reconstruction_quality(mrf, D, op, p, dic, dev, stream, args.iters,
-                                         fp32=not args.no_fp32, forms=not args.no_forms)
+        quality, D2 = reconstruction_quality(mrf, D, op, p, dic, dev, stream, args.iters,
+                                             fp32=not args.no_fp32, forms=not args.no_forms,
+                                             keep=True)
+    # ------------------------------------------------------------- batching form (rank 0)
+    # the 64-slice workload (its dictionary is this one): BF16 and, with the quality leg's
+    # trained network, the learned form, each under CUDA-graph replay, groups of 8 slices
+    slices = None
+    if rank == 0 and not args.no_slices:
+        geo, mine, smasks, sYs = slices_inputs(dic, dev)
+        forms = [("bf16", True)] + ([("learned", True)] if D2 is not None else [])
+        Ds = D2 if D2 is not None else D
+        sout, _, stuned = slices_leg(mrf, Ds, dic, dev, stream, smasks, sYs, geo, mine, forms,
+                                     8, args.iters, 1, True, both=False,
+                                     model=True if D2 is not None else None)
+        slices = {"workload": SLICES_WORKLOAD, "forms": sout,
+                  "autotune": {m: {"tune": t["tune"], "ms": t["ms"]} for m, t in stuned.items()}}
+        del smasks, sYs
+    if D2 is not None:
+        D2.close()
+    # ------------------------------------------------------------- cover tree, 1M atoms (rank 0)
+    tree = None
+    if rank == 0 and not args.no_tree:
+        tree = tree_leg(mrf, dev, stream, args.iters)
     if world > 1:
         dist.barrier()
     if rank != 0:
@@ -1085,6 +1167,8 @@ def run_ours(args) -> None:
                       "autotune": tuned,
                       "fp32_exact_matches_per_s": fp32_rate,
                       "exact_tc": exact_leg,
+                      "slices64": slices,
+                      "tree1m_eps_sweep": tree,
                       "fp32_sample_voxels": args.fp32_sample}}
     print(json.dumps(line), flush=True)
     if world > 1:
@@ -1114,6 +1198,10 @@ def main():
                     help="slices64: keep the library's default search geometry")
     ap.add_argument("--fp32-sample", type=int, default=0)
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-slices", action="store_true",
+                    help="skip the 64-slice batching leg of the default run")
+    ap.add_argument("--no-tree", action="store_true",
+                    help="skip the million-atom cover-tree leg of the default run")
     ap.add_argument("--no-exact", action="store_true",
                     help="skip the exact tensor-core (split-BF16) leg of the default run")
     ap.add_argument("--workload", default="slice", choices=["slice", "slices64", "tree1m"],

@@ -25,13 +25,20 @@ mrf_status fail(mrf_status s, const std::string& msg) {
     return s;
 }
 
+
 // Fault injection (mrf_debug_fail_alloc): the number of allocations still to succeed before one
 // is refused, or -1.
 std::atomic<int64_t> g_fail_alloc_after{-1};
 
+std::atomic<uint64_t> g_scratch_epoch{0};
+
 template <typename T>
 mrf_status dalloc(T** p, size_t count) {
-    if (*p) { cudaFree(*p); *p = nullptr; }
+    if (*p) {
+        cudaFree(*p);
+        *p = nullptr;
+        scratch_epoch_bump();
+    }
     if (count == 0) return MRF_OK;
     int64_t left = g_fail_alloc_after.load();
     while (left >= 0 && !g_fail_alloc_after.compare_exchange_weak(left, left - 1)) {}
@@ -51,6 +58,9 @@ std::mutex g_plan_mu;
 std::map<std::tuple<int, int, int, int>, cufftHandle> g_plans;
 
 }  // namespace
+
+uint64_t scratch_epoch() { return g_scratch_epoch.load(); }
+void scratch_epoch_bump() { g_scratch_epoch.fetch_add(1); }
 
 mrf_status get_plan(int kind, int Ny, int Nx, int L, cudaStream_t st, cufftHandle* out) {
     std::lock_guard<std::mutex> lk(g_plan_mu);
@@ -136,7 +146,10 @@ mrf_status ensure_scratch(mrf_dict* D, int64_t n) {
 mrf_status ensure_part(mrf_dict* D, int64_t n, int S, int K) {
     size_t need = static_cast<size_t>(S) * n * K * (sizeof(float) + sizeof(int32_t));
     if (need <= D->part_bytes) return MRF_OK;
-    if (D->part) cudaFree(D->part);
+    if (D->part) {
+        cudaFree(D->part);
+        scratch_epoch_bump();
+    }
     D->part = nullptr;
     D->part_bytes = 0;
     cudaError_t e = cudaMalloc(&D->part, need);
@@ -567,6 +580,10 @@ mrf_status gradient_to(const mrf_op* op, const float2* AHY, const float2* X, flo
     if (grad_fused_supported(op->Ny)) {          // one pass: y-transforms, mask, combine
         ProfScope ps0(0, 1, st);
         return launch_grad_fused(op, AHY, X, mu, Z, zq, Kp, err, st);
+    }
+    if (grad_multi_supported(op->Ny)) {          // the same pass with mixed-radix transforms
+        ProfScope ps0(0, 1, st);
+        return launch_grad_mixed(op, AHY, X, mu, Z, zq, Kp, err, st);
     }
     cufftHandle hy;
     MRF_TRY(get_plan(0, op->Ny, op->Nx, op->L, st, &hy));

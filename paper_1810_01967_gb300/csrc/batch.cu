@@ -2,15 +2,18 @@
 //
 // All slices stay resident in HBM, stacked voxel-major: X, A^H Y, the gradient output Z and the
 // BF16 query operand are [sum n_s][...] with per-slice offsets.  One iteration runs the
-// gradient step of every slice (its own y-FFT plan and line masks, writing its rows of Z and of
-// the packed operand) and then one projection over all stacked voxels -- a single persistent
+// gradient step of every slice -- one launch over all stacked slices when every Ny factors into
+// 2, 3 and 5 (mixed-radix y-transforms in shared memory, a descriptor table locating each
+// slice's rows and masks), else per slice with its own y-FFT plan -- writing the rows of Z and of
+// the packed operand, and then one projection over all stacked voxels: a single persistent
 // launch of the search kernel against the shared dictionary, however uneven the slices.  With
 // `use_graph` the iteration is captured once into a CUDA graph on an internal stream and
 // replayed; the first iteration runs eagerly so that cuFFT plans and scratch are created
-// outside the capture.  Only projections without host synchronisation can be captured: FP32,
-// BF16 or FP8 without certification, and -- with the dictionary's BF16 operand -- the cover-tree
-// and learned forms, whose exhaustive fallback then takes its voxel count from the device
-// (mrf_dict::sync_free) instead of reading it back.
+// outside the capture, and a graph is captured again when any scratch buffer it references has
+// been reallocated since (the scratch epoch).  Only projections without host synchronisation
+// can be captured: FP32, BF16 or FP8 without certification, and -- with the dictionary's BF16
+// operand -- the cover-tree and learned forms, whose exhaustive fallback then takes its voxel
+// count from the device (mrf_dict::sync_free) instead of reading it back.
 #include <cstring>
 #include <vector>
 
@@ -31,6 +34,10 @@ struct mrf_batch {
     cudaGraphExec_t exec = nullptr;
     mrf_proj_opts gopts = {};
     float gmu = 0.f;
+    uint64_t gepoch = 0;        // scratch epoch the graph was captured at
+    void* gtable = nullptr;     // descriptor table of the one-launch gradient (device)
+    int64_t gtiles = 0;         // its CTA tiles; 0: per-slice gradient steps
+    int gmaxNy = 0;
 };
 
 namespace {
@@ -60,10 +67,17 @@ mrf_status iterate(mrf_batch* B, float mu, const mrf_proj_opts* o, cudaStream_t 
     const int L = D->L;
     MRF_TRY(dict_ensure_scratch(D, B->n_total));     // a no-op unless another call shrank it
     const bool zq = (o->mode == MRF_PROJ_BF16);
-    for (size_t s = 0; s < B->ops.size(); ++s) {
-        const int64_t a = B->off[s];
-        MRF_TRY(gradient_to(&B->ops[s], B->AHY + a * L, B->X + a * L, mu, D->zbuf + a * L, D->wbuf,
-                            zq ? D->zq + a * D->Kp : nullptr, D->Kp, D->err, st));
+    if (B->gtiles > 0) {
+        ProfScope ps0(0, 1, st);
+        MRF_TRY(launch_grad_multi(B->gtable, static_cast<int>(B->ops.size()), B->gtiles,
+                                  B->gmaxNy, B->X, B->AHY, L, mu, D->zbuf, zq ? D->zq : nullptr,
+                                  D->Kp, D->err, st));
+    } else {
+        for (size_t s = 0; s < B->ops.size(); ++s) {
+            const int64_t a = B->off[s];
+            MRF_TRY(gradient_to(&B->ops[s], B->AHY + a * L, B->X + a * L, mu, D->zbuf + a * L,
+                                D->wbuf, zq ? D->zq + a * D->Kp : nullptr, D->Kp, D->err, st));
+        }
     }
     return project_core(D, D->zbuf, B->n_total, o, B->idx, B->idx, B->rho, B->X, zq, st);
 }
@@ -85,7 +99,7 @@ void mrf_batch_free(mrf_batch* B) {
     if (B->cs) cudaStreamDestroy(B->cs);
     if (B->ev_in) cudaEventDestroy(B->ev_in);
     if (B->ev_out) cudaEventDestroy(B->ev_out);
-    void* ptrs[] = {B->X, B->AHY, B->idx, B->rho};
+    void* ptrs[] = {B->X, B->AHY, B->idx, B->rho, B->gtable};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     delete B;
@@ -125,6 +139,13 @@ mrf_status mrf_batch_create(mrf_dict* D, int32_t n_slices, const mrf_op* ops, mr
     mrf_status st = dict_ensure_scratch(D, B->n_total);
     if (st != MRF_OK) { mrf_batch_free(B); return st; }
     (void)max_n;
+    bool all_multi = true;
+    for (const mrf_op& o : B->ops) all_multi = all_multi && grad_multi_supported(o.Ny);
+    if (all_multi) {
+        st = grad_multi_table(B->ops.data(), B->off.data(), n_slices, &B->gtable, &B->gtiles,
+                              &B->gmaxNy, nullptr);
+        if (st != MRF_OK) { mrf_batch_free(B); return st; }
+    }
     *out = B;
     return MRF_OK;
 }
@@ -159,7 +180,10 @@ mrf_status mrf_batch_run(mrf_batch* B, int32_t iters, float mu, const mrf_proj_o
             MRF_TRY(iterate(B, mu, &o, st));
             continue;
         }
-        const bool same = B->exec && B->gmu == mu &&
+        // the graph holds the addresses of the dictionary's scratch buffers: replay it only
+        // while none of them has been reallocated since the capture (another batch or
+        // projection may have grown them), else capture again
+        const bool same = B->exec && B->gmu == mu && B->gepoch == scratch_epoch() &&
                           std::memcmp(&B->gopts, &o, sizeof(o)) == 0;
         if (!same) {
             drop_graph(B);
@@ -180,6 +204,7 @@ mrf_status mrf_batch_run(mrf_batch* B, int32_t iters, float mu, const mrf_proj_o
             MRF_CUDA_TRY(cudaGraphInstantiate(&B->exec, g, 0));
             B->gopts = o;
             B->gmu = mu;
+            B->gepoch = scratch_epoch();
         }
         MRF_CUDA_TRY(cudaEventRecord(B->ev_in, st));
         MRF_CUDA_TRY(cudaStreamWaitEvent(B->cs, B->ev_in, 0));

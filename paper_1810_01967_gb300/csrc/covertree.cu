@@ -533,7 +533,10 @@ mrf_status launch_ct_search(const float2* Z, int64_t n, const mrf_dict* D, int c
             }
             for (void** p : {reinterpret_cast<void**>(&tm->okey), reinterpret_cast<void**>(&tm->oval),
                              &tm->otmp}) {
-                if (*p) cudaFree(*p);
+                if (*p) {
+                    cudaFree(*p);
+                    scratch_epoch_bump();
+                }
                 *p = nullptr;
             }
             tm->ocap = 0;

@@ -176,7 +176,6 @@ k_grad_pow2(const float2* __restrict__ X, const float2* __restrict__ AHY,
     const int64_t ct = c0 + jt;
     const bool live = ct < NxL;
     const int tcol = live ? static_cast<int>(ct % L) : 0;      // frame of the column
-    const int64_t xcol = live ? ct / L : 0;                     // x of the column
     // load X bit-reversed along y
     for (int i = tid; i < Ny * TC; i += NT) {
         const int ky = i >> LTC;
@@ -366,4 +365,297 @@ mrf_status launch_yfft_inv_combine(const float2* W2, const float2* X, const floa
         return MRF_ECUDA;
     }
     return MRF_OK;
+}
+
+// ------------------------------------------------------------------ any Ny with factors 2, 3, 5
+// The same gradient step for Ny = 2^a 3^b 5^c (up to kMultiMaxNy), and for many slices of
+// different sizes in one launch (the stacked slices of a batch): a CTA owns TC columns of one
+// slice, found from its tile index in the slices' descriptor table.  The y-transforms are
+// Stockham autosort passes of radix 4, 2, 3 and 5 between two shared-memory buffers (natural
+// order in and out), with a full-length twiddle table exp(-2 pi i m / Ny).
+namespace {
+
+constexpr int kMultiMaxNy = 512;
+constexpr float kC3 = 0.86602540378443864676f;          // sin(2 pi / 3)
+constexpr float kC51 = 0.30901699437494742410f;         // cos(2 pi / 5)
+constexpr float kC52 = -0.80901699437494742410f;        // cos(4 pi / 5)
+constexpr float kS51 = 0.95105651629515357212f;         // sin(2 pi / 5)
+constexpr float kS52 = 0.58778525229247312917f;         // sin(4 pi / 5)
+
+__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ float2 cscale(float2 a, float s) { return make_float2(a.x * s, a.y * s); }
+// s i z for the sign s = +1 / -1
+__device__ __forceinline__ float2 cmul_si(float2 z, float s) { return make_float2(-s * z.y, s * z.x); }
+
+// In-place DFT of size R (2, 3, 4, 5) with kernel exp(s 2 pi i r k / R).
+__device__ __forceinline__ void small_dft(float2 (&v)[5], int R, float s) {
+    if (R == 2) {
+        const float2 a = v[0], b = v[1];
+        v[0] = cadd(a, b);
+        v[1] = csub(a, b);
+    } else if (R == 4) {
+        const float2 t0 = cadd(v[0], v[2]), t1 = csub(v[0], v[2]);
+        const float2 t2 = cadd(v[1], v[3]), t3 = cmul_si(csub(v[1], v[3]), s);
+        v[0] = cadd(t0, t2);
+        v[2] = csub(t0, t2);
+        v[1] = cadd(t1, t3);
+        v[3] = csub(t1, t3);
+    } else if (R == 3) {
+        const float2 u = cadd(v[1], v[2]), w = cmul_si(csub(v[1], v[2]), s * kC3);
+        const float2 m = csub(v[0], cscale(u, 0.5f));
+        v[0] = cadd(v[0], u);
+        v[1] = cadd(m, w);
+        v[2] = csub(m, w);
+    } else {   // R == 5
+        const float2 b1 = cadd(v[1], v[4]), b2 = cadd(v[2], v[3]);
+        const float2 d1 = csub(v[1], v[4]), d2 = csub(v[2], v[3]);
+        const float2 a0 = v[0];
+        const float2 p1 = cadd(a0, cadd(cscale(b1, kC51), cscale(b2, kC52)));
+        const float2 p2 = cadd(a0, cadd(cscale(b1, kC52), cscale(b2, kC51)));
+        const float2 q1 = cmul_si(cadd(cscale(d1, kS51), cscale(d2, kS52)), s);
+        const float2 q2 = cmul_si(csub(cscale(d1, kS52), cscale(d2, kS51)), s);
+        v[0] = cadd(a0, cadd(b1, b2));
+        v[1] = cadd(p1, q1);
+        v[4] = csub(p1, q1);
+        v[2] = cadd(p2, q2);
+        v[3] = csub(p2, q2);
+    }
+}
+
+// Stockham y-transform of the TC columns of `a` ([Ny][TC], natural order); the result is in
+// the returned buffer (a or b).  s = -1 forward, +1 inverse (unscaled).  Ends with a barrier.
+template <int LTC>
+__device__ float2* tile_fft_mixed(float2* a, float2* b, const float2* tw, int Ny, float s,
+                                  int tid, int jt) {
+    constexpr int TC = 1 << LTC;
+    int rem = Ny, Ns = 1;
+    while (rem > 1) {
+        const int R = (rem % 4 == 0) ? 4 : (rem % 2 == 0) ? 2 : (rem % 3 == 0) ? 3 : 5;
+        const int NR = Ny / R;
+        const int step = Ny / (Ns * R);          // twiddle index stride for k * r
+        for (int q = tid; q < NR * TC; q += NT) {
+            const int j = q >> LTC;
+            const int k = j % Ns;
+            float2 v[5];
+#pragma unroll
+            for (int r = 0; r < 5; ++r)
+                if (r < R) v[r] = a[((j + r * NR) << LTC) + jt];
+            if (Ns > 1) {
+#pragma unroll
+                for (int r = 1; r < 5; ++r)
+                    if (r < R) {
+                        float2 w = tw[(k * r * step) % Ny];      // exp(-2 pi i m / Ny)
+                        if (s > 0.f) w.y = -w.y;                   // inverse: conjugate
+                        v[r] = cmul(v[r], w);
+                    }
+            }
+            small_dft(v, R, s);
+            const int base = (j / Ns) * Ns * R + k;
+#pragma unroll
+            for (int r = 0; r < 5; ++r)
+                if (r < R) b[((base + r * Ns) << LTC) + jt] = v[r];
+        }
+        __syncthreads();
+        float2* t = a;
+        a = b;
+        b = t;
+        Ns *= R;
+        rem /= R;
+    }
+    return a;
+}
+
+
+// Per-slice descriptor of a multi-slice launch (slices stacked voxel-major: slice i's voxels
+// start at row voff of the stacked [n][L] arrays).
+struct SliceDesc {
+    int64_t voff;          // first stacked voxel of the slice
+    int64_t tile0;         // first CTA tile of the slice
+    int32_t Ny, Nx;
+    const uint8_t* mask;   // [L][Ny]
+    const float2* tw;      // [Ny] exp(-2 pi i m / Ny)
+};
+
+// One CTA: TC consecutive columns c = x L + t of one slice.  Dynamic shared memory: two
+// [maxNy][TC] buffers and the twiddles.
+template <int LTC>
+__global__ void __launch_bounds__(NT)
+k_grad_multi(const SliceDesc* __restrict__ descs, SliceDesc one, int nslices, int maxNy,
+             const float2* __restrict__ X, const float2* __restrict__ AHY, int L, float mu,
+             float2* __restrict__ Z, __nv_bfloat162* __restrict__ zq, int Kp, uint32_t* err) {
+    constexpr int TC = 1 << LTC;
+    extern __shared__ float2 sbuf[];
+    __shared__ int s_slice;
+    const int tid = threadIdx.x;
+    const int64_t tile = blockIdx.x;
+    if (tid == 0) {
+        int lo = 0, hi = nslices - 1;             // last slice whose tile0 <= tile
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (descs[mid].tile0 <= tile) lo = mid; else hi = mid - 1;
+        }
+        s_slice = lo;
+    }
+    __syncthreads();
+    const SliceDesc sd = (nslices == 1 && descs == nullptr) ? one : descs[s_slice];
+    const int Ny = sd.Ny, Nx = sd.Nx;
+    float2* bufA = sbuf;
+    float2* bufB = sbuf + static_cast<int64_t>(maxNy) * TC;
+    float2* w = sbuf + 2 * static_cast<int64_t>(maxNy) * TC;
+    for (int k = tid; k < Ny; k += NT) w[k] = sd.tw[k];
+    const int64_t NxL = static_cast<int64_t>(Nx) * L;
+    const int jt = tid & (TC - 1);
+    const int64_t ct = (tile - sd.tile0) * TC + jt;
+    const bool live = ct < NxL;
+    const int tcol = live ? static_cast<int>(ct % L) : 0;
+    const int64_t xcol = live ? ct / L : 0;
+    const float2* Xs = X + sd.voff * L;
+    const float2* As = AHY + sd.voff * L;
+    float2* Zs = Z + sd.voff * L;
+    for (int i = tid; i < Ny * TC; i += NT) {
+        const int ky = i >> LTC;
+        bufA[i] = live ? Xs[static_cast<int64_t>(ky) * NxL + ct] : make_float2(0.f, 0.f);
+    }
+    __syncthreads();
+    float2* kf = tile_fft_mixed<LTC>(bufA, bufB, w, Ny, -1.f, tid, jt);
+    const uint8_t* mrow = sd.mask + static_cast<int64_t>(tcol) * Ny;
+    for (int i = tid; i < Ny * TC; i += NT) {
+        const int ky = i >> LTC;
+        if (!live || !mrow[ky]) kf[i] = make_float2(0.f, 0.f);
+    }
+    __syncthreads();
+    float2* other = (kf == bufA) ? bufB : bufA;
+    const float2* g = tile_fft_mixed<LTC>(kf, other, w, Ny, 1.f, tid, jt);
+    if (!live) return;
+    const float gs = 1.0f / static_cast<float>(Ny);
+    const int half = Kp / 2;
+    for (int i = tid; i < Ny * TC; i += NT) {
+        const int ky = i >> LTC;
+        const float2 gv = g[i];
+        const int64_t o = static_cast<int64_t>(ky) * NxL + ct;
+        const float2 x = Xs[o], a = As[o];
+        float2 z;
+        z.x = x.x - mu * (gs * gv.x - a.x);
+        z.y = x.y - mu * (gs * gv.y - a.y);
+        if (!isfinite(z.x) || !isfinite(z.y)) atomicOr(err, MRF_DERR_NONFINITE);
+        Zs[o] = z;
+        if (zq) {
+            const int64_t v = sd.voff + static_cast<int64_t>(ky) * Nx + xcol;
+            zq[v * half + tcol] = __floats2bfloat162_rn(z.x, z.y);
+            if (tcol == L - 1)
+                for (int tt = L; tt < half; ++tt) zq[v * half + tt] = __floats2bfloat162_rn(0.f, 0.f);
+        }
+    }
+}
+
+std::mutex g_twf_mu;
+std::map<std::pair<int, int>, float2*> g_twf;    // (device, Ny) -> full-length twiddles
+
+mrf_status twiddles_full(int Ny, const float2** out) {
+    int dev = 0;
+    MRF_CUDA_TRY(cudaGetDevice(&dev));
+    std::lock_guard<std::mutex> lk(g_twf_mu);
+    auto key = std::make_pair(dev, Ny);
+    auto it = g_twf.find(key);
+    if (it != g_twf.end()) { *out = it->second; return MRF_OK; }
+    std::vector<float2> h(Ny);
+    const double two_pi = 6.283185307179586476925286766559;
+    for (int k = 0; k < Ny; ++k) {
+        const double a = two_pi * k / Ny;
+        h[k] = make_float2(static_cast<float>(std::cos(a)), static_cast<float>(-std::sin(a)));
+    }
+    float2* d = nullptr;
+    MRF_CUDA_TRY(cudaMalloc(&d, sizeof(float2) * h.size()));
+    MRF_CUDA_TRY(cudaMemcpy(d, h.data(), sizeof(float2) * h.size(), cudaMemcpyHostToDevice));
+    g_twf[key] = d;
+    *out = d;
+    return MRF_OK;
+}
+
+size_t multi_smem(int maxNy) {
+    constexpr int TC = 1 << kTileLog;
+    return sizeof(float2) * (2 * static_cast<size_t>(maxNy) * TC + maxNy);
+}
+
+mrf_status launch_multi(const SliceDesc* descs, SliceDesc one, int nslices, int64_t tiles,
+                        int maxNy, const float2* X, const float2* AHY, int L, float mu, float2* Z,
+                        __nv_bfloat16* zq, int Kp, uint32_t* err, cudaStream_t st) {
+    constexpr int LTC = kTileLog;
+    const size_t sm = multi_smem(maxNy);
+    cudaError_t e = cudaFuncSetAttribute(k_grad_multi<LTC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         static_cast<int>(sm));
+    if (e == cudaSuccess) {
+        k_grad_multi<LTC><<<static_cast<unsigned>(tiles), NT, sm, st>>>(
+            descs, one, nslices, maxNy, X, AHY, L, mu, Z, reinterpret_cast<__nv_bfloat162*>(zq),
+            zq ? Kp : 2 * L, err);
+        e = cudaGetLastError();
+    }
+    if (e != cudaSuccess) {
+        mrf_set_error(std::string("multi-slice gradient launch: ") + cudaGetErrorString(e));
+        return MRF_ECUDA;
+    }
+    return MRF_OK;
+}
+
+}  // namespace
+
+bool grad_multi_supported(int Ny) {
+    if (Ny < 2 || Ny > kMultiMaxNy) return false;
+    int r = Ny;
+    for (int f : {2, 3, 5})
+        while (r % f == 0) r /= f;
+    return r == 1;
+}
+
+mrf_status launch_grad_mixed(const mrf_op* op, const float2* AHY, const float2* X, float mu,
+                             float2* Z, __nv_bfloat16* zq, int Kp, uint32_t* err, cudaStream_t st) {
+    SliceDesc one{};
+    one.voff = 0;
+    one.tile0 = 0;
+    one.Ny = op->Ny;
+    one.Nx = op->Nx;
+    one.mask = op->mask;
+    MRF_TRY(twiddles_full(op->Ny, &one.tw));
+    constexpr int TC = 1 << kTileLog;
+    const int64_t tiles = (static_cast<int64_t>(op->Nx) * op->L + TC - 1) / TC;
+    return launch_multi(nullptr, one, 1, tiles, op->Ny, X, AHY, op->L, mu, Z, zq, Kp, err, st);
+}
+
+// The batch's slices in one launch: builds the descriptor table (device memory owned by the
+// caller through *table, reused while the slices stay the same).
+mrf_status grad_multi_table(const mrf_op* ops, const int64_t* voff, int nslices, void** table,
+                            int64_t* tiles, int* maxNy, cudaStream_t st) {
+    constexpr int TC = 1 << kTileLog;
+    std::vector<SliceDesc> h(nslices);
+    int64_t t = 0;
+    int mx = 0;
+    for (int i = 0; i < nslices; ++i) {
+        if (!grad_multi_supported(ops[i].Ny)) {
+            mrf_set_error("multi-slice gradient: Ny must be 2^a 3^b 5^c, at most 512");
+            return MRF_EUNSUPPORTED;
+        }
+        h[i].voff = voff[i];
+        h[i].tile0 = t;
+        h[i].Ny = ops[i].Ny;
+        h[i].Nx = ops[i].Nx;
+        h[i].mask = ops[i].mask;
+        MRF_TRY(twiddles_full(ops[i].Ny, &h[i].tw));
+        t += (static_cast<int64_t>(ops[i].Nx) * ops[i].L + TC - 1) / TC;
+        mx = ops[i].Ny > mx ? ops[i].Ny : mx;
+    }
+    if (!*table) MRF_CUDA_TRY(cudaMalloc(table, sizeof(SliceDesc) * nslices));
+    MRF_CUDA_TRY(cudaMemcpyAsync(*table, h.data(), sizeof(SliceDesc) * nslices,
+                                 cudaMemcpyHostToDevice, st));
+    MRF_CUDA_TRY(cudaStreamSynchronize(st));
+    *tiles = t;
+    *maxNy = mx;
+    return MRF_OK;
+}
+
+mrf_status launch_grad_multi(const void* table, int nslices, int64_t tiles, int maxNy,
+                             const float2* X, const float2* AHY, int L, float mu, float2* Z,
+                             __nv_bfloat16* zq, int Kp, uint32_t* err, cudaStream_t st) {
+    return launch_multi(static_cast<const SliceDesc*>(table), SliceDesc{}, nslices, tiles, maxNy,
+                        X, AHY, L, mu, Z, zq, Kp, err, st);
 }

@@ -629,7 +629,11 @@ namespace {
 
 template <typename T>
 mrf_status alloc(T** p, size_t count) {
-    if (*p) { cudaFree(*p); *p = nullptr; }
+    if (*p) {
+        cudaFree(*p);
+        *p = nullptr;
+        scratch_epoch_bump();
+    }
     if (!count) return MRF_OK;
     if (cudaMalloc(reinterpret_cast<void**>(p), count * sizeof(T)) != cudaSuccess) {
         cudaGetLastError();

@@ -93,6 +93,12 @@ struct mrf_dict {
 // thread-local error text
 void mrf_set_error(const std::string& msg);
 
+// Epoch of the device buffers a captured iteration may reference: bumped whenever such a buffer
+// (dictionary scratch, candidate partials, learned-proposal and tree workspaces) is freed to be
+// reallocated.  A CUDA graph captured at one epoch is replayed only at that epoch.
+uint64_t scratch_epoch();
+void scratch_epoch_bump();
+
 #define MRF_CUDA_TRY(expr)                                                              \
     do {                                                                                \
         cudaError_t e_ = (expr);                                                        \
@@ -195,6 +201,16 @@ mrf_status ct_export(const mrf_dict* D, int32_t* first_level, int32_t* parent, i
 bool grad_fused_supported(int Ny);
 mrf_status launch_grad_fused(const mrf_op* op, const float2* AHY, const float2* X, float mu,
                              float2* Z, __nv_bfloat16* zq, int Kp, uint32_t* err, cudaStream_t st);
+// any Ny = 2^a 3^b 5^c up to 512 (mixed-radix y-transforms): one slice, or the stacked slices
+// of a batch in one launch from a descriptor table (grad_multi_table builds it in *table)
+bool grad_multi_supported(int Ny);
+mrf_status launch_grad_mixed(const mrf_op* op, const float2* AHY, const float2* X, float mu,
+                             float2* Z, __nv_bfloat16* zq, int Kp, uint32_t* err, cudaStream_t st);
+mrf_status grad_multi_table(const mrf_op* ops, const int64_t* voff, int nslices, void** table,
+                            int64_t* tiles, int* maxNy, cudaStream_t st);
+mrf_status launch_grad_multi(const void* table, int nslices, int64_t tiles, int maxNy,
+                             const float2* X, const float2* AHY, int L, float mu, float2* Z,
+                             __nv_bfloat16* zq, int Kp, uint32_t* err, cudaStream_t st);
 // the halves of the fused kernel for an image of C columns per x (power-of-two Ny): W = the
 // unscaled y-DFT of X; Z = X - mu (F_y^-1 W2 (unscaled, then / Ny) - AHY) (+ BF16 operand)
 mrf_status launch_yfft_fwd(const float2* X, int Ny, int Nx, int C, float2* W, cudaStream_t st);

@@ -73,10 +73,18 @@ def test_batch_equals_slices_alone(mrf, setup, mode):
         Xe, ie, _ = res[False][s]
         assert np.array_equal(ig, ie) and np.array_equal(Xg, Xe)   # graph replay == eager
         Xa, ia = alone(mrf, D, p, iters, opts)
-        if mode == "fp32":
-            # same gradient plans and the same exact projection: identical iterates
+        pow2 = (p["Ny"] & (p["Ny"] - 1)) == 0
+        if mode == "fp32" and not pow2:
+            # the batch's one-launch gradient is the single slice's mixed-radix kernel on the
+            # same tiles, and the projection is exact: identical iterates
             assert np.array_equal(ie, ia)
             np.testing.assert_allclose(Xe, Xa, rtol=0, atol=1e-6 * np.abs(Xa).max())
+        elif mode == "fp32":
+            # a power-of-two slice alone runs the radix-2 kernel, in the batch the mixed-radix
+            # one: the transforms round differently (~1e-7), so atoms may differ at near-ties
+            same = ie == ia
+            assert same.mean() >= 0.995
+            np.testing.assert_allclose(Xe[same], Xa[same], rtol=0, atol=1e-5 * np.abs(Xa).max())
         else:
             # BF16 candidate sets depend on the atom split of the launch: same answers up to
             # the BF16 near-ties
@@ -231,6 +239,33 @@ def test_graph_replay_with_device_side_fallback(mrf, setup, mode, pair):
             print(f"{mode} pair={pair} replayed iteration {k} slice {s}: agreement with the "
                   f"oracle {agree:.4f}")
         B.close()
+
+
+def test_graph_replay_after_the_scratch_grew(mrf, setup):
+    """A batch's captured iteration references the dictionary's scratch buffers; when another,
+    larger batch on the same dictionary grows (reallocates) them, the first batch's next replay
+    captures again instead of touching the freed buffers: its iterates equal an eager run of
+    the same slices bit for bit."""
+    dic, probs = setup
+    D = mrf.build_dict_index(dic["atoms"], dic["params"], pack_bf16=True)
+    opts = mrf.proj_opts(mode="fp32", certify=False)
+    small = [probs[0]]
+    big = [mrfgen.make_problem(1, 7 + k, dic=dic, N=64) for k in range(3)]
+    A, _ = make_batch(mrf, D, small)
+    A.run(2, 1.0, opts, use_graph=True)           # eager iteration, then a captured one
+    Bb, _ = make_batch(mrf, D, big)               # grows the dictionary's scratch
+    Bb.run(2, 1.0, opts, use_graph=True)
+    A.run(3, 1.0, opts, use_graph=True)           # eager, then replays: captured again
+    torch.cuda.synchronize()
+    Xg, ig, _ = slice_arrays(A, 0)
+    E, _ = make_batch(mrf, D, small)
+    E.run(5, 1.0, opts)
+    torch.cuda.synchronize()
+    Xe, ie, _ = slice_arrays(E, 0)
+    assert np.array_equal(ig, ie) and np.array_equal(Xg, Xe)
+    D.check()
+    for b in (A, Bb, E):
+        b.close()
 
 
 def test_capture_rules_and_errors(mrf, setup):

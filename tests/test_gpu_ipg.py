@@ -224,10 +224,12 @@ def test_kappa_rescale_matches_oracle(mrf, cfg1):
           f"largest row error / RMS row norm {np.max(num / rms):.2e}")
 
 
-@pytest.mark.parametrize("N", [16, 24, 32, 64, 40])
+@pytest.mark.parametrize("N", [16, 24, 32, 64, 40, 48, 60, 96, 192, 28])
 def test_gradient_step_both_paths(mrf, cfg1, N):
     """Z = X - mu A^H(A X - Y) against the oracle for power-of-two Ny (the one-pass kernel:
-    y-transforms, mask and combine in shared memory) and other Ny (cuFFT path)."""
+    radix-2 y-transforms, mask and combine in shared memory), Ny = 2^a 3^b 5^c (the same pass
+    with mixed-radix Stockham transforms: 24, 40, 48, 60, 96, 192) and other Ny (cuFFT path:
+    28)."""
     dic, _ = cfg1
     p = mrfgen.make_problem(1, dic=dic, N=N)
     Ny, Nx, L = p["Ny"], p["Nx"], p["L"]
