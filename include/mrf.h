@@ -56,12 +56,26 @@ typedef enum mrf_proj_mode {
     MRF_PROJ_FP8 = 2,         /* exhaustive, FP8 e4m3 tensor cores, rescored as BF16 */
     MRF_PROJ_COVERTREE = 3,   /* cover-tree (1+eps)-ANNS, Algorithm 1 (§4.1) */
     MRF_PROJ_LEARNED = 4,     /* MLP proposal + exact neighbourhood rescore + fallback */
-    MRF_PROJ_BF16X3 = 5       /* exact exhaustive projection on the tensor cores: split-BF16
+    MRF_PROJ_BF16X3 = 5,      /* exact exhaustive projection on the tensor cores: split-BF16
                                  operands (x = hi + lo, three products per pair in one FP32
                                  accumulation), top-K (default 32) rescored exactly, every voxel
                                  certified against its own error bound (see cert_margin) and
                                  the uncertified ones searched in FP32; needs
                                  mrf_index_opts.pack_bf16x3 */
+    MRF_PROJ_TREE_TC = 6      /* query-batched cover-tree search on the tensor cores (§4.1
+                                 Algorithm 1 and Def. eNN, with the query grouping of §7): the
+                                 tree's depth-first order cut into 128-atom blocks with exact
+                                 enclosing balls; per voxel the blocks that can hold an atom
+                                 closer than r_v / (1 + eps) (r_v: the nearest block centre's
+                                 distance, bounded from the split-BF16 centre correlations);
+                                 voxels grouped into 128-voxel tiles by nearest centre, each
+                                 tile's union of blocks searched on the tensor cores and the
+                                 top K rescored exactly.  With `certify` (and the split-BF16
+                                 operand) the result is certified as for MRF_PROJ_BF16X3: the
+                                 exact nearest atom for eps = 0, a (1 + eps)-approximate one
+                                 otherwise; without, the BF16 operand ranks the candidates.
+                                 Needs mrf_index_opts.tree_tc and a tree whose metric matches
+                                 the cone */
 } mrf_proj_mode;
 
 /* The cone of eq. model/conedef.  COMPLEX: X_v = rho D_j, rho complex, j maximises
@@ -88,7 +102,9 @@ typedef struct mrf_index_opts {
                               Densities are always reported relative to the atoms as given. */
     int32_t pack_bf16x3;   /* build the split-BF16 operand of MRF_PROJ_BF16X3 (default 0):
                               3 x the BF16 operand's memory (2.4 GB for 100k atoms at L = 1000) */
-    int32_t reserved[1];
+    int32_t tree_tc;       /* with build_tree: the block balls of MRF_PROJ_TREE_TC and copies of
+                              the BF16 / split-BF16 operands (those packed) in the tree's
+                              depth-first order (default 0) */
 } mrf_index_opts;
 
 typedef struct mrf_proj_opts {
@@ -220,6 +236,12 @@ mrf_status mrf_tree_get_info(const mrf_dict* dict, mrf_tree_info* info);
  * to its subtree (§4.1, eq. maxdistbound). */
 mrf_status mrf_tree_export(const mrf_dict* dict, int32_t* first_level, int32_t* parent,
                            int32_t* rep, int32_t* en_atom, int32_t* en_level, float* en_maxdist);
+
+/* Blocks of MRF_PROJ_TREE_TC (any output may be NULL): their number, each block's radius
+ * (host float [nblk]: an upper bound on the tree-metric distance from the block's first atom to
+ * each of its atoms) and the depth-first order (host int32 [nblk * 128]: the atom at each
+ * position, -1 past the last atom).  MRF_EUNSUPPORTED without mrf_index_opts.tree_tc. */
+mrf_status mrf_tree_blocks(const mrf_dict* dict, int64_t* nblk, float* radius, int32_t* perm);
 
 /* Build the cover tree of host atoms on the host alone (no GPU; offline use and tests), with
  * the construction mrf_build_dict_index uses.  atoms: host complex64 [d][L]; cone: the metric.
@@ -563,7 +585,8 @@ mrf_status mrf_set_tune(mrf_dict* dict, const mrf_tune* in);
  * FP8), 3 FP32 search,
  * 4 merge / rescore / density, 5 fallback to the exhaustive search (certification, cover-tree
  * routing or overflow, learned-proposal fallback), 6 look-up table, 7 proposal search (cover
- * tree traversal or learned network + neighbourhood rescore).  Enabling or disabling clears the tables.  Not thread-safe.
+ * tree traversal, learned network + neighbourhood rescore, or the tensor-core tree search's
+ * centre product, bounds, voxel sort and tile lists; its block-list search counts as stage 2).  Enabling or disabling clears the tables.  Not thread-safe.
  */
 #define MRF_PROFILE_STAGES 8
 mrf_status mrf_profile_enable(int32_t on);

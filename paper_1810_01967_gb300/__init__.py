@@ -99,7 +99,7 @@ class Dictionary:
     def __init__(self, atoms, params=None, grid_shape=None, pack_bf16: bool = True,
                  build_tree: bool = False, tree_cone: str = "complex",
                  tree_dup_tol: float = 1e-5, stream=None, pack_fp8: bool = False,
-                 phase_align: bool = False, pack_bf16x3: bool = False):
+                 phase_align: bool = False, pack_bf16x3: bool = False, tree_tc: bool = False):
         import numpy as np
         d, L = atoms.shape
         o = IndexOpts()
@@ -109,6 +109,7 @@ class Dictionary:
         o.phase_align = int(phase_align)
         o.pack_bf16x3 = int(pack_bf16x3)
         o.build_tree = int(build_tree)
+        o.tree_tc = int(tree_tc)
         o.tree_cone = CONES[tree_cone]
         o.tree_dup_tol = tree_dup_tol
         P = 0 if params is None else int(params.shape[1])
@@ -160,6 +161,17 @@ class Dictionary:
         out.update(info)
         return out
 
+    def tree_blocks(self) -> dict:
+        """Blocks of the tensor-core tree search (see mrf_tree_blocks): radius [nblk] and the
+        depth-first order perm [nblk * 128] (-1 past the last atom)."""
+        import numpy as np
+        nb = C.c_int64()
+        _check(lib().mrf_tree_blocks(self.handle, C.byref(nb), None, None))
+        radius = np.empty(nb.value, np.float32)
+        perm = np.empty(nb.value * 128, np.int32)
+        _check(lib().mrf_tree_blocks(self.handle, C.byref(nb), _ptr(radius), _ptr(perm)))
+        return {"nblk": nb.value, "radius": radius, "perm": perm}
+
     def get_tune(self) -> dict:
         t = Tune()
         _check(lib().mrf_get_tune(self.handle, C.byref(t)))
@@ -175,9 +187,9 @@ class Dictionary:
 
 def build_dict_index(atoms, params=None, grid_shape=None, pack_bf16=True, build_tree=False,
                      tree_cone="complex", tree_dup_tol=1e-5, stream=None, pack_fp8=False,
-                     phase_align=False, pack_bf16x3=False):
+                     phase_align=False, pack_bf16x3=False, tree_tc=False):
     return Dictionary(atoms, params, grid_shape, pack_bf16, build_tree, tree_cone, tree_dup_tol,
-                      stream, pack_fp8, phase_align, pack_bf16x3)
+                      stream, pack_fp8, phase_align, pack_bf16x3, tree_tc)
 
 
 def tree_build_host(atoms, cone: str = "complex", dup_tol: float = 1e-5) -> dict:

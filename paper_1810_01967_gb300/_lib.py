@@ -14,7 +14,8 @@ LIB_PATH = os.path.join(HERE, "_build", "libmrf.so")
 
 MRF_OK, MRF_EINVAL, MRF_ENOMEM, MRF_ECUDA, MRF_ENONFINITE, MRF_ETIMEOUT, \
     MRF_EUNSUPPORTED, MRF_EINTERNAL = range(8)
-MODES = {"fp32": 0, "bf16": 1, "fp8": 2, "covertree": 3, "learned": 4, "bf16x3": 5}
+MODES = {"fp32": 0, "bf16": 1, "fp8": 2, "covertree": 3, "learned": 4, "bf16x3": 5,
+         "tree_tc": 6}
 CONES = {"complex": 0, "real_pos": 1}
 
 
@@ -22,7 +23,7 @@ class IndexOpts(C.Structure):
     _fields_ = [("pack_bf16", C.c_int32), ("pack_fp8", C.c_int32), ("build_tree", C.c_int32),
                 ("tree_cone", C.c_int32), ("tree_dup_tol", C.c_float),
                 ("phase_align", C.c_int32), ("pack_bf16x3", C.c_int32),
-                ("reserved", C.c_int32 * 1)]
+                ("tree_tc", C.c_int32)]
 
 
 class TreeInfo(C.Structure):
@@ -102,6 +103,7 @@ SIGNATURES = {
                                       C.c_void_p, C.c_void_p, C.POINTER(C.c_int64),
                                       C.POINTER(C.c_double), C.POINTER(C.c_int32)]),
     "mrf_tree_get_info": (C.c_int, [C.c_void_p, C.POINTER(TreeInfo)]),
+    "mrf_tree_blocks": (C.c_int, [C.c_void_p, C.POINTER(C.c_int64), C.c_void_p, C.c_void_p]),
     "mrf_tree_export": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
                                   C.c_void_p, C.c_void_p]),
     "mrf_dict_check": (C.c_int, [C.c_void_p, C.c_void_p]),

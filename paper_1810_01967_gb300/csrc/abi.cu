@@ -111,9 +111,9 @@ mrf_status check_op(const mrf_op* op) {
 
 // ------------------------------------------------------------------------------ scratch
 int topk_slots(const mrf_proj_opts* o) {
-    const int def = o->mode == MRF_PROJ_FP32_EXACT
-                        ? 8
-                        : ((o->mode == MRF_PROJ_FP8 || o->mode == MRF_PROJ_BF16X3) ? 32 : 16);
+    const bool k32 = o->mode == MRF_PROJ_FP8 || o->mode == MRF_PROJ_BF16X3 ||
+                     (o->mode == MRF_PROJ_TREE_TC && o->certify);
+    const int def = o->mode == MRF_PROJ_FP32_EXACT ? 8 : (k32 ? 32 : 16);
     const int k = o->topk > 0 ? o->topk : def;
     if (o->mode == MRF_PROJ_FP32_EXACT) return k <= 8 ? 8 : 16;   // FP32 scores: at most 16
     return k <= 8 ? 8 : (k <= 16 ? 16 : 32);
@@ -185,6 +185,14 @@ mrf_status check_proj_opts(const mrf_dict* D, const mrf_proj_opts* o) {
         case MRF_PROJ_BF16X3:
             if (!D->bop3)
                 return fail(MRF_EUNSUPPORTED, "dictionary built without the split-BF16 operand");
+            return MRF_OK;
+        case MRF_PROJ_TREE_TC:
+            if (!D->ttc)
+                return fail(MRF_EUNSUPPORTED,
+                            "dictionary built without the tensor-core tree search (tree_tc)");
+            if (!(o->eps >= 0.f) || !std::isfinite(o->eps)) return fail(MRF_EINVAL, "eps must be >= 0");
+            if ((o->cone == MRF_CONE_COMPLEX) != (ct_metric(D) == 0))
+                return fail(MRF_EINVAL, "the tree's metric does not match the cone (tree_cone)");
             return MRF_OK;
         default: return fail(MRF_EINVAL, "unknown projection mode");
     }
@@ -498,6 +506,34 @@ mrf_status project_impl(mrf_dict* D, const float2* Z, int64_t n, const mrf_proj_
         if (o->certify) MRF_TRY(research_uncertified(D, Z, K, o, idx_out, rho_out, X_out, st));
         return MRF_OK;
     }
+    if (o->mode == MRF_PROJ_TREE_TC) {
+        // block balls of the tree's depth-first order pruned per voxel, voxel tiles sharing one
+        // block list, the tiles searched on the tensor cores (split-BF16 operand when certifying)
+        const bool split = ttc_has_split(D) && (o->certify || !ttc_has_bf16(D));
+        const float brs = rescore_bound(D->L);
+        TtcOut t;
+        MRF_TRY(ttc_search(D, Z, n, o->cone, o->eps, split, K, brs, &t, st));
+        if (o->certify) MRF_CUDA_TRY(cudaMemsetAsync(D->nlist, 0, sizeof(int32_t), st));
+        float margin = o->cert_margin, window;
+        const float* vm = nullptr;
+        if (split) {
+            window = 2.f * x3_bound_worst(D) + o->tie_tol;
+            if (!(o->cert_margin > 0.f)) vm = D->zmarg;
+        } else {
+            bf16_margin(D, o, &margin);
+            float bound;
+            bf16_margin(D, &kRigorous, &bound);
+            window = 2.f * bound + o->tie_tol;
+        }
+        {
+            ProfScope ps4(4, 1, st);
+            MRF_TRY(launch_merge(Z, n, D, o->cone, K, t.S, t.part_s, t.part_i, t.vorder, t.count,
+                                 o->tie_tol, o->certify, margin, idx_out, rho_out, X_out,
+                                 D->vlist, D->nlist, D->err, D->counters, st, window, vm));
+        }
+        if (o->certify) MRF_TRY(research_uncertified(D, Z, K, o, idx_out, rho_out, X_out, st));
+        return MRF_OK;
+    }
     if (o->mode == MRF_PROJ_COVERTREE) {
         MRF_TRY(ensure_part(D, n, 1, 8));
         float* ps = static_cast<float*>(D->part);
@@ -670,6 +706,7 @@ void mrf_default_recon_opts(mrf_recon_opts* o) {
 
 void mrf_dict_free(mrf_dict* D) {
     if (!D) return;
+    if (D->ttc) ttc_free(D->ttc);
     if (D->tree) ct_free(D->tree);
     if (D->mlp) mlp_detach(D->mlp);
     void* ptrs[] = {D->atoms, D->inv_norm2, D->inv_norm, D->norm2, D->params, D->bop, D->zq, D->fop,
@@ -696,6 +733,9 @@ mrf_status mrf_build_dict_index(const void* atoms, int64_t d, int32_t L, const f
     if (o.build_tree && o.tree_cone != MRF_CONE_COMPLEX && o.tree_cone != MRF_CONE_REAL_POS)
         return fail(MRF_EINVAL, "tree_cone must be a mrf_cone");
     if (o.build_tree && !(o.tree_dup_tol >= 0.f)) return fail(MRF_EINVAL, "tree_dup_tol < 0");
+    if (o.tree_tc && !o.build_tree) return fail(MRF_EINVAL, "tree_tc needs build_tree");
+    if (o.tree_tc && !o.pack_bf16 && !o.pack_bf16x3)
+        return fail(MRF_EINVAL, "tree_tc needs pack_bf16 or pack_bf16x3");
     cudaStream_t st = S_(stream);
     mrf_dict* D = new mrf_dict();
     D->d = d;
@@ -780,6 +820,10 @@ mrf_status mrf_build_dict_index(const void* atoms, int64_t d, int32_t L, const f
     if (o.build_tree) {
         s = ct_build_upload(D, o.tree_cone == MRF_CONE_COMPLEX ? 0 : 1, o.tree_dup_tol);
         if (s != MRF_OK) { mrf_dict_free(D); return s; }
+        if (o.tree_tc) {
+            s = ttc_build(D, st);
+            if (s != MRF_OK) { mrf_dict_free(D); return s; }
+        }
     }
     *out = D;
     return MRF_OK;
@@ -788,6 +832,11 @@ mrf_status mrf_build_dict_index(const void* atoms, int64_t d, int32_t L, const f
 mrf_status mrf_tree_get_info(const mrf_dict* D, mrf_tree_info* info) {
     if (!D || !info) return fail(MRF_EINVAL, "dict and info are required");
     return ct_info(D, info);
+}
+
+mrf_status mrf_tree_blocks(const mrf_dict* D, int64_t* nblk, float* radius, int32_t* perm) {
+    if (!D) return fail(MRF_EINVAL, "dict is NULL");
+    return ttc_blocks(D, nblk, radius, perm);
 }
 
 mrf_status mrf_tree_export(const mrf_dict* D, int32_t* first_level, int32_t* parent,

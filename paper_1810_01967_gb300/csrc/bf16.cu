@@ -68,6 +68,33 @@ struct Sched {
     }
 };
 
+// Block lists of the cover-tree search: tile g owns blist[tfirst[g] .. tfirst[g + 1]), split
+// into chunks of `chunk` blocks (one work unit each); perm maps operand positions to atoms.
+struct ListArgs {
+    const int32_t* tfirst;
+    const int32_t* blist;
+    const int32_t* perm;
+    int chunk;
+};
+
+// The blocks of unit (s, g): positions [b0, b1) of the atom-block range (or of the tile's list,
+// starting at lb); false when the unit has none.
+template <bool LIST>
+__device__ __forceinline__ bool unit_blocks(const ListArgs& la, int64_t s, int64_t g, int bps,
+                                            int64_t nblk, int64_t& b0, int64_t& b1, int64_t& lb) {
+    if (LIST) {
+        lb = la.tfirst[g];
+        const int64_t cnt = la.tfirst[g + 1] - lb;
+        b0 = s * la.chunk;
+        b1 = min(b0 + la.chunk, cnt);
+    } else {
+        lb = 0;
+        b0 = s * bps;
+        b1 = min(b0 + bps, nblk);
+    }
+    return b0 < b1;
+}
+
 // Insert (s, j) into the descending list ts (ties keep the earlier entry first).  Every slot
 // decides on its own from one comparison with s -- stay, take s, or take its upper neighbour
 // -- so the KT steps carry no dependency chain: one warp per SM sub-partition runs this and
@@ -135,12 +162,16 @@ __device__ __forceinline__ void epilogue_block(uint32_t tb, int cone, int64_t b,
 // F8: E4M3 operands (kind::f8f6f4); the K kept scores of voxel v are multiplied by
 // (qs[v] gsc)^2 (complex cone) or qs[v] gsc (real cone), qs = 1 / (the query row's scale) and
 // gsc = 1 / (the dictionary's scale).  BF16: scores are used as computed.
-template <int KT, int C, bool F8>
+// LIST: the block-list mode of the cover-tree search -- unit (chunk s, voxel tile g) scans the
+// blocks la.blist[la.tfirst[g] + s chunk ...] of an operand in the tree's depth-first order, and
+// the kept candidates are mapped back to atom indices through la.perm.
+template <int KT, int C, bool F8, bool LIST = false>
 __global__ void __launch_bounds__(NTHREADS, 1)
 k_tc_topk(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
           int64_t n, int64_t d, int64_t nblk, int Kp, int cone, Sched sc, int blocks_per_split,
           float gsc, const float* __restrict__ qs, const int32_t* __restrict__ count,
-          float* __restrict__ part_s, int32_t* __restrict__ part_i, uint32_t* err) {
+          float* __restrict__ part_s, int32_t* __restrict__ part_i, uint32_t* err,
+          ListArgs la) {
     constexpr int EK = F8 ? 128 : 64;     // elements per stage row
     constexpr int KPER = F8 ? 32 : 16;    // elements per MMA instruction (32 bytes either way)
     extern __shared__ __align__(1024) unsigned char smem_raw[];
@@ -202,9 +233,10 @@ k_tc_topk(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
                 sc.map(uc, s, g);
                 if (g * C * BM >= nact) continue;     // the cluster's tiles are all past the count
                 const int64_t m = g * C + rank;
-                const int64_t b0 = s * blocks_per_split;
-                const int64_t b1 = min(b0 + blocks_per_split, nblk);
-                for (int64_t b = b0; b < b1 && !sh->abort; ++b) {
+                int64_t b0, b1, lb;
+                if (!unit_blocks<LIST>(la, s, g, blocks_per_split, nblk, b0, b1, lb)) continue;
+                for (int64_t q = b0; q < b1 && !sh->abort; ++q) {
+                    const int64_t b = LIST ? static_cast<int64_t>(la.blist[lb + q]) : q;
                     for (int kc = 0; kc < nk; ++kc) {
                         if (!mrfk::mbar_wait(&sh->empty[stage], phase ^ 1u)) { fail(); break; }
                         unsigned char* sa = base + stage * STAGE_BYTES;
@@ -239,9 +271,9 @@ k_tc_topk(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
                 int64_t s, g;
                 sc.map(uc, s, g);
                 if (g * C * BM >= nact) continue;     // the cluster's tiles are all past the count
-                const int64_t b0 = s * blocks_per_split;
-                const int64_t b1 = min(b0 + blocks_per_split, nblk);
-                for (int64_t b = b0; b < b1 && !sh->abort; ++b) {
+                int64_t b0, b1, lb;
+                if (!unit_blocks<LIST>(la, s, g, blocks_per_split, nblk, b0, b1, lb)) continue;
+                for (int64_t q = b0; q < b1 && !sh->abort; ++q) {
                     if (!mrfk::mbar_wait(&sh->tempty[acc], aphase ^ 1u)) { fail(); break; }
                     mrfk::tc_fence_after();
                     const uint32_t dt = tmem + static_cast<uint32_t>(acc * BN);
@@ -293,14 +325,15 @@ k_tc_topk(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
             sc.map(uc, s, g);
             if (g * C * BM >= nact) continue;     // the cluster's tiles are all past the count
             const int64_t m = g * C + rank;
-            const int64_t b0 = s * blocks_per_split;
-            const int64_t b1 = min(b0 + blocks_per_split, nblk);
+            int64_t b0, b1, lb;
+            if (!unit_blocks<LIST>(la, s, g, blocks_per_split, nblk, b0, b1, lb)) continue;
             float ts[KT];
             int32_t ti[KT];
 #pragma unroll
             for (int q = 0; q < KT; ++q) { ts[q] = -INFINITY; ti[q] = -1; }
             bool ok = true;
-            for (int64_t b = b0; b < b1; ++b) {
+            for (int64_t qb = b0; qb < b1; ++qb) {
+                const int64_t b = LIST ? static_cast<int64_t>(la.blist[lb + qb]) : qb;
                 if (!mrfk::mbar_wait(&sh->tfull[acc], aphase)) { fail(); ok = false; break; }
                 mrfk::tc_fence_after();
                 const uint32_t tb = tmem + lane_base + static_cast<uint32_t>(acc * BN);
@@ -320,7 +353,10 @@ k_tc_topk(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
                 }
                 const int64_t o = (s * n + v) * KT;
 #pragma unroll
-                for (int q = 0; q < KT; ++q) { part_s[o + q] = ts[q]; part_i[o + q] = ti[q]; }
+                for (int q = 0; q < KT; ++q) {
+                    part_s[o + q] = ts[q];
+                    part_i[o + q] = (LIST && ti[q] >= 0) ? la.perm[ti[q]] : ti[q];
+                }
             }
         }
     }
@@ -625,7 +661,7 @@ mrf_status launch_t(const CUtensorMap& ta, const CUtensorMap& tb, int64_t n, con
         cfg.attrs = attr;
         cfg.numAttrs = 1;
         e = cudaLaunchKernelEx(&cfg, kern, ta, tb, n, D->d, D->nblk, Kp, cone,
-                               sc, bps, gsc, qs, count, part_s, part_i, D->err);
+                               sc, bps, gsc, qs, count, part_s, part_i, D->err, ListArgs{});
     }
     if (e != cudaSuccess) {
         mrf_set_error(std::string("tensor-core search launch: ") + cudaGetErrorString(e));
@@ -868,4 +904,61 @@ mrf_status launch_fp8_topk(const uint8_t* zq8, const float* qs, int64_t n, mrf_d
 mrf_status launch_x3_topk(const __nv_bfloat16* zq3, int64_t n, mrf_dict* D, int cone, int K,
                           int S, float* part_s, int32_t* part_i, cudaStream_t st) {
     return launch_tc(FORM_X3, zq3, nullptr, n, D, cone, K, S, part_s, part_i, nullptr, st);
+}
+
+// Block-list search of the cover-tree form: queries zq [n][Kp] (grouped into 128-row tiles),
+// the depth-first operand op ([nblk * 256][Kp]; BF16 layout, or the split form with Kp = 3 x
+// the BF16 row length), tile g's blocks
+// blist[tfirst[g] .. tfirst[g + 1]) in chunks of `chunk` (maxchunks units per tile), candidates
+// [maxchunks][n][K] with atom indices perm[position]; single CTAs, persistent grid.
+mrf_status launch_bf16_topk_list(const __nv_bfloat16* zq, int64_t n, mrf_dict* D,
+                                 const __nv_bfloat16* op, int Kp, int cone, int K, int maxchunks,
+                                 int chunk, const int32_t* tfirst, const int32_t* blist,
+                                 const int32_t* perm, float* part_s, int32_t* part_i,
+                                 cudaStream_t st) {
+    if (n == 0) return MRF_OK;
+    if (K != 8 && K != 16 && K != 32) {
+        mrf_set_error("tree search: K must be 8, 16 or 32");
+        return MRF_EINVAL;
+    }
+    CUtensorMap ta, tb;
+    MRF_TRY(tma_map_k128(&ta, zq, n, Kp, BM, false));
+    MRF_TRY(tma_map_k128(&tb, op, D->nblk * 256, Kp, BN, false));
+    const int64_t Mt = (n + BM - 1) / BM;
+    const int64_t live = D->tune.bf16_live_tiles > 0 ? D->tune.bf16_live_tiles : kDefaultLive;
+    Sched sc;
+    sc.NG = Mt;
+    sc.S = maxchunks;
+    sc.PG = live;
+    const int64_t units = sc.NG * sc.S;
+    int nc = (K == 8) ? max_clusters<8, 1>(st) : (K == 16) ? max_clusters<16, 1>(st)
+                                                           : max_clusters<32, 1>(st);
+    if (nc <= 0) {
+        mrf_set_error("tree search: the kernel does not fit on this device");
+        return MRF_EUNSUPPORTED;
+    }
+    if (nc > units) nc = static_cast<int>(units);
+    ListArgs la;
+    la.tfirst = tfirst;
+    la.blist = blist;
+    la.perm = perm;
+    la.chunk = chunk;
+    auto go = [&](auto kern) -> mrf_status {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             static_cast<int>(kSmem));
+        if (e == cudaSuccess) {
+            kern<<<static_cast<unsigned>(nc), NTHREADS, kSmem, st>>>(
+                ta, tb, n, D->d, D->nblk, Kp, cone, sc, 0, 1.f, nullptr, nullptr, part_s,
+                part_i, D->err, la);
+            e = cudaGetLastError();
+        }
+        if (e != cudaSuccess) {
+            mrf_set_error(std::string("tree block-list search launch: ") + cudaGetErrorString(e));
+            return MRF_ECUDA;
+        }
+        return MRF_OK;
+    };
+    if (K == 8) return go(k_tc_topk<8, 1, false, true>);
+    if (K == 16) return go(k_tc_topk<16, 1, false, true>);
+    return go(k_tc_topk<32, 1, false, true>);
 }

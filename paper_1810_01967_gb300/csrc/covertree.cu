@@ -25,6 +25,7 @@
 // cone), both unit vectors.  The first pass computes c = u^H z^ in FP32; when c is close to 1
 // (d < 0.2) a second pass evaluates ||z^ - w u|| with w = c / |c| directly, which keeps the
 // relative accuracy of small distances that 2 - 2|c| loses to cancellation.
+#include <algorithm>
 #include <chrono>
 #include <initializer_list>
 
@@ -658,3 +659,54 @@ extern "C" mrf_status mrf_tree_build_host(const void* atoms, int64_t d, int32_t 
     if (levels) *levels = T.imax;
     return MRF_OK;
 }
+
+// Depth-first (pre-order) order of the tree's atoms: a node, then its children (the atoms whose
+// parent it is, by the level they first appear at, then by index), each subtree contiguous;
+// duplicates, which are not tree nodes, right after their representative.  Consecutive positions are close
+// in the tree metric, so 128-atom blocks of this order have small enclosing balls.
+mrf_status ct_dfs_order(const mrf_dict* D, std::vector<int32_t>* out) {
+    const CoverTreeDev* t = D->tree;
+    if (!t) {
+        mrf_set_error("dictionary built without a cover tree");
+        return MRF_EUNSUPPORTED;
+    }
+    const CtTree& h = t->host;
+    const int64_t d = D->d;
+    std::vector<std::vector<int32_t>> kids(static_cast<size_t>(d));
+    int32_t root = -1;
+    for (int64_t j = 0; j < d; ++j) {
+        if (h.first_level[j] < 0) continue;
+        if (h.parent[j] < 0) root = static_cast<int32_t>(j);
+        else kids[h.parent[j]].push_back(static_cast<int32_t>(j));
+    }
+    if (root < 0) {
+        mrf_set_error("cover tree without a root");
+        return MRF_EINTERNAL;
+    }
+    for (auto& k : kids)
+        std::sort(k.begin(), k.end(), [&](int32_t a, int32_t b) {
+            return h.first_level[a] != h.first_level[b] ? h.first_level[a] < h.first_level[b] : a < b;
+        });
+    // duplicates (atoms represented by an earlier node) follow their representative
+    std::vector<std::vector<int32_t>> dups(static_cast<size_t>(d));
+    for (int64_t j = 0; j < d; ++j)
+        if (h.first_level[j] < 0 && h.rep[j] >= 0 && h.rep[j] != j)
+            dups[h.rep[j]].push_back(static_cast<int32_t>(j));
+    out->clear();
+    out->reserve(static_cast<size_t>(d));
+    std::vector<int32_t> stack{root};
+    while (!stack.empty()) {
+        const int32_t u = stack.back();
+        stack.pop_back();
+        out->push_back(u);
+        for (int32_t j : dups[u]) out->push_back(j);
+        for (auto it = kids[u].rbegin(); it != kids[u].rend(); ++it) stack.push_back(*it);
+    }
+    if (static_cast<int64_t>(out->size()) != d) {
+        mrf_set_error("cover tree depth-first order does not cover the dictionary");
+        return MRF_EINTERNAL;
+    }
+    return MRF_OK;
+}
+
+int ct_metric(const mrf_dict* D) { return D->tree ? D->tree->host.metric : -1; }

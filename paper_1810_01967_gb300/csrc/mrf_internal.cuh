@@ -28,6 +28,7 @@ enum {
 };
 
 struct CoverTreeDev;   // flattened cover tree (covertree.cu)
+struct TreeTC;         // block balls and depth-first operands of the tensor-core tree search
 
 struct mrf_dict {
     int64_t d = 0;
@@ -77,6 +78,7 @@ struct mrf_dict {
     unsigned long long* counters = nullptr;   // [CNT_N]
     double* red = nullptr;          // [8] reductions (norms for the step rule / kappa)
     CoverTreeDev* tree = nullptr;
+    TreeTC* ttc = nullptr;           // tensor-core tree search (treetc.cu)
     mrf_mlp* mlp = nullptr;          // attached learned proposal (not owned)
     // phase alignment (real positive cone on complex data): atoms stored as D_j e^{-i alpha_j}
     bool aligned = false;
@@ -161,6 +163,19 @@ mrf_status launch_pack_bop3(mrf_dict* D, cudaStream_t st);
 mrf_status launch_pack_queries_x3(const float2* Z, int64_t n, const mrf_dict* D, float extra,
                                   __nv_bfloat16* zq3, float* margin, cudaStream_t st);
 mrf_status launch_fill(float* out, int64_t n, float v, cudaStream_t st);
+// split-BF16 operand of the atoms sel[0 .. nsel) in nblk_out blocks of 128 (row length 3 Kp;
+// sel[p] < 0 leaves slot p empty), with their split statistics (host floats); the query split
+// with explicit statistics and Kp: with vlist, row i holds voxel vlist[i] and its margin goes
+// to margin[vlist[i]]; znorm (optional) receives the FP32 norm of each row's voxel
+mrf_status launch_pack_sel3(const mrf_dict* D, const int32_t* sel, int64_t nsel, int64_t nblk_out,
+                            __nv_bfloat16* dst, float* al_out, float* ae_out, cudaStream_t st);
+mrf_status launch_pack_queries_x3_with(const float2* Z, int64_t n, int L, int Kp, float Al,
+                                       float Ae, float extra, __nv_bfloat16* zq3, float* margin,
+                                       cudaStream_t st, const int32_t* vlist = nullptr,
+                                       float* znorm = nullptr);
+// the BF16 operand with atom perm[p] in slot p (perm of length nblk * 128, -1 = empty)
+mrf_status launch_pack_bop_perm(const mrf_dict* D, __nv_bfloat16* dst, const int32_t* perm,
+                                cudaStream_t st);
 mrf_status launch_grad_combine(const float2* X, const float2* G, const float2* AHY, float2* Z,
                                int64_t n, int L, float mu, float g_scale, __nv_bfloat16* zq,
                                int Kp, uint32_t* err, cudaStream_t st);
@@ -188,6 +203,11 @@ mrf_status launch_fp8_topk(const uint8_t* zq8, const float* qs, int64_t n, mrf_d
                            int K, int S, float* part_s, int32_t* part_i, cudaStream_t st);
 mrf_status launch_x3_topk(const __nv_bfloat16* zq3, int64_t n, mrf_dict* D, int cone, int K,
                           int S, float* part_s, int32_t* part_i, cudaStream_t st);
+mrf_status launch_bf16_topk_list(const __nv_bfloat16* zq, int64_t n, mrf_dict* D,
+                                 const __nv_bfloat16* op, int Kp, int cone, int K, int maxchunks,
+                                 int chunk, const int32_t* tfirst, const int32_t* blist,
+                                 const int32_t* perm, float* part_s, int32_t* part_i,
+                                 cudaStream_t st);
 // covertree.cu
 mrf_status ct_build_upload(mrf_dict* D, int metric, double dup_tol);
 void ct_free(CoverTreeDev* t);
@@ -195,8 +215,28 @@ mrf_status launch_ct_search(const float2* Z, int64_t n, const mrf_dict* D, int c
                             const int32_t* warm, float eps, float route, float* part_s,
                             int32_t* part_i, int32_t* fb_list, int32_t* fb_n, cudaStream_t st);
 mrf_status ct_info(const mrf_dict* D, mrf_tree_info* info);
+mrf_status ct_dfs_order(const mrf_dict* D, std::vector<int32_t>* out);
+int ct_metric(const mrf_dict* D);
 mrf_status ct_export(const mrf_dict* D, int32_t* first_level, int32_t* parent, int32_t* rep,
                      int32_t* en_atom, int32_t* en_level, float* en_maxdist);
+// treetc.cu
+struct TtcOut {
+    int S = 0;                   // candidate lists per voxel row
+    int chunk = 0;               // blocks per work unit
+    const float* part_s = nullptr;
+    const int32_t* part_i = nullptr;   // [S][n][K] atom indices (-1 empty)
+    const int32_t* vorder = nullptr;   // [n] voxel of each row
+    const int32_t* count = nullptr;    // device int = n (the merge's list length)
+    int64_t blocks = 0;          // sum of the tiles' list lengths
+    int64_t tiles = 0;
+};
+mrf_status ttc_build(mrf_dict* D, cudaStream_t st);
+void ttc_free(TreeTC* t);
+bool ttc_has_split(const mrf_dict* D);
+bool ttc_has_bf16(const mrf_dict* D);
+mrf_status ttc_search(mrf_dict* D, const float2* Z, int64_t n, int cone, float eps, bool split,
+                      int K, float extra, TtcOut* out, cudaStream_t st);
+mrf_status ttc_blocks(const mrf_dict* D, int64_t* nblk, float* radius_host, int32_t* perm_host);
 // gradfft.cu
 bool grad_fused_supported(int Ny);
 mrf_status launch_grad_fused(const mrf_op* op, const float2* AHY, const float2* X, float mu,
@@ -239,6 +279,10 @@ mrf_status launch_dense_gelu(const __nv_bfloat16* A, int M, int Kp, const __nv_b
                              int N, const float* bias, float* out, __nv_bfloat16* outb,
                              uint32_t* err, cudaStream_t st);
 int dense_tile_n(int N);
+// the same product with act = 0 (identity) or 1 (GELU); bias may be NULL
+mrf_status launch_dense(const __nv_bfloat16* A, int M, int Kp, const __nv_bfloat16* Wt, int N,
+                        const float* bias, int act, float* out, __nv_bfloat16* outb,
+                        uint32_t* err, cudaStream_t st);
 // mlp.cu
 void mlp_detach(mrf_mlp* M);
 mrf_status learned_candidates(mrf_dict* D, const float2* Z, int64_t n, int cone, float* part_s,

@@ -33,9 +33,10 @@ __global__ void k_atom_norms(const float2* __restrict__ atoms, int64_t d, int L,
 // r >= 128 holds (-Im d, Re d), so that a query row (Re z, Im z) gives Re(d^H z) and Im(d^H z).
 // Atom rows are normalised (D_j / ||D_j||, the FP64 norm) before rounding, so the kernels' scores
 // need no per-atom weight.
+// With `perm` (length nblk * 128) the operand slot p holds atom perm[p] (-1: an empty slot).
 __global__ void k_pack_bop(const float2* __restrict__ atoms, const float* __restrict__ inv_norm,
                            int64_t d, int L, int Kp, int64_t nblk,
-                           __nv_bfloat162* __restrict__ bop) {
+                           __nv_bfloat162* __restrict__ bop, const int32_t* __restrict__ perm) {
     int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
     int64_t half = Kp / 2;
     int64_t total = nblk * 256 * half;
@@ -45,6 +46,7 @@ __global__ void k_pack_bop(const float2* __restrict__ atoms, const float* __rest
     int64_t b = row >> 8;
     int r = static_cast<int>(row & 255);
     int64_t j = b * 128 + (r & 127);
+    if (perm) j = perm[j] < 0 ? d : perm[j];
     float2 v = make_float2(0.f, 0.f);
     if (j < d && t < L) {
         const float inv = inv_norm[j];
@@ -300,9 +302,14 @@ mrf_status launch_atom_norms(mrf_dict* D, cudaStream_t st) {
 }
 
 mrf_status launch_pack_bop(mrf_dict* D, cudaStream_t st) {
+    return launch_pack_bop_perm(D, D->bop, nullptr, st);
+}
+
+mrf_status launch_pack_bop_perm(const mrf_dict* D, __nv_bfloat16* dst, const int32_t* perm,
+                                cudaStream_t st) {
     int64_t total = D->nblk * 256 * (D->Kp / 2);
     k_pack_bop<<<grid_for(total), kThreads, 0, st>>>(D->atoms, D->inv_norm, D->d, D->L, D->Kp, D->nblk,
-                                                      reinterpret_cast<__nv_bfloat162*>(D->bop));
+                                                      reinterpret_cast<__nv_bfloat162*>(dst), perm);
     LAUNCH_CHECK();
     return MRF_OK;
 }

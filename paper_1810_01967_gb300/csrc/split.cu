@@ -54,16 +54,20 @@ __device__ __forceinline__ double warp_sumd(double x) {
 // each as [hi | lo | hi]; and per atom the largest ||lo|| and ||d/||d|| - hi - lo|| (the exact
 // unit atom in FP64) into `bits` (float bit patterns, rounded up; non-negative floats order like
 // their bits).
+// With `sel` (length nsel) operand slot p holds atom sel[p] for p < nsel (nothing where
+// sel[p] < 0) and nothing after.
 __global__ void k_pack_bop3(const float2* __restrict__ atoms, const float* __restrict__ inv_norm,
                             const double* __restrict__ norm2, int64_t d, int L, int Kp,
                             int64_t nblk, __nv_bfloat162* __restrict__ bop3,
-                            unsigned int* __restrict__ bits) {
+                            unsigned int* __restrict__ bits, const int32_t* __restrict__ sel,
+                            int64_t nsel) {
     const int64_t slot = (static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
     if (slot >= nblk * 128) return;
     const int64_t b = slot >> 7;
     const int r = static_cast<int>(slot & 127);
-    const int64_t j = slot;
+    int64_t j = sel ? (slot < nsel ? static_cast<int64_t>(sel[slot]) : d) : slot;
+    if (j < 0) j = d;                                   // empty slot of a selection
     const bool real = j < d;
     const float inv = real ? inv_norm[j] : 0.f;
     const double invd = real ? 1.0 / sqrt(norm2[j]) : 0.0;
@@ -109,12 +113,14 @@ struct BoundConsts {
 // One warp per voxel: the query row [lo | hi | hi] and the voxel's margin.
 __global__ void k_pack_queries_x3(const float2* __restrict__ Z, int64_t n, int L, int Kp,
                                   BoundConsts bc, __nv_bfloat162* __restrict__ zq3,
-                                  float* __restrict__ margin) {
+                                  float* __restrict__ margin, const int32_t* __restrict__ vlist,
+                                  float* __restrict__ znorm) {
     const int64_t v = (static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
     if (v >= n) return;
     const int half = Kp / 2;
-    const float2* z = Z + v * L;
+    const int64_t src = vlist ? static_cast<int64_t>(vlist[v]) : v;
+    const float2* z = Z + src * L;
     __nv_bfloat162* row = zq3 + v * (3 * half);
     // squared norms in FP32 (each a sum of non-negative terms: relative error below
     // (L / 32 + 5) 2^-24, covered by the final (1 + 2^-10) inflation of the ratios below)
@@ -139,6 +145,7 @@ __global__ void k_pack_queries_x3(const float2* __restrict__ Z, int64_t n, int L
         ee += __shfl_xor_sync(0xffffffffu, ee, o);
         hh += __shfl_xor_sync(0xffffffffu, hh, o);
     }
+    if (lane == 0 && znorm) znorm[v] = sqrtf(zz);
     if (lane == 0 && margin) {
         float m = 0.f;
         if (zz > 0.f) {
@@ -156,7 +163,7 @@ __global__ void k_pack_queries_x3(const float2* __restrict__ Z, int64_t n, int L
             const double b = e_op + 1.4142135623730951 * e_acc + eps;
             m = __double2float_ru(b * (1.0 + 1e-6)) + bc.extra;
         }
-        margin[v] = m;
+        margin[src] = m;
     }
 }
 
@@ -177,7 +184,7 @@ mrf_status launch_pack_bop3(mrf_dict* D, cudaStream_t st) {
     const int64_t slots = D->nblk * 128;
     k_pack_bop3<<<grid_for(slots * 32), kThreads, 0, st>>>(
         D->atoms, D->inv_norm, D->norm2, D->d, D->L, D->Kp3 / 3, D->nblk,
-        reinterpret_cast<__nv_bfloat162*>(D->bop3), bits);
+        reinterpret_cast<__nv_bfloat162*>(D->bop3), bits, nullptr, 0);
     MRF_CUDA_TRY(cudaGetLastError());
     unsigned int h[2] = {0u, 0u};
     MRF_CUDA_TRY(cudaMemcpyAsync(h, bits, sizeof(h), cudaMemcpyDeviceToHost, st));
@@ -190,18 +197,40 @@ mrf_status launch_pack_bop3(mrf_dict* D, cudaStream_t st) {
     return MRF_OK;
 }
 
+mrf_status launch_pack_sel3(const mrf_dict* D, const int32_t* sel, int64_t nsel, int64_t nblk_out,
+                            __nv_bfloat16* dst, float* al_out, float* ae_out, cudaStream_t st) {
+    unsigned int* bits = reinterpret_cast<unsigned int*>(D->red);
+    MRF_CUDA_TRY(cudaMemsetAsync(bits, 0, 2 * sizeof(unsigned int), st));
+    k_pack_bop3<<<grid_for(nblk_out * 128 * 32), kThreads, 0, st>>>(
+        D->atoms, D->inv_norm, D->norm2, D->d, D->L, D->Kp, nblk_out,
+        reinterpret_cast<__nv_bfloat162*>(dst), bits, sel, nsel);
+    MRF_CUDA_TRY(cudaGetLastError());
+    unsigned int h[2] = {0u, 0u};
+    MRF_CUDA_TRY(cudaMemcpyAsync(h, bits, sizeof(h), cudaMemcpyDeviceToHost, st));
+    MRF_CUDA_TRY(cudaStreamSynchronize(st));
+    std::memcpy(al_out, &h[0], sizeof(float));
+    std::memcpy(ae_out, &h[1], sizeof(float));
+    return MRF_OK;
+}
+
 mrf_status launch_pack_queries_x3(const float2* Z, int64_t n, const mrf_dict* D, float extra,
                                   __nv_bfloat16* zq3, float* margin, cudaStream_t st) {
+    return launch_pack_queries_x3_with(Z, n, D->L, D->Kp3 / 3, D->x3_al, D->x3_ae, extra, zq3,
+                                       margin, st);
+}
+
+mrf_status launch_pack_queries_x3_with(const float2* Z, int64_t n, int L, int Kp, float Al,
+                                       float Ae, float extra, __nv_bfloat16* zq3, float* margin,
+                                       cudaStream_t st, const int32_t* vlist, float* znorm) {
     if (n == 0) return MRF_OK;
-    const int Kp = D->Kp3 / 3;
     BoundConsts bc;
-    bc.Al = D->x3_al;
-    bc.Ae = D->x3_ae;
+    bc.Al = Al;
+    bc.Ae = Ae;
     bc.n_lo = 2.0 * Kp / 16.0;
     bc.n_hi = Kp / 16.0;
     bc.extra = extra;
     k_pack_queries_x3<<<grid_for(n * 32), kThreads, 0, st>>>(
-        Z, n, D->L, Kp, bc, reinterpret_cast<__nv_bfloat162*>(zq3), margin);
+        Z, n, L, Kp, bc, reinterpret_cast<__nv_bfloat162*>(zq3), margin, vlist, znorm);
     MRF_CUDA_TRY(cudaGetLastError());
     return MRF_OK;
 }

@@ -1,6 +1,8 @@
-// Dense layers of the learned proposal's network on the 5th-generation tensor cores:
-//   out[m][n] = gelu(sum_k A[m][k] W[k][n] + bias[n]),  A [M][Kp] BF16, W given transposed as
-//   Wt [N][Kp] BF16 (both K-major), FP32 accumulation in tensor memory, bias and GELU in FP32.
+// Dense products on the 5th-generation tensor cores -- the learned proposal's network layers and
+// the cover-tree search's query-to-centre correlations:
+//   out[m][n] = act(sum_k A[m][k] W[k][n] + bias[n]),  A [M][Kp] BF16, W given transposed as
+//   Wt [N][Kp] BF16 (both K-major), FP32 accumulation in tensor memory, bias (optional) and the
+//   activation (GELU or identity) in FP32.
 //
 // One CTA per 128-row x BN-column tile (BN <= 256, a multiple of 16 dividing N): warp 0 streams
 // 128-byte K slices of the A tile and of the BN weight rows with TMA into a 4-stage ring
@@ -44,7 +46,8 @@ __device__ __forceinline__ float gelu(float v) {
 __global__ void __launch_bounds__(T_THREADS, 1)
 k_tc_dense_gelu(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                 int M, int N, int Kp, int BN, uint32_t idesc, const float* __restrict__ bias,
-                float* __restrict__ out, __nv_bfloat16* __restrict__ outb, uint32_t* err) {
+                int act, float* __restrict__ out, __nv_bfloat16* __restrict__ outb,
+                uint32_t* err) {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char* base = reinterpret_cast<unsigned char*>(
         (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
@@ -146,8 +149,10 @@ k_tc_dense_gelu(const __grid_constant__ CUtensorMap tmA, const __grid_constant__
             const int cnt = BN - c * 32 < 32 ? BN - c * 32 : 32;
             float g[32];
 #pragma unroll
-            for (int i = 0; i < 32; ++i)
-                g[i] = i < cnt ? gelu(__uint_as_float(r[i]) + bias[nb + i]) : 0.f;
+            for (int i = 0; i < 32; ++i) {
+                const float v = i < cnt ? __uint_as_float(r[i]) + (bias ? bias[nb + i] : 0.f) : 0.f;
+                g[i] = act ? gelu(v) : v;
+            }
             const int64_t o = static_cast<int64_t>(m) * N + nb;
             if (cnt == 32) {           // 16-byte stores (N and nb are multiples of 16)
                 if (out) {
@@ -193,6 +198,12 @@ int dense_tile_n(int N) {
 mrf_status launch_dense_gelu(const __nv_bfloat16* A, int M, int Kp, const __nv_bfloat16* Wt,
                              int N, const float* bias, float* out, __nv_bfloat16* outb,
                              uint32_t* err, cudaStream_t st) {
+    return launch_dense(A, M, Kp, Wt, N, bias, 1, out, outb, err, st);
+}
+
+mrf_status launch_dense(const __nv_bfloat16* A, int M, int Kp, const __nv_bfloat16* Wt, int N,
+                        const float* bias, int act, float* out, __nv_bfloat16* outb,
+                        uint32_t* err, cudaStream_t st) {
     if (M == 0) return MRF_OK;
     const int BN = dense_tile_n(N);
     if (BN == 0 || Kp <= 0 || (Kp * 2) % 16) {
@@ -209,7 +220,7 @@ mrf_status launch_dense_gelu(const __nv_bfloat16* A, int M, int Kp, const __nv_b
     if (e == cudaSuccess) {
         dim3 grid(static_cast<unsigned>(N / BN), static_cast<unsigned>((M + TM - 1) / TM));
         k_tc_dense_gelu<<<grid, T_THREADS, kDenseSmem, st>>>(ta, tb, M, N, Kp, BN, idesc, bias,
-                                                             out, outb, err);
+                                                             act, out, outb, err);
         e = cudaGetLastError();
     }
     if (e != cudaSuccess) {
