@@ -299,7 +299,7 @@ def reconstruction_quality(mrf, D, op, p, dic, dev, stream, iters: int, fp32: bo
         # open (its owner closes it)
         t0 = time.perf_counter()
         D2 = mrf.build_dict_index(dic["atoms"], dic["params"], grid_shape=dic["grid_shape"],
-                                  build_tree=True, pack_fp8=True)
+                                  build_tree=True, pack_fp8=True, tree_tc=True)
         out["tree_build_s"] = time.perf_counter() - t0
         M, tsec, hist = train_learned(mrf, D2, dic, dev)
         mrf.attach_mlp(D2, M)
@@ -307,7 +307,8 @@ def reconstruction_quality(mrf, D, op, p, dic, dev, stream, iters: int, fp32: bo
                                 "loss_first": float(hist[:20].mean()),
                                 "loss_last": float(hist[-100:].mean())}
         D = D2
-        runs += [("covertree", {"eps": 0.4}), ("learned", {"fallback_thr": 0.98})]
+        runs += [("covertree", {"eps": 0.4}), ("tree_tc", {"eps": 0.4}),
+                 ("learned", {"fallback_thr": 0.98})]
     for mode, kw in runs:
         X = torch.empty((n, L), dtype=torch.complex64, device=dev)
         idx = torch.empty(n, dtype=torch.int32, device=dev)
@@ -777,7 +778,7 @@ def tree_leg(mrf, dev, stream, iters: int, tree_svd=()) -> dict:
     Ny, Nx = p["Ny"], p["Nx"]
     n = Ny * Nx
     t0 = time.perf_counter()
-    D = mrf.build_dict_index(atoms, params, build_tree=True)
+    D = mrf.build_dict_index(atoms, params, build_tree=True, tree_tc=True)
     build_s = time.perf_counter() - t0
     info = D.tree_info()
     op = mrf.make_op(Ny, Nx, L, torch.from_numpy(p["masks"]).to(dev))
@@ -786,7 +787,8 @@ def tree_leg(mrf, dev, stream, iters: int, tree_svd=()) -> dict:
     fg = ph["labels"] >= 0
     AHY = torch.empty((n, L), dtype=torch.complex64, device=dev)
     mrf.adjoint(op, Yd, AHY)
-    runs = [("bf16", {})] + [("covertree", {"eps": e}) for e in (0.0, 0.2, 0.5, 1.0)]
+    runs = ([("bf16", {})] + [("covertree", {"eps": e}) for e in (0.0, 0.2, 0.5, 1.0)]
+            + [("tree_tc", {"eps": e}) for e in (0.0, 0.2, 0.5, 1.0)])
     out = {}
     ref_idx = None
     for mode, kw in runs:
@@ -811,6 +813,19 @@ def tree_leg(mrf, dev, stream, iters: int, tree_svd=()) -> dict:
              "atom_agreement_vs_bf16": float(np.mean(gi == ref_idx)),
              "distance_evals": st["n_dist_evals"],
              "exhaustive_voxel_iters": st["n_fallback"], **kw}
+        if mode == "tree_tc":
+            # one cold projection of A^H Y: centre bounds and tile lists, then the block-list
+            # search on the tensor cores
+            ii = torch.empty(n, dtype=torch.int32, device=dev)
+            mrf.profile_enable(True)
+            s2 = mrf.project(D, AHY, ii, opts=mrf.proj_opts(mode="tree_tc", eps=kw["eps"],
+                                                           certify=False), stats=True)
+            prof = mrf.profile_read()
+            mrf.profile_enable(False)
+            r["first_projection"] = {
+                "bounds_lists_ms": prof["search_proposal"][0], "search_ms": prof["search_tc"][0],
+                "merge_ms": prof["merge"][0],
+                "pairs_fraction_of_bruteforce": s2["n_dist_evals"] / (d * n)}
         if mode == "covertree":
             # one cold projection of A^H Y: the tree search kernel's own rate
             ii = torch.empty(n, dtype=torch.int32, device=dev)

@@ -569,7 +569,15 @@ typedef struct mrf_tune {
                                   queries of one subtree run side by side and share cached tree
                                   nodes and atoms (results are the same either way); 2 = voxel
                                   order; 0 = the library's default */
-    int32_t reserved[5];
+    int32_t tree_tc_group;     /* MRF_PROJ_TREE_TC: consecutive 128-voxel tiles that share one
+                                  block list (the union of their voxels' lists), 1..64: larger
+                                  groups search more blocks per voxel but stream each block
+                                  once for the whole group, as the exhaustive search does;
+                                  0 = the library's default (2) */
+    int32_t tree_tc_chunks;    /* MRF_PROJ_TREE_TC: chunks a full block list is cut into, the
+                                  work units of the persistent search and the candidate lists
+                                  per voxel, 1..64; 0 = the library's default (32) */
+    int32_t reserved[3];
 } mrf_tune;
 
 mrf_status mrf_get_tune(const mrf_dict* dict, mrf_tune* out);

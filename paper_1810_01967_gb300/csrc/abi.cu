@@ -1021,11 +1021,18 @@ mrf_status mrf_set_tune(mrf_dict* D, const mrf_tune* in) {
         return fail(MRF_EINVAL, "tuning values out of range");
     if (in->tree_list_cap != 0 && (in->tree_list_cap < 64 || in->tree_list_cap > 512))
         return fail(MRF_EINVAL, "tree_list_cap must be 0 or in 64..512");
-    D->tune.tree_list_cap = in->tree_list_cap;
     if (in->bf16_pair < 0 || in->bf16_pair > 1) return fail(MRF_EINVAL, "bf16_pair must be 0 or 1");
-    D->tune.bf16_pair = in->bf16_pair;
     if (in->tree_order < 0 || in->tree_order > 2) return fail(MRF_EINVAL, "tree_order must be 0, 1 or 2");
+    if (in->tree_tc_group < 0 || in->tree_tc_group > 64)
+        return fail(MRF_EINVAL, "tree_tc_group must be in 0..64");
+    if (in->tree_tc_chunks < 0 || in->tree_tc_chunks > 64)
+        return fail(MRF_EINVAL, "tree_tc_chunks must be in 0..64");
+    // all values checked: none is applied when one is refused
+    D->tune.tree_list_cap = in->tree_list_cap;
+    D->tune.bf16_pair = in->bf16_pair;
     D->tune.tree_order = in->tree_order;
+    D->tune.tree_tc_group = in->tree_tc_group;
+    D->tune.tree_tc_chunks = in->tree_tc_chunks;
     D->tune.bf16_cluster = in->bf16_cluster;
     D->tune.bf16_live_tiles = in->bf16_live_tiles;
     D->tune.bf16_splits = in->bf16_splits;

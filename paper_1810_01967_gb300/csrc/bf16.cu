@@ -68,26 +68,46 @@ struct Sched {
     }
 };
 
-// Block lists of the cover-tree search: tile g owns blist[tfirst[g] .. tfirst[g + 1]), split
-// into chunks of `chunk` blocks (one work unit each); perm maps operand positions to atoms.
+// Block lists of the cover-tree search: the tiles of group k (tiles [k group, (k + 1) group))
+// share the ascending block list blist[tfirst[k] .. tfirst[k + 1]), cut into chunks of `chunk`
+// blocks; a work unit is (group, chunk, tile), numbered group by group from uoff[k] (chunks of
+// a group times its tiles, the tiles of one chunk consecutive so they stream the chunk's blocks
+// together), *units in all.  perm maps operand positions to atoms.
 struct ListArgs {
     const int32_t* tfirst;
     const int32_t* blist;
     const int32_t* perm;
-    int chunk;
+    const int32_t* uoff;
+    const int32_t* units;
+    int group, chunk;
+    int64_t ngroups, ntiles;
 };
 
-// The blocks of unit (s, g): positions [b0, b1) of the atom-block range (or of the tile's list,
-// starting at lb); false when the unit has none.
+// The work unit uc: tile g, candidate slot s (its chunk), positions [b0, b1) of the group's
+// list starting at lb (LIST); or the exhaustive schedule's unit: split s, tile group g, block
+// range [b0, b1).  False when the unit has no block.
 template <bool LIST>
-__device__ __forceinline__ bool unit_blocks(const ListArgs& la, int64_t s, int64_t g, int bps,
-                                            int64_t nblk, int64_t& b0, int64_t& b1, int64_t& lb) {
+__device__ __forceinline__ bool unit_of(const Sched& sc, const ListArgs& la, int64_t uc, int bps,
+                                        int64_t nblk, int64_t& s, int64_t& g, int64_t& b0,
+                                        int64_t& b1, int64_t& lb) {
     if (LIST) {
-        lb = la.tfirst[g];
-        const int64_t cnt = la.tfirst[g + 1] - lb;
+        int64_t lo = 0, hi = la.ngroups;                 // last k with uoff[k] <= uc
+        while (hi - lo > 1) {
+            const int64_t mid = (lo + hi) >> 1;
+            if (la.uoff[mid] <= uc) lo = mid;
+            else hi = mid;
+        }
+        const int64_t t0 = lo * la.group;
+        const int64_t gsz = min(static_cast<int64_t>(la.group), la.ntiles - t0);
+        const int64_t l = uc - la.uoff[lo];
+        s = l / gsz;
+        g = t0 + (l - s * gsz);
+        lb = la.tfirst[lo];
+        const int64_t cnt = la.tfirst[lo + 1] - lb;
         b0 = s * la.chunk;
         b1 = min(b0 + la.chunk, cnt);
     } else {
+        sc.map(uc, s, g);
         lb = 0;
         b0 = s * bps;
         b1 = min(b0 + bps, nblk);
@@ -162,8 +182,8 @@ __device__ __forceinline__ void epilogue_block(uint32_t tb, int cone, int64_t b,
 // F8: E4M3 operands (kind::f8f6f4); the K kept scores of voxel v are multiplied by
 // (qs[v] gsc)^2 (complex cone) or qs[v] gsc (real cone), qs = 1 / (the query row's scale) and
 // gsc = 1 / (the dictionary's scale).  BF16: scores are used as computed.
-// LIST: the block-list mode of the cover-tree search -- unit (chunk s, voxel tile g) scans the
-// blocks la.blist[la.tfirst[g] + s chunk ...] of an operand in the tree's depth-first order, and
+// LIST: the block-list mode of the cover-tree search -- unit (group, chunk s, voxel tile g) scans
+// chunk s of the group's block list of an operand in the tree's depth-first order, and
 // the kept candidates are mapped back to atom indices through la.perm.
 template <int KT, int C, bool F8, bool LIST = false>
 __global__ void __launch_bounds__(NTHREADS, 1)
@@ -184,7 +204,7 @@ k_tc_topk(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
     const uint32_t rank = (C > 1) ? mrfk::cluster_ctarank() : 0u;
     const int64_t cluster = blockIdx.x / C;
     const int64_t nclusters = gridDim.x / C;
-    const int64_t units = sc.NG * sc.S;
+    const int64_t units = LIST ? static_cast<int64_t>(*la.units) : sc.NG * sc.S;
     // with a device-side voxel count (lists built on the device) the tiles past it are skipped
     const int64_t nact = count ? min(static_cast<int64_t>(*count), n) : n;
     const int nk = (Kp + EK - 1) / EK;
@@ -229,12 +249,11 @@ k_tc_topk(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
             bool slot_used[STAGES];
             for (int i = 0; i < STAGES; ++i) { slot_used[i] = false; slot_phase[i] = 0; }
             for (int64_t uc = cluster; uc < units && !sh->abort; uc += nclusters) {
-                int64_t s, g;
-                sc.map(uc, s, g);
+                int64_t s, g, b0, b1, lb;
+                const bool has = unit_of<LIST>(sc, la, uc, blocks_per_split, nblk, s, g, b0, b1, lb);
                 if (g * C * BM >= nact) continue;     // the cluster's tiles are all past the count
                 const int64_t m = g * C + rank;
-                int64_t b0, b1, lb;
-                if (!unit_blocks<LIST>(la, s, g, blocks_per_split, nblk, b0, b1, lb)) continue;
+                if (!has) continue;
                 for (int64_t q = b0; q < b1 && !sh->abort; ++q) {
                     const int64_t b = LIST ? static_cast<int64_t>(la.blist[lb + q]) : q;
                     for (int kc = 0; kc < nk; ++kc) {
@@ -268,11 +287,10 @@ k_tc_topk(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
             uint32_t aphase = 0;
             bool any = false;
             for (int64_t uc = cluster; uc < units && !sh->abort; uc += nclusters) {
-                int64_t s, g;
-                sc.map(uc, s, g);
+                int64_t s, g, b0, b1, lb;
+                const bool has = unit_of<LIST>(sc, la, uc, blocks_per_split, nblk, s, g, b0, b1, lb);
                 if (g * C * BM >= nact) continue;     // the cluster's tiles are all past the count
-                int64_t b0, b1, lb;
-                if (!unit_blocks<LIST>(la, s, g, blocks_per_split, nblk, b0, b1, lb)) continue;
+                if (!has) continue;
                 for (int64_t q = b0; q < b1 && !sh->abort; ++q) {
                     if (!mrfk::mbar_wait(&sh->tempty[acc], aphase ^ 1u)) { fail(); break; }
                     mrfk::tc_fence_after();
@@ -321,12 +339,11 @@ k_tc_topk(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
         int acc = 0;
         uint32_t aphase = 0;
         for (int64_t uc = cluster; uc < units && !sh->abort; uc += nclusters) {
-            int64_t s, g;
-            sc.map(uc, s, g);
+            int64_t s, g, b0, b1, lb;
+            const bool has = unit_of<LIST>(sc, la, uc, blocks_per_split, nblk, s, g, b0, b1, lb);
             if (g * C * BM >= nact) continue;     // the cluster's tiles are all past the count
             const int64_t m = g * C + rank;
-            int64_t b0, b1, lb;
-            if (!unit_blocks<LIST>(la, s, g, blocks_per_split, nblk, b0, b1, lb)) continue;
+            if (!has) continue;
             float ts[KT];
             int32_t ti[KT];
 #pragma unroll
@@ -908,14 +925,16 @@ mrf_status launch_x3_topk(const __nv_bfloat16* zq3, int64_t n, mrf_dict* D, int 
 
 // Block-list search of the cover-tree form: queries zq [n][Kp] (grouped into 128-row tiles),
 // the depth-first operand op ([nblk * 256][Kp]; BF16 layout, or the split form with Kp = 3 x
-// the BF16 row length), tile g's blocks
-// blist[tfirst[g] .. tfirst[g + 1]) in chunks of `chunk` (maxchunks units per tile), candidates
-// [maxchunks][n][K] with atom indices perm[position]; single CTAs, persistent grid.
+// the BF16 row length), the block lists of the tile groups (see ListArgs: tfirst, blist, uoff,
+// *units = uoff[groups], all on the device), chunks of `chunk` blocks, at most S per group;
+// candidates [S][n][K] (slot = chunk) with atom indices perm[position]; slots of chunks a group
+// does not have are not written.  Persistent grid of single CTAs; the unit count is read on the
+// device.
 mrf_status launch_bf16_topk_list(const __nv_bfloat16* zq, int64_t n, mrf_dict* D,
-                                 const __nv_bfloat16* op, int Kp, int cone, int K, int maxchunks,
+                                 const __nv_bfloat16* op, int Kp, int cone, int K, int group,
                                  int chunk, const int32_t* tfirst, const int32_t* blist,
-                                 const int32_t* perm, float* part_s, int32_t* part_i,
-                                 cudaStream_t st) {
+                                 const int32_t* uoff, const int32_t* perm, float* part_s,
+                                 int32_t* part_i, cudaStream_t st) {
     if (n == 0) return MRF_OK;
     if (K != 8 && K != 16 && K != 32) {
         mrf_set_error("tree search: K must be 8, 16 or 32");
@@ -925,24 +944,23 @@ mrf_status launch_bf16_topk_list(const __nv_bfloat16* zq, int64_t n, mrf_dict* D
     MRF_TRY(tma_map_k128(&ta, zq, n, Kp, BM, false));
     MRF_TRY(tma_map_k128(&tb, op, D->nblk * 256, Kp, BN, false));
     const int64_t Mt = (n + BM - 1) / BM;
-    const int64_t live = D->tune.bf16_live_tiles > 0 ? D->tune.bf16_live_tiles : kDefaultLive;
-    Sched sc;
-    sc.NG = Mt;
-    sc.S = maxchunks;
-    sc.PG = live;
-    const int64_t units = sc.NG * sc.S;
+    ListArgs la;
+    la.tfirst = tfirst;
+    la.blist = blist;
+    la.perm = perm;
+    la.uoff = uoff;
+    la.group = group;
+    la.chunk = chunk;
+    la.ntiles = Mt;
+    la.ngroups = (Mt + group - 1) / group;
+    la.units = uoff + la.ngroups;
+    Sched sc{Mt, 1, 1};
     int nc = (K == 8) ? max_clusters<8, 1>(st) : (K == 16) ? max_clusters<16, 1>(st)
                                                            : max_clusters<32, 1>(st);
     if (nc <= 0) {
         mrf_set_error("tree search: the kernel does not fit on this device");
         return MRF_EUNSUPPORTED;
     }
-    if (nc > units) nc = static_cast<int>(units);
-    ListArgs la;
-    la.tfirst = tfirst;
-    la.blist = blist;
-    la.perm = perm;
-    la.chunk = chunk;
     auto go = [&](auto kern) -> mrf_status {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              static_cast<int>(kSmem));

@@ -204,10 +204,10 @@ mrf_status launch_fp8_topk(const uint8_t* zq8, const float* qs, int64_t n, mrf_d
 mrf_status launch_x3_topk(const __nv_bfloat16* zq3, int64_t n, mrf_dict* D, int cone, int K,
                           int S, float* part_s, int32_t* part_i, cudaStream_t st);
 mrf_status launch_bf16_topk_list(const __nv_bfloat16* zq, int64_t n, mrf_dict* D,
-                                 const __nv_bfloat16* op, int Kp, int cone, int K, int maxchunks,
+                                 const __nv_bfloat16* op, int Kp, int cone, int K, int group,
                                  int chunk, const int32_t* tfirst, const int32_t* blist,
-                                 const int32_t* perm, float* part_s, int32_t* part_i,
-                                 cudaStream_t st);
+                                 const int32_t* uoff, const int32_t* perm, float* part_s,
+                                 int32_t* part_i, cudaStream_t st);
 // covertree.cu
 mrf_status ct_build_upload(mrf_dict* D, int metric, double dup_tol);
 void ct_free(CoverTreeDev* t);
@@ -222,12 +222,10 @@ mrf_status ct_export(const mrf_dict* D, int32_t* first_level, int32_t* parent, i
 // treetc.cu
 struct TtcOut {
     int S = 0;                   // candidate lists per voxel row
-    int chunk = 0;               // blocks per work unit
     const float* part_s = nullptr;
     const int32_t* part_i = nullptr;   // [S][n][K] atom indices (-1 empty)
     const int32_t* vorder = nullptr;   // [n] voxel of each row
     const int32_t* count = nullptr;    // device int = n (the merge's list length)
-    int64_t blocks = 0;          // sum of the tiles' list lengths
     int64_t tiles = 0;
 };
 mrf_status ttc_build(mrf_dict* D, cudaStream_t st);

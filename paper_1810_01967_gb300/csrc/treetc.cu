@@ -46,11 +46,11 @@ struct TreeTC {
     float* radius = nullptr;     // [nblk] R_b, rounded up
     double build_ms = 0.0;
     // per-projection scratch (grown on demand)
-    int64_t cap = 0, chunk = 0, tiles_cap = 0, blist_cap = 0;
-    __nv_bfloat16* zc3 = nullptr;   // [chunk][3 Kp] queries of the centre product
-    float* cs = nullptr;         // [chunk][ncbblk * 256] centre correlations (re, im rows)
-    float* znorm = nullptr;      // [chunk]
-    float* cmarg = nullptr;      // [chunk] bound of the centre correlations
+    int64_t cap = 0, crows = 0, tiles_cap = 0, blist_cap = 0;
+    __nv_bfloat16* zc3 = nullptr;   // [crows][3 Kp] queries of the centre product
+    float* cs = nullptr;         // [crows][ncbblk * 256] centre correlations (re, im rows)
+    float* znorm = nullptr;      // [crows]
+    float* cmarg = nullptr;      // [crows] bound of the centre correlations
     uint32_t* keep = nullptr;    // [cap][words] per-voxel block masks
     int32_t* key = nullptr;      // [cap] nearest centre
     int32_t* val = nullptr;      // [cap] voxel
@@ -59,10 +59,13 @@ struct TreeTC {
     void* tmp = nullptr;
     size_t tmp_bytes = 0;
     uint32_t* tmask = nullptr;   // [tiles][words]
-    int32_t* tcnt = nullptr;     // [tiles + 1]
-    int32_t* tfirst = nullptr;   // [tiles + 1]
+    uint32_t* gmask = nullptr;   // [tiles][words] (groups of tiles; at most one per tile)
+    int32_t* tcnt = nullptr;     // [tiles + 1] group list lengths
+    int32_t* tfirst = nullptr;   // [tiles + 1] group list offsets
+    int32_t* ucnt = nullptr;     // [tiles + 1] group work units
+    int32_t* uoff = nullptr;     // [tiles + 1] first work unit of each group
     int32_t* blist = nullptr;    // [blist_cap]
-    int32_t* misc = nullptr;     // [4]: total blocks, largest tile list, voxel count
+    int32_t* misc = nullptr;     // [4]: total blocks, longest tile list, voxel count
     void* part = nullptr;        // candidates [S][cap][K] scores then indices
     size_t part_bytes = 0;
 };
@@ -70,6 +73,9 @@ struct TreeTC {
 namespace {
 
 constexpr int kThreads = 256;
+constexpr int kGroupBf16 = 2;     // default tiles per block list (BF16 operand)
+constexpr int kGroupSplit = 2;    // the same for the split-BF16 operand
+constexpr int kChunks = 32;       // chunks (candidate slots) a full block list is cut into
 
 inline unsigned grid_for(int64_t work) {
     return static_cast<unsigned>((work + kThreads - 1) / kThreads);
@@ -133,7 +139,7 @@ __global__ void k_block_radius(const float2* __restrict__ atoms, const double* _
 
 namespace {
 
-// One warp per voxel of a chunk: bounds on delta(z^, c_b) for every centre from the split-BF16
+// One warp per voxel of a row chunk: bounds on delta(z^, c_b) for every centre from the split-BF16
 // correlations cs (row v: for centre b, Re at (b / 128) 256 + b % 128, Im 128 further), the
 // voxel's correlation bound bz (normalised units) and the relative bound kappa of its FP32
 // norm; every step rounded away from the side it bounds.  Writes the voxel's block mask, its
@@ -214,38 +220,66 @@ __global__ void k_tree_bounds(const float* __restrict__ cs, int64_t ld, int64_t 
     }
 }
 
-// One CTA per 128-voxel tile (voxels vorder[128 g ...]): the union of their block masks, its
-// population (the tile's list length), the running total and maximum, and the voxel-atom pairs
-// the search will evaluate (distance-evaluation counter).
+// One CTA per 128-voxel tile (voxels vorder[128 g ...]): the union of their block masks.  The
+// threads split the (word, row) pairs, OR-ing into shared memory (words x 4 bytes, dynamic).
 __global__ void k_tile_union(const uint32_t* __restrict__ keep, int64_t words,
                              const int32_t* __restrict__ vorder, int64_t n,
-                             uint32_t* __restrict__ tmask, int32_t* __restrict__ tcnt,
-                             int32_t* __restrict__ misc, unsigned long long* counters) {
-    __shared__ int red[kThreads / 32];
+                             uint32_t* __restrict__ tmask) {
+    extern __shared__ uint32_t sm[];
     const int64_t g = blockIdx.x;
     const int64_t i0 = g * 128;
     const int rows = static_cast<int>(n - i0 < 128 ? n - i0 : 128);
+    for (int64_t w = threadIdx.x; w < words; w += blockDim.x) sm[w] = 0u;
+    __syncthreads();
+    const int64_t rp = words >= blockDim.x ? 1 : blockDim.x / words;   // row parts
+    for (int64_t i = threadIdx.x; i < rp * words; i += blockDim.x) {
+        const int64_t w = i % words, part = i / words;
+        uint32_t m = 0;
+        for (int64_t r = part; r < rows; r += rp)
+            m |= keep[static_cast<int64_t>(vorder[i0 + r]) * words + w];
+        if (m) atomicOr(&sm[w], m);
+    }
+    __syncthreads();
+    for (int64_t w = threadIdx.x; w < words; w += blockDim.x) tmask[g * words + w] = sm[w];
+}
+
+// One CTA per group of `group` consecutive tiles: the union of their masks (the group's block
+// list), its length and work units (chunks of `chunk` blocks times tiles), the running total
+// and maximum, and the voxel-atom pairs the search will evaluate (distance-evaluation
+// counter); block 0 also stores the voxel count for the merge.
+__global__ void k_group_union(const uint32_t* __restrict__ tmask, int64_t words, int64_t ntiles,
+                              int group, int chunk, int64_t n, uint32_t* __restrict__ gmask,
+                              int32_t* __restrict__ gcnt, int32_t* __restrict__ ucnt,
+                              int32_t* __restrict__ misc, unsigned long long* counters) {
+    __shared__ int red[kThreads / 32];
+    const int64_t k = blockIdx.x;
+    const int64_t t0 = k * group;
+    const int64_t t1 = t0 + group < ntiles ? t0 + group : ntiles;
     int cnt = 0;
     for (int64_t w = threadIdx.x; w < words; w += blockDim.x) {
         uint32_t m = 0;
-        for (int r = 0; r < rows; ++r) m |= keep[static_cast<int64_t>(vorder[i0 + r]) * words + w];
-        tmask[g * words + w] = m;
+        for (int64_t t = t0; t < t1; ++t) m |= tmask[t * words + w];
+        gmask[k * words + w] = m;
         cnt += __popc(m);
     }
     for (int o = 16; o; o >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
     if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = cnt;
     __syncthreads();
+    if (threadIdx.x == 0 && k == 0) misc[2] = static_cast<int32_t>(n);   // the merge's count
     if (threadIdx.x == 0) {
-        int t = 0;
-        for (int i = 0; i < static_cast<int>(blockDim.x >> 5); ++i) t += red[i];
-        tcnt[g] = t;
-        atomicAdd(misc, t);
-        atomicMax(misc + 1, t);
-        atomicAdd(counters + CNT_DIST, static_cast<unsigned long long>(t) * 128ull * rows);
+        int c = 0;
+        for (int i = 0; i < static_cast<int>(blockDim.x >> 5); ++i) c += red[i];
+        gcnt[k] = c;
+        ucnt[k] = ((c + chunk - 1) / chunk) * static_cast<int32_t>(t1 - t0);   // work units
+        atomicAdd(misc, c);
+        atomicMax(misc + 1, c);
+        const int64_t v0 = t0 * 128, v1 = t1 * 128 < n ? t1 * 128 : n;
+        atomicAdd(counters + CNT_DIST, static_cast<unsigned long long>(c) * 128ull *
+                                           static_cast<unsigned long long>(v1 - v0));
     }
 }
 
-// One warp per tile: the set bits of its mask, in increasing block order, written to
+// One warp per group: the set bits of its mask, in increasing block order, written to
 // blist[tfirst[g] ...].
 __global__ void k_tile_list(const uint32_t* __restrict__ tmask, int64_t words, int64_t ntiles,
                             const int32_t* __restrict__ tfirst, int32_t* __restrict__ blist) {
@@ -278,7 +312,8 @@ void ttc_free(TreeTC* t) {
     if (!t) return;
     void* ptrs[] = {t->perm, t->op,   t->op3,   t->cidx,  t->cop3, t->radius, t->zc3,
                     t->cs,   t->znorm, t->cmarg, t->keep, t->key,  t->val,    t->skey,
-                    t->vorder, t->tmp, t->tmask, t->tcnt, t->tfirst, t->blist, t->misc, t->part};
+                    t->vorder, t->tmp, t->tmask, t->gmask, t->tcnt, t->tfirst, t->ucnt,
+                    t->uoff, t->blist, t->misc, t->part};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     delete t;
@@ -305,6 +340,11 @@ mrf_status ttc_build(mrf_dict* D, cudaStream_t st) {
     t->metric = ct_metric(D);
     t->nblk = D->nblk;
     t->words = (t->nblk + 31) / 32;
+    if (t->words * 4 > 48 * 1024) {        // block masks are OR-ed in shared memory
+        delete t;
+        mrf_set_error("tree search: more than 1.5M blocks of 128 atoms");
+        return MRF_EUNSUPPORTED;
+    }
     const int64_t npos = t->nblk * 128;
     std::vector<int32_t> perm(static_cast<size_t>(npos), -1);
     std::copy(order.begin(), order.end(), perm.begin());
@@ -387,25 +427,28 @@ mrf_status ttc_scratch(TreeTC* t, const mrf_dict* D, int64_t n) {
     t->cap = 0;
     const int64_t Kp3 = 3 * D->Kp;
     const int64_t ld = t->ncbblk * 256;
-    // centre product in chunks of at most ~512 MB of rows and correlations
+    // centre product in row chunks of at most ~512 MB of rows and correlations
     const int64_t per_row = ld * 4 + Kp3 * 2;
-    int64_t chunk = ((int64_t{1} << 29) / per_row) / 128 * 128;
-    chunk = std::max<int64_t>(chunk, 128);
-    chunk = std::min<int64_t>(chunk, (n + 127) / 128 * 128);
-    t->chunk = chunk;
+    int64_t crows = ((int64_t{1} << 29) / per_row) / 128 * 128;
+    crows = std::max<int64_t>(crows, 128);
+    crows = std::min<int64_t>(crows, (n + 127) / 128 * 128);
+    t->crows = crows;
     const int64_t tiles = (n + 127) / 128;
-    MRF_TRY(talloc(&t->zc3, static_cast<size_t>(chunk * Kp3)));
-    MRF_TRY(talloc(&t->cs, static_cast<size_t>(chunk * ld)));
-    MRF_TRY(talloc(&t->znorm, static_cast<size_t>(chunk)));
-    MRF_TRY(talloc(&t->cmarg, static_cast<size_t>(chunk)));
+    MRF_TRY(talloc(&t->zc3, static_cast<size_t>(crows * Kp3)));
+    MRF_TRY(talloc(&t->cs, static_cast<size_t>(crows * ld)));
+    MRF_TRY(talloc(&t->znorm, static_cast<size_t>(crows)));
+    MRF_TRY(talloc(&t->cmarg, static_cast<size_t>(crows)));
     MRF_TRY(talloc(&t->keep, static_cast<size_t>(n * t->words)));
     MRF_TRY(talloc(&t->key, static_cast<size_t>(n)));
     MRF_TRY(talloc(&t->val, static_cast<size_t>(n)));
     MRF_TRY(talloc(&t->skey, static_cast<size_t>(n)));
     MRF_TRY(talloc(&t->vorder, static_cast<size_t>(n)));
     MRF_TRY(talloc(&t->tmask, static_cast<size_t>(tiles * t->words)));
+    MRF_TRY(talloc(&t->gmask, static_cast<size_t>(tiles * t->words)));
     MRF_TRY(talloc(&t->tcnt, static_cast<size_t>(tiles + 1)));
     MRF_TRY(talloc(&t->tfirst, static_cast<size_t>(tiles + 1)));
+    MRF_TRY(talloc(&t->ucnt, static_cast<size_t>(tiles + 1)));
+    MRF_TRY(talloc(&t->uoff, static_cast<size_t>(tiles + 1)));
     MRF_TRY(talloc(&t->blist, static_cast<size_t>(tiles * t->nblk)));
     MRF_TRY(talloc(&t->misc, 4));
     size_t b1 = 0, b2 = 0;
@@ -439,10 +482,9 @@ mrf_status ttc_part(TreeTC* t, size_t need) {
 
 // Steps 1-4 of the tree search for Z [n][L] (device): fills `out` with the candidate lists
 // ([S][n][K] scores then atom indices, rows in tile order), the tile order itself (voxel of each
-// row), a device count of the rows (= n) for the merge, and the number of blocks searched.
+// row) and a device count of the rows (= n) for the merge.
 // split: search the split-BF16 operand (rows packed with the per-voxel bound plus `extra` into
-// D->zmarg, indexed by voxel); else the BF16 operand (rows in D->zq).  Synchronises `st` once
-// (the longest tile list sizes the launch).
+// D->zmarg, indexed by voxel); else the BF16 operand (rows in D->zq).  Asynchronous on `st`.
 mrf_status ttc_search(mrf_dict* D, const float2* Z, int64_t n, int cone, float eps, bool split,
                       int K, float extra, TtcOut* out, cudaStream_t st) {
     TreeTC* t = D->ttc;
@@ -469,10 +511,10 @@ mrf_status ttc_search(mrf_dict* D, const float2* Z, int64_t n, int cone, float e
     const float kappa = static_cast<float>((m + 8) * std::ldexp(1.0, -24));
     const float inv1e = std::nextafter(static_cast<float>(1.0 / (1.0 + static_cast<double>(eps))),
                                        2.f);
-    for (int64_t r0 = 0; r0 < n; r0 += t->chunk) {
+    for (int64_t r0 = 0; r0 < n; r0 += t->crows) {
         {
             ProfScope ps(7, 3, st);   // query split, centre product, bounds
-            const int64_t rows = std::min<int64_t>(t->chunk, n - r0);
+            const int64_t rows = std::min<int64_t>(t->crows, n - r0);
             MRF_TRY(launch_pack_queries_x3_with(Z + r0 * L, rows, L, Kp, t->c_al, t->c_ae,
                                                 std::ldexp(1.f, -22), t->zc3, t->cmarg, st,
                                                 nullptr, t->znorm));
@@ -485,9 +527,22 @@ mrf_status ttc_search(mrf_dict* D, const float2* Z, int64_t n, int cone, float e
         }
     }
     const int64_t tiles = (n + 127) / 128;
+    // tiles sharing one block list: the units of a group stream the same blocks of a split
+    // together, so L2 serves the repeats (with one list per tile they drift apart and stream
+    // from DRAM); a few tiles keep most of the per-voxel pruning
+    const int group = D->tune.tree_tc_group > 0 ? D->tune.tree_tc_group
+                                                : (split ? kGroupSplit : kGroupBf16);
+    const int64_t groups = (tiles + group - 1) / group;
+    // a group's list in chunks of equal length (a fixed fraction of the dictionary), the work
+    // units of the persistent search: equal units keep its CTAs balanced whatever the lists'
+    // lengths
+    const int nch = D->tune.tree_tc_chunks > 0 ? D->tune.tree_tc_chunks : kChunks;
+    const int chunk = static_cast<int>((t->nblk + nch - 1) / nch);
+    const int S = static_cast<int>((t->nblk + chunk - 1) / chunk);
     {
-        // sort (histogram, bin scan, two digit passes), row packing, union, scan (two), lists
-        ProfScope ps(7, 9, st);
+        // sort (histogram, bin scan, two digit passes), row packing, two unions, two scans (two
+        // launches each), lists
+        ProfScope ps(7, 12, st);
         int bits = 1;
         while ((int64_t{1} << bits) <= t->ncb) ++bits;
         size_t tb = t->tmp_bytes;
@@ -499,45 +554,43 @@ mrf_status ttc_search(mrf_dict* D, const float2* Z, int64_t n, int cone, float e
         else
             MRF_TRY(launch_pack_gather(Z, t->vorder, n, L, Kp, D->zq, st));
         MRF_CUDA_TRY(cudaMemsetAsync(t->misc, 0, 4 * sizeof(int32_t), st));
-        MRF_CUDA_TRY(cudaMemsetAsync(t->tcnt + tiles, 0, sizeof(int32_t), st));
-        k_tile_union<<<static_cast<unsigned>(tiles), kThreads, 0, st>>>(
-            t->keep, t->words, t->vorder, n, t->tmask, t->tcnt, t->misc, D->counters);
+        MRF_CUDA_TRY(cudaMemsetAsync(t->tcnt + groups, 0, sizeof(int32_t), st));
+        MRF_CUDA_TRY(cudaMemsetAsync(t->ucnt + groups, 0, sizeof(int32_t), st));
+        k_tile_union<<<static_cast<unsigned>(tiles), kThreads, t->words * sizeof(uint32_t), st>>>(
+            t->keep, t->words, t->vorder, n, t->tmask);
+        MRF_CUDA_TRY(cudaGetLastError());
+        k_group_union<<<static_cast<unsigned>(groups), kThreads, 0, st>>>(
+            t->tmask, t->words, tiles, group, chunk, n, t->gmask, t->tcnt, t->ucnt, t->misc,
+            D->counters);
         MRF_CUDA_TRY(cudaGetLastError());
         tb = t->tmp_bytes;
         MRF_CUDA_TRY(cub::DeviceScan::ExclusiveSum(t->tmp, tb, t->tcnt, t->tfirst,
-                                                   static_cast<int>(tiles + 1), st));
-        k_tile_list<<<grid_for(tiles * 32), kThreads, 0, st>>>(t->tmask, t->words, tiles,
-                                                               t->tfirst, t->blist);
+                                                   static_cast<int>(groups + 1), st));
+        tb = t->tmp_bytes;
+        MRF_CUDA_TRY(cub::DeviceScan::ExclusiveSum(t->tmp, tb, t->ucnt, t->uoff,
+                                                   static_cast<int>(groups + 1), st));
+        k_tile_list<<<grid_for(groups * 32), kThreads, 0, st>>>(t->gmask, t->words, groups,
+                                                                t->tfirst, t->blist);
         MRF_CUDA_TRY(cudaGetLastError());
     }
-    int32_t h[3] = {0, 0, static_cast<int32_t>(n)};
-    MRF_CUDA_TRY(cudaMemcpyAsync(h, t->misc, 2 * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
-    MRF_CUDA_TRY(cudaStreamSynchronize(st));
-    h[2] = static_cast<int32_t>(n);
-    MRF_CUDA_TRY(cudaMemcpyAsync(t->misc + 2, &h[2], sizeof(int32_t), cudaMemcpyHostToDevice, st));
-    // work units: tile lists cut into chunks of at least 4 blocks, at most 8 chunks per tile
-    const int maxcnt = std::max(h[1], 1);
-    const int chunk = std::max(4, (maxcnt + 7) / 8);
-    const int S = (maxcnt + chunk - 1) / chunk;
     const size_t pn = static_cast<size_t>(S) * n * K;
     MRF_TRY(ttc_part(t, pn * (sizeof(float) + sizeof(int32_t))));
     float* ps = static_cast<float*>(t->part);
     int32_t* pi = reinterpret_cast<int32_t*>(ps + pn);
-    // units past a tile's list write nothing: their slots read as empty (index -1, NaN score)
+    // slots of chunks a group does not have are not written: they read as empty (index -1,
+    // NaN score)
     MRF_CUDA_TRY(cudaMemsetAsync(t->part, 0xff, pn * (sizeof(float) + sizeof(int32_t)), st));
     {
         ProfScope ps2(2, 1, st);
         MRF_TRY(launch_bf16_topk_list(split ? D->zq3 : D->zq, n, D, split ? t->op3 : t->op,
-                                      split ? 3 * Kp : Kp, cone, K, S, chunk, t->tfirst, t->blist,
-                                      t->perm, ps, pi, st));
+                                      split ? 3 * Kp : Kp, cone, K, group, chunk, t->tfirst,
+                                      t->blist, t->uoff, t->perm, ps, pi, st));
     }
     out->S = S;
     out->part_s = ps;
     out->part_i = pi;
     out->vorder = t->vorder;
     out->count = t->misc + 2;
-    out->blocks = h[0];
     out->tiles = tiles;
-    out->chunk = chunk;
     return MRF_OK;
 }
