@@ -573,7 +573,8 @@ typedef struct mrf_tune {
                                   block list (the union of their voxels' lists), 1..64: larger
                                   groups search more blocks per voxel but stream each block
                                   once for the whole group, as the exhaustive search does;
-                                  0 = the library's default (2) */
+                                  0 = the library's default (2 for the BF16 operand, 4 for the
+                                  split-BF16 one) */
     int32_t tree_tc_chunks;    /* MRF_PROJ_TREE_TC: chunks a full block list is cut into, the
                                   work units of the persistent search and the candidate lists
                                   per voxel, 1..64; 0 = the library's default (32) */

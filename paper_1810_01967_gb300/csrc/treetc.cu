@@ -13,9 +13,10 @@
 //      the nearest atom is at most r_v away), and the blocks that can still hold an atom closer
 //      than r_v / (1 + eps): delta_lo(b) - R_b <= r_v / (1 + eps) (triangle inequality), plus
 //      the nearest centre's block;
-//   3. voxels sorted by their nearest centre, so a 128-voxel tile holds voxels of one region
-//      of the tree; a tile's block list is the union of its voxels' lists (the query batch
-//      shares one candidate set);
+//   3. voxels sorted by radius class (r_v in steps of 0.1), then by nearest centre, so a
+//      128-voxel tile holds voxels of one region of the tree with lists of similar reach; a few
+//      consecutive tiles share one block list, the union of their voxels' lists (the query
+//      batch shares one candidate set);
 //   4. the tensor-core search kernel in block-list mode scans each tile's blocks of the
 //      depth-first operand (BF16, or split-BF16 for certified results) and keeps its top K;
 //      the merge rescoring and certification follow in the caller.
@@ -74,8 +75,9 @@ namespace {
 
 constexpr int kThreads = 256;
 constexpr int kGroupBf16 = 2;     // default tiles per block list (BF16 operand)
-constexpr int kGroupSplit = 2;    // the same for the split-BF16 operand
+constexpr int kGroupSplit = 4;    // the same for the split-BF16 operand (3x the MMA per block)
 constexpr int kChunks = 32;       // chunks (candidate slots) a full block list is cut into
+constexpr int kRadiusBins = 16;   // radius classes of the voxel sort (r_v in steps of 0.1)
 
 inline unsigned grid_for(int64_t work) {
     return static_cast<unsigned>((work + kThreads - 1) / kThreads);
@@ -143,12 +145,12 @@ namespace {
 // correlations cs (row v: for centre b, Re at (b / 128) 256 + b % 128, Im 128 further), the
 // voxel's correlation bound bz (normalised units) and the relative bound kappa of its FP32
 // norm; every step rounded away from the side it bounds.  Writes the voxel's block mask, its
-// nearest centre (sort key) and its index.
+// sort key (radius class, then nearest centre in the low cbits bits) and its index.
 __global__ void k_tree_bounds(const float* __restrict__ cs, int64_t ld, int64_t rows,
                               int64_t row0, const float* __restrict__ znorm,
                               const float* __restrict__ cmarg, float kappa,
                               const float* __restrict__ radius, int64_t ncb, int64_t words,
-                              int metric, float inv1e, uint32_t* __restrict__ keep,
+                              int metric, float inv1e, int cbits, uint32_t* __restrict__ keep,
                               int32_t* __restrict__ key, int32_t* __restrict__ val) {
     const int64_t v = (static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
@@ -160,7 +162,7 @@ __global__ void k_tree_bounds(const float* __restrict__ cs, int64_t ld, int64_t 
         // zero (or non-finite) query: the merge assigns atom 0 (or flags the voxel); one block
         for (int64_t w = lane; w < words; w += 32) km[w] = (w == 0) ? 1u : 0u;
         if (lane == 0) {
-            key[g] = 0;
+            key[g] = (kRadiusBins - 1) << cbits;
             val[g] = static_cast<int32_t>(g);
         }
         return;
@@ -215,7 +217,12 @@ __global__ void k_tree_bounds(const float* __restrict__ cs, int64_t ld, int64_t 
         if (lane == 0) km[w] = m;
     }
     if (lane == 0) {
-        key[g] = static_cast<int32_t>(bbest);
+        // sort key: the voxel's radius class (r_v in steps of 0.1), then its nearest centre --
+        // the voxels of a tile then share both their region of the tree and the reach of their
+        // block lists, so the tile's union stays close to each voxel's own list
+        const int32_t rb =
+            static_cast<int32_t>(fminf(best * 10.f, static_cast<float>(kRadiusBins - 1)));
+        key[g] = (rb << cbits) | static_cast<int32_t>(bbest);
         val[g] = static_cast<int32_t>(g);
     }
 }
@@ -511,6 +518,8 @@ mrf_status ttc_search(mrf_dict* D, const float2* Z, int64_t n, int cone, float e
     const float kappa = static_cast<float>((m + 8) * std::ldexp(1.0, -24));
     const float inv1e = std::nextafter(static_cast<float>(1.0 / (1.0 + static_cast<double>(eps))),
                                        2.f);
+    int cbits = 1;
+    while ((int64_t{1} << cbits) <= t->ncb) ++cbits;
     for (int64_t r0 = 0; r0 < n; r0 += t->crows) {
         {
             ProfScope ps(7, 3, st);   // query split, centre product, bounds
@@ -522,7 +531,7 @@ mrf_status ttc_search(mrf_dict* D, const float2* Z, int64_t n, int cone, float e
                                  static_cast<int>(ld), nullptr, 0, t->cs, nullptr, D->err, st));
             k_tree_bounds<<<grid_for(rows * 32), kThreads, 0, st>>>(
                 t->cs, ld, rows, r0, t->znorm, t->cmarg, kappa, t->radius, t->ncb, t->words,
-                t->metric, inv1e, t->keep, t->key, t->val);
+                t->metric, inv1e, cbits, t->keep, t->key, t->val);
             MRF_CUDA_TRY(cudaGetLastError());
         }
     }
@@ -543,11 +552,10 @@ mrf_status ttc_search(mrf_dict* D, const float2* Z, int64_t n, int cone, float e
         // sort (histogram, bin scan, two digit passes), row packing, two unions, two scans (two
         // launches each), lists
         ProfScope ps(7, 12, st);
-        int bits = 1;
-        while ((int64_t{1} << bits) <= t->ncb) ++bits;
         size_t tb = t->tmp_bytes;
         MRF_CUDA_TRY(cub::DeviceRadixSort::SortPairs(t->tmp, tb, t->key, t->skey, t->val,
-                                                     t->vorder, static_cast<int>(n), 0, bits, st));
+                                                     t->vorder, static_cast<int>(n), 0,
+                                                     cbits + 4, st));
         if (split)
             MRF_TRY(launch_pack_queries_x3_with(Z, n, L, Kp, t->op3_al, t->op3_ae, extra, D->zq3,
                                                 D->zmarg, st, t->vorder, nullptr));

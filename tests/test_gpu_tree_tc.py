@@ -181,3 +181,22 @@ def test_every_iteration_follows_the_oracle(mrf, cfg1, dicts, eps):
     X, idx, rho, rates = iterate_checked(mrf, dicts["complex"], op, AHY, A, p["iters"], opts,
                                          check=None if eps == 0.0 else eps_rule)
     print(f"eps={eps}: per-iteration exact agreement {np.round(rates, 4)}")
+
+
+@pytest.mark.parametrize("group,chunks", [(1, 1), (3, 7), (64, 64), (2, 32)])
+def test_schedule_knobs_keep_the_exact_result(mrf, cfg1, dicts, group, chunks):
+    """Tiles per block list and chunks per list change the work schedule and the candidate
+    slots, never the answer: eps = 0 stays the exact projection (ragged voxel count)."""
+    dic, p, Z = cfg1
+    D = dicts["complex"]
+    D.set_tune(tree_tc_group=group, tree_tc_chunks=chunks)
+    try:
+        for certify in (True, False):
+            idx, rho, X, st = run(mrf, D, Z[:999], 0.0, certify=certify)
+            if certify:
+                check_projection(Z[:999], dic["atoms"], idx, rho, g_X=X)
+            else:
+                check_bound_rule(Z[:999], dic["atoms"], idx, rho,
+                                 bf16_bound(dic["atoms"].shape[1]), g_X=X)
+    finally:
+        D.set_tune(tree_tc_group=0, tree_tc_chunks=0)
