@@ -144,8 +144,9 @@ namespace {
 // One warp per voxel of a row chunk: bounds on delta(z^, c_b) for every centre from the split-BF16
 // correlations cs (row v: for centre b, Re at (b / 128) 256 + b % 128, Im 128 further), the
 // voxel's correlation bound bz (normalised units) and the relative bound kappa of its FP32
-// norm; every step rounded away from the side it bounds.  Writes the voxel's block mask, its
-// sort key (radius class, then nearest centre in the low cbits bits) and its index.
+// norm; every step rounded away from the side it bounds (delta^2 = 2 - 2 c for unit vectors).
+// Writes the voxel's block mask, its sort key (radius class, then nearest centre in the low
+// cbits bits) and its index.
 __global__ void k_tree_bounds(const float* __restrict__ cs, int64_t ld, int64_t rows,
                               int64_t row0, const float* __restrict__ znorm,
                               const float* __restrict__ cmarg, float kappa,
@@ -168,50 +169,56 @@ __global__ void k_tree_bounds(const float* __restrict__ cs, int64_t ld, int64_t 
         return;
     }
     const float zlo = __fmul_rd(zn, 1.f - kappa), zhi = __fmul_ru(zn, 1.f + kappa);
+    const float rlo = __frcp_ru(zlo), rhi = __frcp_rd(zhi);   // >= 1 / ||z||, <= 1 / ||z||
     const float bz = cmarg[v];
     const float* row = cs + v * ld;
-    const float cmin = (metric == 0) ? 0.f : -1.f;
-    auto dbounds = [&](int64_t b, float& dlo, float& dhi) {
-        const int64_t col = (b >> 7) * 256 + (b & 127);
-        const float re = row[col];
-        float hi, lo;
-        if (metric == 0) {
-            const float im = row[col + 128];
-            const float mh = __fsqrt_ru(__fmaf_ru(re, re, __fmul_ru(im, im)));
-            const float ml = __fsqrt_rd(__fmaf_rd(re, re, __fmul_rd(im, im)));
-            hi = __fadd_ru(__fdiv_ru(mh, zlo), bz);
-            lo = __fsub_rd(__fdiv_rd(ml, zhi), bz);
-        } else {
-            hi = __fadd_ru(__fdiv_ru(re, re >= 0.f ? zlo : zhi), bz);
-            lo = __fsub_rd(__fdiv_rd(re, re >= 0.f ? zhi : zlo), bz);
-        }
-        hi = fminf(hi, 1.f);
-        lo = fmaxf(lo, cmin);
-        dlo = __fsqrt_rd(fmaxf(0.f, __fmaf_rd(-2.f, hi, 2.f)));
-        dhi = __fsqrt_ru(fmaxf(0.f, __fmaf_ru(-2.f, lo, 2.f)));
-    };
-    // r_v = min_b delta_hi and its (first) centre
-    float best = INFINITY;
+    const bool cplx = (metric == 0);
+    // Pass 1: the centre with the largest lower bound of c = |u^H z^| (or Re u^H z^): the lower
+    // bound is a non-decreasing function of |c~|^2 rounded down (of Re c~), so the arg max of
+    // that plain quantity is the centre of r_v = min_b delta_hi (ties: the first centre).
+    float sbest = -INFINITY;
     int64_t bbest = ncb;
     for (int64_t b = lane; b < ncb; b += 32) {
-        float dlo, dhi;
-        dbounds(b, dlo, dhi);
-        if (dhi < best) { best = dhi; bbest = b; }
+        const int64_t col = (b >> 7) * 256 + (b & 127);
+        const float re = row[col];
+        const float sv = cplx ? __fmaf_rd(re, re, __fmul_rd(row[col + 128], row[col + 128])) : re;
+        if (sv > sbest) { sbest = sv; bbest = b; }
     }
     for (int o = 16; o; o >>= 1) {
-        const float ob = __shfl_xor_sync(0xffffffffu, best, o);
+        const float os = __shfl_xor_sync(0xffffffffu, sbest, o);
         const int64_t oi = __shfl_xor_sync(0xffffffffu, bbest, o);
-        if (ob < best || (ob == best && oi < bbest)) { best = ob; bbest = oi; }
+        if (os > sbest || (os == sbest && oi < bbest)) { sbest = os; bbest = oi; }
     }
     if (bbest >= ncb) bbest = 0;   // non-finite correlations: the merge flags the voxel
+    float clo;
+    if (cplx) clo = __fmul_rd(__fsqrt_rd(fmaxf(sbest, 0.f)), rhi);
+    else clo = sbest >= 0.f ? __fmul_rd(sbest, rhi) : __fmul_rd(sbest, rlo);
+    clo = fmaxf(__fsub_rd(clo, bz), cplx ? 0.f : -1.f);
+    const float best = __fsqrt_ru(fmaxf(0.f, __fmaf_ru(-2.f, clo, 2.f)));   // r_v
     const float thr = __fmul_ru(best, inv1e);
+    // Pass 2: block b can be dropped when even the upper bound of c is below the correlation
+    // 1 - (thr + R_b)^2 / 2 of distance thr + R_b (rounded down); for the complex cone the test
+    // runs on |c~|^2 rounded up against ((bound - b_v) ||z||)^2 rounded down: no square root
+    // or division per centre.
     for (int64_t w = 0; w < words; ++w) {
         const int64_t b = w * 32 + lane;
         bool k = false;
         if (b < ncb) {
-            float dlo, dhi;
-            dbounds(b, dlo, dhi);
-            k = (b == bbest) || (__fsub_rd(dlo, radius[b]) <= thr);
+            const int64_t col = (b >> 7) * 256 + (b & 127);
+            const float re = row[col];
+            const float q = __fadd_ru(thr, radius[b]);
+            const float rhs = __fmaf_rd(-0.5f, __fmul_ru(q, q), 1.f);
+            bool drop;
+            if (cplx) {
+                const float im = row[col + 128];
+                const float m2 = __fmaf_ru(re, re, __fmul_ru(im, im));
+                const float t = __fmul_rd(__fsub_rd(rhs, bz), zlo);
+                drop = t > 0.f && m2 < __fmul_rd(t, t);
+            } else {
+                const float ub = __fadd_ru(re >= 0.f ? __fmul_ru(re, rlo) : __fmul_ru(re, rhi), bz);
+                drop = ub < rhs;
+            }
+            k = (b == bbest) || !drop;
         }
         const uint32_t m = __ballot_sync(0xffffffffu, k);
         if (lane == 0) km[w] = m;
