@@ -451,7 +451,9 @@ def exact_tc_leg(mrf, D, op, AHY, n, d, L, stream, peak, steps: int = 5) -> dict
 def run_profile_case(args) -> None:
     """Projection only (mrf_project) on N voxels of the workload's slice: the small case for
     kernel-level ncu captures (about 2 GB on the device).  Exhaustive modes project the first
-    N rows of A^H Y; the cover tree (eps 0.4) projects the phantom's object fingerprints with
+    N rows of A^H Y (so does the tensor-core tree search, eps 0.5, uncertified: its
+    block-list kernel over the depth-first BF16 operand); the cover tree (eps 0.4) projects the
+    phantom's object fingerprints with
     the slice's noise level, i.e. queries near the dictionary, where the tree search does its
     work instead of routing far queries to the exhaustive search.  Two more cases time single
     stages: `gradient` runs whole IPG steps (mrf_ipg_step, fixed mu = 1) of the full N x N x L
@@ -471,8 +473,10 @@ def run_profile_case(args) -> None:
         run_stage_case(args, mrf, dic, p)
         return
     tree = args.mode == "covertree"
+    ttc = args.mode == "tree_tc"
     D = mrf.build_dict_index(dic["atoms"], dic["params"], pack_fp8=(args.mode == "fp8"),
-                             build_tree=tree, pack_bf16x3=(args.mode == "bf16x3"))
+                             build_tree=tree or ttc, tree_tc=ttc,
+                             pack_bf16x3=(args.mode == "bf16x3"))
     if tree:
         fg = np.flatnonzero(p["phantom"]["labels"] >= 0)
         g = np.random.Generator(np.random.PCG64(123))
@@ -490,15 +494,17 @@ def run_profile_case(args) -> None:
     idx = torch.empty(n, dtype=torch.int32, device="cuda")
     rho = torch.empty(n, dtype=torch.complex64, device="cuda")
     o = mrf.proj_opts(mode=args.mode, certify=(args.mode == "bf16x3"),
-                      eps=0.4 if tree else 0.0)
+                      eps=0.4 if tree else (0.5 if ttc else 0.0))
     mrf.profile_enable(True)
-    for _ in range(args.steps):
-        mrf.project(D, Z, idx, rho, opts=o)
+    st = None
+    for i in range(args.steps):
+        st = mrf.project(D, Z, idx, rho, opts=o, stats=(i == args.steps - 1))
     prof = mrf.profile_read()
     torch.cuda.synchronize()
     print(json.dumps({"profile_case": n, "d": int(dic["atoms"].shape[0]), "L": L,
                       "stage_ms": {k: v[0] for k, v in prof.items()},
-                      "stage_launches": {k: v[1] for k, v in prof.items()}}))
+                      "stage_launches": {k: v[1] for k, v in prof.items()},
+                      "stats_last_step": st}))
 
 
 def run_stage_case(args, mrf, dic, p) -> None:
@@ -1201,10 +1207,10 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--mode", default="bf16",
-                    choices=["bf16", "fp8", "fp32", "bf16x3", "covertree", "gradient", "mlp",
-                             "learned"],
-                    help="projection of the timed step (covertree, gradient, mlp, learned: "
-                         "--profile-case only)")
+                    choices=["bf16", "fp8", "fp32", "bf16x3", "covertree", "tree_tc", "gradient",
+                             "mlp", "learned"],
+                    help="projection of the timed step (covertree, tree_tc, gradient, mlp, "
+                         "learned: --profile-case only)")
     ap.add_argument("--autotune", action="store_true",
                     help="time the search geometries on the workload first and use the fastest "
                          "(always on for the slices64 workload, whose batching form picks its "
@@ -1228,7 +1234,7 @@ def main():
     ap.add_argument("--profile-case", type=int, default=0,
                     help="projection-only small case with N voxels (for ncu captures)")
     args = ap.parse_args()
-    if args.mode in ("covertree", "gradient", "mlp", "learned") and args.profile_case <= 0:
+    if args.mode in ("covertree", "tree_tc", "gradient", "mlp", "learned") and args.profile_case <= 0:
         ap.error(f"--mode {args.mode} needs --profile-case")
     if args.profile_case > 0:
         run_profile_case(args)

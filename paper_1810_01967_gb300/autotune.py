@@ -1,9 +1,11 @@
 """Launch-geometry autotuner for the tensor-core search (mrf_get_tune / mrf_set_tune).
 
-The search kernel's geometry has three knobs: the cluster size C (CTAs co-scheduled on the
-same atom blocks, each loading its own copy with plain TMA tile loads), the number of voxel
-tiles kept live per super-group (how many query tiles the persistent clusters sweep together,
-i.e. the L2 working set), and the atom split S (work
+The search kernel's geometry has four knobs: the MMA tile shape (bf16_pair = 0: 128 voxels x
+256 atom rows per CTA; 1: 256 voxels x 256 rows on a CTA pair, each CTA staging half of every
+atom block, so the pair reads each block once for twice the voxels), the cluster size C (CTAs
+co-scheduled on the same atom blocks, each loading its own copy with plain TMA tile loads;
+single CTAs only), the number of voxel tiles kept live per super-group (how many query tiles
+the persistent clusters sweep together, i.e. the L2 working set), and the atom split S (work
 units per voxel tile; 0 lets the library pick it from its makespan model).  `tune` times
 mrf_project on the caller's queries for each combination with CUDA events on the current
 stream, keeps the fastest, applies it to the dictionary and records it in a JSON cache keyed by
@@ -20,8 +22,8 @@ import os
 
 from . import Dictionary, proj_opts, project
 
-DEFAULT_GRID = {"bf16_cluster": (1, 2, 4), "bf16_live_tiles": (16, 32, 64),
-                "bf16_splits": (0,)}
+DEFAULT_GRID = {"bf16_pair": (0, 1), "bf16_cluster": (1, 2, 4),
+                "bf16_live_tiles": (16, 32, 64), "bf16_splits": (0,)}
 
 
 def _key(D: Dictionary, n: int, mode: str) -> str:
@@ -60,6 +62,8 @@ def tune(D: Dictionary, Z, mode: str = "bf16", grid: dict | None = None, reps: i
     best = None
     for values in itertools.product(*(grid[k] for k in names)):
         setting = dict(zip(names, values))
+        if setting.get("bf16_pair", 0) and setting.get("bf16_cluster", 1) != 1:
+            continue                               # the pair form ignores the cluster size
         D.set_tune(**setting)
         project(D, Z, idx, opts=o)                 # warm-up (and first-use set-up)
         a = torch.cuda.Event(enable_timing=True)

@@ -1,5 +1,5 @@
-"""The launch-geometry autotuner and every geometry it explores: each cluster size, live-tile
-count and atom split gives the oracle's projection (certified BF16 and FP8), the fastest setting
+"""The launch-geometry autotuner and every geometry it explores: each tile shape, cluster size,
+live-tile count and atom split gives the oracle's projection (certified BF16 and FP8), the fastest setting
 is applied to the dictionary and cached, and the cache is applied again without timing."""
 import numpy as np
 import pytest
@@ -70,6 +70,27 @@ def test_tune_applies_and_caches(mrf, cfg1, tmp_path):
     t2 = D2.get_tune()
     for k, v in res["tune"].items():
         assert t2[k] == v
+
+
+def test_default_grid_explores_both_tile_shapes(mrf, cfg1):
+    """The default grid times the single-CTA tile (128 voxels) with every cluster size and the
+    CTA-pair tile (256 voxels; cluster size ignored, so timed once per live-tile count), and
+    the projection under the chosen geometry is still the oracle's."""
+    from paper_1810_01967_gb300 import autotune
+    dic, Z = cfg1
+    A = dic["atoms"]
+    D = mrf.build_dict_index(A)
+    Zd = to_dev(np.tile(Z, (4, 1)))
+    res = autotune.tune(D, Zd, "bf16", reps=1)
+    shapes = [(r["tune"]["bf16_pair"], r["tune"]["bf16_cluster"]) for r in res["table"]]
+    assert len(res["table"]) == 12
+    assert (1, 1) in shapes and (1, 2) not in shapes and (0, 4) in shapes
+    n = Z.shape[0]
+    idx = torch.empty(n, dtype=torch.int32, device="cuda")
+    rho = torch.empty(n, dtype=torch.complex64, device="cuda")
+    mrf.project(D, to_dev(Z), idx, rho, opts=mrf.proj_opts(mode="bf16", certify=True))
+    check_projection(Z, A, idx.cpu().numpy(), rho.cpu().numpy())
+    print("autotuned:", res["tune"], f"{res['ms']:.3f} ms")
 
 
 @pytest.mark.parametrize("mode", ["bf16", "fp8"])
