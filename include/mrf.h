@@ -562,8 +562,10 @@ typedef struct mrf_tune {
                                   route fewer voxels to the exhaustive search */
     int32_t bf16_pair;         /* 1: the tensor-core search on CTA pairs (2-SM MMA, M = 256,
                                   each CTA staging half of every atom block) instead of single
-                                  CTAs or clusters (bf16_cluster is then ignored);
-                                  0 = the library's default */
+                                  CTAs or clusters (bf16_cluster is then ignored); 2: single
+                                  CTAs or clusters; 0 = the library's default (single CTAs for
+                                  the exhaustive forms and the tree search's split operand,
+                                  CTA pairs for the tree search's BF16 operand) */
     int32_t tree_order;        /* cover-tree queries of a warm-started search: 1 = processed in
                                   the order of their warm-start atom's tree position, so that
                                   queries of one subtree run side by side and share cached tree

@@ -62,7 +62,7 @@ def tune(D: Dictionary, Z, mode: str = "bf16", grid: dict | None = None, reps: i
     best = None
     for values in itertools.product(*(grid[k] for k in names)):
         setting = dict(zip(names, values))
-        if setting.get("bf16_pair", 0) and setting.get("bf16_cluster", 1) != 1:
+        if setting.get("bf16_pair", 0) == 1 and setting.get("bf16_cluster", 1) != 1:
             continue                               # the pair form ignores the cluster size
         D.set_tune(**setting)
         project(D, Z, idx, opts=o)                 # warm-up (and first-use set-up)

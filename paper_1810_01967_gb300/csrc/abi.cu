@@ -1021,7 +1021,7 @@ mrf_status mrf_set_tune(mrf_dict* D, const mrf_tune* in) {
         return fail(MRF_EINVAL, "tuning values out of range");
     if (in->tree_list_cap != 0 && (in->tree_list_cap < 64 || in->tree_list_cap > 512))
         return fail(MRF_EINVAL, "tree_list_cap must be 0 or in 64..512");
-    if (in->bf16_pair < 0 || in->bf16_pair > 1) return fail(MRF_EINVAL, "bf16_pair must be 0 or 1");
+    if (in->bf16_pair < 0 || in->bf16_pair > 2) return fail(MRF_EINVAL, "bf16_pair must be 0, 1 or 2");
     if (in->tree_order < 0 || in->tree_order > 2) return fail(MRF_EINVAL, "tree_order must be 0, 1 or 2");
     if (in->tree_tc_group < 0 || in->tree_tc_group > 64)
         return fail(MRF_EINVAL, "tree_tc_group must be in 0..64");

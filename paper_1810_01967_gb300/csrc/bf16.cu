@@ -80,12 +80,13 @@ struct ListArgs {
     const int32_t* uoff;
     const int32_t* units;
     int group, chunk;
+    int tpu;                     // voxel tiles per unit: 1 (single CTA) or 2 (CTA pair)
     int64_t ngroups, ntiles;
 };
 
-// The work unit uc: tile g, candidate slot s (its chunk), positions [b0, b1) of the group's
-// list starting at lb (LIST); or the exhaustive schedule's unit: split s, tile group g, block
-// range [b0, b1).  False when the unit has no block.
+// The work unit uc: tile g (tile pair g with CTA pairs), candidate slot s (its chunk),
+// positions [b0, b1) of the group's list starting at lb (LIST); or the exhaustive schedule's
+// unit: split s, tile group g, block range [b0, b1).  False when the unit has no block.
 template <bool LIST>
 __device__ __forceinline__ bool unit_of(const Sched& sc, const ListArgs& la, int64_t uc, int bps,
                                         int64_t nblk, int64_t& s, int64_t& g, int64_t& b0,
@@ -99,9 +100,10 @@ __device__ __forceinline__ bool unit_of(const Sched& sc, const ListArgs& la, int
         }
         const int64_t t0 = lo * la.group;
         const int64_t gsz = min(static_cast<int64_t>(la.group), la.ntiles - t0);
+        const int64_t psz = (gsz + la.tpu - 1) / la.tpu;      // units per chunk of the group
         const int64_t l = uc - la.uoff[lo];
-        s = l / gsz;
-        g = t0 + (l - s * gsz);
+        s = l / psz;
+        g = t0 / la.tpu + (l - s * psz);                      // tile (or tile pair) index
         lb = la.tfirst[lo];
         const int64_t cnt = la.tfirst[lo + 1] - lb;
         b0 = s * la.chunk;
@@ -409,13 +411,13 @@ struct SharedP {
     volatile int abort;
 };
 
-template <int KT, bool F8>
+template <int KT, bool F8, bool LIST = false>
 __global__ void __launch_bounds__(NTHREADS, 1)
 k_tc_topk_pair(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                int64_t n, int64_t d, int64_t nblk, int Kp, int cone, Sched sc,
                int blocks_per_split, float gsc, const float* __restrict__ qs,
                const int32_t* __restrict__ count, float* __restrict__ part_s,
-               int32_t* __restrict__ part_i, uint32_t* err) {
+               int32_t* __restrict__ part_i, uint32_t* err, ListArgs la) {
     constexpr int EK = F8 ? 128 : 64;
     constexpr int KPER = F8 ? 32 : 16;
     extern __shared__ __align__(1024) unsigned char smem_raw[];
@@ -428,7 +430,7 @@ k_tc_topk_pair(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
     const uint32_t rank = mrfk::cluster_ctarank();      // 0 = issues the MMAs
     const int64_t cluster = blockIdx.x / 2;
     const int64_t nclusters = gridDim.x / 2;
-    const int64_t units = sc.NG * sc.S;
+    const int64_t units = LIST ? static_cast<int64_t>(*la.units) : sc.NG * sc.S;
     const int64_t nact = count ? min(static_cast<int64_t>(*count), n) : n;
     const int nk = (Kp + EK - 1) / EK;
 
@@ -473,13 +475,13 @@ k_tc_topk_pair(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
             bool slot_used[P_STAGES];
             for (int i = 0; i < P_STAGES; ++i) { slot_used[i] = false; slot_phase[i] = 0; }
             for (int64_t uc = cluster; uc < units && !sh->abort; uc += nclusters) {
-                int64_t s, g;
-                sc.map(uc, s, g);
+                int64_t s, g, b0, b1, lb;
+                const bool has = unit_of<LIST>(sc, la, uc, blocks_per_split, nblk, s, g, b0, b1, lb);
                 if (g * 2 * BM >= nact) continue;     // the cluster's tiles are all past the count
                 const int64_t m = g * 2 + rank;
-                const int64_t b0 = s * blocks_per_split;
-                const int64_t b1 = min(b0 + blocks_per_split, nblk);
-                for (int64_t b = b0; b < b1 && !sh->abort; ++b) {
+                if (!has) continue;
+                for (int64_t q = b0; q < b1 && !sh->abort; ++q) {
+                    const int64_t b = LIST ? static_cast<int64_t>(la.blist[lb + q]) : q;
                     for (int kc = 0; kc < nk; ++kc) {
                         if (!mrfk::mbar_wait(&sh->empty[stage], phase ^ 1u)) { fail(); break; }
                         unsigned char* sa = base + stage * P_STAGE_BYTES;
@@ -511,12 +513,11 @@ k_tc_topk_pair(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
             uint32_t aphase = 0;
             bool any = false;
             for (int64_t uc = cluster; uc < units && !sh->abort; uc += nclusters) {
-                int64_t s, g;
-                sc.map(uc, s, g);
+                int64_t s, g, b0, b1, lb;
+                const bool has = unit_of<LIST>(sc, la, uc, blocks_per_split, nblk, s, g, b0, b1, lb);
                 if (g * 2 * BM >= nact) continue;     // the cluster's tiles are all past the count
-                const int64_t b0 = s * blocks_per_split;
-                const int64_t b1 = min(b0 + blocks_per_split, nblk);
-                for (int64_t b = b0; b < b1 && !sh->abort; ++b) {
+                if (!has) continue;
+                for (int64_t q = b0; q < b1 && !sh->abort; ++q) {
                     if (!mrfk::mbar_wait_cluster(&sh->tempty[acc], aphase ^ 1u)) { fail(); break; }
                     mrfk::tc_fence_after();
                     const uint32_t dt = tmem + static_cast<uint32_t>(acc * BN);
@@ -560,18 +561,18 @@ k_tc_topk_pair(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
         int acc = 0;
         uint32_t aphase = 0;
         for (int64_t uc = cluster; uc < units && !sh->abort; uc += nclusters) {
-            int64_t s, g;
-            sc.map(uc, s, g);
+            int64_t s, g, b0, b1, lb;
+            const bool has = unit_of<LIST>(sc, la, uc, blocks_per_split, nblk, s, g, b0, b1, lb);
             if (g * 2 * BM >= nact) continue;     // the cluster's tiles are all past the count
             const int64_t m = g * 2 + rank;
-            const int64_t b0 = s * blocks_per_split;
-            const int64_t b1 = min(b0 + blocks_per_split, nblk);
+            if (!has) continue;
             float ts[KT];
             int32_t ti[KT];
 #pragma unroll
             for (int q = 0; q < KT; ++q) { ts[q] = -INFINITY; ti[q] = -1; }
             bool ok = true;
-            for (int64_t b = b0; b < b1; ++b) {
+            for (int64_t qb = b0; qb < b1; ++qb) {
+                const int64_t b = LIST ? static_cast<int64_t>(la.blist[lb + qb]) : qb;
                 if (!mrfk::mbar_wait(&sh->tfull[acc], aphase)) { fail(); ok = false; break; }
                 mrfk::tc_fence_after();
                 const uint32_t tb = tmem + lane_base + static_cast<uint32_t>(acc * BN);
@@ -594,7 +595,10 @@ k_tc_topk_pair(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
                 }
                 const int64_t o = (s * n + v) * KT;
 #pragma unroll
-                for (int q = 0; q < KT; ++q) { part_s[o + q] = ts[q]; part_i[o + q] = ti[q]; }
+                for (int q = 0; q < KT; ++q) {
+                    part_s[o + q] = ts[q];
+                    part_i[o + q] = (LIST && ti[q] >= 0) ? la.perm[ti[q]] : ti[q];
+                }
             }
         }
     }
@@ -709,7 +713,7 @@ mrf_status launch_pair(const CUtensorMap& ta, const CUtensorMap& tb, int64_t n, 
         cfg.attrs = attr;
         cfg.numAttrs = 1;
         e = cudaLaunchKernelEx(&cfg, kern, ta, tb, n, D->d, D->nblk, Kp, cone,
-                               sc, bps, gsc, qs, count, part_s, part_i, D->err);
+                               sc, bps, gsc, qs, count, part_s, part_i, D->err, ListArgs{});
     }
     if (e != cudaSuccess) {
         mrf_set_error(std::string("tensor-core search (CTA pairs) launch: ") + cudaGetErrorString(e));
@@ -815,7 +819,7 @@ int max_clusters_any(int C, cudaStream_t st) {
 
 int bf16_choose_splits(const mrf_dict* D, int64_t n) {
     if (D->tune.bf16_splits > 0) return static_cast<int>(D->tune.bf16_splits);
-    const int C = D->tune.bf16_pair > 0 ? 2 : cluster_of(D);
+    const int C = D->tune.bf16_pair == 1 ? 2 : cluster_of(D);
     const int64_t Mt = (n + BM - 1) / BM;
     const int64_t NG = (Mt + C - 1) / C;
     return choose_splits(NG, D->nblk, D->num_sms / C);
@@ -859,7 +863,7 @@ mrf_status launch_tc(int form, const void* zq, const float* qs, int64_t n, mrf_d
         mrf_set_error("tensor-core search: K must be 8, 16 or 32");
         return MRF_EINVAL;
     }
-    const bool pair = D->tune.bf16_pair > 0;
+    const bool pair = D->tune.bf16_pair == 1;
     const int C = pair ? 2 : cluster_of(D);
     const int Kp = f8 ? D->Kp8 : (form == FORM_X3 ? D->Kp3 : D->Kp);
     CUtensorMap ta, tb;
@@ -928,21 +932,26 @@ mrf_status launch_x3_topk(const __nv_bfloat16* zq3, int64_t n, mrf_dict* D, int 
 // the BF16 row length), the block lists of the tile groups (see ListArgs: tfirst, blist, uoff,
 // *units = uoff[groups], all on the device), chunks of `chunk` blocks, at most S per group;
 // candidates [S][n][K] (slot = chunk) with atom indices perm[position]; slots of chunks a group
-// does not have are not written.  Persistent grid of single CTAs; the unit count is read on the
-// device.
+// does not have are not written.  Persistent grid of single CTAs, or of CTA pairs (256 voxels
+// per unit, each CTA staging half of every block; `group` must then be even); the unit count
+// is read on the device.
 mrf_status launch_bf16_topk_list(const __nv_bfloat16* zq, int64_t n, mrf_dict* D,
                                  const __nv_bfloat16* op, int Kp, int cone, int K, int group,
-                                 int chunk, const int32_t* tfirst, const int32_t* blist,
-                                 const int32_t* uoff, const int32_t* perm, float* part_s,
-                                 int32_t* part_i, cudaStream_t st) {
+                                 int chunk, bool pair, const int32_t* tfirst,
+                                 const int32_t* blist, const int32_t* uoff, const int32_t* perm,
+                                 float* part_s, int32_t* part_i, cudaStream_t st) {
     if (n == 0) return MRF_OK;
     if (K != 8 && K != 16 && K != 32) {
         mrf_set_error("tree search: K must be 8, 16 or 32");
         return MRF_EINVAL;
     }
+    if (pair && (group % 2)) {
+        mrf_set_error("tree search: CTA pairs need an even number of tiles per block list");
+        return MRF_EINVAL;
+    }
     CUtensorMap ta, tb;
     MRF_TRY(tma_map_k128(&ta, zq, n, Kp, BM, false));
-    MRF_TRY(tma_map_k128(&tb, op, D->nblk * 256, Kp, BN, false));
+    MRF_TRY(tma_map_k128(&tb, op, D->nblk * 256, Kp, pair ? BN / 2 : BN, false));
     const int64_t Mt = (n + BM - 1) / BM;
     ListArgs la;
     la.tfirst = tfirst;
@@ -951,10 +960,50 @@ mrf_status launch_bf16_topk_list(const __nv_bfloat16* zq, int64_t n, mrf_dict* D
     la.uoff = uoff;
     la.group = group;
     la.chunk = chunk;
+    la.tpu = pair ? 2 : 1;
     la.ntiles = Mt;
     la.ngroups = (Mt + group - 1) / group;
     la.units = uoff + la.ngroups;
-    Sched sc{Mt, 1, 1};
+    Sched sc{pair ? (Mt + 1) / 2 : Mt, 1, 1};
+    if (pair) {
+        const int nc = (K == 8) ? max_pairs<8>(st) : (K == 16) ? max_pairs<16>(st)
+                                                               : max_pairs<32>(st);
+        if (nc <= 0) {
+            mrf_set_error("tree search: no CTA pair fits on this device");
+            return MRF_EUNSUPPORTED;
+        }
+        auto go = [&](auto kern) -> mrf_status {
+            cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                 static_cast<int>(kSmemP));
+            if (e == cudaSuccess) {
+                cudaLaunchConfig_t cfg = {};
+                cfg.gridDim = dim3(static_cast<unsigned>(nc * 2));
+                cfg.blockDim = dim3(NTHREADS);
+                cfg.dynamicSmemBytes = kSmemP;
+                cfg.stream = st;
+                cudaLaunchAttribute attr[1];
+                attr[0].id = cudaLaunchAttributeClusterDimension;
+                attr[0].val.clusterDim.x = 2;
+                attr[0].val.clusterDim.y = 1;
+                attr[0].val.clusterDim.z = 1;
+                cfg.attrs = attr;
+                cfg.numAttrs = 1;
+                e = cudaLaunchKernelEx(&cfg, kern, ta, tb, n, D->d, D->nblk, Kp, cone, sc, 0, 1.f,
+                                       static_cast<const float*>(nullptr),
+                                       static_cast<const int32_t*>(nullptr), part_s, part_i,
+                                       D->err, la);
+            }
+            if (e != cudaSuccess) {
+                mrf_set_error(std::string("tree block-list search (CTA pairs) launch: ") +
+                              cudaGetErrorString(e));
+                return MRF_ECUDA;
+            }
+            return MRF_OK;
+        };
+        if (K == 8) return go(k_tc_topk_pair<8, false, true>);
+        if (K == 16) return go(k_tc_topk_pair<16, false, true>);
+        return go(k_tc_topk_pair<32, false, true>);
+    }
     int nc = (K == 8) ? max_clusters<8, 1>(st) : (K == 16) ? max_clusters<16, 1>(st)
                                                            : max_clusters<32, 1>(st);
     if (nc <= 0) {

@@ -262,7 +262,7 @@ __global__ void k_tile_union(const uint32_t* __restrict__ keep, int64_t words,
 // and maximum, and the voxel-atom pairs the search will evaluate (distance-evaluation
 // counter); block 0 also stores the voxel count for the merge.
 __global__ void k_group_union(const uint32_t* __restrict__ tmask, int64_t words, int64_t ntiles,
-                              int group, int chunk, int64_t n, uint32_t* __restrict__ gmask,
+                              int group, int chunk, int tpu, int64_t n, uint32_t* __restrict__ gmask,
                               int32_t* __restrict__ gcnt, int32_t* __restrict__ ucnt,
                               int32_t* __restrict__ misc, unsigned long long* counters) {
     __shared__ int red[kThreads / 32];
@@ -284,7 +284,8 @@ __global__ void k_group_union(const uint32_t* __restrict__ tmask, int64_t words,
         int c = 0;
         for (int i = 0; i < static_cast<int>(blockDim.x >> 5); ++i) c += red[i];
         gcnt[k] = c;
-        ucnt[k] = ((c + chunk - 1) / chunk) * static_cast<int32_t>(t1 - t0);   // work units
+        // work units: chunks times the group's tiles (tile pairs with CTA pairs)
+        ucnt[k] = ((c + chunk - 1) / chunk) * static_cast<int32_t>((t1 - t0 + tpu - 1) / tpu);
         atomicAdd(misc, c);
         atomicMax(misc + 1, c);
         const int64_t v0 = t0 * 128, v1 = t1 * 128 < n ? t1 * 128 : n;
@@ -546,8 +547,13 @@ mrf_status ttc_search(mrf_dict* D, const float2* Z, int64_t n, int cone, float e
     // tiles sharing one block list: the units of a group stream the same blocks of a split
     // together, so L2 serves the repeats (with one list per tile they drift apart and stream
     // from DRAM); a few tiles keep most of the per-voxel pruning
-    const int group = D->tune.tree_tc_group > 0 ? D->tune.tree_tc_group
-                                                : (split ? kGroupSplit : kGroupBf16);
+    // tile shape: CTA pairs (256 voxels, each CTA staging half of every block, a 6-stage ring)
+    // for the BF16 operand, whose lists stream from DRAM; single CTAs for the split operand,
+    // where the three-times-longer blocks already give each load more products to cover it
+    const bool pair = D->tune.bf16_pair == 1 || (D->tune.bf16_pair == 0 && !split);
+    int group = D->tune.tree_tc_group > 0 ? D->tune.tree_tc_group
+                                          : (split ? kGroupSplit : kGroupBf16);
+    if (pair && (group % 2)) ++group;          // a CTA pair takes two tiles of one group
     const int64_t groups = (tiles + group - 1) / group;
     // a group's list in chunks of equal length (a fixed fraction of the dictionary), the work
     // units of the persistent search: equal units keep its CTAs balanced whatever the lists'
@@ -575,8 +581,8 @@ mrf_status ttc_search(mrf_dict* D, const float2* Z, int64_t n, int cone, float e
             t->keep, t->words, t->vorder, n, t->tmask);
         MRF_CUDA_TRY(cudaGetLastError());
         k_group_union<<<static_cast<unsigned>(groups), kThreads, 0, st>>>(
-            t->tmask, t->words, tiles, group, chunk, n, t->gmask, t->tcnt, t->ucnt, t->misc,
-            D->counters);
+            t->tmask, t->words, tiles, group, chunk, pair ? 2 : 1, n, t->gmask, t->tcnt, t->ucnt,
+            t->misc, D->counters);
         MRF_CUDA_TRY(cudaGetLastError());
         tb = t->tmp_bytes;
         MRF_CUDA_TRY(cub::DeviceScan::ExclusiveSum(t->tmp, tb, t->tcnt, t->tfirst,
@@ -598,8 +604,8 @@ mrf_status ttc_search(mrf_dict* D, const float2* Z, int64_t n, int cone, float e
     {
         ProfScope ps2(2, 1, st);
         MRF_TRY(launch_bf16_topk_list(split ? D->zq3 : D->zq, n, D, split ? t->op3 : t->op,
-                                      split ? 3 * Kp : Kp, cone, K, group, chunk, t->tfirst,
-                                      t->blist, t->uoff, t->perm, ps, pi, st));
+                                      split ? 3 * Kp : Kp, cone, K, group, chunk, pair,
+                                      t->tfirst, t->blist, t->uoff, t->perm, ps, pi, st));
     }
     out->S = S;
     out->part_s = ps;

@@ -183,13 +183,15 @@ def test_every_iteration_follows_the_oracle(mrf, cfg1, dicts, eps):
     print(f"eps={eps}: per-iteration exact agreement {np.round(rates, 4)}")
 
 
-@pytest.mark.parametrize("group,chunks", [(1, 1), (3, 7), (64, 64), (2, 32)])
-def test_schedule_knobs_keep_the_exact_result(mrf, cfg1, dicts, group, chunks):
-    """Tiles per block list and chunks per list change the work schedule and the candidate
-    slots, never the answer: eps = 0 stays the exact projection (ragged voxel count)."""
+@pytest.mark.parametrize("group,chunks,pair", [(1, 1, 2), (3, 7, 2), (64, 64, 2), (2, 32, 2),
+                                               (2, 32, 1), (3, 7, 1), (64, 1, 1), (0, 0, 0)])
+def test_schedule_knobs_keep_the_exact_result(mrf, cfg1, dicts, group, chunks, pair):
+    """Tiles per block list, chunks per list and the tile shape (single CTAs, or CTA pairs of
+    256 voxels: an odd group is rounded up) change the work schedule and the candidate slots,
+    never the answer: eps = 0 stays the exact projection (ragged voxel count)."""
     dic, p, Z = cfg1
     D = dicts["complex"]
-    D.set_tune(tree_tc_group=group, tree_tc_chunks=chunks)
+    D.set_tune(tree_tc_group=group, tree_tc_chunks=chunks, bf16_pair=pair)
     try:
         for certify in (True, False):
             idx, rho, X, st = run(mrf, D, Z[:999], 0.0, certify=certify)
@@ -199,4 +201,4 @@ def test_schedule_knobs_keep_the_exact_result(mrf, cfg1, dicts, group, chunks):
                 check_bound_rule(Z[:999], dic["atoms"], idx, rho,
                                  bf16_bound(dic["atoms"].shape[1]), g_X=X)
     finally:
-        D.set_tune(tree_tc_group=0, tree_tc_chunks=0)
+        D.set_tune(tree_tc_group=0, tree_tc_chunks=0, bf16_pair=0)
