@@ -449,8 +449,9 @@ mrf_status mrf_dict_attach_mlp(mrf_dict* dict, mrf_mlp* mlp);
  * and each iteration is every slice's gradient step followed by one projection of all stacked
  * voxels (one persistent launch of the search).  With use_graph the iteration is captured once
  * into a CUDA graph and replayed (projections without host synchronisation only, certify = 0:
- * FP32, BF16, FP8, and -- when the dictionary has the BF16 operand -- the cover-tree and learned
- * forms, whose exhaustive fallback then reads its voxel count on the device).  The masks of
+ * FP32, BF16, FP8, the tensor-core tree search, and -- when the dictionary has the BF16
+ * operand -- the cover-tree and learned forms, whose exhaustive fallback then reads its voxel
+ * count on the device).  The masks of
  * `ops` are read at every iteration and must stay alive.
  */
 typedef struct mrf_batch mrf_batch;

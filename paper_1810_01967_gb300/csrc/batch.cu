@@ -51,6 +51,8 @@ bool capturable(const mrf_dict* D, const mrf_proj_opts& o) {
     if (o.certify) return false;
     if (o.mode == MRF_PROJ_FP32_EXACT || o.mode == MRF_PROJ_BF16 || o.mode == MRF_PROJ_FP8)
         return true;
+    // the tensor-core tree search reads nothing back to the host when uncertified
+    if (o.mode == MRF_PROJ_TREE_TC) return D->ttc != nullptr;
     return (o.mode == MRF_PROJ_COVERTREE || o.mode == MRF_PROJ_LEARNED) && D->bop != nullptr;
 }
 

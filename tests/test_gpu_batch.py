@@ -113,16 +113,20 @@ def gpu_z(mrf, D, B, ins, s):
     return Z.cpu().numpy()
 
 
-@pytest.mark.parametrize("mode,certify", [("fp32", False), ("bf16", False), ("bf16x3", True)])
+@pytest.mark.parametrize("mode,certify", [("fp32", False), ("bf16", False), ("bf16x3", True),
+                                          ("tree_tc", True)])
 def test_batch_follows_the_oracle_every_iteration(mrf, setup, mode, certify):
     """Every iteration of the stacked batch: the oracle projects each slice's own Z (the GPU's
     gradient step of the batch's iterate) and the batch's answers follow the exact rule (FP32,
-    certified split-BF16) or the kernel-bound rule (uncertified BF16); the look-up table then
-    returns the atoms' parameters."""
+    certified split-BF16, the certified tensor-core tree search at eps = 0) or the kernel-bound
+    rule (uncertified BF16); the look-up table then returns the atoms' parameters."""
     dic, probs = setup
     A = dic["atoms"]
     L = A.shape[1]
-    D = mrf.build_dict_index(A, dic["params"], pack_bf16=True, pack_bf16x3=(mode == "bf16x3"))
+    tree = mode == "tree_tc"
+    D = mrf.build_dict_index(A, dic["params"], pack_bf16=True,
+                             pack_bf16x3=(mode in ("bf16x3", "tree_tc")), build_tree=tree,
+                             tree_tc=tree)
     B, ops = make_batch(mrf, D, probs)
     ins = slice_inputs(mrf, D, probs)
     opts = mrf.proj_opts(mode=mode, certify=certify)
@@ -185,7 +189,8 @@ def check_learned_rule(Z, A, dic, gi, grho, thr, bound):
     return float(np.mean(gi == ref["idx"]))
 
 
-@pytest.mark.parametrize("mode,pair", [("covertree", 0), ("learned", 0), ("learned", 1)])
+@pytest.mark.parametrize("mode,pair", [("covertree", 0), ("learned", 0), ("learned", 1),
+                                       ("tree_tc", 0)])
 def test_graph_replay_with_device_side_fallback(mrf, setup, mode, pair):
     """The cover-tree and learned forms under graph replay: their exhaustive fallback takes the
     listed voxel count from the device (no read-back inside the captured iteration).  Graph and
@@ -194,12 +199,15 @@ def test_graph_replay_with_device_side_fallback(mrf, setup, mode, pair):
     the oracle on the GPU's own Z: a fresh batch run of k - 1 iterations gives the iterate, a
     fresh run of k iterations replays iteration k from the captured graph, and its answers
     obey the form's rule (eps = 0 cover tree with its exhaustive fallback: the kernel-bound
-    rule; learned: that, or an accepted proposal above the threshold and a local maximum)."""
+    rule; learned: that, or an accepted proposal above the threshold and a local maximum; the
+    uncertified tensor-core tree search at eps = 0, which has no fallback and reads nothing
+    back: the kernel-bound rule)."""
     dic, probs = setup
     A = dic["atoms"]
     L = A.shape[1]
     D = mrf.build_dict_index(A, dic["params"], grid_shape=dic["grid_shape"],
-                             pack_bf16=True, build_tree=(mode == "covertree"))
+                             pack_bf16=True, build_tree=(mode in ("covertree", "tree_tc")),
+                             tree_tc=(mode == "tree_tc"))
     if mode == "learned":
         M = mrf.MLP(D, dic["axes"], dic["cell_atom"], hidden=32)
         mrf.attach_mlp(D, M)
@@ -232,7 +240,7 @@ def test_graph_replay_with_device_side_fallback(mrf, setup, mode, pair):
         for s in range(len(probs)):
             X, idx, v = slice_arrays(B, s)
             rho = v["rho"].cpu().numpy()
-            if mode == "covertree":
+            if mode in ("covertree", "tree_tc"):
                 agree = check_bound_rule(Zs[s], A, idx, rho, bf16_bound(L), g_X=X)
             else:
                 agree = check_learned_rule(Zs[s], A, dic, idx, rho, 0.98, bf16_bound(L))
