@@ -630,6 +630,8 @@ def slices_leg(mrf, D, dic, dev, stream, masks, Ys, geo, mine, forms, group, ite
                 M, mlp_s, _ = train_learned(mrf, D, dic, dev)
                 mrf.attach_mlp(D, M)
             kw = {"fallback_thr": 0.98}
+        if mode == "tree_tc":
+            kw = {"eps": 0.4}
         o = mrf.proj_opts(mode=mode, certify=False, **kw)
         # --- all slices in one batch
         t_all = None
@@ -1095,11 +1097,13 @@ def run_ours(args) -> None:
                                              keep=True)
     # ------------------------------------------------------------- batching form (rank 0)
     # the 64-slice workload (its dictionary is this one): BF16 and, with the quality leg's
-    # trained network, the learned form, each under CUDA-graph replay, groups of 8 slices
+    # trained network and tree, the learned form and the tensor-core tree search (eps 0.4),
+    # each under CUDA-graph replay, groups of 8 slices
     slices = None
     if rank == 0 and not args.no_slices:
         geo, mine, smasks, sYs = slices_inputs(dic, dev)
-        forms = [("bf16", True)] + ([("learned", True)] if D2 is not None else [])
+        forms = [("bf16", True)] + ([("learned", True), ("tree_tc", True)]
+                                    if D2 is not None else [])
         Ds = D2 if D2 is not None else D
         sout, _, stuned = slices_leg(mrf, Ds, dic, dev, stream, smasks, sYs, geo, mine, forms,
                                      8, args.iters, 1, True, both=False,
