@@ -5,8 +5,9 @@
 //   activation (GELU or identity) in FP32.
 //
 // Persistent CTAs, one per SM, walk the 128-row x BN-column output tiles (BN <= 256, a multiple
-// of 16 dividing N; tiles row by row, so CTAs running together share A rows and stream the same
-// weights): warp 0 streams 128-byte K slices of the A tile and of the BN weight rows with TMA
+// of 16 dividing N; tiles column by column, so the CTAs running together share one or two BN-row
+// slices of W while the A rows of all of M stay in L2 -- W can be far larger than L2, as with
+// the tree search's block centres): warp 0 streams 128-byte K slices of the A tile and of the BN weight rows with TMA
 // into a 4-stage ring (128-byte swizzle), warp 1 issues tcgen05.mma kind::f16 128 x BN x 16 (four
 // per stage) into one of two 256-column TMEM accumulators, and warps 2..5 drain the other one
 // row by row (TMEM lanes 32 (w mod 4) ...), fusing bias + GELU and writing the FP32 activations
@@ -50,7 +51,7 @@ __device__ __forceinline__ float gelu(float v) {
 
 __global__ void __launch_bounds__(T_THREADS, 1)
 k_tc_dense_gelu(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
-                int M, int N, int Kp, int BN, int tiles_n, int tiles, uint32_t idesc,
+                int M, int N, int Kp, int BN, int tiles_m, int tiles, uint32_t idesc,
                 const float* __restrict__ bias, int act, float* __restrict__ out,
                 __nv_bfloat16* __restrict__ outb, uint32_t* err) {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
@@ -101,8 +102,8 @@ k_tc_dense_gelu(const __grid_constant__ CUtensorMap tmA, const __grid_constant__
             bool used[TSTAGES] = {};
             uint32_t last[TSTAGES] = {};
             for (int t = blockIdx.x; t < tiles && !*abort_flag; t += gridDim.x) {
-                const int m0 = (t / tiles_n) * TM;
-                const int n0 = (t % tiles_n) * BN;
+                const int m0 = (t % tiles_m) * TM;
+                const int n0 = (t / tiles_m) * BN;
                 for (int kc = 0; kc < nk; ++kc) {
                     if (!mrfk::mbar_wait(&sh->empty[stage], phase ^ 1u)) { fail(); break; }
                     unsigned char* sa = base + stage * T_STAGE;
@@ -166,8 +167,8 @@ k_tc_dense_gelu(const __grid_constant__ CUtensorMap tmA, const __grid_constant__
         int acc = 0;
         uint32_t aphase = 0;
         for (int t = blockIdx.x; t < tiles && !*abort_flag; t += gridDim.x) {
-            const int m = (t / tiles_n) * TM + row;
-            const int n0 = (t % tiles_n) * BN;
+            const int m = (t % tiles_m) * TM + row;
+            const int n0 = (t / tiles_m) * BN;
             if (!mrfk::mbar_wait(&sh->tfull[acc], aphase)) { fail(); break; }
             mrfk::tc_fence_after();
             const uint32_t tb = tmem + (static_cast<uint32_t>(quarter * 32) << 16) +
@@ -252,8 +253,8 @@ mrf_status launch_dense(const __nv_bfloat16* A, int M, int Kp, const __nv_bfloat
     MRF_TRY(tma_map_k128(&ta, A, M, Kp, TM, false));
     MRF_TRY(tma_map_k128(&tb, Wt, N, Kp, BN, false));
     const uint32_t idesc = mrfk::idesc_bf16(TM, static_cast<uint32_t>(BN));
-    const int tiles_n = N / BN;
-    const int64_t tiles64 = static_cast<int64_t>(tiles_n) * ((M + TM - 1) / TM);
+    const int tiles_m = (M + TM - 1) / TM;
+    const int64_t tiles64 = static_cast<int64_t>(tiles_m) * (N / BN);
     if (tiles64 > INT32_MAX) {
         mrf_set_error("dense layer: more than 2^31 - 1 output tiles");
         return MRF_EINVAL;
@@ -267,7 +268,7 @@ mrf_status launch_dense(const __nv_bfloat16* A, int M, int Kp, const __nv_bfloat
                                  static_cast<int>(kDenseSmem));
     if (e == cudaSuccess) {
         const int grid = sms < tiles ? sms : tiles;          // one persistent CTA per SM
-        k_tc_dense_gelu<<<grid, T_THREADS, kDenseSmem, st>>>(ta, tb, M, N, Kp, BN, tiles_n,
+        k_tc_dense_gelu<<<grid, T_THREADS, kDenseSmem, st>>>(ta, tb, M, N, Kp, BN, tiles_m,
                                                              tiles, idesc, bias, act, out, outb,
                                                              err);
         e = cudaGetLastError();
