@@ -830,10 +830,17 @@ def tree_leg(mrf, dev, stream, iters: int, tree_svd=()) -> dict:
                                                            certify=False), stats=True)
             prof = mrf.profile_read()
             mrf.profile_enable(False)
+            sms = prof["search_tc"][0]
+            ach = 8.0 * L * s2["n_dist_evals"] / (sms / 1e3) / 1e12 if sms else None
+            sus, sus_src = peaks_sustained()
             r["first_projection"] = {
-                "bounds_lists_ms": prof["search_proposal"][0], "search_ms": prof["search_tc"][0],
+                "bounds_lists_ms": prof["search_proposal"][0], "search_ms": sms,
                 "merge_ms": prof["merge"][0],
-                "pairs_fraction_of_bruteforce": s2["n_dist_evals"] / (d * n)}
+                "pairs_fraction_of_bruteforce": s2["n_dist_evals"] / (d * n),
+                # the block-list kernel's rate on the pairs it searched (8 L flop per pair)
+                "search_roofline": {"bound": "tensor", "achieved": ach, "unit": "TFLOP/s",
+                                    "peak": sus, "peak_source": sus_src,
+                                    "frac": (ach / sus) if ach else None}}
         if mode == "covertree":
             # one cold projection of A^H Y: the tree search kernel's own rate
             ii = torch.empty(n, dtype=torch.int32, device=dev)
