@@ -220,3 +220,56 @@ def test_cover_tree_long_fingerprints(mrf, full, eps):
         dn = np.array([ct.pair_dist(Zn[v:v + 1], U[ref["idx"][v]:ref["idx"][v] + 1], "phase")[0, 0]
                        for v in range(n)])
         assert np.all(dg <= (1 + eps) * dn + 1e-5), np.max(dg - (1 + eps) * dn)
+
+
+@pytest.fixture(scope="module")
+def tree_full(mrf, full):
+    """The workload's dictionary with the cover tree and the tensor-core tree search's block
+    balls and depth-first operands (BF16 and split-BF16)."""
+    dic = full["dic"]
+    return mrf.build_dict_index(dic["atoms"], dic["params"], build_tree=True, tree_tc=True,
+                                pack_bf16x3=True)
+
+
+@pytest.mark.parametrize("eps,certify", [(0.0, True), (0.5, True), (0.5, False)])
+def test_tree_tc_full_slice(mrf, full, tree_full, eps, certify):
+    """The tensor-core tree search on the whole first iterate of the full slice, in the launch
+    configuration bench.py times (default groups, chunks and tile shapes): certified at eps = 0
+    the answers follow the exact rule on a seeded 2,048-voxel sample; at eps = 0.5 every sampled
+    voxel's atom is within (1 + eps) of the nearest (Def. eNN, oracle distances; uncertified:
+    up to the BF16 kernel's bound), and the densities are exact for the returned atoms."""
+    from oracle import covertree as ct
+    A = full["dic"]["atoms"]
+    n, L = full["AHY"].shape
+    idx = torch.empty(n, dtype=torch.int32, device="cuda")
+    rho = torch.empty(n, dtype=torch.complex64, device="cuda")
+    st = mrf.project(tree_full, full["AHY"], idx, rho, stats=True,
+                     opts=mrf.proj_opts(mode="tree_tc", eps=eps, certify=certify))
+    torch.cuda.synchronize()
+    assert st["device_error"] == 0
+    g = np.random.Generator(np.random.PCG64(777 + int(10 * eps) + int(certify)))
+    s = np.sort(g.choice(n, 2048, replace=False))
+    Zs = full["AHY"].cpu().numpy()[s]
+    gi, gr = idx.cpu().numpy()[s], rho.cpu().numpy()[s]
+    frac = st["n_dist_evals"] / (n * A.shape[0])
+    if eps == 0.0:
+        agree, ties = check_projection(Zs, A, gi, gr)
+        print(f"full slice, tree search eps 0 certified: agreement {agree:.4f} ({ties} ties), "
+              f"{st['n_uncertified']} uncertified, pairs {frac:.3f} of brute force")
+        return
+    ref = mo.project(Zs, A)
+    U = ct.unit_atoms(A.astype(np.complex128))
+    Zn = Zs.astype(np.complex128) / np.linalg.norm(Zs, axis=1)[:, None]
+    dg = np.sqrt(np.maximum(2 - 2 * np.abs(np.sum(np.conj(U[gi]) * Zn, axis=1)), 0))
+    dn = np.sqrt(np.maximum(2 - 2 * np.abs(np.sum(np.conj(U[ref["idx"]]) * Zn, axis=1)), 0))
+    if certify:
+        assert np.all(dg <= (1 + eps) * dn + 1e-6), float(np.max(dg - (1 + eps) * dn))
+    else:
+        # the BF16 ranking picks an atom whose correlation is within twice the kernel's bound
+        # of the best searched one: delta^2 = 2 - 2 c grows by at most 4 bound
+        lim = ((1 + eps) * dn) ** 2 + 4 * bf16_bound(L) + 1e-12
+        assert np.all(dg ** 2 <= lim), float(np.max(dg ** 2 - lim))
+    rr = mo.density(Zs, A, gi)
+    assert np.max(np.abs(gr - rr) / np.abs(rr)) <= 1e-4
+    print(f"full slice, tree search eps {eps} certify={certify}: exact agreement "
+          f"{np.mean(gi == ref['idx']):.4f}, pairs {frac:.3f} of brute force")
