@@ -581,7 +581,11 @@ typedef struct mrf_tune {
     int32_t tree_tc_chunks;    /* MRF_PROJ_TREE_TC: chunks a full block list is cut into, the
                                   work units of the persistent search and the candidate lists
                                   per voxel, 1..64; 0 = the library's default (32) */
-    int32_t reserved[3];
+    int32_t tree_tc_super;     /* MRF_PROJ_TREE_TC: neighbouring block lists whose work units
+                                  run chunk round by chunk round together (so the CTAs share
+                                  the blocks their lists have in common through L2), 1..256;
+                                  0 = the library's default (1) */
+    int32_t reserved[2];
 } mrf_tune;
 
 mrf_status mrf_get_tune(const mrf_dict* dict, mrf_tune* out);

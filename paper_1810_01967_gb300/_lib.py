@@ -71,7 +71,8 @@ class Tune(C.Structure):
                 ("last_bf16_splits", C.c_int32), ("last_fp32_splits", C.c_int32),
                 ("tree_list_cap", C.c_int32), ("bf16_pair", C.c_int32),
                 ("tree_order", C.c_int32), ("tree_tc_group", C.c_int32),
-                ("tree_tc_chunks", C.c_int32), ("reserved", C.c_int32 * 3)]
+                ("tree_tc_chunks", C.c_int32), ("tree_tc_super", C.c_int32),
+                ("reserved", C.c_int32 * 2)]
 
     def as_dict(self) -> dict:
         return {f: getattr(self, f) for f, _ in self._fields_ if f != "reserved"}

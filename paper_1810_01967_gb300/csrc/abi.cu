@@ -1027,12 +1027,15 @@ mrf_status mrf_set_tune(mrf_dict* D, const mrf_tune* in) {
         return fail(MRF_EINVAL, "tree_tc_group must be in 0..64");
     if (in->tree_tc_chunks < 0 || in->tree_tc_chunks > 64)
         return fail(MRF_EINVAL, "tree_tc_chunks must be in 0..64");
+    if (in->tree_tc_super < 0 || in->tree_tc_super > 256)
+        return fail(MRF_EINVAL, "tree_tc_super must be in 0..256");
     // all values checked: none is applied when one is refused
     D->tune.tree_list_cap = in->tree_list_cap;
     D->tune.bf16_pair = in->bf16_pair;
     D->tune.tree_order = in->tree_order;
     D->tune.tree_tc_group = in->tree_tc_group;
     D->tune.tree_tc_chunks = in->tree_tc_chunks;
+    D->tune.tree_tc_super = in->tree_tc_super;
     D->tune.bf16_cluster = in->bf16_cluster;
     D->tune.bf16_live_tiles = in->bf16_live_tiles;
     D->tune.bf16_splits = in->bf16_splits;

@@ -70,18 +70,23 @@ struct Sched {
 
 // Block lists of the cover-tree search: the tiles of group k (tiles [k group, (k + 1) group))
 // share the ascending block list blist[tfirst[k] .. tfirst[k + 1]), cut into chunks of `chunk`
-// blocks; a work unit is (group, chunk, tile), numbered group by group from uoff[k] (chunks of
-// a group times its tiles, the tiles of one chunk consecutive so they stream the chunk's blocks
-// together), *units in all.  perm maps operand positions to atoms.
+// blocks.  Groups are gathered into super-groups of `sg` consecutive groups (similar lists:
+// voxels are sorted by where they lie in the tree); super-group q owns the work units
+// [uoff[q], uoff[q + 1]), numbered chunk by chunk -- chunk c of every group of q, then chunk c
+// + 1 -- and within a chunk group by group, tile (or tile pair) by tile, so the CTAs running
+// together scan the same part of neighbouring lists and L2 serves the blocks they share.  A
+// super-group has as many chunk rounds as its longest list; units past a shorter list, or past
+// a short last group's tiles, are empty.  *units = uoff[nsg]; perm maps operand positions to
+// atoms.
 struct ListArgs {
     const int32_t* tfirst;
     const int32_t* blist;
     const int32_t* perm;
     const int32_t* uoff;
     const int32_t* units;
-    int group, chunk;
+    int group, chunk, sg;
     int tpu;                     // voxel tiles per unit: 1 (single CTA) or 2 (CTA pair)
-    int64_t ngroups, ntiles;
+    int64_t ngroups, nsg, ntiles;
 };
 
 // The work unit uc: tile g (tile pair g with CTA pairs), candidate slot s (its chunk),
@@ -92,20 +97,27 @@ __device__ __forceinline__ bool unit_of(const Sched& sc, const ListArgs& la, int
                                         int64_t nblk, int64_t& s, int64_t& g, int64_t& b0,
                                         int64_t& b1, int64_t& lb) {
     if (LIST) {
-        int64_t lo = 0, hi = la.ngroups;                 // last k with uoff[k] <= uc
+        int64_t lo = 0, hi = la.nsg;                     // last q with uoff[q] <= uc
         while (hi - lo > 1) {
             const int64_t mid = (lo + hi) >> 1;
             if (la.uoff[mid] <= uc) lo = mid;
             else hi = mid;
         }
-        const int64_t t0 = lo * la.group;
-        const int64_t gsz = min(static_cast<int64_t>(la.group), la.ntiles - t0);
-        const int64_t psz = (gsz + la.tpu - 1) / la.tpu;      // units per chunk of the group
+        const int64_t k0 = lo * la.sg;                    // first group of the super-group
+        const int64_t ng = min(static_cast<int64_t>(la.sg), la.ngroups - k0);
+        const int64_t ppg = (la.group + la.tpu - 1) / la.tpu;   // unit slots per group
         const int64_t l = uc - la.uoff[lo];
-        s = l / psz;
-        g = t0 / la.tpu + (l - s * psz);                      // tile (or tile pair) index
-        lb = la.tfirst[lo];
-        const int64_t cnt = la.tfirst[lo + 1] - lb;
+        const int64_t per = ng * ppg;                     // units per chunk round
+        s = l / per;
+        const int64_t r = l - s * per;
+        const int64_t k = k0 + r / ppg;
+        const int64_t pi = r - (r / ppg) * ppg;
+        const int64_t t0 = k * la.group;
+        const int64_t gsz = min(static_cast<int64_t>(la.group), la.ntiles - t0);
+        g = t0 / la.tpu + pi;                             // tile (or tile pair) index
+        if (pi * la.tpu >= gsz) { b0 = b1 = lb = 0; return false; }
+        lb = la.tfirst[k];
+        const int64_t cnt = la.tfirst[k + 1] - lb;
         b0 = s * la.chunk;
         b1 = min(b0 + la.chunk, cnt);
     } else {
@@ -929,15 +941,16 @@ mrf_status launch_x3_topk(const __nv_bfloat16* zq3, int64_t n, mrf_dict* D, int 
 
 // Block-list search of the cover-tree form: queries zq [n][Kp] (grouped into 128-row tiles),
 // the depth-first operand op ([nblk * 256][Kp]; BF16 layout, or the split form with Kp = 3 x
-// the BF16 row length), the block lists of the tile groups (see ListArgs: tfirst, blist, uoff,
-// *units = uoff[groups], all on the device), chunks of `chunk` blocks, at most S per group;
+// the BF16 row length), the block lists of the tile groups (see ListArgs: tfirst, blist, uoff
+// per super-group of `sg` groups, *units = uoff[super-groups], all on the device), chunks of
+// `chunk` blocks, at most S per group;
 // candidates [S][n][K] (slot = chunk) with atom indices perm[position]; slots of chunks a group
 // does not have are not written.  Persistent grid of single CTAs, or of CTA pairs (256 voxels
 // per unit, each CTA staging half of every block; `group` must then be even); the unit count
 // is read on the device.
 mrf_status launch_bf16_topk_list(const __nv_bfloat16* zq, int64_t n, mrf_dict* D,
                                  const __nv_bfloat16* op, int Kp, int cone, int K, int group,
-                                 int chunk, bool pair, const int32_t* tfirst,
+                                 int chunk, int sg, bool pair, const int32_t* tfirst,
                                  const int32_t* blist, const int32_t* uoff, const int32_t* perm,
                                  float* part_s, int32_t* part_i, cudaStream_t st) {
     if (n == 0) return MRF_OK;
@@ -962,8 +975,10 @@ mrf_status launch_bf16_topk_list(const __nv_bfloat16* zq, int64_t n, mrf_dict* D
     la.chunk = chunk;
     la.tpu = pair ? 2 : 1;
     la.ntiles = Mt;
+    la.sg = sg;
     la.ngroups = (Mt + group - 1) / group;
-    la.units = uoff + la.ngroups;
+    la.nsg = (la.ngroups + sg - 1) / sg;
+    la.units = uoff + la.nsg;
     Sched sc{pair ? (Mt + 1) / 2 : Mt, 1, 1};
     if (pair) {
         const int nc = (K == 8) ? max_pairs<8>(st) : (K == 16) ? max_pairs<16>(st)

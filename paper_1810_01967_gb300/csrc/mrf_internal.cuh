@@ -205,7 +205,7 @@ mrf_status launch_x3_topk(const __nv_bfloat16* zq3, int64_t n, mrf_dict* D, int 
                           int S, float* part_s, int32_t* part_i, cudaStream_t st);
 mrf_status launch_bf16_topk_list(const __nv_bfloat16* zq, int64_t n, mrf_dict* D,
                                  const __nv_bfloat16* op, int Kp, int cone, int K, int group,
-                                 int chunk, bool pair, const int32_t* tfirst,
+                                 int chunk, int sg, bool pair, const int32_t* tfirst,
                                  const int32_t* blist, const int32_t* uoff, const int32_t* perm,
                                  float* part_s, int32_t* part_i, cudaStream_t st);
 // covertree.cu

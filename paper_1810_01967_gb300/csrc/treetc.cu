@@ -63,8 +63,9 @@ struct TreeTC {
     uint32_t* gmask = nullptr;   // [tiles][words] (groups of tiles; at most one per tile)
     int32_t* tcnt = nullptr;     // [tiles + 1] group list lengths
     int32_t* tfirst = nullptr;   // [tiles + 1] group list offsets
-    int32_t* ucnt = nullptr;     // [tiles + 1] group work units
-    int32_t* uoff = nullptr;     // [tiles + 1] first work unit of each group
+    int32_t* sgmax = nullptr;    // [tiles + 1] chunk rounds of each super-group
+    int32_t* ucnt = nullptr;     // [tiles + 1] super-group work units
+    int32_t* uoff = nullptr;     // [tiles + 1] first work unit of each super-group
     int32_t* blist = nullptr;    // [blist_cap]
     int32_t* misc = nullptr;     // [4]: total blocks, longest tile list, voxel count
     void* part = nullptr;        // candidates [S][cap][K] scores then indices
@@ -78,6 +79,7 @@ constexpr int kGroupBf16 = 2;     // default tiles per block list (BF16 operand)
 constexpr int kGroupSplit = 4;    // the same for the split-BF16 operand (3x the MMA per block)
 constexpr int kChunks = 32;       // chunks (candidate slots) a full block list is cut into
 constexpr int kRadiusBins = 16;   // radius classes of the voxel sort (r_v in steps of 0.1)
+constexpr int kSuper = 1;         // groups per super-group
 
 inline unsigned grid_for(int64_t work) {
     return static_cast<unsigned>((work + kThreads - 1) / kThreads);
@@ -258,12 +260,13 @@ __global__ void k_tile_union(const uint32_t* __restrict__ keep, int64_t words,
 }
 
 // One CTA per group of `group` consecutive tiles: the union of their masks (the group's block
-// list), its length and work units (chunks of `chunk` blocks times tiles), the running total
-// and maximum, and the voxel-atom pairs the search will evaluate (distance-evaluation
-// counter); block 0 also stores the voxel count for the merge.
+// list), its length, its super-group's chunk rounds (the longest list of the super-group in
+// chunks of `chunk` blocks), the running total and maximum, and the voxel-atom pairs the
+// search will evaluate (distance-evaluation counter); block 0 also stores the voxel count for
+// the merge.
 __global__ void k_group_union(const uint32_t* __restrict__ tmask, int64_t words, int64_t ntiles,
-                              int group, int chunk, int tpu, int64_t n, uint32_t* __restrict__ gmask,
-                              int32_t* __restrict__ gcnt, int32_t* __restrict__ ucnt,
+                              int group, int chunk, int sg, int64_t n, uint32_t* __restrict__ gmask,
+                              int32_t* __restrict__ gcnt, int32_t* __restrict__ sgmax,
                               int32_t* __restrict__ misc, unsigned long long* counters) {
     __shared__ int red[kThreads / 32];
     const int64_t k = blockIdx.x;
@@ -284,14 +287,22 @@ __global__ void k_group_union(const uint32_t* __restrict__ tmask, int64_t words,
         int c = 0;
         for (int i = 0; i < static_cast<int>(blockDim.x >> 5); ++i) c += red[i];
         gcnt[k] = c;
-        // work units: chunks times the group's tiles (tile pairs with CTA pairs)
-        ucnt[k] = ((c + chunk - 1) / chunk) * static_cast<int32_t>((t1 - t0 + tpu - 1) / tpu);
+        atomicMax(sgmax + k / sg, (c + chunk - 1) / chunk);    // chunk rounds of the super-group
         atomicAdd(misc, c);
         atomicMax(misc + 1, c);
         const int64_t v0 = t0 * 128, v1 = t1 * 128 < n ? t1 * 128 : n;
         atomicAdd(counters + CNT_DIST, static_cast<unsigned long long>(c) * 128ull *
                                            static_cast<unsigned long long>(v1 - v0));
     }
+}
+
+// Work units of each super-group of sg groups: chunk rounds x groups x unit slots per group.
+__global__ void k_sg_units(const int32_t* __restrict__ sgmax, int64_t nsg, int64_t ngroups,
+                           int sg, int ppg, int32_t* __restrict__ ucnt) {
+    const int64_t q = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (q >= nsg) return;
+    const int64_t ng = ngroups - q * sg < sg ? ngroups - q * sg : sg;
+    ucnt[q] = sgmax[q] * static_cast<int32_t>(ng) * ppg;
 }
 
 // One warp per group: the set bits of its mask, in increasing block order, written to
@@ -327,8 +338,8 @@ void ttc_free(TreeTC* t) {
     if (!t) return;
     void* ptrs[] = {t->perm, t->op,   t->op3,   t->cidx,  t->cop3, t->radius, t->zc3,
                     t->cs,   t->znorm, t->cmarg, t->keep, t->key,  t->val,    t->skey,
-                    t->vorder, t->tmp, t->tmask, t->gmask, t->tcnt, t->tfirst, t->ucnt,
-                    t->uoff, t->blist, t->misc, t->part};
+                    t->vorder, t->tmp, t->tmask, t->gmask, t->tcnt, t->tfirst, t->sgmax,
+                    t->ucnt, t->uoff, t->blist, t->misc, t->part};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     delete t;
@@ -462,6 +473,7 @@ mrf_status ttc_scratch(TreeTC* t, const mrf_dict* D, int64_t n) {
     MRF_TRY(talloc(&t->gmask, static_cast<size_t>(tiles * t->words)));
     MRF_TRY(talloc(&t->tcnt, static_cast<size_t>(tiles + 1)));
     MRF_TRY(talloc(&t->tfirst, static_cast<size_t>(tiles + 1)));
+    MRF_TRY(talloc(&t->sgmax, static_cast<size_t>(tiles + 1)));
     MRF_TRY(talloc(&t->ucnt, static_cast<size_t>(tiles + 1)));
     MRF_TRY(talloc(&t->uoff, static_cast<size_t>(tiles + 1)));
     MRF_TRY(talloc(&t->blist, static_cast<size_t>(tiles * t->nblk)));
@@ -555,6 +567,10 @@ mrf_status ttc_search(mrf_dict* D, const float2* Z, int64_t n, int cone, float e
                                           : (split ? kGroupSplit : kGroupBf16);
     if (pair && (group % 2)) ++group;          // a CTA pair takes two tiles of one group
     const int64_t groups = (tiles + group - 1) / group;
+    const int tpu = pair ? 2 : 1;
+    // super-groups: neighbouring groups whose units run chunk round by chunk round together
+    const int sg = D->tune.tree_tc_super > 0 ? D->tune.tree_tc_super : kSuper;
+    const int64_t nsg = (groups + sg - 1) / sg;
     // a group's list in chunks of equal length (a fixed fraction of the dictionary), the work
     // units of the persistent search: equal units keep its CTAs balanced whatever the lists'
     // lengths
@@ -576,20 +592,24 @@ mrf_status ttc_search(mrf_dict* D, const float2* Z, int64_t n, int cone, float e
             MRF_TRY(launch_pack_gather(Z, t->vorder, n, L, Kp, D->zq, st));
         MRF_CUDA_TRY(cudaMemsetAsync(t->misc, 0, 4 * sizeof(int32_t), st));
         MRF_CUDA_TRY(cudaMemsetAsync(t->tcnt + groups, 0, sizeof(int32_t), st));
-        MRF_CUDA_TRY(cudaMemsetAsync(t->ucnt + groups, 0, sizeof(int32_t), st));
+        MRF_CUDA_TRY(cudaMemsetAsync(t->sgmax, 0, (nsg + 1) * sizeof(int32_t), st));
+        MRF_CUDA_TRY(cudaMemsetAsync(t->ucnt + nsg, 0, sizeof(int32_t), st));
         k_tile_union<<<static_cast<unsigned>(tiles), kThreads, t->words * sizeof(uint32_t), st>>>(
             t->keep, t->words, t->vorder, n, t->tmask);
         MRF_CUDA_TRY(cudaGetLastError());
         k_group_union<<<static_cast<unsigned>(groups), kThreads, 0, st>>>(
-            t->tmask, t->words, tiles, group, chunk, pair ? 2 : 1, n, t->gmask, t->tcnt, t->ucnt,
-            t->misc, D->counters);
+            t->tmask, t->words, tiles, group, chunk, sg, n, t->gmask, t->tcnt, t->sgmax, t->misc,
+            D->counters);
+        MRF_CUDA_TRY(cudaGetLastError());
+        k_sg_units<<<grid_for(nsg), kThreads, 0, st>>>(t->sgmax, nsg, groups, sg,
+                                                       (group + tpu - 1) / tpu, t->ucnt);
         MRF_CUDA_TRY(cudaGetLastError());
         tb = t->tmp_bytes;
         MRF_CUDA_TRY(cub::DeviceScan::ExclusiveSum(t->tmp, tb, t->tcnt, t->tfirst,
                                                    static_cast<int>(groups + 1), st));
         tb = t->tmp_bytes;
         MRF_CUDA_TRY(cub::DeviceScan::ExclusiveSum(t->tmp, tb, t->ucnt, t->uoff,
-                                                   static_cast<int>(groups + 1), st));
+                                                   static_cast<int>(nsg + 1), st));
         k_tile_list<<<grid_for(groups * 32), kThreads, 0, st>>>(t->gmask, t->words, groups,
                                                                 t->tfirst, t->blist);
         MRF_CUDA_TRY(cudaGetLastError());
@@ -604,7 +624,7 @@ mrf_status ttc_search(mrf_dict* D, const float2* Z, int64_t n, int cone, float e
     {
         ProfScope ps2(2, 1, st);
         MRF_TRY(launch_bf16_topk_list(split ? D->zq3 : D->zq, n, D, split ? t->op3 : t->op,
-                                      split ? 3 * Kp : Kp, cone, K, group, chunk, pair,
+                                      split ? 3 * Kp : Kp, cone, K, group, chunk, sg, pair,
                                       t->tfirst, t->blist, t->uoff, t->perm, ps, pi, st));
     }
     out->S = S;

@@ -183,15 +183,17 @@ def test_every_iteration_follows_the_oracle(mrf, cfg1, dicts, eps):
     print(f"eps={eps}: per-iteration exact agreement {np.round(rates, 4)}")
 
 
-@pytest.mark.parametrize("group,chunks,pair", [(1, 1, 2), (3, 7, 2), (64, 64, 2), (2, 32, 2),
-                                               (2, 32, 1), (3, 7, 1), (64, 1, 1), (0, 0, 0)])
-def test_schedule_knobs_keep_the_exact_result(mrf, cfg1, dicts, group, chunks, pair):
-    """Tiles per block list, chunks per list and the tile shape (single CTAs, or CTA pairs of
-    256 voxels: an odd group is rounded up) change the work schedule and the candidate slots,
-    never the answer: eps = 0 stays the exact projection (ragged voxel count)."""
+@pytest.mark.parametrize("group,chunks,pair,sup", [(1, 1, 2, 1), (3, 7, 2, 5), (64, 64, 2, 1),
+                                                   (2, 32, 2, 16), (2, 32, 1, 16), (3, 7, 1, 3),
+                                                   (64, 1, 1, 2), (0, 0, 0, 0)])
+def test_schedule_knobs_keep_the_exact_result(mrf, cfg1, dicts, group, chunks, pair, sup):
+    """Tiles per block list, chunks per list, lists per super-group and the tile shape (single
+    CTAs, or CTA pairs of 256 voxels: an odd group is rounded up) change the work schedule and
+    the candidate slots, never the answer: eps = 0 stays the exact projection (ragged voxel
+    count, a short last group and super-group)."""
     dic, p, Z = cfg1
     D = dicts["complex"]
-    D.set_tune(tree_tc_group=group, tree_tc_chunks=chunks, bf16_pair=pair)
+    D.set_tune(tree_tc_group=group, tree_tc_chunks=chunks, bf16_pair=pair, tree_tc_super=sup)
     try:
         for certify in (True, False):
             idx, rho, X, st = run(mrf, D, Z[:999], 0.0, certify=certify)
@@ -201,4 +203,4 @@ def test_schedule_knobs_keep_the_exact_result(mrf, cfg1, dicts, group, chunks, p
                 check_bound_rule(Z[:999], dic["atoms"], idx, rho,
                                  bf16_bound(dic["atoms"].shape[1]), g_X=X)
     finally:
-        D.set_tune(tree_tc_group=0, tree_tc_chunks=0, bf16_pair=0)
+        D.set_tune(tree_tc_group=0, tree_tc_chunks=0, bf16_pair=0, tree_tc_super=0)
