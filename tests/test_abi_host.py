@@ -63,3 +63,18 @@ def test_host_argument_errors(L):
     L.mrf_batch_free(None)
     o = mrf.proj_opts()
     assert o.topk == 0 and o.mode == 0 and abs(o.tie_tol - 1e-5) < 1e-12
+    # the tensor-core tree search's index options are checked before any device work
+    import numpy as np
+    from paper_1810_01967_gb300._lib import IndexOpts
+    atoms = np.ones((4, 8), np.complex64)
+    io = IndexOpts()
+    L.mrf_default_index_opts(C.byref(io))
+    io.tree_tc = 1
+    assert L.mrf_build_dict_index(atoms.ctypes.data, 4, 8, None, 0, None, 0, C.byref(io),
+                                  C.byref(h), None) == MRF_EINVAL
+    assert b"build_tree" in L.mrf_last_error()
+    io.build_tree, io.pack_bf16, io.pack_bf16x3 = 1, 0, 0
+    assert L.mrf_build_dict_index(atoms.ctypes.data, 4, 8, None, 0, None, 0, C.byref(io),
+                                  C.byref(h), None) == MRF_EINVAL
+    assert b"pack_bf16" in L.mrf_last_error()
+    assert L.mrf_tree_blocks(None, None, None, None) == MRF_EINVAL
