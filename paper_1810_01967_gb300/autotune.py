@@ -6,7 +6,11 @@ atom block, so the pair reads each block once for twice the voxels), the cluster
 co-scheduled on the same atom blocks, each loading its own copy with plain TMA tile loads;
 single CTAs only), the number of voxel tiles kept live per super-group (how many query tiles
 the persistent clusters sweep together, i.e. the L2 working set), and the atom split S (work
-units per voxel tile; 0 lets the library pick it from its makespan model).  `tune` times
+units per voxel tile; 0 lets the library pick it from its makespan model).  For the
+tensor-core tree search (mode "tree_tc") the grid is its own schedule instead: the tile shape of
+the block-list search (CTA pairs or single CTAs), the voxel tiles that share one block list and
+the chunks a list is cut into (`TREE_GRID`); the approximation factor of the timed projections
+is passed with `proj`, e.g. {"eps": 0.5}, since the lists depend on it.  `tune` times
 mrf_project on the caller's queries for each combination with CUDA events on the current
 stream, keeps the fastest, applies it to the dictionary and records it in a JSON cache keyed by
 device, dictionary size, frame count, voxel count and precision, so later processes can apply
@@ -24,6 +28,7 @@ from . import Dictionary, proj_opts, project
 
 DEFAULT_GRID = {"bf16_pair": (0, 1), "bf16_cluster": (1, 2, 4),
                 "bf16_live_tiles": (16, 32, 64), "bf16_splits": (0,)}
+TREE_GRID = {"bf16_pair": (1, 2), "tree_tc_group": (2, 4, 8), "tree_tc_chunks": (16, 32)}
 
 
 def _key(D: Dictionary, n: int, mode: str) -> str:
@@ -48,14 +53,17 @@ def apply_cached(D: Dictionary, n: int, mode: str, path: str) -> dict | None:
 
 
 def tune(D: Dictionary, Z, mode: str = "bf16", grid: dict | None = None, reps: int = 3,
-         cache: str | None = None) -> dict:
+         cache: str | None = None, proj: dict | None = None) -> dict:
     """Time every geometry of `grid` on the device queries Z ([n][L] complex64) and keep the
-    fastest.  Returns {"tune": best settings, "ms": its time, "table": all timings}."""
+    fastest (uncertified projections of `mode`, with the extra projection options `proj`).
+    Returns {"tune": best settings, "ms": its time, "table": all timings}."""
     import torch
-    grid = dict(DEFAULT_GRID if grid is None else grid)
+    if grid is None:
+        grid = TREE_GRID if mode == "tree_tc" else DEFAULT_GRID
+    grid = dict(grid)
     n = Z.shape[0]
     idx = torch.empty(n, dtype=torch.int32, device=Z.device)
-    o = proj_opts(mode=mode, certify=False)
+    o = proj_opts(mode=mode, certify=False, **(proj or {}))
     stream = torch.cuda.current_stream()
     names = list(grid)
     table = []

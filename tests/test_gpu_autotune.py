@@ -93,6 +93,25 @@ def test_default_grid_explores_both_tile_shapes(mrf, cfg1):
     print("autotuned:", res["tune"], f"{res['ms']:.3f} ms")
 
 
+def test_tree_search_grid(mrf, cfg1):
+    """The tensor-core tree search's schedule grid (tile shape, tiles per block list, chunks per
+    list) is timed at eps = 0.5 and the chosen schedule still gives the oracle's projection at
+    eps = 0 with certification."""
+    from paper_1810_01967_gb300 import autotune
+    dic, Z = cfg1
+    A = dic["atoms"]
+    D = mrf.build_dict_index(A, build_tree=True, tree_tc=True, pack_bf16x3=True)
+    res = autotune.tune(D, to_dev(np.tile(Z, (4, 1))), "tree_tc", reps=1, proj={"eps": 0.5})
+    assert len(res["table"]) == 12
+    assert set(res["tune"]) == {"bf16_pair", "tree_tc_group", "tree_tc_chunks"}
+    n = Z.shape[0]
+    idx = torch.empty(n, dtype=torch.int32, device="cuda")
+    rho = torch.empty(n, dtype=torch.complex64, device="cuda")
+    mrf.project(D, to_dev(Z), idx, rho, opts=mrf.proj_opts(mode="tree_tc", eps=0.0))
+    check_projection(Z, A, idx.cpu().numpy(), rho.cpu().numpy())
+    print("tree search autotuned:", res["tune"], f"{res['ms']:.3f} ms")
+
+
 @pytest.mark.parametrize("mode", ["bf16", "fp8"])
 def test_cta_pair_kernel_is_exact(mrf, cfg1, mode):
     """The 2-SM (CTA pair) variant of the search under several schedules: certified results
