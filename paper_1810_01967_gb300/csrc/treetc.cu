@@ -17,8 +17,9 @@
 //      128-voxel tile holds voxels of one region of the tree with lists of similar reach; a few
 //      consecutive tiles share one block list, the union of their voxels' lists (the query
 //      batch shares one candidate set);
-//   4. the tensor-core search kernel in block-list mode scans each tile's blocks of the
-//      depth-first operand (BF16, or split-BF16 for certified results) and keeps its top K;
+//   4. the tensor-core search kernel in block-list mode scans each group's list in chunks of
+//      equal length over the depth-first operand (BF16 on CTA pairs of 256 voxels, or
+//      split-BF16 on single CTAs for certified results) and keeps each voxel's top K per chunk;
 //      the merge rescoring and certification follow in the caller.
 // A block is dropped only when none of its atoms can be closer than r_v / (1 + eps), so the best
 // atom over the searched blocks is a (1 + eps)-approximate nearest neighbour (Def. eNN), and the
